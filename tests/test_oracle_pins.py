@@ -1,0 +1,465 @@
+"""Pins of the FP64 oracle against what lattice Boltzmann theory fixes.
+
+Each test checks the oracle against something other than itself: lattice
+isotropy, the product equilibrium's closed-form moments, the textbook
+set-partition moment/cumulant relation, exact conservation, the BGK and
+identity special cases, the textbook boundary rules on one step, the exact
+Navier-Stokes decay of a Taylor-Green vortex (with and without a uniform
+drift), the analytic Poiseuille profile and mirror symmetry.
+"""
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+import oracle.lbm as O
+from paper_2606_16765_gb300 import inputs as I
+
+Q = 27
+CV = O.velocities()
+OPP = Q - 1 - np.arange(Q)
+
+
+def rng(seed=0):
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+def near_eq_state(r, amp=0.02):
+    rho = 1.0 + r.uniform(-0.05, 0.05)
+    u = r.uniform(-0.1, 0.1, 3)
+    f = O.equilibrium(rho, *u)
+    return f * (1.0 + amp * r.uniform(-1, 1, Q))
+
+
+def mi(a, b, c):
+    return a + 3 * b + 9 * c
+
+
+# --------------------------------------------------------------------------
+# lattice and equilibrium
+# --------------------------------------------------------------------------
+def test_velocity_set_and_opposites():
+    assert len({tuple(c) for c in CV}) == 27
+    assert np.all(CV[OPP] == -CV)
+    assert np.all(CV[13] == 0)
+
+
+def test_weight_isotropy():
+    """Sec. 3.2 D3Q27 stencil: sum w = 1, second moments c_s^2 = 1/3,
+    fourth moments 1/9 (mixed) and 1/3 (pure) -- the lattice tensor identities."""
+    w = O.weights()
+    assert abs(w.sum() - 1) < 1e-15
+    for a in range(3):
+        assert abs((w * CV[:, a]).sum()) < 1e-16
+        for b in range(3):
+            m2 = (w * CV[:, a] * CV[:, b]).sum()
+            assert abs(m2 - (1 / 3 if a == b else 0)) < 1e-15
+            m4 = (w * CV[:, a] ** 2 * CV[:, b] ** 2).sum()
+            assert abs(m4 - (1 / 3 if a == b else 1 / 9)) < 1e-15
+    assert abs((w * CV[:, 0] ** 2 * CV[:, 1] ** 2 * CV[:, 2] ** 2).sum() - 1 / 27) < 1e-16
+
+
+def test_equilibrium_closed_form_moments():
+    """Product equilibrium: density rho, velocity u, central second moments
+    rho/3 (isotropic), vanishing third central moments, k_220 = 1/9 and
+    f_eq(rho, 0) = rho w."""
+    r = rng(1)
+    w = O.weights()
+    assert np.allclose(O.equilibrium(1.3, 0, 0, 0), 1.3 * w, atol=1e-16, rtol=0)
+    for _ in range(20):
+        rho = 1 + r.uniform(-0.1, 0.1)
+        u = r.uniform(-0.15, 0.15, 3)
+        f = O.equilibrium(rho, *u)
+        assert abs(f.sum() - rho) < 1e-14
+        assert np.allclose((f[:, None] * CV).sum(0), rho * u, atol=1e-15)
+        d = CV - u
+        for a, b in itertools.product(range(3), repeat=2):
+            assert abs((f * d[:, a] * d[:, b]).sum() / rho - (1 / 3 if a == b else 0)) < 1e-14
+        # third-order moments of the 27-moment basis (no axis power above 2)
+        for a, b, c in itertools.product(range(3), repeat=3):
+            if a + b + c == 3:
+                m = (f * d[:, 0] ** a * d[:, 1] ** b * d[:, 2] ** c).sum()
+                assert abs(m) < 1e-14
+        assert abs((f * d[:, 0] ** 2 * d[:, 1] ** 2).sum() / rho - 1 / 9) < 1e-14
+
+
+# --------------------------------------------------------------------------
+# moments and cumulants
+# --------------------------------------------------------------------------
+def raw_to_central(f, u):
+    """Central moments from raw moments by the binomial expansion (a route
+    independent of the oracle's direct sums)."""
+    raw = np.zeros((3, 3, 3))
+    for a, b, c in itertools.product(range(3), repeat=3):
+        raw[a, b, c] = (f * CV[:, 0] ** a * CV[:, 1] ** b * CV[:, 2] ** c).sum()
+    rho = raw[0, 0, 0]
+    k = np.zeros(Q)
+    for a, b, c in itertools.product(range(3), repeat=3):
+        s = 0.0
+        for i, j, l in itertools.product(range(a + 1), range(b + 1), range(c + 1)):
+            s += (math.comb(a, i) * math.comb(b, j) * math.comb(c, l)
+                  * (-u[0]) ** (a - i) * (-u[1]) ** (b - j) * (-u[2]) ** (c - l) * raw[i, j, l])
+        k[mi(a, b, c)] = s / rho
+    return k
+
+
+def set_partitions(elems):
+    if not elems:
+        yield []
+        return
+    first, rest = elems[0], elems[1:]
+    for part in set_partitions(rest):
+        yield [[first]] + part
+        for n in range(len(part)):
+            yield part[:n] + [[first] + part[n]] + part[n + 1:]
+
+
+def partition_cumulant(k, a, b, c):
+    """Textbook multivariate moment->cumulant relation:
+    kappa = sum over set partitions pi of (-1)^(|pi|-1) (|pi|-1)! prod_B mu_B,
+    with mu_B the central moment of the block's axis counts."""
+    labels = [0] * a + [1] * b + [2] * c
+    tot = 0.0
+    for part in set_partitions(list(range(len(labels)))):
+        prod = 1.0
+        for blk in part:
+            cnt = [0, 0, 0]
+            for e in blk:
+                cnt[labels[e]] += 1
+            prod *= k[mi(*cnt)]
+        n = len(part)
+        tot += (-1) ** (n - 1) * math.factorial(n - 1) * prod
+    return tot
+
+
+def test_central_moments_match_binomial_expansion():
+    r = rng(2)
+    for _ in range(10):
+        f = near_eq_state(r, amp=0.2)
+        k, rho, u = O.central_moments(f)
+        assert np.allclose(k, raw_to_central(f, u), atol=1e-14, rtol=0)
+        assert abs(k[mi(0, 0, 0)] - 1) < 1e-15
+        assert max(abs(k[1]), abs(k[3]), abs(k[9])) < 1e-15
+
+
+def test_cumulants_match_set_partition_formula():
+    """The oracle's hand-written order-4..6 cumulants equal the generic
+    set-partition formula, on states near and far from equilibrium."""
+    r = rng(3)
+    for amp in (0.05, 0.5):
+        for _ in range(5):
+            f = near_eq_state(r, amp=amp)
+            k, _, _ = O.central_moments(f)
+            Cm = O.cumulants(k)
+            for a, b, c in itertools.product(range(3), repeat=3):
+                if a + b + c < 2:
+                    continue
+                ref = partition_cumulant(k, a, b, c)
+                assert abs(Cm[mi(a, b, c)] - ref) < 1e-14, (a, b, c)
+
+
+def test_cumulants_of_equilibrium_vanish_above_second_order():
+    f = O.equilibrium(1.07, 0.08, -0.05, 0.11)
+    k, _, _ = O.central_moments(f)
+    Cm = O.cumulants(k)
+    for a, b, c in itertools.product(range(3), repeat=3):
+        if a + b + c >= 3:
+            assert abs(Cm[mi(a, b, c)]) < 1e-15
+    assert abs(Cm[mi(2, 0, 0)] - 1 / 3) < 1e-15 and abs(Cm[mi(1, 1, 0)]) < 1e-15
+
+
+def test_cumulant_and_moment_round_trips():
+    r = rng(4)
+    for _ in range(10):
+        f = near_eq_state(r, amp=0.3)
+        k, rho, u = O.central_moments(f)
+        assert np.allclose(O.moments_from_cumulants(O.cumulants(k)), k, atol=1e-15, rtol=0)
+        assert np.allclose(O.pdfs_from_moments(k, rho, u), f, atol=1e-14, rtol=0)
+
+
+# --------------------------------------------------------------------------
+# collision
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("gal", [0, 1])
+def test_equilibrium_is_fixed_point(gal):
+    r = rng(5)
+    for _ in range(20):
+        p = O.params(4, 4, 4, r.uniform(0.5, 1.99), r.uniform(0.5, 1.99), r.uniform(0.5, 1.99), galilean=gal)
+        f = O.equilibrium(1 + r.uniform(-0.05, 0.05), *r.uniform(-0.15, 0.15, 3))
+        assert np.abs(O.collide(p, f) - f).max() < 1e-15
+
+
+def test_collision_conserves_mass_and_momentum():
+    r = rng(6)
+    for _ in range(30):
+        p = O.params(4, 4, 4, r.uniform(0.5, 1.99), r.uniform(0.5, 1.99), r.uniform(0.0, 1.99))
+        f = near_eq_state(r, amp=0.1)
+        fs = O.collide(p, f)
+        assert abs(fs.sum() - f.sum()) < 2e-15
+        assert np.abs((fs[:, None] * CV).sum(0) - (f[:, None] * CV).sum(0)).max() < 2e-15
+
+
+def test_bgk_special_case_returns_equilibrium():
+    """All rates 1 without the Galilean correction resets every cumulant to
+    its equilibrium value, i.e. f* = f_eq(rho, u)."""
+    r = rng(7)
+    p = O.params(4, 4, 4, 1.0, 1.0, 1.0, galilean=0)
+    for _ in range(20):
+        f = near_eq_state(r, amp=0.2)
+        k, rho, u = O.central_moments(f)
+        assert np.abs(O.collide(p, f) - O.equilibrium(rho, *u)).max() < 1e-15
+
+
+def test_zero_rates_give_identity_collision():
+    r = rng(8)
+    p = O.params(4, 4, 4, 0.0, 0.0, 0.0, galilean=1)
+    for _ in range(10):
+        f = near_eq_state(r, amp=0.2)
+        assert np.abs(O.collide(p, f) - f).max() < 1e-15
+
+
+def test_shear_relaxation_rate():
+    """Off-diagonal second-order cumulants relax by exactly (1 - omega1)."""
+    r = rng(9)
+    w1 = 1.37
+    p = O.params(4, 4, 4, w1, 1.0, 1.0)
+    f = near_eq_state(r, amp=0.1)
+    k, _, _ = O.central_moments(f)
+    ks, _, _ = O.central_moments(O.collide(p, f))
+    for m in (mi(1, 1, 0), mi(1, 0, 1), mi(0, 1, 1)):
+        assert abs(ks[m] - (1 - w1) * k[m]) < 1e-15
+
+
+# --------------------------------------------------------------------------
+# streaming and boundaries, one step with the identity collision
+# --------------------------------------------------------------------------
+def random_field(shape, seed):
+    r = rng(seed)
+    w = O.weights()
+    return w[:, None, None, None] * (1 + 0.1 * r.uniform(-1, 1, (Q,) + shape))
+
+
+def identity_params(nx, ny, nz, faces, u_in=0.0):
+    return O.params(nx, ny, nz, 0.0, 0.0, 0.0, galilean=0, u_in=u_in, faces=faces)
+
+
+def test_periodic_streaming_shifts_each_population_by_its_velocity():
+    shape = (3, 4, 5)
+    f = random_field(shape, 10)
+    L = O.Lattice(identity_params(5, 4, 3, ("periodic",) * 4))
+    L.set_f(f)
+    L.step(1)
+    g = L.get_f()
+    for i in range(Q):
+        cx, cy, cz = CV[i]
+        assert np.abs(g[i] - np.roll(f[i], shift=(cz, cy, cx), axis=(0, 1, 2))).max() < 2e-15
+
+
+def test_wall_and_obstacle_bounce_back():
+    """Halfway bounce-back: a population that would come from a wall or a
+    solid cell is the reversed one of the cell itself."""
+    nx, ny, nz = 6, 5, 4
+    solid = np.zeros((nz, ny, nx), np.uint8)
+    solid[2, 2, 3] = 1
+    f = random_field((nz, ny, nx), 11)
+    L = O.Lattice(identity_params(nx, ny, nz, ("periodic", "periodic", "wall", "wall")), solid)
+    L.set_f(f)
+    L.step(1)
+    g = L.get_f()
+    for z, y, x in itertools.product(range(nz), range(ny), range(nx)):
+        if solid[z, y, x]:
+            continue
+        for i in range(Q):
+            cx, cy, cz = CV[i]
+            sx, sy, sz = x - cx, y - cy, z - cz
+            if not (0 <= sy < ny and 0 <= sz < nz) or solid[sz, sy, sx % nx]:
+                exp = f[OPP[i], z, y, x]
+            else:
+                exp = f[i, sz, sy, sx % nx]
+            assert abs(g[i, z, y, x] - exp) < 2e-15
+
+
+def test_closed_box_conserves_mass():
+    nx, ny, nz = 8, 6, 5
+    solid = I.sphere((nx, ny, nz), (3.5, 2.5, 2.0), 1.6)
+    r = rng(12)
+    f = np.zeros((Q, nz, ny, nx))
+    for z, y, x in itertools.product(range(nz), range(ny), range(nx)):
+        f[:, z, y, x] = near_eq_state(r, amp=0.05)
+    p = O.params(nx, ny, nz, 1.9, faces=("wall", "wall", "wall", "wall"))
+    L = O.Lattice(p, solid)
+    L.set_f(f)
+    m0 = L.totals()[0]
+    L.step(60)
+    assert abs(L.totals()[0] - m0) < 1e-12 * m0
+
+
+def test_periodic_box_conserves_mass_and_momentum():
+    nx, ny, nz = 6, 5, 4
+    r = rng(13)
+    f = np.zeros((Q, nz, ny, nx))
+    for z, y, x in itertools.product(range(nz), range(ny), range(nx)):
+        f[:, z, y, x] = near_eq_state(r, amp=0.05)
+    L = O.Lattice(O.params(nx, ny, nz, 1.95, faces=("periodic",) * 4))
+    L.set_f(f)
+    t0 = L.totals()
+    L.step(60)
+    assert np.abs(L.totals() - t0).max() < 1e-12
+
+
+def test_velocity_inlet_rule():
+    """Moving-wall bounce-back at the inlet (x = -1/2 moving with (U, 0, 0)):
+    f_i = f*_opp(i) + 6 w_i rho_w c_i.u_in for links entering through x = 0."""
+    nx, ny, nz = 4, 3, 3
+    U = 0.07
+    f = random_field((nz, ny, nx), 14)
+    L = O.Lattice(identity_params(nx, ny, nz, ("inlet", "outlet", "periodic", "periodic"), u_in=U))
+    L.set_f(f)
+    L.step(1)
+    g = L.get_f()
+    w = O.weights()
+    for i in np.nonzero(CV[:, 0] == 1)[0]:
+        assert np.allclose(g[i, :, :, 0], f[OPP[i], :, :, 0] + 6 * w[i] * U, atol=2e-15, rtol=0)
+
+
+def test_pressure_outlet_rule():
+    """Anti-bounce-back at the outlet (x = nx - 1/2) against the even part of
+    the equilibrium at rho_out = 1 and the cell's own pre-step velocity."""
+    nx, ny, nz = 4, 3, 3
+    f = random_field((nz, ny, nx), 15)
+    L = O.Lattice(identity_params(nx, ny, nz, ("inlet", "outlet", "periodic", "periodic")))
+    L.set_f(f)
+    rho, u = L.macros()
+    L.step(1)
+    g = L.get_f()
+    w = O.weights()
+    for i in np.nonzero(CV[:, 0] == -1)[0]:
+        ub = u[:, :, nx - 1]
+        cu = ub @ CV[i]
+        uu = (ub ** 2).sum(-1)
+        exp = -f[OPP[i], :, :, nx - 1] + 2 * w[i] * (1 + 4.5 * cu ** 2 - 1.5 * uu)
+        assert np.allclose(g[i, :, :, nx - 1], exp, atol=2e-15, rtol=0)
+
+
+# --------------------------------------------------------------------------
+# hydrodynamics
+# --------------------------------------------------------------------------
+def eq_field(rho, u):
+    f = np.zeros((Q,) + rho.shape)
+    for idx in np.ndindex(rho.shape):
+        f[(slice(None),) + idx] = O.equilibrium(rho[idx], *u[idx])
+    return f
+
+
+def taylor_green_nu(N, w1, drift=(0.0, 0.0, 0.0), gal=1, plane="xy", U0=1e-3):
+    """Decay of a 2-D Taylor-Green vortex, an exact Navier-Stokes solution
+    whose amplitude falls as exp(-2 nu k^2 t) (also when carried by a uniform
+    drift); returns the fitted and the nominal viscosity."""
+    nx, ny, nz = (N, N, 1) if plane == "xy" else (1, N, N)
+    k = 2 * np.pi / N
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    u = np.zeros((nz, ny, nx, 3))
+    a, b, ia, ib = (x, y, 0, 1) if plane == "xy" else (y, z, 1, 2)
+    u[..., ia] = U0 * np.sin(k * a) * np.cos(k * b)
+    u[..., ib] = -U0 * np.cos(k * a) * np.sin(k * b)
+    p = -U0 ** 2 / 4 * (np.cos(2 * k * a) + np.cos(2 * k * b))
+    L = O.Lattice(O.params(nx, ny, nz, w1, galilean=gal, faces=("periodic",) * 4))
+    L.set_f(eq_field(1 + 3 * p, u + np.asarray(drift)))
+    nu = (1 / w1 - 0.5) / 3
+    T = int(1.0 / (2 * nu * k * k))
+    t1 = T // 4
+    amp = []
+    for t in (t1, T):
+        L.step(t - L.t)
+        _, uu = L.macros()
+        du = uu - uu.reshape(-1, 3).mean(0)
+        amp.append(np.sqrt((du ** 2).sum()))
+    return -np.log(amp[1] / amp[0]) / (2 * k * k * (T - t1)), nu
+
+
+@pytest.mark.parametrize("w1", [1.2, 1.8])
+def test_taylor_green_viscosity_second_order(w1):
+    e16 = abs(taylor_green_nu(16, w1)[0] / taylor_green_nu(16, w1)[1] - 1)
+    nf, nu = taylor_green_nu(32, w1)
+    e32 = abs(nf / nu - 1)
+    assert e32 < 2e-3
+    assert e16 / e32 > 3.0            # second order: ratio ~4 on halving dx
+
+
+def test_taylor_green_other_orientation():
+    nf, nu = taylor_green_nu(16, 1.5, plane="yz")
+    assert abs(nf / nu - 1) < 5e-3
+
+
+def test_galilean_correction_removes_drift_dependence():
+    """A Taylor-Green vortex carried by a uniform drift decays at the rest
+    viscosity (Galilean invariance).  The corrected diagonal relaxation keeps
+    the error at the rest-frame level; without it the error grows with u^2."""
+    drift = (0.15, 0.0, 0.0)
+    nu_c, nu = taylor_green_nu(32, 1.8, drift=drift, gal=1)
+    nu_u, _ = taylor_green_nu(32, 1.8, drift=drift, gal=0)
+    err_c, err_u = abs(nu_c / nu - 1), abs(nu_u / nu - 1)
+    assert err_c < 1e-2
+    assert err_u > 3e-2
+    assert err_u > 5 * err_c
+
+
+def test_plane_poiseuille_profile():
+    """Channel with velocity inlet, pressure outlet, no-slip walls at
+    y = -1/2 and ny - 1/2 and periodic z at Re = 2: the developed profile at
+    mid-length is the parabola 1.5 U_mean (1 - (2 eta)^2)."""
+    NY, NX, U, re = 8, 64, 0.02, 2.0
+    nu = U * NY / re
+    p = O.params(NX, NY, 1, 1 / (3 * nu + 0.5), u_in=U, faces=("inlet", "outlet", "wall", "periodic"))
+    L = O.Lattice(p)
+    L.step(1200)
+    _, u = L.macros()
+    prof = u[0, :, NX // 2, 0]
+    eta = (np.arange(NY) - (NY - 1) / 2) / NY
+    ref = 1.5 * (1 - (2 * eta) ** 2)
+    a, b = prof / prof.mean(), ref / ref.mean()
+    assert np.sqrt(((a - b) ** 2).sum() / (b ** 2).sum()) < 1e-2
+    assert np.abs(u[0, :, NX // 2, 1:]).max() < 1e-3 * U
+
+
+def test_sphere_channel_mirror_symmetry():
+    """A sphere centred in y and z: the flow is symmetric under y -> ny-1-y,
+    z -> nz-1-z and y <-> z, to rounding."""
+    nx, ny, nz = 32, 16, 16
+    solid = I.sphere((nx, ny, nz), (8.0, 7.5, 7.5), 2.5)
+    p = O.params(nx, ny, nz, 1.9, u_in=0.05)
+    L = O.Lattice(p, solid)
+    L.step(60)
+    rho, u = L.macros()
+    assert np.abs(u).max() > 0.01
+    assert np.abs(rho - rho[:, ::-1, :]).max() < 1e-13
+    assert np.abs(u[..., 0] - u[:, ::-1, :, 0]).max() < 1e-13
+    assert np.abs(u[..., 1] + u[:, ::-1, :, 1]).max() < 1e-13
+    assert np.abs(u[..., 0] - u[::-1, :, :, 0]).max() < 1e-13
+    assert np.abs(u[..., 2] + u[::-1, :, :, 2]).max() < 1e-13
+    assert np.abs(rho - rho.transpose(1, 0, 2)).max() < 1e-13
+    assert np.abs(u[..., 1] - u[..., 2].transpose(1, 0, 2)).max() < 1e-13
+    F = L.forces()
+    assert F[-1, 0] > 0                       # drag points downstream
+    assert np.abs(F[:, 1:]).max() < 1e-12 * max(1.0, np.abs(F[:, 0]).max())
+
+
+def test_force_vanishes_at_rest_and_means_average_macros():
+    nx, ny, nz = 16, 8, 8
+    solid = I.sphere((nx, ny, nz), (6.0, 3.5, 3.5), 2.0)
+    L = O.Lattice(O.params(nx, ny, nz, 1.5, u_in=0.0, mean=(0, 100, 1)), solid)
+    L.step(3)
+    assert np.abs(L.forces()).max() < 1e-13
+    # mean window [2, 11) every 3 steps -> samples at t = 2, 5, 8
+    L2 = O.Lattice(O.params(nx, ny, nz, 1.7, u_in=0.05, mean=(2, 11, 3)), solid)
+    acc = np.zeros((nz, ny, nx, 4))
+    for t in range(12):
+        if t in (2, 5, 8):
+            rho, u = L2.macros()
+            fl = (solid == 0)[..., None]
+            acc += np.concatenate([u, (rho[..., None] - 1) / 3], -1) * fl
+        L2.step(1)
+    m, s = L2.means()
+    assert s == 3
+    assert np.abs(m - acc / 3).max() < 1e-15
