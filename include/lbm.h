@@ -1,0 +1,175 @@
+/*
+ * lbm.h -- C ABI of the GB300 D3Q27 cumulant lattice Boltzmann library.
+ *
+ * The library advances the channel flow of the paper's data pipeline
+ * (Sec. 2 "Pipeline description": simulation, capture of mean velocity and
+ * pressure, strided snapshots and obstacle forces; Sec. 3.1 "Generated
+ * dataset": velocity inlet, outflow, no-slip lateral walls, Re set through
+ * the lattice viscosity at constant inlet velocity; Sec. 3.2: D3Q27 stencil,
+ * cumulant collision operator, bounce-back on the obstacle).
+ *
+ * Conventions shared by every entry point
+ *   - Grid (nx, ny, nz), x streamwise.  Cell index c = x + nx*(y + ny*z).
+ *   - Velocities c_i in {-1,0,1}^3 with i = (cx+1) + 3(cy+1) + 9(cz+1); the
+ *     opposite of i is 26 - i.
+ *   - Every call returns lbm_status and never throws.  Argument errors are
+ *     reported synchronously; device-side conditions (non-finite or
+ *     out-of-range density) are latched in a device word and reported by the
+ *     next lbm_sync or read as LBM_ERR_UNSTABLE, after which lbm_step refuses
+ *     to run (LBM_ERR_STATE) but reads still work.
+ *   - Work is enqueued on the CUDA stream given at creation (borrowed, never
+ *     destroyed; NULL = legacy default stream).  lbm_step is asynchronous;
+ *     every read synchronises that stream.
+ *   - Destination/source buffers of reads and writes may live in host memory
+ *     or device memory (detected per call); the caller owns them.
+ *   - Masks and parameters are copied at creation; the caller keeps them.
+ */
+#ifndef GB300_LBM_H
+#define GB300_LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_ctx lbm_ctx;
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_ERR_ARG = 1,       /* invalid argument (nothing was enqueued)          */
+    LBM_ERR_CUDA = 2,      /* a CUDA runtime call failed                        */
+    LBM_ERR_OOM = 3,       /* device allocation failed / workspace too small    */
+    LBM_ERR_UNSTABLE = 4,  /* density left (0.5, 1.5) or became non-finite     */
+    LBM_ERR_TIMEOUT = 5,   /* a bounded device-side wait expired               */
+    LBM_ERR_STATE = 6,     /* call not valid in the context's current state    */
+    LBM_ERR_IO = 7         /* checkpoint file could not be written or read     */
+} lbm_status;
+
+/* Storage of the shifted populations f_i - w_i (arithmetic is FP32 for the
+ * three reduced formats, FP64 for LBM_F64). */
+typedef enum { LBM_F64 = 0, LBM_F32 = 1, LBM_F16S = 2, LBM_BF16S = 3 } lbm_storage;
+
+/* Boundary kind of a pair of faces (x has a low and a high face). */
+typedef enum {
+    LBM_FACE_WALL = 0,      /* no-slip halfway bounce-back                       */
+    LBM_FACE_PERIODIC = 1,  /* wrap-around                                       */
+    LBM_FACE_INLET = 2,     /* x low only: bounce-back from a wall moving at u_in */
+    LBM_FACE_OUTLET = 3     /* x high only: anti-bounce-back at rho_out           */
+} lbm_face;
+
+typedef struct { int32_t nx, ny, nz; } lbm_grid;
+
+typedef struct {
+    /* Sec. 3.1: nu = u_in * l_ref / re, omega1 = 1 / (3 nu + 1/2) */
+    double re, u_in, l_ref;
+    double omega1;          /* > 0 overrides the Re-derived shear rate          */
+    double omega_bulk;      /* bulk rate (default 1)                            */
+    double omega_higher;    /* rate of every cumulant of order 3..6 (default 1) */
+    double rho_in;          /* density of the moving inlet wall (default 1)     */
+    double rho_out;         /* outlet density (default 1)                       */
+    int32_t storage;        /* lbm_storage (default LBM_F32)                    */
+    int32_t galilean_correction; /* 1 (default): corrected diagonal relaxation  */
+    int32_t face_x_lo, face_x_hi, face_y, face_z; /* lbm_face; default inlet/outlet/wall/wall */
+    /* time average (Sec. 2: mean velocity and pressure): steps t with
+     * mean_start <= t < mean_end and (t - mean_start) % mean_every == 0 are
+     * sampled from the pre-collision state of step t; mean_every = 0: off */
+    int64_t mean_start, mean_end, mean_every;
+    /* snapshots (Sec. 2: 20 snapshots 25 steps apart): u, v, w, p of the
+     * pre-collision state at t = snap_first + k * snap_every, k < snap_count */
+    int64_t snap_first, snap_every, snap_count;
+    int32_t snap_halfres;   /* 1: 2x2x2 box mean (Sec. 3.1: half resolution)    */
+    int32_t force_every;    /* record the obstacle force every n steps (0: off) */
+    int64_t force_capacity; /* rows kept on the device between host flushes     */
+    int32_t block_x;        /* threads per block along x (0: library default)   */
+    int32_t reserved[7];
+} lbm_params;
+
+/* Fill *p with the defaults listed above (re = 1000, u_in = 0.05, l_ref = 1,
+ * averaging and snapshots off, force off). */
+void lbm_params_default(lbm_params *p);
+
+/* Bytes of device memory a context with these arguments needs (pdfs,
+ * cell flags, boundary list, accumulators, snapshot ring, scratch). */
+size_t lbm_workspace_bytes(const lbm_grid *grid, const lbm_params *p);
+
+/* Create a context.  mask: nx*ny*nz bytes, 1 = solid obstacle cell, host or
+ * device, may be NULL (no obstacle).  State starts at rest (f = w, t = 0).
+ * The library allocates its own device memory. */
+lbm_status lbm_create(const lbm_grid *grid, const uint8_t *mask, const lbm_params *p,
+                      void *cuda_stream, lbm_ctx **out);
+
+/* As lbm_create, but every device buffer is carved from the caller's
+ * device allocation `workspace` of `workspace_bytes` (at least
+ * lbm_workspace_bytes(); 256-byte aligned).  The caller keeps ownership and
+ * must keep it alive until lbm_destroy. */
+lbm_status lbm_create_in(const lbm_grid *grid, const uint8_t *mask, const lbm_params *p,
+                         void *cuda_stream, void *workspace, size_t workspace_bytes,
+                         lbm_ctx **out);
+
+lbm_status lbm_destroy(lbm_ctx *ctx);
+
+/* Advance n time steps (fused collide + stream in place, AA pattern; the
+ * epilogues sample means, forces and snapshots as configured).  Async. */
+lbm_status lbm_step(lbm_ctx *ctx, int64_t n);
+
+/* Wait for the stream; report latched device conditions. */
+lbm_status lbm_sync(lbm_ctx *ctx);
+
+/* Number of steps taken so far. */
+int64_t lbm_time(const lbm_ctx *ctx);
+
+/* Time-averaged fields: 4 values per cell (ux, uy, uz, p), cell-major
+ * [z][y][x][4], p = (rho - 1)/3; solid cells give 0.  dtype 0 = double,
+ * 1 = float.  halfres = 1: 2x2x2 box means on a ceil(n/2) grid.
+ * samples (may be NULL) receives the sample count. */
+lbm_status lbm_read_mean(lbm_ctx *ctx, int32_t dtype, int32_t halfres, void *dst,
+                         int64_t *samples);
+
+/* Snapshot k (0 <= k < snap_count) as float [z][y][x][4] (ux, uy, uz, p) at
+ * full or half resolution (params.snap_halfres); LBM_ERR_STATE if not taken. */
+lbm_status lbm_read_snapshot(lbm_ctx *ctx, int32_t k, float *dst);
+
+/* Density and velocity of the current state: rho [N], u [N][3] (doubles). */
+lbm_status lbm_read_macros(lbm_ctx *ctx, double *rho, double *u);
+
+/* Obstacle force F(t) = sum over obstacle links of 2 c_i f*_i (momentum
+ * exchange), one row (Fx, Fy, Fz) per recorded step, oldest first.  Writes at
+ * most max_rows rows; *n_rows receives the number recorded. */
+lbm_status lbm_read_forces(lbm_ctx *ctx, double *dst, int64_t max_rows, int64_t *n_rows);
+
+/* Full populations f_i (stored value + w_i) of the current state in natural
+ * order, direction-major [27][N] doubles. */
+lbm_status lbm_get_pdfs(lbm_ctx *ctx, double *dst);
+
+/* Overwrite the state with full populations [27][N] (values of solid cells
+ * are ignored).  Only at even t (LBM_ERR_STATE otherwise). */
+lbm_status lbm_set_pdfs(lbm_ctx *ctx, const double *src);
+
+/* Full populations of n selected cells: dst [n][27] doubles; cells [n]
+ * (host or device int64 cell indices, each in [0, N)). */
+lbm_status lbm_get_cells(lbm_ctx *ctx, int64_t n, const int64_t *cells, double *dst);
+
+/* Seeded near-rest state: stored f_i - w_i = amplitude * r, r uniform in
+ * [-1, 1) from SplitMix64 started at `seed`, stream counter cell*27 + i;
+ * solid cells 0.  Only at even t. */
+lbm_status lbm_init_noise(lbm_ctx *ctx, uint64_t seed, double amplitude);
+
+/* Totals over fluid cells of the current state: out[0] = sum_i (f_i - w_i)
+ * (mass minus the rest mass), out[1..3] = momentum.  Two-pass deterministic
+ * FP64 reduction. */
+lbm_status lbm_totals(lbm_ctx *ctx, double out[4]);
+
+/* Checkpoint: pdfs, time step, outlet plane, accumulators, force rows. */
+lbm_status lbm_save(lbm_ctx *ctx, const char *path);
+lbm_status lbm_load(lbm_ctx *ctx, const char *path);
+
+/* Last error message of this context (never NULL). */
+const char *lbm_last_error(const lbm_ctx *ctx);
+const char *lbm_status_string(lbm_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GB300_LBM_H */

@@ -1,0 +1,669 @@
+// lbm_api.cu -- host side of the C ABI declared in include/lbm.h: context
+// creation (cell flags, edge-cell list, device memory layout), the time loop
+// with its epilogue schedule (time average, snapshots, obstacle force), read
+// and write of the state, checkpoints.
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/lbm.h"
+#include "lbm_internal.h"
+
+using namespace lbm;
+
+namespace {
+
+thread_local std::string g_err;
+
+constexpr size_t ALIGN = 256;
+size_t align_up(size_t v) { return (v + ALIGN - 1) / ALIGN * ALIGN; }
+
+size_t storage_bytes(int s) { return s == LBM_F64 ? 8 : (s == LBM_F32 ? 4 : 2); }
+
+// Device memory layout of a context (byte offsets into one allocation).
+struct Layout {
+    int64_t n = 0, slot = 0, n_half = 0, snap_cells = 0;
+    size_t pdf = 0, flags = 0, edge = 0, ub = 0, msum = 0, snaps = 0, stage = 0, force = 0,
+           fpart = 0, fcount = 0, tpart = 0, tout = 0, status = 0, total = 0;
+    int tot_blocks = 0;
+};
+
+Layout make_layout(const lbm_grid &g, const lbm_params &p)
+{
+    Layout L;
+    L.n = (int64_t)g.nx * g.ny * g.nz;
+    L.slot = (L.n + 63) / 64 * 64;
+    L.n_half = (int64_t)((g.nx + 1) / 2) * ((g.ny + 1) / 2) * ((g.nz + 1) / 2);
+    L.snap_cells = p.snap_halfres ? L.n_half : L.n;
+    const size_t rsz = p.storage == LBM_F64 ? 8 : 4;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes); return o; };
+    L.pdf = take((size_t)Q * L.slot * storage_bytes(p.storage));
+    L.flags = take((size_t)L.n);
+    L.edge = take((size_t)L.n * 4);
+    L.ub = take((size_t)3 * g.ny * g.nz * rsz);
+    L.msum = take(p.mean_every > 0 ? (size_t)4 * L.n * 8 : 0);
+    L.snaps = take(p.snap_count > 0 ? (size_t)p.snap_count * 4 * L.snap_cells * 4 : 0);
+    L.stage = take(p.snap_count > 0 && p.snap_halfres ? (size_t)4 * L.n * 4 : 0);
+    const int64_t cap = p.force_capacity > 0 ? p.force_capacity : 65536;
+    L.force = take(p.force_every > 0 ? (size_t)cap * 3 * 8 : 0);
+    L.fpart = take((size_t)3 * 8 * ((L.n + EDGE_BLOCK - 1) / EDGE_BLOCK + 1));
+    L.fcount = take(sizeof(unsigned));
+    L.tot_blocks = (int)std::max<int64_t>(1, std::min<int64_t>((L.n + 255) / 256, 152 * 8));
+    L.tpart = take((size_t)4 * 8 * L.tot_blocks);
+    L.tout = take(4 * 8);
+    L.status = take(sizeof(int));
+    L.total = off;
+    return L;
+}
+
+bool is_device_ptr(const void *p)
+{
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+struct lbm_ctx {
+    lbm_grid g;
+    lbm_params p;
+    Layout L;
+    cudaStream_t stream = nullptr;
+    bool owns = false;
+    char *base = nullptr;
+    int64_t n_edge = 0;
+    int64_t t = 0;
+    double w1 = 0;
+    bool plain = true;
+    int block_x = 128;
+    int64_t msamples = 0;
+    std::vector<char> snap_taken;
+    std::vector<double> force_host;   // flushed rows (deviation part)
+    int64_t force_rows_dev = 0, force_cap = 0;
+    double force_w[3] = {0, 0, 0};    // constant w-part of the obstacle force
+    bool unstable = false;
+    std::string err;
+
+    template <class T> T *at(size_t off) { return reinterpret_cast<T *>(base + off); }
+
+    StepArgs args()
+    {
+        StepArgs a{};
+        a.pdf = base + L.pdf;
+        a.slot = L.slot;
+        a.flags = at<uint8_t>(L.flags);
+        a.edge = at<uint32_t>(L.edge);
+        a.n_edge = n_edge;
+        a.nx = g.nx; a.ny = g.ny; a.nz = g.nz;
+        a.nxy = (int64_t)g.nx * g.ny;
+        a.n = L.n;
+        a.w1 = w1; a.w2 = p.omega_bulk; a.w3 = p.omega_higher;
+        a.galilean = p.galilean_correction;
+        a.face_x_lo = p.face_x_lo; a.face_x_hi = p.face_x_hi; a.face_y = p.face_y; a.face_z = p.face_z;
+        a.u_in = p.u_in; a.rho_in = p.rho_in; a.rho_out = p.rho_out;
+        a.ub = base + L.ub;
+        a.fcount = at<unsigned>(L.fcount);
+        a.status = at<int>(L.status);
+        return a;
+    }
+};
+
+#define CK(call)                                                                          \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess) {                                                          \
+            ctx->err = std::string(#call) + ": " + cudaGetErrorString(e_);                \
+            return LBM_ERR_CUDA;                                                          \
+        }                                                                                 \
+    } while (0)
+
+static lbm_status fail(lbm_ctx *ctx, lbm_status s, const std::string &m)
+{
+    if (ctx) ctx->err = m; else g_err = m;
+    return s;
+}
+
+// ---------------------------------------------------------------------------
+extern "C" void lbm_params_default(lbm_params *p)
+{
+    std::memset(p, 0, sizeof(*p));
+    p->re = 1000.0; p->u_in = 0.05; p->l_ref = 1.0;
+    p->omega1 = 0.0; p->omega_bulk = 1.0; p->omega_higher = 1.0;
+    p->rho_in = 1.0; p->rho_out = 1.0;
+    p->storage = LBM_F32; p->galilean_correction = 1;
+    p->face_x_lo = LBM_FACE_INLET; p->face_x_hi = LBM_FACE_OUTLET;
+    p->face_y = LBM_FACE_WALL; p->face_z = LBM_FACE_WALL;
+    p->force_capacity = 65536;
+}
+
+static std::string validate(const lbm_grid *g, const lbm_params *p)
+{
+    if (!g || !p) return "null grid or params";
+    if (g->nx < 1 || g->ny < 1 || g->nz < 1) return "grid dimensions must be >= 1";
+    if (g->ny > 65535 || g->nz > 65535) return "ny and nz must be <= 65535";
+    if ((int64_t)g->nx * g->ny * g->nz >= (int64_t(1) << 32)) return "grid must have fewer than 2^32 cells";
+    if (p->storage < 0 || p->storage > 3) return "unknown storage";
+    if (p->face_x_lo != LBM_FACE_INLET && p->face_x_lo != LBM_FACE_WALL && p->face_x_lo != LBM_FACE_PERIODIC)
+        return "face_x_lo must be inlet, wall or periodic";
+    if (p->face_x_hi != LBM_FACE_OUTLET && p->face_x_hi != LBM_FACE_WALL && p->face_x_hi != LBM_FACE_PERIODIC)
+        return "face_x_hi must be outlet, wall or periodic";
+    if ((p->face_x_lo == LBM_FACE_PERIODIC) != (p->face_x_hi == LBM_FACE_PERIODIC))
+        return "periodic x needs both x faces periodic";
+    if ((p->face_y != LBM_FACE_WALL && p->face_y != LBM_FACE_PERIODIC) ||
+        (p->face_z != LBM_FACE_WALL && p->face_z != LBM_FACE_PERIODIC))
+        return "y and z faces must be wall or periodic";
+    if (p->omega1 <= 0 && !(p->re > 0 && p->u_in >= 0 && p->l_ref > 0)) return "need omega1 > 0 or re, l_ref > 0";
+    if (p->mean_every < 0 || p->snap_count < 0 || p->force_every < 0) return "negative schedule";
+    if (p->snap_count > 0 && p->snap_every < 1) return "snap_every must be >= 1";
+    if (p->block_x != 0 && (p->block_x % 32 != 0 || p->block_x > 256)) return "block_x must be a multiple of 32, <= 256";
+    return "";
+}
+
+extern "C" size_t lbm_workspace_bytes(const lbm_grid *g, const lbm_params *p)
+{
+    if (!validate(g, p).empty()) return 0;
+    return make_layout(*g, *p).total;
+}
+
+static lbm_status create_impl(const lbm_grid *g, const uint8_t *mask, const lbm_params *p, void *stream,
+                              void *workspace, size_t ws_bytes, lbm_ctx **out)
+{
+    if (!out) return fail(nullptr, LBM_ERR_ARG, "out is null");
+    *out = nullptr;
+    std::string v = validate(g, p);
+    if (!v.empty()) return fail(nullptr, LBM_ERR_ARG, v);
+    lbm_ctx *ctx = new lbm_ctx();
+    ctx->g = *g;
+    ctx->p = *p;
+    if (ctx->p.force_capacity <= 0) ctx->p.force_capacity = 65536;
+    ctx->L = make_layout(*g, ctx->p);
+    ctx->stream = static_cast<cudaStream_t>(stream);
+    ctx->w1 = p->omega1 > 0 ? p->omega1 : 1.0 / (3.0 * p->u_in * p->l_ref / p->re + 0.5);
+    ctx->plain = (p->omega_higher == 1.0);
+    ctx->block_x = p->block_x ? p->block_x : 128;
+    ctx->force_cap = ctx->p.force_capacity;
+    ctx->snap_taken.assign(std::max<int64_t>(0, p->snap_count), 0);
+    const Layout &L = ctx->L;
+    auto bail = [&](lbm_status s) {
+        g_err = ctx->err;
+        if (ctx->owns && ctx->base) cudaFree(ctx->base);
+        delete ctx;
+        return s;
+    };
+    if (workspace) {
+        if (ws_bytes < L.total || (reinterpret_cast<uintptr_t>(workspace) % ALIGN) != 0) {
+            ctx->err = "workspace too small or not 256-byte aligned";
+            return bail(LBM_ERR_OOM);
+        }
+        ctx->base = static_cast<char *>(workspace);
+    } else {
+        cudaError_t e = cudaMalloc(&ctx->base, L.total);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            ctx->err = std::string("cudaMalloc of ") + std::to_string(L.total) + " bytes failed";
+            return bail(LBM_ERR_OOM);
+        }
+        ctx->owns = true;
+    }
+    cudaStream_t s = ctx->stream;
+    const int64_t n = L.n;
+    // the mask goes through the (not yet used) edge-list region
+    uint8_t *dmask = nullptr;
+    if (mask) {
+        dmask = ctx->at<uint8_t>(L.edge);
+        if (cudaMemcpyAsync(dmask, mask, n, is_device_ptr(mask) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s) != cudaSuccess) {
+            ctx->err = "mask upload failed";
+            return bail(LBM_ERR_CUDA);
+        }
+    }
+    launch_flags(dmask, ctx->at<uint8_t>(L.flags), g->nx, g->ny, g->nz, s);
+    std::vector<uint8_t> hflags(n);
+    if (cudaMemcpyAsync(hflags.data(), ctx->at<uint8_t>(L.flags), n, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        ctx->err = std::string("flag build failed: ") + cudaGetErrorString(cudaGetLastError());
+        return bail(LBM_ERR_CUDA);
+    }
+    // edge-cell list (ascending cell order keeps rows contiguous) and the
+    // constant part sum 2 c_i w_i of the obstacle force over obstacle links
+    std::vector<uint32_t> edge;
+    double fw[3] = {0, 0, 0};
+    const int nx = g->nx, ny = g->ny, nz = g->nz;
+    for (int64_t c = 0; c < n; ++c) {
+        if (hflags[c] != CELL_EDGE) continue;
+        edge.push_back((uint32_t)c);
+        const int x = (int)(c % nx), y = (int)((c / nx) % ny), z = (int)(c / ((int64_t)nx * ny));
+        for (int j = 0; j < Q; ++j) {
+            int xx = x + cx_of(j), yy = y + cy_of(j), zz = z + cz_of(j);
+            if (yy < 0 || yy >= ny) { if (p->face_y != LBM_FACE_PERIODIC) continue; yy = (yy + ny) % ny; }
+            if (zz < 0 || zz >= nz) { if (p->face_z != LBM_FACE_PERIODIC) continue; zz = (zz + nz) % nz; }
+            if (xx < 0 || xx >= nx) { if (p->face_x_lo != LBM_FACE_PERIODIC) continue; xx = (xx + nx) % nx; }
+            if (!(hflags[xx + (int64_t)nx * (yy + (int64_t)ny * zz)] & CELL_SOLID)) continue;
+            fw[0] += 2.0 * cx_of(j) * w_of(j);
+            fw[1] += 2.0 * cy_of(j) * w_of(j);
+            fw[2] += 2.0 * cz_of(j) * w_of(j);
+        }
+    }
+    ctx->n_edge = (int64_t)edge.size();
+    for (int d = 0; d < 3; ++d) ctx->force_w[d] = fw[d];
+    if (!edge.empty() && cudaMemcpyAsync(ctx->at<uint32_t>(L.edge), edge.data(), edge.size() * 4,
+                                         cudaMemcpyHostToDevice, s) != cudaSuccess) {
+        ctx->err = "edge list upload failed";
+        return bail(LBM_ERR_CUDA);
+    }
+    // state at rest (shifted populations 0), accumulators cleared
+    bool ok = cudaMemsetAsync(ctx->base + L.pdf, 0, (size_t)Q * L.slot * storage_bytes(p->storage), s) == cudaSuccess;
+    ok = ok && cudaMemsetAsync(ctx->base + L.ub, 0, (size_t)3 * ny * nz * (p->storage == LBM_F64 ? 8 : 4), s) == cudaSuccess;
+    if (p->mean_every > 0) ok = ok && cudaMemsetAsync(ctx->base + L.msum, 0, (size_t)4 * n * 8, s) == cudaSuccess;
+    if (p->snap_count > 0) {
+        ok = ok && cudaMemsetAsync(ctx->base + L.snaps, 0, (size_t)p->snap_count * 4 * L.snap_cells * 4, s) == cudaSuccess;
+        if (p->snap_halfres) ok = ok && cudaMemsetAsync(ctx->base + L.stage, 0, (size_t)4 * n * 4, s) == cudaSuccess;
+    }
+    ok = ok && cudaMemsetAsync(ctx->base + L.fcount, 0, sizeof(unsigned), s) == cudaSuccess;
+    ok = ok && cudaMemsetAsync(ctx->base + L.status, 0, sizeof(int), s) == cudaSuccess;
+    ok = ok && cudaStreamSynchronize(s) == cudaSuccess;
+    if (!ok) {
+        ctx->err = std::string("initialisation failed: ") + cudaGetErrorString(cudaGetLastError());
+        return bail(LBM_ERR_CUDA);
+    }
+    *out = ctx;
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_create(const lbm_grid *g, const uint8_t *mask, const lbm_params *p, void *stream,
+                                 lbm_ctx **out)
+{
+    return create_impl(g, mask, p, stream, nullptr, 0, out);
+}
+
+extern "C" lbm_status lbm_create_in(const lbm_grid *g, const uint8_t *mask, const lbm_params *p, void *stream,
+                                    void *workspace, size_t ws_bytes, lbm_ctx **out)
+{
+    if (!workspace) return fail(nullptr, LBM_ERR_ARG, "workspace is null");
+    return create_impl(g, mask, p, stream, workspace, ws_bytes, out);
+}
+
+extern "C" lbm_status lbm_destroy(lbm_ctx *ctx)
+{
+    if (!ctx) return LBM_ERR_ARG;
+    cudaStreamSynchronize(ctx->stream);
+    if (ctx->owns && ctx->base) cudaFree(ctx->base);
+    delete ctx;
+    return LBM_OK;
+}
+
+extern "C" int64_t lbm_time(const lbm_ctx *ctx) { return ctx ? ctx->t : -1; }
+
+static lbm_status flush_forces(lbm_ctx *ctx)
+{
+    if (ctx->force_rows_dev == 0) return LBM_OK;
+    const size_t old = ctx->force_host.size();
+    ctx->force_host.resize(old + 3 * ctx->force_rows_dev);
+    CK(cudaMemcpyAsync(ctx->force_host.data() + old, ctx->base + ctx->L.force,
+                       sizeof(double) * 3 * ctx->force_rows_dev, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->force_rows_dev = 0;
+    return LBM_OK;
+}
+
+static void step_launch(lbm_ctx *ctx, const StepArgs &a, bool odd, bool epi)
+{
+    switch (ctx->p.storage) {
+    case LBM_F64: launch_step_f64(a, odd, epi, ctx->plain, ctx->block_x, ctx->stream); break;
+    case LBM_F32: launch_step_f32(a, odd, epi, ctx->plain, ctx->block_x, ctx->stream); break;
+    case LBM_F16S: launch_step_f16(a, odd, epi, ctx->plain, ctx->block_x, ctx->stream); break;
+    default: launch_step_bf16(a, odd, epi, ctx->plain, ctx->block_x, ctx->stream); break;
+    }
+}
+
+extern "C" lbm_status lbm_step(lbm_ctx *ctx, int64_t nsteps)
+{
+    if (!ctx || nsteps < 0) return ctx ? fail(ctx, LBM_ERR_ARG, "negative step count") : LBM_ERR_ARG;
+    if (ctx->unstable) return fail(ctx, LBM_ERR_STATE, "state is unstable; steps refused");
+    const lbm_params &p = ctx->p;
+    const Layout &L = ctx->L;
+    const StepArgs base = ctx->args();
+    for (int64_t k = 0; k < nsteps; ++k) {
+        const int64_t t = ctx->t;
+        StepArgs a = base;
+        if (p.mean_every > 0 && t >= p.mean_start && t < p.mean_end && (t - p.mean_start) % p.mean_every == 0) {
+            a.msum = ctx->at<double>(L.msum);
+            ctx->msamples++;
+        }
+        int64_t snap_k = -1;
+        if (p.snap_count > 0 && t >= p.snap_first && (t - p.snap_first) % p.snap_every == 0) {
+            const int64_t kk = (t - p.snap_first) / p.snap_every;
+            if (kk < p.snap_count) snap_k = kk;
+        }
+        float *slot = nullptr;
+        if (snap_k >= 0) {
+            slot = ctx->at<float>(L.snaps) + (size_t)snap_k * 4 * L.snap_cells;
+            if (p.snap_halfres) {
+                a.snap = ctx->at<float>(L.stage);
+            } else {
+                CK(cudaMemsetAsync(slot, 0, sizeof(float) * 4 * L.n, ctx->stream));
+                a.snap = slot;
+            }
+            ctx->snap_taken[snap_k] = 1;
+        }
+        const bool rec_force = p.force_every > 0 && t % p.force_every == 0;
+        if (rec_force) {
+            if (ctx->force_rows_dev == ctx->force_cap) {
+                lbm_status st = flush_forces(ctx);
+                if (st != LBM_OK) return st;
+            }
+            a.fout = ctx->at<double>(L.force) + 3 * ctx->force_rows_dev;
+            if (ctx->n_edge > 0) a.fpart = ctx->at<double>(L.fpart);
+            else CK(cudaMemsetAsync(a.fout, 0, 3 * sizeof(double), ctx->stream));
+            ctx->force_rows_dev++;
+        }
+        step_launch(ctx, a, (t & 1) != 0, a.msum != nullptr || a.snap != nullptr);
+        if (snap_k >= 0 && p.snap_halfres)
+            launch_halfres(a.snap, ctx->g.nx, ctx->g.ny, ctx->g.nz, true, slot, ctx->stream);
+        ctx->t = t + 1;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(ctx, LBM_ERR_CUDA, std::string("step launch: ") + cudaGetErrorString(e));
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_sync(lbm_ctx *ctx)
+{
+    if (!ctx) return LBM_ERR_ARG;
+    CK(cudaStreamSynchronize(ctx->stream));
+    int st = 0;
+    CK(cudaMemcpy(&st, ctx->base + ctx->L.status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (st & STATUS_UNSTABLE) {
+        ctx->unstable = true;
+        return fail(ctx, LBM_ERR_UNSTABLE, "density left (0.5, 1.5) or became non-finite");
+    }
+    return LBM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// reads and writes
+// ---------------------------------------------------------------------------
+namespace {
+struct DevBuf {
+    void *p = nullptr;
+    ~DevBuf() { if (p) cudaFree(p); }
+    cudaError_t alloc(size_t b) { return cudaMalloc(&p, b ? b : 1); }
+};
+}  // namespace
+
+// Run fn(dev_ptr) producing `bytes` of output at a device pointer, then place
+// it into dst (device: directly; host: through a temporary).
+template <class F>
+static lbm_status produce(lbm_ctx *ctx, void *dst, size_t bytes, F fn)
+{
+    if (is_device_ptr(dst)) {
+        fn(dst);
+        CK(cudaGetLastError());
+        CK(cudaStreamSynchronize(ctx->stream));
+        return LBM_OK;
+    }
+    DevBuf tmp;
+    CK(tmp.alloc(bytes));
+    fn(tmp.p);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(dst, tmp.p, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_read_mean(lbm_ctx *ctx, int32_t dtype, int32_t halfres, void *dst, int64_t *samples)
+{
+    if (!ctx || !dst || (dtype != 0 && dtype != 1)) return ctx ? fail(ctx, LBM_ERR_ARG, "bad read_mean arguments") : LBM_ERR_ARG;
+    if (ctx->p.mean_every <= 0) return fail(ctx, LBM_ERR_STATE, "time average not enabled");
+    lbm_status st = lbm_sync(ctx);
+    if (st != LBM_OK && st != LBM_ERR_UNSTABLE) return st;
+    if (samples) *samples = ctx->msamples;
+    const bool f32 = dtype == 1;
+    const size_t es = f32 ? 4 : 8;
+    const int64_t n = ctx->L.n, nh = ctx->L.n_half;
+    const double inv = ctx->msamples > 0 ? 1.0 / (double)ctx->msamples : 0.0;
+    const double *msum = ctx->at<double>(ctx->L.msum);
+    if (!halfres)
+        return produce(ctx, dst, 4 * es * n, [&](void *o) { launch_mean_out(msum, n, inv, f32, o, ctx->stream); });
+    DevBuf full;
+    CK(full.alloc(4 * es * n));
+    launch_mean_out(msum, n, inv, f32, full.p, ctx->stream);
+    return produce(ctx, dst, 4 * es * nh, [&](void *o) {
+        launch_halfres(full.p, ctx->g.nx, ctx->g.ny, ctx->g.nz, f32, o, ctx->stream);
+    });
+}
+
+extern "C" lbm_status lbm_read_snapshot(lbm_ctx *ctx, int32_t k, float *dst)
+{
+    if (!ctx || !dst) return LBM_ERR_ARG;
+    if (k < 0 || k >= ctx->p.snap_count) return fail(ctx, LBM_ERR_ARG, "snapshot index out of range");
+    if (!ctx->snap_taken[k]) return fail(ctx, LBM_ERR_STATE, "snapshot not taken yet");
+    CK(cudaStreamSynchronize(ctx->stream));
+    const size_t bytes = sizeof(float) * 4 * ctx->L.snap_cells;
+    CK(cudaMemcpyAsync(dst, ctx->at<float>(ctx->L.snaps) + (size_t)k * 4 * ctx->L.snap_cells, bytes,
+                       cudaMemcpyDefault, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_read_macros(lbm_ctx *ctx, double *rho, double *u)
+{
+    if (!ctx || !rho || !u) return LBM_ERR_ARG;
+    CK(cudaStreamSynchronize(ctx->stream));
+    const int64_t n = ctx->L.n;
+    DevBuf br, bu;
+    CK(br.alloc(8 * n));
+    CK(bu.alloc(24 * n));
+    AuxArgs x;
+    x.out = (double *)br.p;
+    x.out2 = (double *)bu.p;
+    launch_aux(ctx->p.storage, AUX_MACROS, ctx->args(), ctx->t & 1, x, ctx->stream);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(rho, br.p, 8 * n, cudaMemcpyDefault, ctx->stream));
+    CK(cudaMemcpyAsync(u, bu.p, 24 * n, cudaMemcpyDefault, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_read_forces(lbm_ctx *ctx, double *dst, int64_t max_rows, int64_t *n_rows)
+{
+    if (!ctx || max_rows < 0 || (max_rows > 0 && !dst)) return LBM_ERR_ARG;
+    lbm_status st = flush_forces(ctx);
+    if (st != LBM_OK) return st;
+    const int64_t rows = (int64_t)ctx->force_host.size() / 3;
+    if (n_rows) *n_rows = rows;
+    const int64_t m = std::min(rows, max_rows);
+    std::vector<double> out(3 * m);
+    for (int64_t r = 0; r < m; ++r)
+        for (int d = 0; d < 3; ++d) out[3 * r + d] = ctx->force_host[3 * r + d] + ctx->force_w[d];
+    if (m > 0) {
+        if (is_device_ptr(dst)) CK(cudaMemcpy(dst, out.data(), sizeof(double) * 3 * m, cudaMemcpyHostToDevice));
+        else std::memcpy(dst, out.data(), sizeof(double) * 3 * m);
+    }
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_get_pdfs(lbm_ctx *ctx, double *dst)
+{
+    if (!ctx || !dst) return LBM_ERR_ARG;
+    CK(cudaStreamSynchronize(ctx->stream));
+    const int64_t n = ctx->L.n;
+    return produce(ctx, dst, sizeof(double) * Q * n, [&](void *o) {
+        AuxArgs x;
+        x.count = n; x.out = (double *)o; x.si = n; x.sc = 1;
+        launch_aux(ctx->p.storage, AUX_GATHER, ctx->args(), ctx->t & 1, x, ctx->stream);
+    });
+}
+
+extern "C" lbm_status lbm_get_cells(lbm_ctx *ctx, int64_t count, const int64_t *cells, double *dst)
+{
+    if (!ctx || count < 0 || (count > 0 && (!cells || !dst))) return LBM_ERR_ARG;
+    if (count == 0) return LBM_OK;
+    CK(cudaStreamSynchronize(ctx->stream));
+    DevBuf dc;
+    const int64_t *dcells = cells;
+    if (!is_device_ptr(cells)) {
+        for (int64_t k = 0; k < count; ++k)
+            if (cells[k] < 0 || cells[k] >= ctx->L.n) return fail(ctx, LBM_ERR_ARG, "cell index out of range");
+        CK(dc.alloc(8 * count));
+        CK(cudaMemcpyAsync(dc.p, cells, 8 * count, cudaMemcpyHostToDevice, ctx->stream));
+        dcells = (const int64_t *)dc.p;
+    }
+    return produce(ctx, dst, sizeof(double) * Q * count, [&](void *o) {
+        AuxArgs x;
+        x.cells = dcells; x.count = count; x.out = (double *)o; x.si = 1; x.sc = Q;
+        launch_aux(ctx->p.storage, AUX_GATHER, ctx->args(), ctx->t & 1, x, ctx->stream);
+    });
+}
+
+extern "C" lbm_status lbm_set_pdfs(lbm_ctx *ctx, const double *src)
+{
+    if (!ctx || !src) return LBM_ERR_ARG;
+    if (ctx->t & 1) return fail(ctx, LBM_ERR_STATE, "set_pdfs needs an even time step");
+    CK(cudaStreamSynchronize(ctx->stream));
+    const int64_t n = ctx->L.n;
+    DevBuf tmp;
+    const double *dsrc = src;
+    if (!is_device_ptr(src)) {
+        CK(tmp.alloc(sizeof(double) * Q * n));
+        CK(cudaMemcpyAsync(tmp.p, src, sizeof(double) * Q * n, cudaMemcpyHostToDevice, ctx->stream));
+        dsrc = (const double *)tmp.p;
+    }
+    AuxArgs x;
+    x.src = dsrc;
+    launch_aux(ctx->p.storage, AUX_SET, ctx->args(), false, x, ctx->stream);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(ctx->stream));
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_init_noise(lbm_ctx *ctx, uint64_t seed, double amplitude)
+{
+    if (!ctx) return LBM_ERR_ARG;
+    if (ctx->t & 1) return fail(ctx, LBM_ERR_STATE, "init_noise needs an even time step");
+    AuxArgs x;
+    x.seed = seed;
+    x.amp = amplitude;
+    launch_aux(ctx->p.storage, AUX_NOISE, ctx->args(), false, x, ctx->stream);
+    CK(cudaGetLastError());
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_totals(lbm_ctx *ctx, double out[4])
+{
+    if (!ctx || !out) return LBM_ERR_ARG;
+    AuxArgs x;
+    x.partials = ctx->at<double>(ctx->L.tpart);
+    x.nblocks = ctx->L.tot_blocks;
+    x.out = ctx->at<double>(ctx->L.tout);
+    launch_aux(ctx->p.storage, AUX_TOTALS, ctx->args(), ctx->t & 1, x, ctx->stream);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(out, x.out, 4 * sizeof(double), cudaMemcpyDefault, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return LBM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// checkpoints
+// ---------------------------------------------------------------------------
+namespace {
+struct CkptHeader {
+    char magic[8];
+    int32_t version, storage, nx, ny, nz, pad;
+    int64_t t, msamples, force_rows, n_edge, snap_count;
+};
+}  // namespace
+
+extern "C" lbm_status lbm_save(lbm_ctx *ctx, const char *path)
+{
+    if (!ctx || !path) return LBM_ERR_ARG;
+    lbm_status st = flush_forces(ctx);
+    if (st != LBM_OK) return st;
+    const Layout &L = ctx->L;
+    const size_t es = storage_bytes(ctx->p.storage);
+    const size_t pdf_bytes = (size_t)Q * L.slot * es;
+    const size_t ub_bytes = (size_t)3 * ctx->g.ny * ctx->g.nz * (ctx->p.storage == LBM_F64 ? 8 : 4);
+    const size_t ms_bytes = ctx->p.mean_every > 0 ? (size_t)4 * L.n * 8 : 0;
+    std::vector<char> buf(pdf_bytes + ub_bytes + ms_bytes);
+    CK(cudaStreamSynchronize(ctx->stream));
+    CK(cudaMemcpy(buf.data(), ctx->base + L.pdf, pdf_bytes, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(buf.data() + pdf_bytes, ctx->base + L.ub, ub_bytes, cudaMemcpyDeviceToHost));
+    if (ms_bytes) CK(cudaMemcpy(buf.data() + pdf_bytes + ub_bytes, ctx->base + L.msum, ms_bytes, cudaMemcpyDeviceToHost));
+    CkptHeader h{};
+    std::memcpy(h.magic, "GBLBMCK1", 8);
+    h.version = 1; h.storage = ctx->p.storage; h.nx = ctx->g.nx; h.ny = ctx->g.ny; h.nz = ctx->g.nz;
+    h.t = ctx->t; h.msamples = ctx->msamples; h.force_rows = (int64_t)ctx->force_host.size() / 3;
+    h.n_edge = ctx->n_edge; h.snap_count = ctx->p.snap_count;
+    FILE *fp = std::fopen(path, "wb");
+    if (!fp) return fail(ctx, LBM_ERR_IO, std::string("cannot open ") + path);
+    bool ok = std::fwrite(&h, sizeof(h), 1, fp) == 1;
+    ok = ok && std::fwrite(buf.data(), 1, buf.size(), fp) == buf.size();
+    if (h.force_rows) ok = ok && std::fwrite(ctx->force_host.data(), sizeof(double), ctx->force_host.size(), fp) == ctx->force_host.size();
+    if (h.snap_count) ok = ok && std::fwrite(ctx->snap_taken.data(), 1, ctx->snap_taken.size(), fp) == ctx->snap_taken.size();
+    ok = (std::fclose(fp) == 0) && ok;
+    return ok ? LBM_OK : fail(ctx, LBM_ERR_IO, "checkpoint write failed");
+}
+
+extern "C" lbm_status lbm_load(lbm_ctx *ctx, const char *path)
+{
+    if (!ctx || !path) return LBM_ERR_ARG;
+    FILE *fp = std::fopen(path, "rb");
+    if (!fp) return fail(ctx, LBM_ERR_IO, std::string("cannot open ") + path);
+    CkptHeader h{};
+    if (std::fread(&h, sizeof(h), 1, fp) != 1 || std::memcmp(h.magic, "GBLBMCK1", 8) != 0 ||
+        h.storage != ctx->p.storage || h.nx != ctx->g.nx || h.ny != ctx->g.ny || h.nz != ctx->g.nz ||
+        h.n_edge != ctx->n_edge || h.snap_count != ctx->p.snap_count) {
+        std::fclose(fp);
+        return fail(ctx, LBM_ERR_IO, "checkpoint does not match this context");
+    }
+    const Layout &L = ctx->L;
+    const size_t es = storage_bytes(ctx->p.storage);
+    const size_t pdf_bytes = (size_t)Q * L.slot * es;
+    const size_t ub_bytes = (size_t)3 * ctx->g.ny * ctx->g.nz * (ctx->p.storage == LBM_F64 ? 8 : 4);
+    const size_t ms_bytes = ctx->p.mean_every > 0 ? (size_t)4 * L.n * 8 : 0;
+    std::vector<char> buf(pdf_bytes + ub_bytes + ms_bytes);
+    std::vector<double> frows(3 * h.force_rows);
+    std::vector<char> taken(h.snap_count);
+    bool ok = std::fread(buf.data(), 1, buf.size(), fp) == buf.size();
+    if (h.force_rows) ok = ok && std::fread(frows.data(), sizeof(double), frows.size(), fp) == frows.size();
+    if (h.snap_count) ok = ok && std::fread(taken.data(), 1, taken.size(), fp) == taken.size();
+    std::fclose(fp);
+    if (!ok) return fail(ctx, LBM_ERR_IO, "checkpoint truncated");
+    CK(cudaStreamSynchronize(ctx->stream));
+    CK(cudaMemcpy(ctx->base + L.pdf, buf.data(), pdf_bytes, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->base + L.ub, buf.data() + pdf_bytes, ub_bytes, cudaMemcpyHostToDevice));
+    if (ms_bytes) CK(cudaMemcpy(ctx->base + L.msum, buf.data() + pdf_bytes + ub_bytes, ms_bytes, cudaMemcpyHostToDevice));
+    CK(cudaMemset(ctx->base + L.status, 0, sizeof(int)));
+    ctx->t = h.t;
+    ctx->msamples = h.msamples;
+    ctx->force_host = frows;
+    ctx->force_rows_dev = 0;
+    ctx->snap_taken = taken;
+    ctx->unstable = false;
+    return LBM_OK;
+}
+
+extern "C" const char *lbm_last_error(const lbm_ctx *ctx)
+{
+    return ctx ? ctx->err.c_str() : g_err.c_str();
+}
+
+extern "C" const char *lbm_status_string(lbm_status s)
+{
+    switch (s) {
+    case LBM_OK: return "ok";
+    case LBM_ERR_ARG: return "invalid argument";
+    case LBM_ERR_CUDA: return "CUDA error";
+    case LBM_ERR_OOM: return "out of device memory";
+    case LBM_ERR_UNSTABLE: return "unstable state";
+    case LBM_ERR_TIMEOUT: return "device wait timed out";
+    case LBM_ERR_STATE: return "invalid state for this call";
+    case LBM_ERR_IO: return "checkpoint I/O error";
+    }
+    return "unknown status";
+}

@@ -1,0 +1,290 @@
+// lbm_aux.cu -- set-up and read-out kernels around the step: cell flags,
+// seeded initial states, natural-order gathers of the AA state, macroscopic
+// fields, time-average read-out, half-resolution box means and deterministic
+// FP64 totals.
+#include "lbm_internal.h"
+
+namespace lbm {
+
+// ---------------------------------------------------------------------------
+// cell flags: solid, or edge (some neighbour outside the domain or solid)
+// ---------------------------------------------------------------------------
+__global__ void k_flags(const uint8_t *mask, uint8_t *flags, int nx, int ny, int nz)
+{
+    const int64_t n = (int64_t)nx * ny * nz;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x) {
+        const int x = (int)(c % nx), y = (int)((c / nx) % ny), z = (int)(c / ((int64_t)nx * ny));
+        if (mask && mask[c]) { flags[c] = CELL_SOLID; continue; }
+        uint8_t fl = 0;
+        if (x == 0 || y == 0 || z == 0 || x == nx - 1 || y == ny - 1 || z == nz - 1) {
+            fl = CELL_EDGE;
+        } else if (mask) {
+            for (int dz = -1; dz <= 1 && !fl; ++dz)
+                for (int dy = -1; dy <= 1 && !fl; ++dy)
+                    for (int dx = -1; dx <= 1; ++dx)
+                        if (mask[c + dx + (int64_t)nx * (dy + (int64_t)ny * dz)]) { fl = CELL_EDGE; break; }
+        }
+        flags[c] = fl;
+    }
+}
+
+void launch_flags(const uint8_t *mask, uint8_t *flags, int nx, int ny, int nz, cudaStream_t s)
+{
+    k_flags<<<1216, 256, 0, s>>>(mask, flags, nx, ny, nz);
+}
+
+// ---------------------------------------------------------------------------
+// SplitMix64 (Steele, Lea & Flood 2014; Vigna's reference constants):
+// output `ctr` of the stream started at `seed` is mix(seed + (ctr+1) golden).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t splitmix64(uint64_t seed, uint64_t ctr)
+{
+    uint64_t z = seed + (ctr + 1ull) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+template <class S>
+__global__ void k_noise(S *pdf, int64_t slot, const uint8_t *flags, int64_t n, uint64_t seed, double amp)
+{
+    using T = Store<S>;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x) {
+        const bool solid = flags[c] & CELL_SOLID;
+        for (int i = 0; i < Q; ++i) {
+            double v = 0.0;
+            if (!solid) {
+                const uint64_t z = splitmix64(seed, (uint64_t)c * Q + i);
+                const double u = (double)(z >> 11) * (1.0 / 9007199254740992.0);
+                v = amp * (2.0 * u - 1.0);
+            }
+            T::st(pdf + i * slot + c, (typename T::R)v);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// natural-order populations of the current state (FP64, shifted)
+// ---------------------------------------------------------------------------
+template <class S>
+__device__ __forceinline__ void gather_natural(const StepArgs &a, bool odd, int64_t c, double *f)
+{
+    using T = Store<S>;
+    using R = typename T::R;
+    const S *p = static_cast<const S *>(a.pdf);
+    if (!odd) {
+        for (int i = 0; i < Q; ++i) f[i] = (double)T::ld(p + (int64_t)i * a.slot + c);
+        return;
+    }
+    const int x = (int)(c % a.nx), y = (int)((c / a.nx) % a.ny), z = (int)(c / a.nxy);
+    const R *ub = static_cast<const R *>(a.ub);
+    const int64_t pl = 3 * ((int64_t)y + (int64_t)a.ny * z);
+    for (int i = 0; i < Q; ++i) {
+        int64_t nbr = 0;
+        const int kind = classify(a, x - cx_of(i), y - cy_of(i), z - cz_of(i), nbr);
+        if (kind == LINK_FLUID) {
+            f[i] = (double)T::ld(p + (int64_t)(Q - 1 - i) * a.slot + nbr);
+        } else {
+            const double own = (double)T::ld(p + (int64_t)i * a.slot + c);
+            if (kind == LINK_OUTLET)
+                f[i] = boundary_value<double>(a, kind, i, own, (double)ub[pl], (double)ub[pl + 1], (double)ub[pl + 2]);
+            else
+                f[i] = boundary_value<double>(a, kind, i, own, 0.0, 0.0, 0.0);
+        }
+    }
+}
+
+// out[i * si + k * sc] = w_i + fbar_i of cell cells[k] (or cell k when cells is null)
+template <class S>
+__global__ void k_gather(StepArgs a, bool odd, const int64_t *cells, int64_t count, double *out, int64_t si, int64_t sc)
+{
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < count; k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = cells ? cells[k] : k;
+        double f[Q];
+        if (c < 0 || c >= a.n) {            // out-of-range request: NaN, no access
+            for (int i = 0; i < Q; ++i) out[i * si + k * sc] = __longlong_as_double(0x7ff8000000000000ll);
+            continue;
+        }
+        if (a.flags[c] & CELL_SOLID) {
+            for (int i = 0; i < Q; ++i) f[i] = 0.0;
+        } else {
+            gather_natural<S>(a, odd, c, f);
+        }
+        for (int i = 0; i < Q; ++i) out[i * si + k * sc] = w_of(i) + f[i];
+    }
+}
+
+template <class S>
+__global__ void k_set(S *pdf, int64_t slot, const uint8_t *flags, int64_t n, const double *src)
+{
+    using T = Store<S>;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x) {
+        const bool solid = flags[c] & CELL_SOLID;
+        for (int i = 0; i < Q; ++i)
+            T::st(pdf + i * slot + c, (typename T::R)(solid ? 0.0 : src[i * n + c] - w_of(i)));
+    }
+}
+
+template <class S>
+__global__ void k_macros(StepArgs a, bool odd, double *rho, double *u)
+{
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < a.n; c += (int64_t)gridDim.x * blockDim.x) {
+        if (a.flags[c] & CELL_SOLID) {
+            rho[c] = 1.0;
+            u[3 * c] = u[3 * c + 1] = u[3 * c + 2] = 0.0;
+            continue;
+        }
+        double f[Q];
+        gather_natural<S>(a, odd, c, f);
+        double d = 0, jx = 0, jy = 0, jz = 0;
+        for (int i = 0; i < Q; ++i) {
+            d += f[i];
+            jx += cx_of(i) * f[i];
+            jy += cy_of(i) * f[i];
+            jz += cz_of(i) * f[i];
+        }
+        const double r = 1.0 + d;
+        rho[c] = r;
+        u[3 * c] = jx / r;
+        u[3 * c + 1] = jy / r;
+        u[3 * c + 2] = jz / r;
+    }
+}
+
+// Per-block partial totals (mass deviation, momentum) in fixed order; the
+// second kernel adds the partials in fixed order.
+constexpr int TOT_BLOCK = 256;
+
+template <class S>
+__global__ void __launch_bounds__(TOT_BLOCK) k_totals_partial(StepArgs a, bool odd, double *partials)
+{
+    __shared__ double sh[4][TOT_BLOCK];
+    double acc[4] = {0, 0, 0, 0};
+    for (int64_t c = (int64_t)blockIdx.x * TOT_BLOCK + threadIdx.x; c < a.n; c += (int64_t)gridDim.x * TOT_BLOCK) {
+        if (a.flags[c] & CELL_SOLID) continue;
+        double f[Q];
+        gather_natural<S>(a, odd, c, f);
+        for (int i = 0; i < Q; ++i) {
+            acc[0] += f[i];
+            acc[1] += cx_of(i) * f[i];
+            acc[2] += cy_of(i) * f[i];
+            acc[3] += cz_of(i) * f[i];
+        }
+    }
+    for (int d = 0; d < 4; ++d) sh[d][threadIdx.x] = acc[d];
+    __syncthreads();
+    for (int h = TOT_BLOCK / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h)
+            for (int d = 0; d < 4; ++d) sh[d][threadIdx.x] += sh[d][threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int d = 0; d < 4; ++d) partials[4 * (int64_t)blockIdx.x + d] = sh[d][0];
+}
+
+__global__ void __launch_bounds__(TOT_BLOCK) k_totals_final(const double *partials, int nblocks, double *out)
+{
+    __shared__ double sh[4][TOT_BLOCK];
+    double acc[4] = {0, 0, 0, 0};
+    for (int b = threadIdx.x; b < nblocks; b += TOT_BLOCK)
+        for (int d = 0; d < 4; ++d) acc[d] += partials[4 * (int64_t)b + d];
+    for (int d = 0; d < 4; ++d) sh[d][threadIdx.x] = acc[d];
+    __syncthreads();
+    for (int h = TOT_BLOCK / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h)
+            for (int d = 0; d < 4; ++d) sh[d][threadIdx.x] += sh[d][threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int d = 0; d < 4; ++d) out[d] = sh[d][0];
+}
+
+// ---------------------------------------------------------------------------
+// time average read-out: (ux, uy, uz, p) per cell from the FP64 sums
+// ---------------------------------------------------------------------------
+template <class T>
+__global__ void k_mean_out(const double *msum, int64_t n, double inv_samples, T *out)
+{
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x) {
+        out[4 * c + 0] = (T)(msum[n + c] * inv_samples);
+        out[4 * c + 1] = (T)(msum[2 * n + c] * inv_samples);
+        out[4 * c + 2] = (T)(msum[3 * n + c] * inv_samples);
+        out[4 * c + 3] = (T)(msum[c] * inv_samples * (1.0 / 3.0));
+    }
+}
+
+// 2x2x2 box mean of a [z][y][x][4] field; a trailing odd cell is a block of its own.
+template <class T>
+__global__ void k_halfres(const T *in, int nx, int ny, int nz, T *out)
+{
+    const int hx = (nx + 1) / 2, hy = (ny + 1) / 2, hz = (nz + 1) / 2;
+    const int64_t nh = (int64_t)hx * hy * hz;
+    for (int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; h < nh; h += (int64_t)gridDim.x * blockDim.x) {
+        const int X = (int)(h % hx), Y = (int)((h / hx) % hy), Z = (int)(h / ((int64_t)hx * hy));
+        double s[4] = {0, 0, 0, 0};
+        int cnt = 0;
+        for (int dz = 0; dz < 2; ++dz)
+            for (int dy = 0; dy < 2; ++dy)
+                for (int dx = 0; dx < 2; ++dx) {
+                    const int x = 2 * X + dx, y = 2 * Y + dy, z = 2 * Z + dz;
+                    if (x >= nx || y >= ny || z >= nz) continue;
+                    const int64_t c = x + (int64_t)nx * (y + (int64_t)ny * z);
+                    for (int d = 0; d < 4; ++d) s[d] += (double)in[4 * c + d];
+                    ++cnt;
+                }
+        for (int d = 0; d < 4; ++d) out[4 * h + d] = (T)(s[d] / cnt);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host launchers
+// ---------------------------------------------------------------------------
+static int grid_for(int64_t n, int block) { return (int)std::min<int64_t>((n + block - 1) / block, 152 * 32); }
+
+template <class S>
+static void launch_aux_t(AuxOp op, const StepArgs &a, bool odd, const AuxArgs &x, cudaStream_t s)
+{
+    switch (op) {
+    case AUX_NOISE:
+        k_noise<S><<<grid_for(a.n, 256), 256, 0, s>>>((S *)a.pdf, a.slot, a.flags, a.n, x.seed, x.amp);
+        break;
+    case AUX_GATHER:
+        k_gather<S><<<grid_for(x.count, 128), 128, 0, s>>>(a, odd, x.cells, x.count, x.out, x.si, x.sc);
+        break;
+    case AUX_SET:
+        k_set<S><<<grid_for(a.n, 256), 256, 0, s>>>((S *)a.pdf, a.slot, a.flags, a.n, x.src);
+        break;
+    case AUX_MACROS:
+        k_macros<S><<<grid_for(a.n, 128), 128, 0, s>>>(a, odd, x.out, x.out2);
+        break;
+    case AUX_TOTALS:
+        k_totals_partial<S><<<x.nblocks, TOT_BLOCK, 0, s>>>(a, odd, x.partials);
+        k_totals_final<<<1, TOT_BLOCK, 0, s>>>(x.partials, x.nblocks, x.out);
+        break;
+    }
+}
+
+void launch_aux(int storage, AuxOp op, const StepArgs &a, bool odd, const AuxArgs &x, cudaStream_t s)
+{
+    switch (storage) {
+    case 0: launch_aux_t<double>(op, a, odd, x, s); break;
+    case 1: launch_aux_t<float>(op, a, odd, x, s); break;
+    case 2: launch_aux_t<__half>(op, a, odd, x, s); break;
+    default: launch_aux_t<__nv_bfloat16>(op, a, odd, x, s); break;
+    }
+}
+
+void launch_mean_out(const double *msum, int64_t n, double inv_samples, bool f32, void *out, cudaStream_t s)
+{
+    if (f32) k_mean_out<float><<<grid_for(n, 256), 256, 0, s>>>(msum, n, inv_samples, (float *)out);
+    else k_mean_out<double><<<grid_for(n, 256), 256, 0, s>>>(msum, n, inv_samples, (double *)out);
+}
+
+void launch_halfres(const void *in, int nx, int ny, int nz, bool f32, void *out, cudaStream_t s)
+{
+    const int64_t nh = (int64_t)((nx + 1) / 2) * ((ny + 1) / 2) * ((nz + 1) / 2);
+    if (f32) k_halfres<float><<<grid_for(nh, 256), 256, 0, s>>>((const float *)in, nx, ny, nz, (float *)out);
+    else k_halfres<double><<<grid_for(nh, 256), 256, 0, s>>>((const double *)in, nx, ny, nz, (double *)out);
+}
+
+}  // namespace lbm

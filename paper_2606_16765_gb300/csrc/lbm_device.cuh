@@ -1,0 +1,385 @@
+// lbm_device.cuh -- device-side building blocks of the D3Q27 cumulant step:
+// storage traits, link classification, the shifted-form chimera transform
+// and the cumulant collision (Sec. 3.2 of the paper: D3Q27 stencil and
+// cumulant collision operator; relaxation after Geier et al. 2015, cited there).
+//
+// Populations are stored shifted, fbar_i = f_i - w_i, and every step of the
+// collision works on deviations from the rest state so that FP32 arithmetic
+// keeps the small hydrodynamic signal (|fbar| ~ 1e-2) instead of rounding it
+// against the O(1) weights.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbm {
+
+constexpr int Q = 27;
+// threads per block of the edge-cell kernel (also sizes the force partials)
+constexpr int EDGE_BLOCK = 128;
+
+// Velocity components of direction i = (cx+1) + 3(cy+1) + 9(cz+1).
+__host__ __device__ constexpr int cx_of(int i) { return i % 3 - 1; }
+__host__ __device__ constexpr int cy_of(int i) { return (i / 3) % 3 - 1; }
+__host__ __device__ constexpr int cz_of(int i) { return i / 9 - 1; }
+// 1-D weight factors t(c): 2/3 at rest, 1/6 for +-1; w_i = t(cx) t(cy) t(cz).
+__host__ __device__ constexpr double tw(int k) { return k == 1 ? 2.0 / 3.0 : 1.0 / 6.0; }
+__host__ __device__ constexpr double w_of(int i) { return tw(i % 3) * tw((i / 3) % 3) * tw(i / 9); }
+// Moments of t about the mean in one dimension: order 0 -> 1, 1 -> 0, 2 -> 1/3.
+__host__ __device__ constexpr double zw(int a) { return a == 0 ? 1.0 : (a == 1 ? 0.0 : 1.0 / 3.0); }
+
+// cell flag bits
+enum : uint8_t { CELL_SOLID = 1, CELL_EDGE = 2 };
+// face kinds (lbm_face)
+enum { FACE_WALL = 0, FACE_PERIODIC = 1, FACE_INLET = 2, FACE_OUTLET = 3 };
+// link kinds of the cell a population comes from (pull view)
+enum { LINK_FLUID = 0, LINK_WALL = 1, LINK_SOLID = 2, LINK_INLET = 3, LINK_OUTLET = 4 };
+// device status bits
+enum { STATUS_UNSTABLE = 1 };
+
+// ---------------------------------------------------------------------------
+// storage traits
+// ---------------------------------------------------------------------------
+template <class S> struct Store;
+template <> struct Store<double> {
+    using R = double;
+    static __device__ __forceinline__ double ld(const double *p) { return *p; }
+    static __device__ __forceinline__ void st(double *p, double v) { *p = v; }
+};
+template <> struct Store<float> {
+    using R = float;
+    static __device__ __forceinline__ float ld(const float *p) { return *p; }
+    static __device__ __forceinline__ void st(float *p, float v) { *p = v; }
+};
+template <> struct Store<__half> {
+    using R = float;
+    static __device__ __forceinline__ float ld(const __half *p) { return __half2float(*p); }
+    static __device__ __forceinline__ void st(__half *p, float v) { *p = __float2half_rn(v); }
+};
+template <> struct Store<__nv_bfloat16> {
+    using R = float;
+    static __device__ __forceinline__ float ld(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
+    static __device__ __forceinline__ void st(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
+};
+
+// ---------------------------------------------------------------------------
+// launch arguments shared by the step kernels (plain data, passed by value)
+// ---------------------------------------------------------------------------
+struct StepArgs {
+    void *pdf;              // 27 slots of `slot` elements each
+    int64_t slot;
+    const uint8_t *flags;   // per cell: CELL_SOLID / CELL_EDGE
+    const uint32_t *edge;   // edge-cell list
+    int64_t n_edge;
+    int nx, ny, nz;
+    int64_t nxy, n;
+    double w1, w2, w3;      // shear, bulk, higher-order rates
+    int galilean;
+    int face_x_lo, face_x_hi, face_y, face_z;
+    double u_in, rho_in, rho_out;
+    void *ub;               // outlet plane velocity [nz*ny][3] (compute type)
+    double *msum;           // mean sums [4][n] when this step is sampled, else null
+    float *snap;            // full-resolution float4 target when snapshotting, else null
+    double *fpart;          // force partials per edge block when recorded, else null
+    unsigned int *fcount;   // arrival counter of the last-block reduction
+    double *fout;           // force row of this step (3 doubles)
+    int *status;            // latched device conditions
+};
+
+// ---------------------------------------------------------------------------
+// link classification (Sec. 3.1: velocity inlet, outflow, no-slip lateral
+// walls; obstacle cells bounce back).  A link that leaves through y or z is a
+// wall link even when it also crosses x; then x; then obstacle cells.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int classify(const StepArgs &a, int sx, int sy, int sz, int64_t &nbr)
+{
+    if (sy < 0 || sy >= a.ny) {
+        if (a.face_y != FACE_PERIODIC) return LINK_WALL;
+        sy = sy < 0 ? sy + a.ny : sy - a.ny;
+    }
+    if (sz < 0 || sz >= a.nz) {
+        if (a.face_z != FACE_PERIODIC) return LINK_WALL;
+        sz = sz < 0 ? sz + a.nz : sz - a.nz;
+    }
+    if (sx < 0) {
+        if (a.face_x_lo == FACE_INLET) return LINK_INLET;
+        if (a.face_x_lo == FACE_WALL) return LINK_WALL;
+        sx += a.nx;
+    } else if (sx >= a.nx) {
+        if (a.face_x_hi == FACE_OUTLET) return LINK_OUTLET;
+        if (a.face_x_hi == FACE_WALL) return LINK_WALL;
+        sx -= a.nx;
+    }
+    nbr = (int64_t)sx + (int64_t)a.nx * ((int64_t)sy + (int64_t)a.ny * sz);
+    return (a.flags[nbr] & CELL_SOLID) ? LINK_SOLID : LINK_FLUID;
+}
+
+// Shifted value delivered through a boundary link into direction i of a cell
+// whose own slot holds `own` (the post-collision population of the opposite
+// direction).  Halfway bounce-back for walls and obstacles, bounce-back from
+// a wall moving with (u_in, 0, 0) at the inlet, anti-bounce-back against the
+// even part of the equilibrium at rho_out with velocity ub at the outlet.
+template <class R>
+__device__ __forceinline__ R boundary_value(const StepArgs &a, int kind, int i, R own, R ubx, R uby, R ubz)
+{
+    const R w = R(w_of(i));
+    if (kind == LINK_INLET) return own + R(6) * w * R(a.rho_in) * (R(cx_of(i)) * R(a.u_in));
+    if (kind == LINK_OUTLET) {
+        const R cu = R(cx_of(i)) * ubx + R(cy_of(i)) * uby + R(cz_of(i)) * ubz;
+        const R uu = ubx * ubx + uby * uby + ubz * ubz;
+        // shifted form: -(own + w) + 2 w rho_out (1 + 4.5 cu^2 - 1.5 uu) - w
+        return -own + R(2) * w * (R(a.rho_out) * (R(1) + R(4.5) * cu * cu - R(1.5) * uu) - R(1));
+    }
+    return own;
+}
+
+// ---------------------------------------------------------------------------
+// chimera line transforms in shifted form.  A line holds (f-, f0, f+) whose
+// rest values are (K/6, 2K/3, K/6); the outputs are the zeroth moment minus K,
+// the first central moment, and the second central moment minus K/3.
+// ---------------------------------------------------------------------------
+template <class R>
+__device__ __forceinline__ void fwd_line(R &a, R &b, R &c, R u, R K)
+{
+    const R s = c + a, d = c - a;
+    const R m0 = s + b;
+    const R mk = m0 + K;
+    const R m1 = d - u * mk;
+    const R m2 = s - R(2) * u * d + u * u * mk;
+    a = m0;
+    b = m1;
+    c = m2;
+}
+
+template <class R>
+__device__ __forceinline__ void inv_line(R &a, R &b, R &c, R u, R K)
+{
+    const R m0 = a, m1 = b, m2 = c;
+    const R M0 = m0 + K;
+    const R uu = u * u;
+    b = m0 - M0 * uu - m2 - R(2) * u * m1;
+    a = R(0.5) * ((uu - u) * M0 + (R(2) * u - R(1)) * m1 + m2);
+    c = R(0.5) * ((uu + u) * M0 + (R(2) * u + R(1)) * m1 + m2);
+}
+
+#define MI(a, b, c) ((a) + 3 * (b) + 9 * (c))
+
+// Forward chimera: populations (index (cx+1)+3(cy+1)+9(cz+1)) -> central
+// moment deviations m[a + 3b + 9c] = kappa_abc - zw(a) zw(b) zw(c).
+template <class R>
+__device__ __forceinline__ void chimera_forward(R *f, R ux, R uy, R uz)
+{
+#pragma unroll
+    for (int yi = 0; yi < 3; ++yi)
+#pragma unroll
+        for (int xi = 0; xi < 3; ++xi)
+            fwd_line<R>(f[xi + 3 * yi], f[xi + 3 * yi + 9], f[xi + 3 * yi + 18], uz, R(tw(xi) * tw(yi)));
+#pragma unroll
+    for (int az = 0; az < 3; ++az)
+#pragma unroll
+        for (int xi = 0; xi < 3; ++xi)
+            fwd_line<R>(f[xi + 9 * az], f[xi + 3 + 9 * az], f[xi + 6 + 9 * az], uy, R(tw(xi) * zw(az)));
+#pragma unroll
+    for (int az = 0; az < 3; ++az)
+#pragma unroll
+        for (int ay = 0; ay < 3; ++ay)
+            fwd_line<R>(f[3 * ay + 9 * az], f[1 + 3 * ay + 9 * az], f[2 + 3 * ay + 9 * az], ux, R(zw(ay) * zw(az)));
+}
+
+template <class R>
+__device__ __forceinline__ void chimera_inverse(R *f, R ux, R uy, R uz)
+{
+#pragma unroll
+    for (int az = 0; az < 3; ++az)
+#pragma unroll
+        for (int ay = 0; ay < 3; ++ay)
+            inv_line<R>(f[3 * ay + 9 * az], f[1 + 3 * ay + 9 * az], f[2 + 3 * ay + 9 * az], ux, R(zw(ay) * zw(az)));
+#pragma unroll
+    for (int az = 0; az < 3; ++az)
+#pragma unroll
+        for (int xi = 0; xi < 3; ++xi)
+            inv_line<R>(f[xi + 9 * az], f[xi + 3 + 9 * az], f[xi + 6 + 9 * az], uy, R(tw(xi) * zw(az)));
+#pragma unroll
+    for (int yi = 0; yi < 3; ++yi)
+#pragma unroll
+        for (int xi = 0; xi < 3; ++xi)
+            inv_line<R>(f[xi + 3 * yi], f[xi + 3 * yi + 9], f[xi + 3 * yi + 18], uz, R(tw(xi) * tw(yi)));
+}
+
+struct Rates {
+    double w1, w2, w3;
+    int galilean;
+};
+
+// Cumulant collision of one cell, in place on the shifted populations f[27].
+// Returns the pre-collision density deviation and velocity.
+// PLAIN: every cumulant of order >= 3 relaxes to zero (omega_higher = 1).
+template <class R, bool PLAIN>
+__device__ __forceinline__ void collide(R *f, const Rates &rt, R &drho_out, R &ux, R &uy, R &uz)
+{
+    // macroscopic quantities (the weights carry no mass flux)
+    R drho = R(0), jx = R(0), jy = R(0), jz = R(0);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        drho += f[i];
+        if (cx_of(i) == 1) jx += f[i];
+        if (cx_of(i) == -1) jx -= f[i];
+        if (cy_of(i) == 1) jy += f[i];
+        if (cy_of(i) == -1) jy -= f[i];
+        if (cz_of(i) == 1) jz += f[i];
+        if (cz_of(i) == -1) jz -= f[i];
+    }
+    const R rho = R(1) + drho;
+    const R ir = R(1) / rho;
+    ux = jx * ir;
+    uy = jy * ir;
+    uz = jz * ir;
+    drho_out = drho;
+
+    chimera_forward<R>(f, ux, uy, uz);
+    R *m = f;
+    const R third = R(1.0 / 3.0), ninth = R(1.0 / 9.0), t27 = R(1.0 / 27.0);
+
+    // second order: normalised deviations from the rest values (1/3 on the diagonal)
+    const R d200 = (m[MI(2, 0, 0)] - drho * third) * ir;
+    const R d020 = (m[MI(0, 2, 0)] - drho * third) * ir;
+    const R d002 = (m[MI(0, 0, 2)] - drho * third) * ir;
+    const R k110 = m[MI(1, 1, 0)] * ir, k101 = m[MI(1, 0, 1)] * ir, k011 = m[MI(0, 1, 1)] * ir;
+
+    // relaxation of second order (shear rate on deviators and off-diagonals,
+    // bulk rate on the trace), with the Galilean correction built from the
+    // velocity-derivative estimates implied by the non-equilibrium moments
+    const R w1 = R(rt.w1), w2 = R(rt.w2);
+    const R Dxy = d200 - d020, Dxz = d200 - d002, dTr = d200 + d020 + d002;
+    const R dxu = -R(0.5) * w1 * (R(2) * d200 - d020 - d002) - R(0.5) * w2 * dTr;
+    const R dyv = dxu + R(1.5) * w1 * Dxy;
+    const R dzw = dxu + R(1.5) * w1 * Dxz;
+    const R g = rt.galilean ? R(1) : R(0);
+    const R ux2 = ux * ux, uy2 = uy * uy, uz2 = uz * uz;
+    const R Dxy_s = (R(1) - w1) * Dxy - g * R(3) * (R(1) - R(0.5) * w1) * (ux2 * dxu - uy2 * dyv);
+    const R Dxz_s = (R(1) - w1) * Dxz - g * R(3) * (R(1) - R(0.5) * w1) * (ux2 * dxu - uz2 * dzw);
+    const R dTr_s = (R(1) - w2) * dTr - g * R(3) * (R(1) - R(0.5) * w2) * (ux2 * dxu + uy2 * dyv + uz2 * dzw);
+    const R s200 = (Dxy_s + Dxz_s + dTr_s) * third;
+    const R s020 = s200 - Dxy_s;
+    const R s002 = s200 - Dxz_s;
+    const R s110 = (R(1) - w1) * k110, s101 = (R(1) - w1) * k101, s011 = (R(1) - w1) * k011;
+
+    // post-collision central moments of orders 3..6 (normalised)
+    R s111, s210, s201, s120, s021, s102, s012;   // third
+    R s211, s121, s112, e220s, e202s, e022s;      // fourth (e = deviation from 1/9)
+    R s122, s212, s221, e222s;                    // fifth, sixth (e = deviation from 1/27)
+    if (PLAIN) {
+        s111 = s210 = s201 = s120 = s021 = s102 = s012 = R(0);
+        s211 = (third + s200) * s011 + R(2) * s110 * s101;
+        s121 = (third + s020) * s101 + R(2) * s110 * s011;
+        s112 = (third + s002) * s110 + R(2) * s101 * s011;
+        e220s = (s200 + s020) * third + s200 * s020 + R(2) * s110 * s110;
+        e202s = (s200 + s002) * third + s200 * s002 + R(2) * s101 * s101;
+        e022s = (s020 + s002) * third + s020 * s002 + R(2) * s011 * s011;
+        s122 = s212 = s221 = R(0);
+        e222s = R(0);
+    } else {
+        const R w3 = R(rt.w3), r3 = R(1) - w3;
+        // third order: cumulants equal central moments
+        const R k111 = m[MI(1, 1, 1)] * ir;
+        const R k210 = m[MI(2, 1, 0)] * ir, k201 = m[MI(2, 0, 1)] * ir, k120 = m[MI(1, 2, 0)] * ir;
+        const R k021 = m[MI(0, 2, 1)] * ir, k102 = m[MI(1, 0, 2)] * ir, k012 = m[MI(0, 1, 2)] * ir;
+        // fourth
+        const R k211 = m[MI(2, 1, 1)] * ir, k121 = m[MI(1, 2, 1)] * ir, k112 = m[MI(1, 1, 2)] * ir;
+        const R e220 = (m[MI(2, 2, 0)] - drho * ninth) * ir;
+        const R e202 = (m[MI(2, 0, 2)] - drho * ninth) * ir;
+        const R e022 = (m[MI(0, 2, 2)] - drho * ninth) * ir;
+        // fifth, sixth
+        const R k122 = m[MI(1, 2, 2)] * ir, k212 = m[MI(2, 1, 2)] * ir, k221 = m[MI(2, 2, 1)] * ir;
+        const R e222 = (m[MI(2, 2, 2)] - drho * t27) * ir;
+
+        // cumulants of order 4..6 (zero-mean moment->cumulant relations, written
+        // on deviations so that the constant parts cancel exactly)
+        const R C211 = k211 - ((third + d200) * k011 + R(2) * k110 * k101);
+        const R C121 = k121 - ((third + d020) * k101 + R(2) * k110 * k011);
+        const R C112 = k112 - ((third + d002) * k110 + R(2) * k101 * k011);
+        const R C220 = e220 - ((d200 + d020) * third + d200 * d020 + R(2) * k110 * k110);
+        const R C202 = e202 - ((d200 + d002) * third + d200 * d002 + R(2) * k101 * k101);
+        const R C022 = e022 - ((d020 + d002) * third + d020 * d002 + R(2) * k011 * k011);
+        const R C122 = k122 - ((third + d002) * k120 + (third + d020) * k102 + R(4) * k011 * k111
+                               + R(2) * (k101 * k021 + k110 * k012));
+        const R C212 = k212 - ((third + d200) * k012 + (third + d002) * k210 + R(4) * k101 * k111
+                               + R(2) * (k110 * k102 + k011 * k201));
+        const R C221 = k221 - ((third + d200) * k021 + (third + d020) * k201 + R(4) * k110 * k111
+                               + R(2) * (k101 * k120 + k011 * k210));
+        const R S42 = (d200 + d020 + d002) * ninth + (e022 + e202 + e220) * third
+                    + d200 * e022 + d020 * e202 + d002 * e220
+                    + R(4) * (k011 * k211 + k101 * k121 + k110 * k112);
+        const R S33 = R(4) * k111 * k111 + R(2) * (k120 * k102 + k210 * k012 + k201 * k021);
+        const R S222 = R(8) * k110 * k101 * k011
+                     + R(2) * (k101 * k101 * (third + d020) + k011 * k011 * (third + d200)
+                               + k110 * k110 * (third + d002))
+                     + (d200 + d020 + d002) * ninth + (d200 * d020 + d200 * d002 + d020 * d002) * third
+                     + d200 * d020 * d002;
+        const R C222 = e222 - S42 - S33 + R(2) * S222;
+
+        // relax every cumulant of order 3..6 with omega_higher, then rebuild
+        // central moments order by order from the post-collision lower orders
+        s111 = r3 * k111;
+        s210 = r3 * k210; s201 = r3 * k201; s120 = r3 * k120;
+        s021 = r3 * k021; s102 = r3 * k102; s012 = r3 * k012;
+        s211 = r3 * C211 + (third + s200) * s011 + R(2) * s110 * s101;
+        s121 = r3 * C121 + (third + s020) * s101 + R(2) * s110 * s011;
+        s112 = r3 * C112 + (third + s002) * s110 + R(2) * s101 * s011;
+        e220s = r3 * C220 + (s200 + s020) * third + s200 * s020 + R(2) * s110 * s110;
+        e202s = r3 * C202 + (s200 + s002) * third + s200 * s002 + R(2) * s101 * s101;
+        e022s = r3 * C022 + (s020 + s002) * third + s020 * s002 + R(2) * s011 * s011;
+        s122 = r3 * C122 + (third + s002) * s120 + (third + s020) * s102 + R(4) * s011 * s111
+             + R(2) * (s101 * s021 + s110 * s012);
+        s212 = r3 * C212 + (third + s200) * s012 + (third + s002) * s210 + R(4) * s101 * s111
+             + R(2) * (s110 * s102 + s011 * s201);
+        s221 = r3 * C221 + (third + s200) * s021 + (third + s020) * s201 + R(4) * s110 * s111
+             + R(2) * (s101 * s120 + s011 * s210);
+        e222s = r3 * C222;   // plus the product terms added below
+    }
+    {
+        // sixth order: add sum(4,2) + sum(3,3) - 2 sum(2,2,2) of post-collision moments
+        const R S42s = (s200 + s020 + s002) * ninth + (e022s + e202s + e220s) * third
+                     + s200 * e022s + s020 * e202s + s002 * e220s
+                     + R(4) * (s011 * s211 + s101 * s121 + s110 * s112);
+        const R S33s = R(4) * s111 * s111 + R(2) * (s120 * s102 + s210 * s012 + s201 * s021);
+        const R S222s = R(8) * s110 * s101 * s011
+                      + R(2) * (s101 * s101 * (third + s020) + s011 * s011 * (third + s200)
+                                + s110 * s110 * (third + s002))
+                      + (s200 + s020 + s002) * ninth + (s200 * s020 + s200 * s002 + s020 * s002) * third
+                      + s200 * s020 * s002;
+        e222s += S42s + S33s - R(2) * S222s;
+    }
+
+    // back to non-normalised central moment deviations
+    m[MI(0, 0, 0)] = drho;
+    m[MI(1, 0, 0)] = R(0); m[MI(0, 1, 0)] = R(0); m[MI(0, 0, 1)] = R(0);
+    m[MI(2, 0, 0)] = rho * s200 + drho * third;
+    m[MI(0, 2, 0)] = rho * s020 + drho * third;
+    m[MI(0, 0, 2)] = rho * s002 + drho * third;
+    m[MI(1, 1, 0)] = rho * s110; m[MI(1, 0, 1)] = rho * s101; m[MI(0, 1, 1)] = rho * s011;
+    m[MI(1, 1, 1)] = rho * s111;
+    m[MI(2, 1, 0)] = rho * s210; m[MI(2, 0, 1)] = rho * s201; m[MI(1, 2, 0)] = rho * s120;
+    m[MI(0, 2, 1)] = rho * s021; m[MI(1, 0, 2)] = rho * s102; m[MI(0, 1, 2)] = rho * s012;
+    m[MI(2, 1, 1)] = rho * s211; m[MI(1, 2, 1)] = rho * s121; m[MI(1, 1, 2)] = rho * s112;
+    m[MI(2, 2, 0)] = rho * e220s + drho * ninth;
+    m[MI(2, 0, 2)] = rho * e202s + drho * ninth;
+    m[MI(0, 2, 2)] = rho * e022s + drho * ninth;
+    m[MI(1, 2, 2)] = rho * s122; m[MI(2, 1, 2)] = rho * s212; m[MI(2, 2, 1)] = rho * s221;
+    m[MI(2, 2, 2)] = rho * e222s + drho * t27;
+
+    chimera_inverse<R>(f, ux, uy, uz);
+}
+
+#undef MI
+
+// Latch instability: density outside (0.5, 1.5) or not a number.
+template <class R>
+__device__ __forceinline__ void check_density(R drho, int *status)
+{
+    if (!(drho > R(-0.5) && drho < R(0.5))) atomicOr(status, STATUS_UNSTABLE);
+}
+
+}  // namespace lbm

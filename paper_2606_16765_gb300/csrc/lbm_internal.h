@@ -1,0 +1,37 @@
+// lbm_internal.h -- declarations shared by the translation units of the
+// library (kernel launchers and the auxiliary-operation argument block).
+#pragma once
+
+#include <algorithm>
+#include <cstdint>
+
+#include "lbm_device.cuh"
+
+namespace lbm {
+
+// fused step (bulk + edge kernels) for one storage type
+void launch_step_f64(const StepArgs &a, bool odd, bool epi, bool plain, int block_x, cudaStream_t s);
+void launch_step_f32(const StepArgs &a, bool odd, bool epi, bool plain, int block_x, cudaStream_t s);
+void launch_step_f16(const StepArgs &a, bool odd, bool epi, bool plain, int block_x, cudaStream_t s);
+void launch_step_bf16(const StepArgs &a, bool odd, bool epi, bool plain, int block_x, cudaStream_t s);
+
+enum AuxOp { AUX_NOISE, AUX_GATHER, AUX_SET, AUX_MACROS, AUX_TOTALS };
+
+struct AuxArgs {
+    uint64_t seed = 0;
+    double amp = 0;
+    const int64_t *cells = nullptr;
+    int64_t count = 0;
+    double *out = nullptr, *out2 = nullptr;
+    int64_t si = 0, sc = 0;
+    const double *src = nullptr;
+    double *partials = nullptr;
+    int nblocks = 0;
+};
+
+void launch_flags(const uint8_t *mask, uint8_t *flags, int nx, int ny, int nz, cudaStream_t s);
+void launch_aux(int storage, AuxOp op, const StepArgs &a, bool odd, const AuxArgs &x, cudaStream_t s);
+void launch_mean_out(const double *msum, int64_t n, double inv_samples, bool f32, void *out, cudaStream_t s);
+void launch_halfres(const void *in, int nx, int ny, int nz, bool f32, void *out, cudaStream_t s);
+
+}  // namespace lbm

@@ -1,0 +1,11 @@
+// lbm_step_bf16.cu -- step kernels instantiated for __nv_bfloat16 storage of the shifted
+// populations (one translation unit per storage type for parallel builds).
+#include "lbm_internal.h"
+#include "lbm_step.cuh"
+
+namespace lbm {
+void launch_step_bf16(const StepArgs &a, bool odd, bool epi, bool plain, int block_x, cudaStream_t s)
+{
+    launch_step_t<__nv_bfloat16>(a, odd, epi, plain, block_x, s);
+}
+}  // namespace lbm

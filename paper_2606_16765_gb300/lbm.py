@@ -1,0 +1,315 @@
+"""Python binding of the C ABI in include/lbm.h (argument marshalling only).
+
+Every step of the lattice Boltzmann path runs in the CUDA library
+``lib/liblbm.so``; this module only converts arguments.  PyTorch supplies the
+device memory (the context's workspace is a torch tensor) and the stream (the
+current torch stream).  If the library is missing the import of the binding
+fails; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "lib", "liblbm.so")
+
+LBM_OK, LBM_ERR_ARG, LBM_ERR_CUDA, LBM_ERR_OOM, LBM_ERR_UNSTABLE, LBM_ERR_TIMEOUT, LBM_ERR_STATE, LBM_ERR_IO = range(8)
+LBM_F64, LBM_F32, LBM_F16S, LBM_BF16S = range(4)
+LBM_FACE_WALL, LBM_FACE_PERIODIC, LBM_FACE_INLET, LBM_FACE_OUTLET = range(4)
+STORAGE = {"f64": LBM_F64, "f32": LBM_F32, "f16s": LBM_F16S, "bf16s": LBM_BF16S}
+FACES = {"wall": LBM_FACE_WALL, "periodic": LBM_FACE_PERIODIC, "inlet": LBM_FACE_INLET, "outlet": LBM_FACE_OUTLET}
+
+
+class lbm_grid(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32)]
+
+
+class lbm_params(C.Structure):
+    _fields_ = [
+        ("re", C.c_double), ("u_in", C.c_double), ("l_ref", C.c_double),
+        ("omega1", C.c_double), ("omega_bulk", C.c_double), ("omega_higher", C.c_double),
+        ("rho_in", C.c_double), ("rho_out", C.c_double),
+        ("storage", C.c_int32), ("galilean_correction", C.c_int32),
+        ("face_x_lo", C.c_int32), ("face_x_hi", C.c_int32), ("face_y", C.c_int32), ("face_z", C.c_int32),
+        ("mean_start", C.c_int64), ("mean_end", C.c_int64), ("mean_every", C.c_int64),
+        ("snap_first", C.c_int64), ("snap_every", C.c_int64), ("snap_count", C.c_int64),
+        ("snap_halfres", C.c_int32), ("force_every", C.c_int32),
+        ("force_capacity", C.c_int64),
+        ("block_x", C.c_int32), ("reserved", C.c_int32 * 7),
+    ]
+
+
+class LBMError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+_lib = None
+
+_vp, _dp, _i64 = C.c_void_p, C.POINTER(C.c_double), C.c_int64
+
+
+def lib():
+    """Load liblbm.so (raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_LIB_PATH):
+            raise ImportError(f"CUDA library not built: {_LIB_PATH} (run __graft_entry__.build())")
+        L = C.CDLL(_LIB_PATH)
+        G, P = C.POINTER(lbm_grid), C.POINTER(lbm_params)
+        sig = {
+            "lbm_params_default": (None, [P]),
+            "lbm_workspace_bytes": (C.c_size_t, [G, P]),
+            "lbm_create": (C.c_int, [G, _vp, P, _vp, C.POINTER(_vp)]),
+            "lbm_create_in": (C.c_int, [G, _vp, P, _vp, _vp, C.c_size_t, C.POINTER(_vp)]),
+            "lbm_destroy": (C.c_int, [_vp]),
+            "lbm_step": (C.c_int, [_vp, _i64]),
+            "lbm_sync": (C.c_int, [_vp]),
+            "lbm_time": (_i64, [_vp]),
+            "lbm_read_mean": (C.c_int, [_vp, C.c_int32, C.c_int32, _vp, C.POINTER(_i64)]),
+            "lbm_read_snapshot": (C.c_int, [_vp, C.c_int32, _vp]),
+            "lbm_read_macros": (C.c_int, [_vp, _vp, _vp]),
+            "lbm_read_forces": (C.c_int, [_vp, _vp, _i64, C.POINTER(_i64)]),
+            "lbm_get_pdfs": (C.c_int, [_vp, _vp]),
+            "lbm_set_pdfs": (C.c_int, [_vp, _vp]),
+            "lbm_get_cells": (C.c_int, [_vp, _i64, _vp, _vp]),
+            "lbm_init_noise": (C.c_int, [_vp, C.c_uint64, C.c_double]),
+            "lbm_totals": (C.c_int, [_vp, _vp]),
+            "lbm_save": (C.c_int, [_vp, C.c_char_p]),
+            "lbm_load": (C.c_int, [_vp, C.c_char_p]),
+            "lbm_last_error": (C.c_char_p, [_vp]),
+            "lbm_status_string": (C.c_char_p, [C.c_int]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(status, ctx=None):
+    if status != LBM_OK:
+        msg = lib().lbm_last_error(ctx).decode() if ctx is not None or status else ""
+        raise LBMError(status, msg or lib().lbm_status_string(status).decode())
+
+
+def _ptr(a):
+    """Raw pointer of a numpy array or a torch tensor (host or device)."""
+    if hasattr(a, "data_ptr"):
+        return C.c_void_p(a.data_ptr())
+    return C.c_void_p(a.ctypes.data)
+
+
+# ---------------------------------------------------------------------------
+# functions with the C names
+# ---------------------------------------------------------------------------
+def lbm_params_default() -> lbm_params:
+    p = lbm_params()
+    lib().lbm_params_default(C.byref(p))
+    return p
+
+
+def lbm_workspace_bytes(grid: lbm_grid, p: lbm_params) -> int:
+    return int(lib().lbm_workspace_bytes(C.byref(grid), C.byref(p)))
+
+
+def lbm_create(grid, mask, p, stream=None):
+    h = C.c_void_p()
+    st = lib().lbm_create(C.byref(grid), _ptr(mask) if mask is not None else None, C.byref(p),
+                          C.c_void_p(stream or 0), C.byref(h))
+    _check(st, None)
+    return h
+
+
+def lbm_create_in(grid, mask, p, stream, workspace, nbytes):
+    h = C.c_void_p()
+    st = lib().lbm_create_in(C.byref(grid), _ptr(mask) if mask is not None else None, C.byref(p),
+                             C.c_void_p(stream or 0), _ptr(workspace), nbytes, C.byref(h))
+    _check(st, None)
+    return h
+
+
+def lbm_destroy(h):
+    _check(lib().lbm_destroy(h), None)
+
+
+def lbm_step(h, n):
+    _check(lib().lbm_step(h, int(n)), h)
+
+
+def lbm_sync(h):
+    _check(lib().lbm_sync(h), h)
+
+
+def lbm_time(h):
+    return int(lib().lbm_time(h))
+
+
+def lbm_read_mean(h, dst, dtype, halfres):
+    s = C.c_int64()
+    _check(lib().lbm_read_mean(h, int(dtype), int(halfres), _ptr(dst), C.byref(s)), h)
+    return s.value
+
+
+def lbm_read_snapshot(h, k, dst):
+    _check(lib().lbm_read_snapshot(h, int(k), _ptr(dst)), h)
+
+
+def lbm_read_macros(h, rho, u):
+    _check(lib().lbm_read_macros(h, _ptr(rho), _ptr(u)), h)
+
+
+def lbm_read_forces(h, dst, max_rows):
+    n = C.c_int64()
+    _check(lib().lbm_read_forces(h, _ptr(dst) if dst is not None else None, int(max_rows), C.byref(n)), h)
+    return n.value
+
+
+def lbm_get_pdfs(h, dst):
+    _check(lib().lbm_get_pdfs(h, _ptr(dst)), h)
+
+
+def lbm_set_pdfs(h, src):
+    _check(lib().lbm_set_pdfs(h, _ptr(src)), h)
+
+
+def lbm_get_cells(h, cells, dst):
+    _check(lib().lbm_get_cells(h, len(cells), _ptr(cells), _ptr(dst)), h)
+
+
+def lbm_init_noise(h, seed, amplitude):
+    _check(lib().lbm_init_noise(h, C.c_uint64(seed), float(amplitude)), h)
+
+
+def lbm_totals(h, out):
+    _check(lib().lbm_totals(h, _ptr(out)), h)
+
+
+def lbm_save(h, path):
+    _check(lib().lbm_save(h, os.fsencode(path)), h)
+
+
+def lbm_load(h, path):
+    _check(lib().lbm_load(h, os.fsencode(path)), h)
+
+
+# ---------------------------------------------------------------------------
+# convenience wrapper: torch workspace + current torch stream
+# ---------------------------------------------------------------------------
+def make_params(**kw) -> lbm_params:
+    p = lbm_params_default()
+    faces = kw.pop("faces", None)
+    if faces is not None:
+        p.face_x_lo, p.face_x_hi, p.face_y, p.face_z = (FACES[f] for f in faces)
+    st = kw.pop("storage", None)
+    if st is not None:
+        p.storage = STORAGE[st] if isinstance(st, str) else int(st)
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+class Solver:
+    """One channel-flow lattice on the current CUDA device.
+
+    grid = (nx, ny, nz); mask: uint8 [nz, ny, nx] (1 = solid) or None;
+    keyword arguments set lbm_params fields (storage='f32', faces=(...), ...).
+    """
+
+    def __init__(self, grid, mask=None, **params):
+        import torch
+
+        self.grid = lbm_grid(*grid)
+        self.p = make_params(**params)
+        self.shape = (grid[2], grid[1], grid[0])
+        self.n = int(np.prod(grid))
+        self._torch = torch
+        nbytes = lbm_workspace_bytes(self.grid, self.p)
+        if nbytes == 0:
+            raise LBMError(LBM_ERR_ARG, "invalid grid or parameters")
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        self.stream = torch.cuda.current_stream()
+        m = None
+        if mask is not None:
+            m = np.ascontiguousarray(mask, dtype=np.uint8)
+            assert m.shape == self.shape, (m.shape, self.shape)
+        self._mask = m
+        self.h = lbm_create_in(self.grid, m, self.p, self.stream.cuda_stream, self.workspace, nbytes)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lbm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def t(self):
+        return lbm_time(self.h)
+
+    def step(self, n=1):
+        lbm_step(self.h, n)
+
+    def sync(self):
+        lbm_sync(self.h)
+
+    def pdfs(self):
+        out = np.zeros((27,) + self.shape)
+        lbm_get_pdfs(self.h, out)
+        return out
+
+    def set_pdfs(self, f):
+        lbm_set_pdfs(self.h, np.ascontiguousarray(f, dtype=np.float64))
+
+    def cells(self, idx):
+        idx = np.ascontiguousarray(idx, dtype=np.int64)
+        out = np.zeros((len(idx), 27))
+        lbm_get_cells(self.h, idx, out)
+        return out
+
+    def macros(self):
+        rho = np.zeros(self.shape)
+        u = np.zeros(self.shape + (3,))
+        lbm_read_macros(self.h, rho, u)
+        return rho, u
+
+    def mean(self, halfres=False, dtype=np.float64):
+        shape = tuple((s + 1) // 2 for s in self.shape) if halfres else self.shape
+        out = np.zeros(shape + (4,), dtype=dtype)
+        s = lbm_read_mean(self.h, out, 1 if dtype == np.float32 else 0, halfres)
+        return out, s
+
+    def snapshot(self, k):
+        shape = tuple((s + 1) // 2 for s in self.shape) if self.p.snap_halfres else self.shape
+        out = np.zeros(shape + (4,), dtype=np.float32)
+        lbm_read_snapshot(self.h, k, out)
+        return out
+
+    def forces(self):
+        n = lbm_read_forces(self.h, None, 0)
+        out = np.zeros((n, 3))
+        if n:
+            lbm_read_forces(self.h, out, n)
+        return out
+
+    def init_noise(self, seed, amplitude):
+        lbm_init_noise(self.h, seed, amplitude)
+
+    def totals(self):
+        out = np.zeros(4)
+        lbm_totals(self.h, out)
+        return out
+
+    def save(self, path):
+        lbm_save(self.h, path)
+
+    def load(self, path):
+        lbm_load(self.h, path)

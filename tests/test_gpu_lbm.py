@@ -1,0 +1,308 @@
+"""GPU parity of the CUDA D3Q27 cumulant step against the FP64 oracle.
+
+Every case runs the same seeded inputs through the C ABI (via the thin
+binding) and through the oracle, and compares element by element:
+  FP64 pdfs   <= 1e-12 (max relative velocity error, density error),
+  FP32 pdfs   <= 1e-5  (sphere channel, 200 steps from rest),
+  FP16S pdfs  <= 1e-3,
+on the 64x32x32 sphere channel; small boxes cover every boundary kind, the
+general (omega_higher != 1) and uncorrected collision variants, ragged grids
+and degenerate sizes; the 1024x512x512 channel is checked on sampled cells.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle.lbm as O
+from paper_2606_16765_gb300 import inputs as I
+from tests import cases as K
+
+pytestmark = pytest.mark.gpu
+
+TOL_U = {"f64": 1e-12, "f32": 1e-5, "f16s": 1e-3}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2606_16765_gb300 import _build
+    _build.build()
+
+
+# --------------------------------------------------------------------------
+# sphere channel 64x32x32, 200 steps from rest (Re = 1000 on the diameter)
+# --------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def sphere64():
+    d = I.sphere_channel_64()
+    w1 = O.omega_from_re(d["re"], d["u_in"], d["l_ref"])
+    c = K.case(d["grid"], d["mask"], omega1=w1, u_in=d["u_in"], mean=(100, 200, 1))
+    L = K.run_oracle(c, 200)
+    rho, u = L.macros()
+    f = L.get_f()
+    means, s = L.means()
+    return dict(case=c, rho=rho, u=u, f=f, means=means, samples=s, forces=L.forces())
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32", "f16s"])
+def test_sphere_channel_200_steps(sphere64, storage):
+    c = sphere64["case"]
+    s = K.make_solver(c, storage, force_every=1)
+    s.step(200)
+    s.sync()
+    rho, u = s.macros()
+    fluid = c["mask"] == 0
+    eu = K.rel_u_err(u, sphere64["u"], fluid)
+    er = K.rho_err(rho, sphere64["rho"], fluid)
+    print(f"{storage}: rel u err {eu:.3e}  rho err {er:.3e}")
+    assert eu <= TOL_U[storage]
+    assert er <= TOL_U[storage]
+    if storage == "f64":
+        f = s.pdfs()
+        assert np.abs(f - sphere64["f"])[:, fluid].max() < 1e-13
+    # time average over steps 100..199 and the force series
+    m, ns = s.mean()
+    assert ns == sphere64["samples"] == 100
+    mref = sphere64["means"]
+    em = np.abs(m - mref)[fluid].max() / np.abs(mref[..., :3])[fluid].max()
+    assert em <= TOL_U[storage]
+    F = s.forces()
+    Fr = sphere64["forces"]
+    assert F.shape == Fr.shape == (200, 3)
+    assert np.abs(F - Fr).max() <= TOL_U[storage] * np.abs(Fr[:, 0]).max() * 10
+
+
+def test_bf16s_runs_and_is_reported(sphere64):
+    """BF16-shifted storage (8-bit mantissa) is reported, not gated."""
+    c = sphere64["case"]
+    s = K.make_solver(c, "bf16s")
+    s.step(200)
+    s.sync()
+    rho, u = s.macros()
+    eu = K.rel_u_err(u, sphere64["u"], c["mask"] == 0)
+    print(f"bf16s: rel u err {eu:.3e}")
+    assert np.isfinite(eu) and eu < 0.5
+
+
+# --------------------------------------------------------------------------
+# small boxes: every boundary kind, ragged sizes, both collision variants
+# --------------------------------------------------------------------------
+def box_cases():
+    g = (37, 13, 11)                     # ragged: not a multiple of the block
+    obs = I.sphere(g, (9.0, 6.0, 5.0), 3.0)
+    wall_obs = I.voxelize(g, [I.Primitive("rectangle", (20.0, 1.0, 5.0), (4.0, 4.0, 20.0))])  # touches y=0 and both z walls
+    return {
+        "channel_obstacle": K.case(g, obs, omega1=1.7, noise=(11, 2e-3)),
+        "obstacle_on_walls": K.case(g, wall_obs, omega1=1.9, noise=(12, 2e-3)),
+        "periodic_all": K.case((9, 7, 5), None, omega1=1.3, faces=("periodic",) * 4, u_in=0.0, noise=(13, 5e-3)),
+        "periodic_yz_inlet": K.case(g, obs, omega1=1.6, faces=("inlet", "outlet", "periodic", "periodic"), noise=(14, 2e-3)),
+        "closed_box": K.case((12, 10, 8), I.sphere((12, 10, 8), (5.5, 4.5, 3.5), 2.0), omega1=1.95,
+                             faces=("wall", "wall", "wall", "wall"), u_in=0.0, noise=(15, 3e-3)),
+        "general_omega_higher": K.case(g, obs, omega1=1.5, omega_bulk=1.2, omega_higher=1.3, noise=(16, 2e-3)),
+        "no_galilean": K.case(g, obs, omega1=1.8, galilean=0, noise=(17, 2e-3)),
+        "thin_slab": K.case((16, 1, 3), None, omega1=1.4, faces=("inlet", "outlet", "periodic", "wall"), noise=(18, 2e-3)),
+        "single_cell": K.case((1, 1, 1), None, omega1=1.1, faces=("periodic",) * 4, u_in=0.0, noise=(19, 5e-3)),
+    }
+
+
+BOXES = box_cases()
+
+
+@pytest.mark.parametrize("name", sorted(BOXES))
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+def test_small_boxes(name, storage):
+    c = BOXES[name]
+    fluid = np.ones(c["grid"][::-1], bool) if c["mask"] is None else c["mask"] == 0
+    s = K.make_solver(c, storage)
+    L = K.run_oracle(c, 0)
+    for steps in (1, 1, 5, 13):          # odd and even counts: both AA parities
+        s.step(steps)
+        L.step(steps)
+        f = s.pdfs()
+        fr = L.get_f()
+        err = np.abs(f - fr)[:, fluid].max()
+        tol = 1e-14 if storage == "f64" else 2e-7
+        assert err <= tol, (name, storage, L.t, err)
+    s.sync()
+
+
+def test_degenerate_all_solid_and_empty_steps():
+    g = (8, 4, 4)
+    s = K.make_solver(K.case(g, np.ones(g[::-1], np.uint8)), "f32")
+    s.step(0)
+    s.step(3)
+    s.sync()
+    assert s.t == 3
+    rho, u = s.macros()
+    assert np.all(rho == 1) and np.all(u == 0)
+
+
+# --------------------------------------------------------------------------
+# conservation, instability flag, checkpoint, workspace ownership
+# --------------------------------------------------------------------------
+def test_periodic_totals_are_conserved():
+    c = K.case((24, 20, 16), None, omega1=1.9, faces=("periodic",) * 4, u_in=0.0, noise=(21, 1e-2))
+    s = K.make_solver(c, "f64")
+    t0 = s.totals()
+    s.step(41)
+    t1 = s.totals()
+    assert np.abs(t1 - t0).max() < 1e-12
+    L = K.run_oracle(c, 0)
+    ref = L.totals()
+    ref[0] -= (c["grid"][0] * c["grid"][1] * c["grid"][2])
+    assert np.abs(t0 - ref).max() < 1e-12
+
+
+def test_instability_is_latched_and_steps_refused():
+    from paper_2606_16765_gb300.lbm import LBMError, LBM_ERR_UNSTABLE, LBM_ERR_STATE
+    c = K.case((16, 8, 8), None, omega1=1.9, faces=("periodic",) * 4, u_in=0.0, noise=(5, 0.2))
+    s = K.make_solver(c, "f32")
+    s.step(2)
+    with pytest.raises(LBMError) as e:
+        s.sync()
+    assert e.value.status == LBM_ERR_UNSTABLE
+    with pytest.raises(LBMError) as e2:
+        s.step(1)
+    assert e2.value.status == LBM_ERR_STATE
+    s.macros()                               # reads still work
+
+
+def test_checkpoint_resume_is_bitwise(tmp_path):
+    d = I.sphere_channel_64()
+    c = K.case(d["grid"], d["mask"], omega1=1.9, mean=(0, 1000, 2))
+    a = K.make_solver(c, "f32", force_every=1)
+    a.step(30)
+    path = str(tmp_path / "ck.bin")
+    a.save(path)
+    a.step(31)
+    b = K.make_solver(c, "f32", force_every=1)
+    b.load(path)
+    assert b.t == 30
+    b.step(31)
+    assert np.array_equal(a.pdfs(), b.pdfs())
+    assert np.array_equal(a.mean()[0], b.mean()[0])
+    assert np.array_equal(a.forces(), b.forces())
+
+
+def test_library_owned_memory_matches_workspace():
+    from paper_2606_16765_gb300 import lbm as B
+    import torch
+    d = I.sphere_channel_64()
+    c = K.case(d["grid"], d["mask"], omega1=1.9, noise=(3, 1e-3))
+    a = K.make_solver(c, "f32")
+    p = B.make_params(storage="f32", omega1=1.9, u_in=0.05)
+    h = B.lbm_create(B.lbm_grid(*d["grid"]), d["mask"], p, torch.cuda.current_stream().cuda_stream)
+    B.lbm_init_noise(h, 3, 1e-3)
+    a.step(7)
+    B.lbm_step(h, 7)
+    out = np.zeros((27,) + a.shape)
+    B.lbm_get_pdfs(h, out)
+    B.lbm_destroy(h)
+    assert np.array_equal(out, a.pdfs())
+
+
+def test_argument_errors_are_reported():
+    from paper_2606_16765_gb300.lbm import LBMError, Solver
+    with pytest.raises(LBMError):
+        Solver((8, 8, 8), faces=("outlet", "inlet", "wall", "wall"))
+    with pytest.raises(LBMError):
+        Solver((0, 8, 8))
+    s = Solver((8, 8, 8), omega1=1.5)
+    with pytest.raises(LBMError):
+        s.step(-1)
+    s.step(1)
+    with pytest.raises(LBMError):            # set needs an even time step
+        s.set_pdfs(np.zeros((27, 8, 8, 8)))
+
+
+# --------------------------------------------------------------------------
+# snapshots (full and half resolution) against oracle macros
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("halfres", [0, 1])
+def test_snapshots(halfres):
+    g = (33, 14, 12)
+    mask = I.sphere(g, (10.0, 6.5, 5.5), 3.0)
+    c = K.case(g, mask, omega1=1.8, noise=(31, 1e-3))
+    s = K.make_solver(c, "f64", snap_first=3, snap_every=4, snap_count=3, snap_halfres=halfres)
+    L = K.run_oracle(c, 0)
+    want = {}
+    for t in range(12):
+        if t in (3, 7, 11):
+            rho, u = L.macros()
+            fld = np.concatenate([u, (rho[..., None] - 1) / 3], -1) * (mask == 0)[..., None]
+            want[(t - 3) // 4] = O.halfres(fld) if halfres else fld
+        L.step(1)
+    s.step(12)
+    for k, ref in want.items():
+        got = s.snapshot(k)
+        assert got.shape == ref.shape
+        assert np.abs(got - ref).max() < 1e-6 * max(1.0, np.abs(ref).max())
+
+
+# --------------------------------------------------------------------------
+# 1024x512x512 channel (composite obstacle), launch configuration of the
+# benchmark, on sampled cells that the oracle computes one by one from a
+# neighbourhood of the seeded initial state
+# --------------------------------------------------------------------------
+def oracle_cell_after(mask, grid, faces, omega1, u_in, seed, amp, cell, steps):
+    nx, ny, nz = grid
+    z, y, x = np.unravel_index(cell, (nz, ny, nx))
+    R = steps + 1
+    x0, x1 = max(0, x - R), min(nx, x + R + 1)
+    y0, y1 = max(0, y - R), min(ny, y + R + 1)
+    z0, z1 = max(0, z - R), min(nz, z + R + 1)
+    sub = np.ascontiguousarray(mask[z0:z1, y0:y1, x0:x1])
+    sg = (x1 - x0, y1 - y0, z1 - z0)
+    zz, yy, xx = np.meshgrid(np.arange(z0, z1), np.arange(y0, y1), np.arange(x0, x1), indexing="ij")
+    gcell = (xx + nx * (yy + ny * zz)).reshape(-1)
+    w = O.weights()
+    f = w[:, None] + amp * I.pdf_noise(seed, gcell)
+    f[:, sub.reshape(-1) != 0] = w[:, None]
+    sub_faces = ("inlet" if x0 == 0 else "wall", "outlet" if x1 == nx else "wall", "wall", "wall")
+    p = O.params(*sg, omega1, u_in=u_in, faces=sub_faces)
+    L = O.Lattice(p, sub)
+    L.set_f(f.reshape(27, *sub.shape))
+    L.step(steps)
+    return L.get_f()[:, z - z0, y - y0, x - x0]
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16s"])
+def test_full_size_channel_sampled_cells(storage):
+    import torch
+    d = I.composite_channel(0)
+    grid, mask = d["grid"], d["mask"]
+    nx, ny, nz = grid
+    w1 = O.omega_from_re(d["re"], d["u_in"], d["l_ref"])
+    from paper_2606_16765_gb300.lbm import Solver
+    seed, amp = 77, 1e-3
+    s = Solver(grid, mask, storage=storage, omega1=w1, u_in=d["u_in"])
+    s.init_noise(seed, amp)
+    rng = np.random.default_rng(0)
+    n = nx * ny * nz
+    fluid_idx = np.flatnonzero(mask.reshape(-1) == 0)
+    pick = list(rng.choice(fluid_idx, 120, replace=False))
+    # cells next to the obstacle, on the inlet/outlet planes, walls and corners
+    zz, yy, xx = np.nonzero(mask)
+    for k in rng.choice(len(xx), 20, replace=False):
+        for dx in (-1, 1):
+            c = (xx[k] + dx) + nx * (yy[k] + ny * zz[k])
+            if mask.reshape(-1)[c] == 0:
+                pick.append(c)
+    for (x, y, z) in [(0, 5, 7), (nx - 1, 100, 300), (0, 0, 0), (nx - 1, ny - 1, nz - 1),
+                      (500, 0, 200), (700, ny - 1, 1), (3, 200, nz - 1), (nx - 1, 0, nz - 1)]:
+        pick.append(x + nx * (y + ny * z))
+    pick = np.array(sorted(set(int(p) for p in pick)), np.int64)
+    tol = 2e-7 if storage == "f32" else 2e-6
+    for steps in (1, 2):
+        s.step(1)
+        got = s.cells(pick)
+        for j, c in enumerate(pick):
+            ref = oracle_cell_after(mask, grid, ("inlet", "outlet", "wall", "wall"), w1, d["u_in"], seed, amp, c, steps)
+            err = np.abs(got[j] - ref).max()
+            assert err <= tol, (storage, steps, int(c), err)
+    s.sync()
+    del s
+    torch.cuda.empty_cache()
