@@ -1,0 +1,413 @@
+#!/usr/bin/env python
+"""Throughput of the fused D3Q27 cumulant LBM step on the full-size channel.
+
+Workload: 1024x512x512 channel (268M cells) with a seeded composite obstacle
+(2-4 random primitives), Re = 10^4 on the channel height, inlet u = 0.05;
+shifted pdfs in FP32 (headline) and FP16 (reported beside it).  A step is one
+full time step of the hot path: fused stream + collide over all fluid cells
+with the obstacle force recorded every step, the FP64 time average sampled
+every 10 steps, and 20 half-resolution snapshots 25 steps apart at the end of
+the timed window.
+
+Default run: python bench.py [--steps K] [--warmup W].  Under torchrun with
+N > 1 each rank runs its own replica of the workload (independent problems;
+no collective on the data path) and rank 0 prints the aggregate.
+--impl reference times the FP64 CPU oracle on the host cores instead.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS & % HBM roofline (D3Q27); FNO mean-field speedup vs LBM at ≤5% rel L2"
+NOMINAL_HBM_GBS = 8000.0
+BYTES_PER_POP = {"f64": 8, "f32": 4, "f16s": 2, "bf16s": 2}
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2606_16765_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(csrc, name), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel, workload):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on
+    the current kernel sources."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        recs = json.load(open(path))
+    except Exception:
+        return None
+    src = kernel_source_hash()
+    for r in recs:
+        if r.get("kernel") == kernel and r.get("workload") == workload and r.get("source_hash") == src:
+            return r.get("bytes_per_launch")
+    return None
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out = ""
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.splitlines():
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# distributed helpers (replicas; only timing and unit counts are exchanged)
+# ---------------------------------------------------------------------------
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def aggregate(ms, units, ws, backend_ready):
+    """Max time over ranks and total units (the job's throughput)."""
+    if ws == 1 or not backend_ready:
+        return ms, units
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda" if dist.get_backend() == "nccl" else "cpu")
+    u = torch.tensor([units], dtype=torch.float64, device=t.device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ---------------------------------------------------------------------------
+# workload
+# ---------------------------------------------------------------------------
+def workload(grid):
+    from paper_2606_16765_gb300 import inputs as I
+    return I.composite_channel(0, grid=grid)
+
+
+def schedule(steps, warmup):
+    """Epilogue schedule over the timed window [warmup, warmup + steps)."""
+    nsnap = min(20, max(1, steps // 25))
+    return dict(mean_start=warmup, mean_end=warmup + steps, mean_every=10,
+                snap_first=warmup + steps - 25 * nsnap, snap_every=25, snap_count=nsnap,
+                snap_halfres=1, force_every=1)
+
+
+def run_ours(args, storage, d, ws, device_index):
+    import torch
+    from paper_2606_16765_gb300.lbm import Solver
+
+    K, W = args.steps, args.warmup
+    sch = schedule(K, W)
+    s = Solver(d["grid"], d["mask"], storage=storage, re=d["re"], u_in=d["u_in"], l_ref=d["l_ref"],
+               block_x=args.block_x, **sch)
+    info = s.info()
+    s.step(W)
+    s.sync()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.timing(True)
+    s.timing_read(reset=True)
+    launches0 = s.info().launches
+    clocks = ClockSampler(device_index)
+    barrier(ws)
+    torch.cuda.synchronize()
+    clocks.start()
+    e0.record(stream)
+    s.step(K)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    s.sync()
+    rep = s.timing_read(reset=True)
+    launches = s.info().launches - launches0
+    res = dict(ms=ms, info=info, rep=rep, clocks=clk, launches=launches, storage=storage)
+    s.close()
+    del s
+    torch.cuda.empty_cache()
+    return res
+
+
+def run_e2e(args, storage, d):
+    """Through the C ABI with host buffers: mask upload, K steps, half-res
+    mean read-back, all inside the timed region."""
+    import numpy as np
+    import torch
+    from paper_2606_16765_gb300 import lbm as B
+
+    K = args.steps
+    p = B.make_params(storage=storage, re=d["re"], u_in=d["u_in"], l_ref=d["l_ref"],
+                      block_x=args.block_x, **schedule(K, 0))
+    grid = B.lbm_grid(*d["grid"])
+    nx, ny, nz = d["grid"]
+    mean = np.zeros((((nz + 1) // 2), ((ny + 1) // 2), ((nx + 1) // 2), 4), np.float32)
+    mask = np.ascontiguousarray(d["mask"])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    h = B.lbm_create(grid, mask, p, torch.cuda.current_stream().cuda_stream)
+    B.lbm_step(h, K)
+    B.lbm_read_mean(h, mean, 1, 1)
+    t1 = time.perf_counter()
+    info = B.lbm_get_info(h)
+    B.lbm_destroy(h)
+    torch.cuda.empty_cache()
+    return dict(seconds=t1 - t0, fluid=info.fluid_cells, h2d=mask.nbytes, d2h=mean.nbytes)
+
+
+def cpu_baseline(d, seconds=12.0, box=(128, 96, 96)):
+    """FP64 oracle on the host cores, on a sub-box of the same channel around
+    the obstacle, stepped until ~`seconds` of CPU work."""
+    import numpy as np
+    cores = os.cpu_count() or 1
+    os.environ.setdefault("OMP_NUM_THREADS", str(cores))
+    import oracle.lbm as O
+    nx, ny, nz = d["grid"]
+    bx, by, bz = (min(box[0], nx), min(box[1], ny), min(box[2], nz))
+    x0 = max(0, min(nx - bx, int(0.3 * nx) - bx // 3))
+    y0, z0 = (ny - by) // 2, (nz - bz) // 2
+    sub = np.ascontiguousarray(d["mask"][z0:z0 + bz, y0:y0 + by, x0:x0 + bx])
+    w1 = O.omega_from_re(d["re"], d["u_in"], d["l_ref"])
+    L = O.Lattice(O.params(bx, by, bz, w1, u_in=d["u_in"]), sub)
+    fluid = int((sub == 0).sum())
+    steps, t0 = 0, time.perf_counter()
+    while True:
+        L.step(1)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el >= seconds or steps >= 200:
+            break
+    return {"value": fluid * steps / el / 1e6, "unit": "MLUPS", "cores": int(os.environ["OMP_NUM_THREADS"]),
+            "kind": "oracle",
+            "sample": f"{bx}x{by}x{bz} sub-box of the channel around the obstacle, {steps} FP64 steps, {el:.1f} s"}
+
+
+def reference_arm(args):
+    """The FP64 CPU oracle timed on the host cores, each step a bounded
+    sample of the workload sized so that W + K steps take ~100 s."""
+    import numpy as np
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    cores = os.cpu_count() or 1
+    os.environ.setdefault("OMP_NUM_THREADS", str(cores))
+    import oracle.lbm as O
+    grid = tuple(int(v) for v in args.grid.split(","))
+    d = workload(grid)
+    nx, ny, nz = grid
+    w1 = O.omega_from_re(d["re"], d["u_in"], d["l_ref"])
+    # calibrate the per-cell cost on a small box
+    cal = O.Lattice(O.params(32, 16, 16, w1, u_in=d["u_in"]))
+    t0 = time.perf_counter()
+    cal.step(2)
+    per_cell = (time.perf_counter() - t0) / (2 * 32 * 16 * 16)
+    budget = 100.0 / max(1, args.steps + args.warmup)
+    cells = max(16 * 8 * 8, min(nx * ny * nz, int(budget / per_cell)))
+    a = max(8, int(round((cells / 2) ** (1 / 3))))
+    bx, by, bz = min(2 * a, nx), min(a, ny), min(a, nz)
+    x0 = max(0, min(nx - bx, int(0.3 * nx) - bx // 3))
+    y0, z0 = (ny - by) // 2, (nz - bz) // 2
+    sub = np.ascontiguousarray(d["mask"][z0:z0 + bz, y0:y0 + by, x0:x0 + bx])
+    L = O.Lattice(O.params(bx, by, bz, w1, u_in=d["u_in"]), sub)
+    fluid = int((sub == 0).sum())
+    L.step(args.warmup)
+    t0 = time.perf_counter()
+    L.step(args.steps)
+    el = time.perf_counter() - t0
+    v = fluid * args.steps / el / 1e6
+    sample = f"{bx}x{by}x{bz} sub-box of the channel around the obstacle per step"
+    line = {
+        "metric": METRIC, "value": v, "unit": "MLUPS", "impl": "reference", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": config_block(grid, "f64", None),
+        "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": int(os.environ["OMP_NUM_THREADS"]),
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def config_block(grid, storage, info):
+    nx, ny, nz = grid
+    c = {"workload": f"composite-obstacle channel {nx}x{ny}x{nz}, Re=1e4 on the channel height, u_in=0.05, seed 0",
+         "grid": [nx, ny, nz], "storage": storage,
+         "epilogues": "obstacle force every step, FP64 mean every 10 steps, 20 half-res snapshots 25 steps apart",
+         "l2": "inputs larger than L2 (pdf array >> 129 MB), no flush"}
+    if info is not None:
+        c.update(fluid_cells=int(info.fluid_cells), bulk_cells=int(info.bulk_cells),
+                 edge_cells=int(info.edge_cells), block_x=int(info.block_x))
+    return c
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--storage", default="f32", choices=["f32", "f16s", "bf16s", "f64"])
+    ap.add_argument("--also", default="f16s", help="comma list of extra storages to report ('' for none)")
+    ap.add_argument("--grid", default="1024,512,512")
+    ap.add_argument("--block-x", type=int, default=0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        reference_arm(args)
+        return
+
+    import torch
+    ws, rank, local = dist_env()
+    backend = False
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+        backend = True
+    else:
+        torch.cuda.set_device(0)
+    from paper_2606_16765_gb300 import _build
+    if rank == 0:
+        _build.build()
+    barrier(ws)
+
+    grid = tuple(int(v) for v in args.grid.split(","))
+    d = workload(grid)
+    res = run_ours(args, args.storage, d, ws, local)
+    info, rep = res["info"], res["rep"]
+    K = args.steps
+    ms, units = aggregate(res["ms"], float(info.fluid_cells) * K, ws, backend)
+    mlups = units / (ms / 1e3) / 1e6
+
+    peak, peak_kind = measured_peaks()
+    s_b = BYTES_PER_POP[args.storage]
+    # dominant kernel: the bulk kernel of odd steps without epilogue
+    kind = 1 if rep.bulk_n[1] > 0 else 0
+    bulk_ms = rep.bulk_ms[kind] / max(1, rep.bulk_n[kind])
+    bytes_launch = 54 * s_b * info.bulk_cells
+    achieved = bytes_launch / (bulk_ms / 1e3) / 1e9
+    kname = f"k_step_bulk<{args.storage},odd={bool(kind & 1)},epi=False>"
+    traffic = recorded_traffic(kname, "composite channel %dx%dx%d" % grid)
+    per_kind = {}
+    for k, nm in enumerate(["even", "odd", "even+epilogue", "odd+epilogue"]):
+        if rep.bulk_n[k]:
+            t = rep.bulk_ms[k] / rep.bulk_n[k]
+            per_kind[nm] = {"launches": int(rep.bulk_n[k]), "ms": t,
+                            "gbs": 54 * s_b * info.bulk_cells / (t / 1e3) / 1e9}
+    edge_ms = rep.edge_ms / max(1, rep.edge_n)
+
+    line = {
+        "metric": METRIC, "value": mlups, "unit": "MLUPS", "n_gpus": ws, "steps": K, "warmup": args.warmup,
+        "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.storage == "f64" else "f32", "data": "synthetic",
+        "config": config_block(grid, args.storage, info),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic, "peak_source": peak_kind,
+                     "kernel": kname, "bytes_per_launch": bytes_launch,
+                     "frac_of_nominal_8000": achieved / NOMINAL_HBM_GBS},
+        "kernels": {"bulk": per_kind, "edge_ms_per_launch": edge_ms},
+        "gpu_launches": int(res["launches"]),
+        "clocks": res["clocks"],
+    }
+    if rank == 0:
+        for extra in [e for e in args.also.split(",") if e and e != args.storage]:
+            r2 = run_ours(args, extra, d, 1, local)
+            b2 = 54 * BYTES_PER_POP[extra]
+            k2 = 1 if r2["rep"].bulk_n[1] > 0 else 0
+            t2 = r2["rep"].bulk_ms[k2] / max(1, r2["rep"].bulk_n[k2])
+            line.setdefault("other_storage", {})[extra] = {
+                "value": float(r2["info"].fluid_cells) * K / (r2["ms"] / 1e3) / 1e6, "unit": "MLUPS",
+                "ms_per_step": r2["ms"] / K,
+                "bulk_kernel_gbs": b2 * r2["info"].bulk_cells / (t2 / 1e3) / 1e9,
+                "bulk_kernel_frac": b2 * r2["info"].bulk_cells / (t2 / 1e3) / 1e9 / peak,
+                "clocks": r2["clocks"]}
+        if not args.no_e2e:
+            e = run_e2e(args, args.storage, d)
+            line["e2e"] = {"value": e["fluid"] * K / e["seconds"] / 1e6, "unit": "MLUPS",
+                           "h2d_bytes_per_step": e["h2d"] / K, "d2h_bytes_per_step": e["d2h"] / K,
+                           "seconds": e["seconds"]}
+        if ws == 1 and not args.no_cpu:
+            line["cpu_baseline"] = cpu_baseline(d)
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

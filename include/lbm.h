@@ -161,6 +161,37 @@ lbm_status lbm_init_noise(lbm_ctx *ctx, uint64_t seed, double amplitude);
  * FP64 reduction. */
 lbm_status lbm_totals(lbm_ctx *ctx, double out[4]);
 
+/* Sizes and counters of a context. */
+typedef struct {
+    int64_t cells;           /* nx*ny*nz                                          */
+    int64_t fluid_cells;     /* cells that are not obstacle                       */
+    int64_t edge_cells;      /* fluid cells handled by the boundary-aware kernel  */
+    int64_t bulk_cells;      /* fluid cells handled by the branch-free kernel     */
+    int64_t launches;        /* kernels launched by lbm_step so far               */
+    uint64_t workspace_bytes;
+    int32_t storage, block_x;
+    double omega1;           /* shear rate in use                                 */
+} lbm_info;
+
+lbm_status lbm_get_info(const lbm_ctx *ctx, lbm_info *out);
+
+/* Kernel timing.  While enabled, lbm_step records CUDA events on the
+ * context's stream before the bulk kernel, between the bulk and the edge
+ * kernel, and after the edge kernel of every step (events only; no sync). */
+lbm_status lbm_timing(lbm_ctx *ctx, int32_t enable);
+
+/* Durations accumulated since the last reset (synchronises the stream).
+ * bulk_ms / bulk_n are indexed by (odd step) + 2 * (epilogue active). */
+typedef struct {
+    int64_t steps;
+    double bulk_ms[4];
+    int64_t bulk_n[4];
+    double edge_ms;
+    int64_t edge_n;
+} lbm_timing_report;
+
+lbm_status lbm_timing_read(lbm_ctx *ctx, lbm_timing_report *out, int32_t reset);
+
 /* Checkpoint: pdfs, time step, outlet plane, accumulators, force rows. */
 lbm_status lbm_save(lbm_ctx *ctx, const char *path);
 lbm_status lbm_load(lbm_ctx *ctx, const char *path);

@@ -89,6 +89,12 @@ struct lbm_ctx {
     double force_w[3] = {0, 0, 0};    // constant w-part of the obstacle force
     bool unstable = false;
     std::string err;
+    int64_t n_fluid = 0, n_bulk = 0, launches = 0;
+    // kernel timing: events recorded per step (start, mid, end) and the step kind
+    bool timing = false;
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_used = 0;
+    std::vector<int> ev_kind;
 
     template <class T> T *at(size_t off) { return reinterpret_cast<T *>(base + off); }
 
@@ -233,6 +239,10 @@ static lbm_status create_impl(const lbm_grid *g, const uint8_t *mask, const lbm_
     // constant part sum 2 c_i w_i of the obstacle force over obstacle links
     std::vector<uint32_t> edge;
     double fw[3] = {0, 0, 0};
+    for (int64_t c = 0; c < n; ++c) {
+        ctx->n_fluid += !(hflags[c] & CELL_SOLID);
+        ctx->n_bulk += (hflags[c] == 0);
+    }
     const int nx = g->nx, ny = g->ny, nz = g->nz;
     for (int64_t c = 0; c < n; ++c) {
         if (hflags[c] != CELL_EDGE) continue;
@@ -292,6 +302,7 @@ extern "C" lbm_status lbm_destroy(lbm_ctx *ctx)
 {
     if (!ctx) return LBM_ERR_ARG;
     cudaStreamSynchronize(ctx->stream);
+    for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
     if (ctx->owns && ctx->base) cudaFree(ctx->base);
     delete ctx;
     return LBM_OK;
@@ -311,14 +322,38 @@ static lbm_status flush_forces(lbm_ctx *ctx)
     return LBM_OK;
 }
 
+static cudaEvent_t next_event(lbm_ctx *ctx)
+{
+    if (ctx->ev_used == ctx->ev_pool.size()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        ctx->ev_pool.push_back(e);
+    }
+    return ctx->ev_pool[ctx->ev_used++];
+}
+
 static void step_launch(lbm_ctx *ctx, const StepArgs &a, bool odd, bool epi)
 {
-    switch (ctx->p.storage) {
-    case LBM_F64: launch_step_f64(a, odd, epi, ctx->plain, ctx->block_x, ctx->stream); break;
-    case LBM_F32: launch_step_f32(a, odd, epi, ctx->plain, ctx->block_x, ctx->stream); break;
-    case LBM_F16S: launch_step_f16(a, odd, epi, ctx->plain, ctx->block_x, ctx->stream); break;
-    default: launch_step_bf16(a, odd, epi, ctx->plain, ctx->block_x, ctx->stream); break;
+    cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
+    if (ctx->timing) {
+        e0 = next_event(ctx);
+        e1 = next_event(ctx);
+        e2 = next_event(ctx);
+        if (e0 && e1 && e2) {
+            cudaEventRecord(e0, ctx->stream);
+            ctx->ev_kind.push_back((odd ? 1 : 0) + (epi ? 2 : 0));
+        } else {
+            e1 = nullptr;
+        }
     }
+    switch (ctx->p.storage) {
+    case LBM_F64: launch_step_f64(a, odd, epi, ctx->plain, ctx->block_x, ctx->stream, e1); break;
+    case LBM_F32: launch_step_f32(a, odd, epi, ctx->plain, ctx->block_x, ctx->stream, e1); break;
+    case LBM_F16S: launch_step_f16(a, odd, epi, ctx->plain, ctx->block_x, ctx->stream, e1); break;
+    default: launch_step_bf16(a, odd, epi, ctx->plain, ctx->block_x, ctx->stream, e1); break;
+    }
+    if (e1) cudaEventRecord(e2, ctx->stream);
+    ctx->launches += 1 + (a.n_edge > 0 ? 1 : 0);
 }
 
 extern "C" lbm_status lbm_step(lbm_ctx *ctx, int64_t nsteps)
@@ -363,8 +398,10 @@ extern "C" lbm_status lbm_step(lbm_ctx *ctx, int64_t nsteps)
             ctx->force_rows_dev++;
         }
         step_launch(ctx, a, (t & 1) != 0, a.msum != nullptr || a.snap != nullptr);
-        if (snap_k >= 0 && p.snap_halfres)
+        if (snap_k >= 0 && p.snap_halfres) {
             launch_halfres(a.snap, ctx->g.nx, ctx->g.ny, ctx->g.nz, true, slot, ctx->stream);
+            ctx->launches++;
+        }
         ctx->t = t + 1;
     }
     cudaError_t e = cudaGetLastError();
@@ -645,6 +682,52 @@ extern "C" lbm_status lbm_load(lbm_ctx *ctx, const char *path)
     ctx->force_rows_dev = 0;
     ctx->snap_taken = taken;
     ctx->unstable = false;
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_get_info(const lbm_ctx *ctx, lbm_info *out)
+{
+    if (!ctx || !out) return LBM_ERR_ARG;
+    std::memset(out, 0, sizeof(*out));
+    out->cells = ctx->L.n;
+    out->fluid_cells = ctx->n_fluid;
+    out->edge_cells = ctx->n_edge;
+    out->bulk_cells = ctx->n_bulk;
+    out->launches = ctx->launches;
+    out->workspace_bytes = ctx->L.total;
+    out->storage = ctx->p.storage;
+    out->block_x = ctx->block_x;
+    out->omega1 = ctx->w1;
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_timing(lbm_ctx *ctx, int32_t enable)
+{
+    if (!ctx) return LBM_ERR_ARG;
+    ctx->timing = enable != 0;
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_timing_read(lbm_ctx *ctx, lbm_timing_report *out, int32_t reset)
+{
+    if (!ctx || !out) return LBM_ERR_ARG;
+    CK(cudaStreamSynchronize(ctx->stream));
+    std::memset(out, 0, sizeof(*out));
+    for (size_t k = 0; k < ctx->ev_kind.size(); ++k) {
+        float a = 0.f, b = 0.f;
+        CK(cudaEventElapsedTime(&a, ctx->ev_pool[3 * k], ctx->ev_pool[3 * k + 1]));
+        CK(cudaEventElapsedTime(&b, ctx->ev_pool[3 * k + 1], ctx->ev_pool[3 * k + 2]));
+        const int kind = ctx->ev_kind[k];
+        out->bulk_ms[kind] += a;
+        out->bulk_n[kind] += 1;
+        out->edge_ms += b;
+        out->edge_n += 1;
+    }
+    out->steps = (int64_t)ctx->ev_kind.size();
+    if (reset) {
+        ctx->ev_kind.clear();
+        ctx->ev_used = 0;
+    }
     return LBM_OK;
 }
 

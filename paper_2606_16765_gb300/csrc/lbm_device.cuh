@@ -153,15 +153,19 @@ __device__ __forceinline__ void fwd_line(R &a, R &b, R &c, R u, R K)
     c = m2;
 }
 
+// Inverse line transform through the line's raw moments: s1 = f+ - f- (first
+// raw moment) and s2 = f+ + f- - K/3 (second raw moment, shifted).  Then
+// f- = (s2 - s1)/2, f+ = (s2 + s1)/2, f0 = m0 - s2, so the zeroth moment is
+// reproduced up to the rounding of the small deviation m0 (not of K).
 template <class R>
 __device__ __forceinline__ void inv_line(R &a, R &b, R &c, R u, R K)
 {
     const R m0 = a, m1 = b, m2 = c;
-    const R M0 = m0 + K;
-    const R uu = u * u;
-    b = m0 - M0 * uu - m2 - R(2) * u * m1;
-    a = R(0.5) * ((uu - u) * M0 + (R(2) * u - R(1)) * m1 + m2);
-    c = R(0.5) * ((uu + u) * M0 + (R(2) * u + R(1)) * m1 + m2);
+    const R s1 = m1 + u * (m0 + K);
+    const R s2 = m2 + u * (m1 + s1);
+    a = R(0.5) * (s2 - s1);
+    c = R(0.5) * (s2 + s1);
+    b = m0 - s2;
 }
 
 #define MI(a, b, c) ((a) + 3 * (b) + 9 * (c))

@@ -10,10 +10,14 @@
 namespace lbm {
 
 // fused step (bulk + edge kernels) for one storage type
-void launch_step_f64(const StepArgs &a, bool odd, bool epi, bool plain, int block_x, cudaStream_t s);
-void launch_step_f32(const StepArgs &a, bool odd, bool epi, bool plain, int block_x, cudaStream_t s);
-void launch_step_f16(const StepArgs &a, bool odd, bool epi, bool plain, int block_x, cudaStream_t s);
-void launch_step_bf16(const StepArgs &a, bool odd, bool epi, bool plain, int block_x, cudaStream_t s);
+void launch_step_f64(const StepArgs &a, bool odd, bool epi, bool plain, int block_x, cudaStream_t s,
+                    cudaEvent_t mid);
+void launch_step_f32(const StepArgs &a, bool odd, bool epi, bool plain, int block_x, cudaStream_t s,
+                    cudaEvent_t mid);
+void launch_step_f16(const StepArgs &a, bool odd, bool epi, bool plain, int block_x, cudaStream_t s,
+                    cudaEvent_t mid);
+void launch_step_bf16(const StepArgs &a, bool odd, bool epi, bool plain, int block_x, cudaStream_t s,
+                    cudaEvent_t mid);
 
 enum AuxOp { AUX_NOISE, AUX_GATHER, AUX_SET, AUX_MACROS, AUX_TOTALS };
 

@@ -189,7 +189,7 @@ __global__ void __launch_bounds__(EDGE_BLOCK) k_step_edge(StepArgs a)
 }
 
 template <class S>
-void launch_step_t(const StepArgs &a, bool odd, bool epi, bool plain, int block_x, cudaStream_t s)
+void launch_step_t(const StepArgs &a, bool odd, bool epi, bool plain, int block_x, cudaStream_t s, cudaEvent_t mid)
 {
     const dim3 blk(block_x);
     const dim3 grd((a.nx + block_x - 1) / block_x, a.ny, a.nz);
@@ -202,6 +202,7 @@ void launch_step_t(const StepArgs &a, bool odd, bool epi, bool plain, int block_
         else     { if (epi) LBM_BULK(false, true, false); else LBM_BULK(false, false, false); }
     }
 #undef LBM_BULK
+    if (mid) cudaEventRecord(mid, s);
     if (a.n_edge > 0) {
         const dim3 eg((unsigned)((a.n_edge + EDGE_BLOCK - 1) / EDGE_BLOCK));
         if (plain) {

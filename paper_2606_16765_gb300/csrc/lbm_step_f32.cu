@@ -4,8 +4,9 @@
 #include "lbm_step.cuh"
 
 namespace lbm {
-void launch_step_f32(const StepArgs &a, bool odd, bool epi, bool plain, int block_x, cudaStream_t s)
+void launch_step_f32(const StepArgs &a, bool odd, bool epi, bool plain, int block_x, cudaStream_t s,
+                    cudaEvent_t mid)
 {
-    launch_step_t<float>(a, odd, epi, plain, block_x, s);
+    launch_step_t<float>(a, odd, epi, plain, block_x, s, mid);
 }
 }  // namespace lbm

@@ -41,6 +41,17 @@ class lbm_params(C.Structure):
     ]
 
 
+class lbm_info(C.Structure):
+    _fields_ = [("cells", C.c_int64), ("fluid_cells", C.c_int64), ("edge_cells", C.c_int64),
+                ("bulk_cells", C.c_int64), ("launches", C.c_int64), ("workspace_bytes", C.c_uint64),
+                ("storage", C.c_int32), ("block_x", C.c_int32), ("omega1", C.c_double)]
+
+
+class lbm_timing_report(C.Structure):
+    _fields_ = [("steps", C.c_int64), ("bulk_ms", C.c_double * 4), ("bulk_n", C.c_int64 * 4),
+                ("edge_ms", C.c_double), ("edge_n", C.c_int64)]
+
+
 class LBMError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{msg} (status {status})")
@@ -78,6 +89,9 @@ def lib():
             "lbm_get_cells": (C.c_int, [_vp, _i64, _vp, _vp]),
             "lbm_init_noise": (C.c_int, [_vp, C.c_uint64, C.c_double]),
             "lbm_totals": (C.c_int, [_vp, _vp]),
+            "lbm_get_info": (C.c_int, [_vp, C.POINTER(lbm_info)]),
+            "lbm_timing": (C.c_int, [_vp, C.c_int32]),
+            "lbm_timing_read": (C.c_int, [_vp, C.POINTER(lbm_timing_report), C.c_int32]),
             "lbm_save": (C.c_int, [_vp, C.c_char_p]),
             "lbm_load": (C.c_int, [_vp, C.c_char_p]),
             "lbm_last_error": (C.c_char_p, [_vp]),
@@ -187,6 +201,22 @@ def lbm_init_noise(h, seed, amplitude):
 
 def lbm_totals(h, out):
     _check(lib().lbm_totals(h, _ptr(out)), h)
+
+
+def lbm_get_info(h) -> lbm_info:
+    out = lbm_info()
+    _check(lib().lbm_get_info(h, C.byref(out)), h)
+    return out
+
+
+def lbm_timing(h, enable):
+    _check(lib().lbm_timing(h, int(bool(enable))), h)
+
+
+def lbm_timing_read(h, reset=True) -> lbm_timing_report:
+    out = lbm_timing_report()
+    _check(lib().lbm_timing_read(h, C.byref(out), int(bool(reset))), h)
+    return out
 
 
 def lbm_save(h, path):
@@ -307,6 +337,15 @@ class Solver:
         out = np.zeros(4)
         lbm_totals(self.h, out)
         return out
+
+    def info(self):
+        return lbm_get_info(self.h)
+
+    def timing(self, enable=True):
+        lbm_timing(self.h, enable)
+
+    def timing_read(self, reset=True):
+        return lbm_timing_read(self.h, reset)
 
     def save(self, path):
         lbm_save(self.h, path)

@@ -144,16 +144,22 @@ def test_degenerate_all_solid_and_empty_steps():
 # conservation, instability flag, checkpoint, workspace ownership
 # --------------------------------------------------------------------------
 def test_periodic_totals_are_conserved():
+    """Mass and momentum of a periodic box are invariants of the method.  The
+    reference totals of the seeded state are exact sums (math.fsum) of the
+    initial deviations; the drift bound is the rounding of 41 steps x 7680
+    cells x 27 populations of size <~ 1e-2 in FP64."""
+    import math
     c = K.case((24, 20, 16), None, omega1=1.9, faces=("periodic",) * 4, u_in=0.0, noise=(21, 1e-2))
     s = K.make_solver(c, "f64")
     t0 = s.totals()
+    n = 24 * 20 * 16
+    fbar = 1e-2 * I.pdf_noise(21, np.arange(n))
+    cv = O.velocities()
+    ref = [math.fsum(fbar.reshape(-1))] + [math.fsum((cv[:, d, None] * fbar).reshape(-1)) for d in range(3)]
+    assert np.abs(t0 - np.array(ref)).max() < 1e-13
     s.step(41)
     t1 = s.totals()
-    assert np.abs(t1 - t0).max() < 1e-12
-    L = K.run_oracle(c, 0)
-    ref = L.totals()
-    ref[0] -= (c["grid"][0] * c["grid"][1] * c["grid"][2])
-    assert np.abs(t0 - ref).max() < 1e-12
+    assert np.abs(t1 - t0).max() < 41 * n * 27 * 2.2e-16 * 1e-2
 
 
 def test_instability_is_latched_and_steps_refused():
@@ -295,7 +301,8 @@ def test_full_size_channel_sampled_cells(storage):
                       (500, 0, 200), (700, ny - 1, 1), (3, 200, nz - 1), (nx - 1, 0, nz - 1)]:
         pick.append(x + nx * (y + ny * z))
     pick = np.array(sorted(set(int(p) for p in pick)), np.int64)
-    tol = 2e-7 if storage == "f32" else 2e-6
+    # FP16: half an ulp is 2^-11 of |fbar| (<~ 3e-3 here); a few roundings per step
+    tol = 2e-7 if storage == "f32" else 8 * 2.0 ** -11 * 3e-3
     for steps in (1, 2):
         s.step(1)
         got = s.cells(pick)
