@@ -196,6 +196,38 @@ lbm_status lbm_timing_read(lbm_ctx *ctx, lbm_timing_report *out, int32_t reset);
 lbm_status lbm_save(lbm_ctx *ctx, const char *path);
 lbm_status lbm_load(lbm_ctx *ctx, const char *path);
 
+/* Totals of a caller-owned population array, allocating nothing.
+ *
+ * The paper has no counterpart: this is a service for callers that cannot
+ * call cudaMalloc where they need the totals -- a monitor thread checking
+ * conservation between the steps of a solver it does not own (cudaMalloc and
+ * cudaFree may synchronise the whole device and stall that solver), or an
+ * application whose device memory is owned entirely by a host framework's
+ * pool (a side allocation could fail or fragment it).  It computes the same
+ * quantities as lbm_totals: out[0] = sum of f_i - w_i over fluid cells,
+ * out[1..3] = momentum, by a deterministic two-pass FP64 reduction.
+ *
+ *   pdf          device array of 27 slots x slot_stride values of `storage`
+ *                type holding f_i - w_i in natural order (the layout a context
+ *                holds at even time steps), cell c of direction i at
+ *                i * slot_stride + c; slot_stride >= nx*ny*nz.
+ *   mask         device array of nx*ny*nz bytes, 1 = solid (skipped), or NULL.
+ *   out          4 doubles, host or device; for a host buffer the call waits
+ *                for the stream, for a device buffer it does not.
+ *
+ * Its only scratch is a fixed array compiled into the library (512 KiB, held
+ * by every GPU that loads the library until the process exits), which limits
+ * grids to 2^30 cells: larger grids return LBM_ERR_ARG with a message in
+ * lbm_last_error(NULL).  The first call on each device looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current; make that
+ * first call before any stream capture begins.  All calls share the array and
+ * it keeps the last call's contents (each call writes every slot it reads, so
+ * nothing needs clearing), but calls that overlap on the GPU race: serialise
+ * them, e.g. on one stream.  Errors go to lbm_last_error(NULL). */
+lbm_status lbm_totals_noalloc(const void *pdf, int32_t storage, int64_t slot_stride,
+                              const uint8_t *mask, int32_t nx, int32_t ny, int32_t nz,
+                              void *cuda_stream, double *out);
+
 /* Last error message of this context (never NULL). */
 const char *lbm_last_error(const lbm_ctx *ctx);
 const char *lbm_status_string(lbm_status s);

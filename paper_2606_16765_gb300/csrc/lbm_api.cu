@@ -70,6 +70,11 @@ bool is_device_ptr(const void *p)
 
 }  // namespace
 
+namespace lbm {
+// Message for lbm_last_error(NULL) from entry points defined in other units.
+void set_global_error(const std::string &m) { g_err = m; }
+}  // namespace lbm
+
 struct lbm_ctx {
     lbm_grid g;
     lbm_params p;

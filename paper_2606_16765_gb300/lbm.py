@@ -94,6 +94,8 @@ def lib():
             "lbm_timing_read": (C.c_int, [_vp, C.POINTER(lbm_timing_report), C.c_int32]),
             "lbm_save": (C.c_int, [_vp, C.c_char_p]),
             "lbm_load": (C.c_int, [_vp, C.c_char_p]),
+            "lbm_totals_noalloc": (C.c_int, [_vp, C.c_int32, C.c_int64, _vp, C.c_int32, C.c_int32,
+                                             C.c_int32, _vp, _vp]),
             "lbm_last_error": (C.c_char_p, [_vp]),
             "lbm_status_string": (C.c_char_p, [C.c_int]),
         }
@@ -217,6 +219,15 @@ def lbm_timing_read(h, reset=True) -> lbm_timing_report:
     out = lbm_timing_report()
     _check(lib().lbm_timing_read(h, C.byref(out), int(bool(reset))), h)
     return out
+
+
+def lbm_totals_noalloc(pdf, storage, slot_stride, mask, grid, stream, out):
+    """Totals of a caller-owned device population array (see include/lbm.h);
+    allocates no device memory."""
+    nx, ny, nz = grid
+    _check(lib().lbm_totals_noalloc(_ptr(pdf), int(storage), int(slot_stride),
+                                    _ptr(mask) if mask is not None else None, nx, ny, nz,
+                                    C.c_void_p(stream or 0), _ptr(out)), None)
 
 
 def lbm_save(h, path):
