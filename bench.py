@@ -28,7 +28,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "MLUPS & % HBM roofline (D3Q27); FNO mean-field speedup vs LBM at ≤5% rel L2"
 NOMINAL_HBM_GBS = 8000.0
-BYTES_PER_POP = {"f64": 8, "f32": 4, "f16s": 2, "bf16s": 2}
+BYTES_PER_POP = {"f64": 8, "f32": 4, "f16s": 2, "bf16s": 2, "f16c": 2}
 
 
 def log(*a):
@@ -308,7 +308,8 @@ def config_block(grid, storage, info):
          "l2": "inputs larger than L2 (pdf array >> 129 MB), no flush"}
     if info is not None:
         c.update(fluid_cells=int(info.fluid_cells), bulk_cells=int(info.bulk_cells),
-                 edge_cells=int(info.edge_cells), block_x=int(info.block_x))
+                 interior_cells=int(info.interior_cells), edge_cells=int(info.edge_cells),
+                 block_x=int(info.block_x))
     return c
 
 
@@ -318,8 +319,8 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--storage", default="f32", choices=["f32", "f16s", "bf16s", "f64"])
-    ap.add_argument("--also", default="f16s", help="comma list of extra storages to report ('' for none)")
+    ap.add_argument("--storage", default="f32", choices=["f32", "f16s", "f16c", "bf16s", "f64"])
+    ap.add_argument("--also", default="f16s,f16c", help="comma list of extra storages to report ('' for none)")
     ap.add_argument("--grid", default="1024,512,512")
     ap.add_argument("--block-x", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
@@ -359,7 +360,7 @@ def main():
     # dominant kernel: the bulk kernel of odd steps without epilogue
     kind = 1 if rep.bulk_n[1] > 0 else 0
     bulk_ms = rep.bulk_ms[kind] / max(1, rep.bulk_n[kind])
-    bytes_launch = 54 * s_b * info.bulk_cells
+    bytes_launch = 54 * s_b * info.interior_cells
     achieved = bytes_launch / (bulk_ms / 1e3) / 1e9
     kname = f"k_step_bulk<{args.storage},odd={bool(kind & 1)},epi=False>"
     traffic = recorded_traffic(kname, "composite channel %dx%dx%d" % grid)
@@ -368,8 +369,8 @@ def main():
         if rep.bulk_n[k]:
             t = rep.bulk_ms[k] / rep.bulk_n[k]
             per_kind[nm] = {"launches": int(rep.bulk_n[k]), "ms": t,
-                            "gbs": 54 * s_b * info.bulk_cells / (t / 1e3) / 1e9}
-    edge_ms = rep.edge_ms / max(1, rep.edge_n)
+                            "gbs": 54 * s_b * info.interior_cells / (t / 1e3) / 1e9}
+    edge_ms = rep.edge_ms / max(1, rep.steps)
 
     line = {
         "metric": METRIC, "value": mlups, "unit": "MLUPS", "n_gpus": ws, "steps": K, "warmup": args.warmup,
@@ -393,8 +394,8 @@ def main():
             line.setdefault("other_storage", {})[extra] = {
                 "value": float(r2["info"].fluid_cells) * K / (r2["ms"] / 1e3) / 1e6, "unit": "MLUPS",
                 "ms_per_step": r2["ms"] / K,
-                "bulk_kernel_gbs": b2 * r2["info"].bulk_cells / (t2 / 1e3) / 1e9,
-                "bulk_kernel_frac": b2 * r2["info"].bulk_cells / (t2 / 1e3) / 1e9 / peak,
+                "interior_kernel_gbs": b2 * r2["info"].interior_cells / (t2 / 1e3) / 1e9,
+                "interior_kernel_frac": b2 * r2["info"].interior_cells / (t2 / 1e3) / 1e9 / peak,
                 "clocks": r2["clocks"]}
         if not args.no_e2e:
             e = run_e2e(args, args.storage, d)

@@ -48,8 +48,11 @@ typedef enum {
 } lbm_status;
 
 /* Storage of the shifted populations f_i - w_i (arithmetic is FP32 for the
- * three reduced formats, FP64 for LBM_F64). */
-typedef enum { LBM_F64 = 0, LBM_F32 = 1, LBM_F16S = 2, LBM_BF16S = 3 } lbm_storage;
+ * reduced formats, FP64 for LBM_F64).  LBM_F16S is IEEE binary16, LBM_BF16S
+ * bfloat16, LBM_F16C a 16-bit float with 4 exponent bits (bias 15) and 11
+ * mantissa bits (range +-2, subnormal step 2^-25, saturating): one mantissa
+ * bit more than binary16 for values that never leave (-1, 1). */
+typedef enum { LBM_F64 = 0, LBM_F32 = 1, LBM_F16S = 2, LBM_BF16S = 3, LBM_F16C = 4 } lbm_storage;
 
 /* Boundary kind of a pair of faces (x has a low and a high face). */
 typedef enum {
@@ -91,8 +94,10 @@ typedef struct {
 void lbm_params_default(lbm_params *p);
 
 /* Bytes of device memory a context with these arguments needs (pdfs,
- * cell flags, boundary list, accumulators, snapshot ring, scratch). */
-size_t lbm_workspace_bytes(const lbm_grid *grid, const lbm_params *p);
+ * cell flags, boundary-cell records, accumulators, snapshot ring, scratch).
+ * mask as for lbm_create (host, device or NULL): the boundary records are
+ * bounded by the face cells plus 26 per solid cell.  0 on invalid input. */
+size_t lbm_workspace_bytes(const lbm_grid *grid, const uint8_t *mask, const lbm_params *p);
 
 /* Create a context.  mask: nx*ny*nz bytes, 1 = solid obstacle cell, host or
  * device, may be NULL (no obstacle).  State starts at rest (f = w, t = 0).
@@ -166,28 +171,30 @@ typedef struct {
     int64_t cells;           /* nx*ny*nz                                          */
     int64_t fluid_cells;     /* cells that are not obstacle                       */
     int64_t edge_cells;      /* fluid cells handled by the boundary-aware kernel  */
-    int64_t bulk_cells;      /* fluid cells handled by the branch-free kernel     */
+    int64_t bulk_cells;      /* fluid cells handled by the bulk kernel (incl. inlet/outlet plane cells) */
     int64_t launches;        /* kernels launched by lbm_step so far               */
     uint64_t workspace_bytes;
     int32_t storage, block_x;
     double omega1;           /* shear rate in use                                 */
+    int64_t interior_cells;  /* equal to bulk_cells (kept for layout stability)     */
 } lbm_info;
 
 lbm_status lbm_get_info(const lbm_ctx *ctx, lbm_info *out);
 
 /* Kernel timing.  While enabled, lbm_step records CUDA events on the
- * context's stream before the bulk kernel, between the bulk and the edge
- * kernel, and after the edge kernel of every step (events only; no sync). */
+ * context's stream around the bulk kernel and the edge kernel of every step
+ * (events only; no sync). */
 lbm_status lbm_timing(lbm_ctx *ctx, int32_t enable);
 
 /* Durations accumulated since the last reset (synchronises the stream).
- * bulk_ms / bulk_n are indexed by (odd step) + 2 * (epilogue active). */
+ * bulk_ms / bulk_n (bulk kernel) are indexed by (odd step) + 2 * (epilogue
+ * active); edge_ms is summed over all steps; rowend_ms is always 0. */
 typedef struct {
     int64_t steps;
     double bulk_ms[4];
     int64_t bulk_n[4];
+    double rowend_ms;
     double edge_ms;
-    int64_t edge_n;
 } lbm_timing_report;
 
 lbm_status lbm_timing_read(lbm_ctx *ctx, lbm_timing_report *out, int32_t reset);

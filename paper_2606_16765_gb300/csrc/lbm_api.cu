@@ -29,7 +29,17 @@ struct Layout {
     int tot_blocks = 0;
 };
 
-Layout make_layout(const lbm_grid &g, const lbm_params &p)
+// Upper bound of the edge-cell count: every cell on a domain face, plus the
+// (at most 26) fluid neighbours of each solid cell.
+int64_t edge_bound(const lbm_grid &g, int64_t n_solid)
+{
+    const int64_t n = (int64_t)g.nx * g.ny * g.nz;
+    int64_t inner = 1;
+    for (int d : {g.nx, g.ny, g.nz}) inner *= (d > 2 ? d - 2 : 0);
+    return std::min<int64_t>(n, (n - inner) + 26 * n_solid) + 1;
+}
+
+Layout make_layout(const lbm_grid &g, const lbm_params &p, int64_t n_solid)
 {
     Layout L;
     L.n = (int64_t)g.nx * g.ny * g.nz;
@@ -41,7 +51,7 @@ Layout make_layout(const lbm_grid &g, const lbm_params &p)
     auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes); return o; };
     L.pdf = take((size_t)Q * L.slot * storage_bytes(p.storage));
     L.flags = take((size_t)L.n);
-    L.edge = take((size_t)L.n * 4);
+    L.edge = take((size_t)edge_bound(g, n_solid) * 16);
     L.ub = take((size_t)3 * g.ny * g.nz * rsz);
     L.msum = take(p.mean_every > 0 ? (size_t)4 * L.n * 8 : 0);
     L.snaps = take(p.snap_count > 0 ? (size_t)p.snap_count * 4 * L.snap_cells * 4 : 0);
@@ -109,7 +119,7 @@ struct lbm_ctx {
         a.pdf = base + L.pdf;
         a.slot = L.slot;
         a.flags = at<uint8_t>(L.flags);
-        a.edge = at<uint32_t>(L.edge);
+        a.edge = at<uint4>(L.edge);
         a.n_edge = n_edge;
         a.nx = g.nx; a.ny = g.ny; a.nz = g.nz;
         a.nxy = (int64_t)g.nx * g.ny;
@@ -118,6 +128,16 @@ struct lbm_ctx {
         a.galilean = p.galilean_correction;
         a.face_x_lo = p.face_x_lo; a.face_x_hi = p.face_x_hi; a.face_y = p.face_y; a.face_z = p.face_z;
         a.u_in = p.u_in; a.rho_in = p.rho_in; a.rho_out = p.rho_out;
+        a.w1f = (float)a.w1; a.w2f = (float)a.w2; a.w3f = (float)a.w3;
+        const int64_t es = (int64_t)storage_bytes(p.storage);
+        for (int i = 0; i < Q; ++i) {
+            const int64_t off = cx_of(i) + (int64_t)cy_of(i) * g.nx + (int64_t)cz_of(i) * a.nxy;
+            a.boff[0][i] = (int64_t)i * L.slot * es;                   // even: own slot i
+            a.boff[1][i] = (int64_t)(Q - 1 - i) * L.slot * es;         // even: own slot 26-i
+            a.boff[2][i] = ((int64_t)(Q - 1 - i) * L.slot - off) * es; // odd: slot 26-i of x - c_i
+            a.boff[3][i] = ((int64_t)i * L.slot + off) * es;           // odd: slot i of x + c_i
+        }
+        a.u_in_f = (float)a.u_in; a.rho_in_f = (float)a.rho_in; a.rho_out_f = (float)a.rho_out;
         a.ub = base + L.ub;
         a.fcount = at<unsigned>(L.fcount);
         a.status = at<int>(L.status);
@@ -159,7 +179,7 @@ static std::string validate(const lbm_grid *g, const lbm_params *p)
     if (g->nx < 1 || g->ny < 1 || g->nz < 1) return "grid dimensions must be >= 1";
     if (g->ny > 65535 || g->nz > 65535) return "ny and nz must be <= 65535";
     if ((int64_t)g->nx * g->ny * g->nz >= (int64_t(1) << 32)) return "grid must have fewer than 2^32 cells";
-    if (p->storage < 0 || p->storage > 3) return "unknown storage";
+    if (p->storage < LBM_F64 || p->storage > LBM_F16C) return "unknown storage";
     if (p->face_x_lo != LBM_FACE_INLET && p->face_x_lo != LBM_FACE_WALL && p->face_x_lo != LBM_FACE_PERIODIC)
         return "face_x_lo must be inlet, wall or periodic";
     if (p->face_x_hi != LBM_FACE_OUTLET && p->face_x_hi != LBM_FACE_WALL && p->face_x_hi != LBM_FACE_PERIODIC)
@@ -176,10 +196,31 @@ static std::string validate(const lbm_grid *g, const lbm_params *p)
     return "";
 }
 
-extern "C" size_t lbm_workspace_bytes(const lbm_grid *g, const lbm_params *p)
+// Number of solid cells of a host or device mask (0 for NULL); -1 on error.
+static int64_t count_solid(const uint8_t *mask, int64_t n)
+{
+    if (!mask) return 0;
+    std::vector<uint8_t> h;
+    const uint8_t *m = mask;
+    if (is_device_ptr(mask)) {
+        h.resize(n);
+        if (cudaMemcpy(h.data(), mask, n, cudaMemcpyDeviceToHost) != cudaSuccess) {
+            cudaGetLastError();
+            return -1;
+        }
+        m = h.data();
+    }
+    int64_t k = 0;
+    for (int64_t c = 0; c < n; ++c) k += (m[c] != 0);
+    return k;
+}
+
+extern "C" size_t lbm_workspace_bytes(const lbm_grid *g, const uint8_t *mask, const lbm_params *p)
 {
     if (!validate(g, p).empty()) return 0;
-    return make_layout(*g, *p).total;
+    const int64_t ns = count_solid(mask, (int64_t)g->nx * g->ny * g->nz);
+    if (ns < 0) return 0;
+    return make_layout(*g, *p, ns).total;
 }
 
 static lbm_status create_impl(const lbm_grid *g, const uint8_t *mask, const lbm_params *p, void *stream,
@@ -193,7 +234,12 @@ static lbm_status create_impl(const lbm_grid *g, const uint8_t *mask, const lbm_
     ctx->g = *g;
     ctx->p = *p;
     if (ctx->p.force_capacity <= 0) ctx->p.force_capacity = 65536;
-    ctx->L = make_layout(*g, ctx->p);
+    const int64_t n_solid = count_solid(mask, (int64_t)g->nx * g->ny * g->nz);
+    if (n_solid < 0) {
+        delete ctx;
+        return fail(nullptr, LBM_ERR_CUDA, "mask could not be read");
+    }
+    ctx->L = make_layout(*g, ctx->p, n_solid);
     ctx->stream = static_cast<cudaStream_t>(stream);
     ctx->w1 = p->omega1 > 0 ? p->omega1 : 1.0 / (3.0 * p->u_in * p->l_ref / p->re + 0.5);
     ctx->plain = (p->omega_higher == 1.0);
@@ -224,49 +270,78 @@ static lbm_status create_impl(const lbm_grid *g, const uint8_t *mask, const lbm_
     }
     cudaStream_t s = ctx->stream;
     const int64_t n = L.n;
-    // the mask goes through the (not yet used) edge-list region
+    // the mask goes through the (not yet used) population region
     uint8_t *dmask = nullptr;
     if (mask) {
-        dmask = ctx->at<uint8_t>(L.edge);
+        dmask = ctx->at<uint8_t>(L.pdf);
         if (cudaMemcpyAsync(dmask, mask, n, is_device_ptr(mask) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s) != cudaSuccess) {
             ctx->err = "mask upload failed";
             return bail(LBM_ERR_CUDA);
         }
     }
-    launch_flags(dmask, ctx->at<uint8_t>(L.flags), g->nx, g->ny, g->nz, s);
+    launch_flags(dmask, ctx->at<uint8_t>(L.flags), g->nx, g->ny, g->nz, p->face_x_lo != LBM_FACE_PERIODIC,
+                 p->face_x_hi != LBM_FACE_PERIODIC, s);
     std::vector<uint8_t> hflags(n);
     if (cudaMemcpyAsync(hflags.data(), ctx->at<uint8_t>(L.flags), n, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess) {
         ctx->err = std::string("flag build failed: ") + cudaGetErrorString(cudaGetLastError());
         return bail(LBM_ERR_CUDA);
     }
-    // edge-cell list (ascending cell order keeps rows contiguous) and the
-    // constant part sum 2 c_i w_i of the obstacle force over obstacle links
-    std::vector<uint32_t> edge;
+    // edge-cell records (ascending cell order keeps rows contiguous): cell
+    // index and the link code of each of the 27 directions in the pull view
+    // (where population i of the cell comes from), plus the constant part
+    // sum 2 c_i w_i of the obstacle force over obstacle links
+    std::vector<uint4> edge;
     double fw[3] = {0, 0, 0};
-    for (int64_t c = 0; c < n; ++c) {
-        ctx->n_fluid += !(hflags[c] & CELL_SOLID);
-        ctx->n_bulk += (hflags[c] == 0);
-    }
     const int nx = g->nx, ny = g->ny, nz = g->nz;
-    for (int64_t c = 0; c < n; ++c) {
-        if (hflags[c] != CELL_EDGE) continue;
-        edge.push_back((uint32_t)c);
-        const int x = (int)(c % nx), y = (int)((c / nx) % ny), z = (int)(c / ((int64_t)nx * ny));
-        for (int j = 0; j < Q; ++j) {
-            int xx = x + cx_of(j), yy = y + cy_of(j), zz = z + cz_of(j);
-            if (yy < 0 || yy >= ny) { if (p->face_y != LBM_FACE_PERIODIC) continue; yy = (yy + ny) % ny; }
-            if (zz < 0 || zz >= nz) { if (p->face_z != LBM_FACE_PERIODIC) continue; zz = (zz + nz) % nz; }
-            if (xx < 0 || xx >= nx) { if (p->face_x_lo != LBM_FACE_PERIODIC) continue; xx = (xx + nx) % nx; }
-            if (!(hflags[xx + (int64_t)nx * (yy + (int64_t)ny * zz)] & CELL_SOLID)) continue;
-            fw[0] += 2.0 * cx_of(j) * w_of(j);
-            fw[1] += 2.0 * cy_of(j) * w_of(j);
-            fw[2] += 2.0 * cz_of(j) * w_of(j);
+    auto link_kind = [&](int sx, int sy, int sz) -> uint32_t {
+        bool wrapped = false;
+        if (sy < 0 || sy >= ny) {
+            if (p->face_y != LBM_FACE_PERIODIC) return LINK_WALL;
+            sy = (sy + ny) % ny; wrapped = true;
         }
+        if (sz < 0 || sz >= nz) {
+            if (p->face_z != LBM_FACE_PERIODIC) return LINK_WALL;
+            sz = (sz + nz) % nz; wrapped = true;
+        }
+        if (sx < 0) {
+            if (p->face_x_lo == LBM_FACE_INLET) return LINK_INLET;
+            if (p->face_x_lo == LBM_FACE_WALL) return LINK_WALL;
+            sx += nx; wrapped = true;
+        } else if (sx >= nx) {
+            if (p->face_x_hi == LBM_FACE_OUTLET) return LINK_OUTLET;
+            if (p->face_x_hi == LBM_FACE_WALL) return LINK_WALL;
+            sx -= nx; wrapped = true;
+        }
+        if (hflags[sx + (int64_t)nx * (sy + (int64_t)ny * sz)] & CELL_SOLID) return LINK_SOLID;
+        return wrapped ? LINK_WRAP : LINK_FLUID;
+    };
+    for (int64_t c = 0; c < n; ++c) {
+        const int x = (int)(c % nx), y = (int)((c / nx) % ny), z = (int)(c / ((int64_t)nx * ny));
+        ctx->n_fluid += !(hflags[c] & CELL_SOLID);
+        ctx->n_bulk += (hflags[c] == 0 || hflags[c] == CELL_XFACE);
+        (void)x;
+        if (hflags[c] != CELL_EDGE) continue;
+        uint32_t w[3] = {0, 0, 0};
+        for (int i = 0; i < Q; ++i) {
+            const uint32_t kind = link_kind(x - cx_of(i), y - cy_of(i), z - cz_of(i));
+            w[i / 9] |= kind << (3 * (i % 9));
+            if (kind == LINK_SOLID) {       // population j = 26 - i heads into the obstacle
+                const int j = Q - 1 - i;
+                fw[0] += 2.0 * cx_of(j) * w_of(j);
+                fw[1] += 2.0 * cy_of(j) * w_of(j);
+                fw[2] += 2.0 * cz_of(j) * w_of(j);
+            }
+        }
+        edge.push_back(make_uint4((uint32_t)c, w[0], w[1], w[2]));
+    }
+    if ((int64_t)edge.size() > edge_bound(*g, n_solid)) {
+        ctx->err = "edge-cell count exceeds its bound";
+        return bail(LBM_ERR_OOM);
     }
     ctx->n_edge = (int64_t)edge.size();
     for (int d = 0; d < 3; ++d) ctx->force_w[d] = fw[d];
-    if (!edge.empty() && cudaMemcpyAsync(ctx->at<uint32_t>(L.edge), edge.data(), edge.size() * 4,
+    if (!edge.empty() && cudaMemcpyAsync(ctx->at<uint4>(L.edge), edge.data(), edge.size() * sizeof(uint4),
                                          cudaMemcpyHostToDevice, s) != cudaSuccess) {
         ctx->err = "edge list upload failed";
         return bail(LBM_ERR_CUDA);
@@ -339,25 +414,27 @@ static cudaEvent_t next_event(lbm_ctx *ctx)
 
 static void step_launch(lbm_ctx *ctx, const StepArgs &a, bool odd, bool epi)
 {
-    cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr, e3 = nullptr;
     if (ctx->timing) {
         e0 = next_event(ctx);
         e1 = next_event(ctx);
         e2 = next_event(ctx);
-        if (e0 && e1 && e2) {
+        e3 = next_event(ctx);
+        if (e0 && e1 && e2 && e3) {
             cudaEventRecord(e0, ctx->stream);
             ctx->ev_kind.push_back((odd ? 1 : 0) + (epi ? 2 : 0));
         } else {
-            e1 = nullptr;
+            e1 = e2 = nullptr;
         }
     }
     switch (ctx->p.storage) {
-    case LBM_F64: launch_step_f64(a, odd, epi, ctx->plain, ctx->block_x, ctx->stream, e1); break;
-    case LBM_F32: launch_step_f32(a, odd, epi, ctx->plain, ctx->block_x, ctx->stream, e1); break;
-    case LBM_F16S: launch_step_f16(a, odd, epi, ctx->plain, ctx->block_x, ctx->stream, e1); break;
-    default: launch_step_bf16(a, odd, epi, ctx->plain, ctx->block_x, ctx->stream, e1); break;
+    case LBM_F64: launch_step_f64(a, odd, epi, ctx->plain, ctx->block_x, ctx->stream, e1, e2); break;
+    case LBM_F32: launch_step_f32(a, odd, epi, ctx->plain, ctx->block_x, ctx->stream, e1, e2); break;
+    case LBM_F16S: launch_step_f16(a, odd, epi, ctx->plain, ctx->block_x, ctx->stream, e1, e2); break;
+    case LBM_BF16S: launch_step_bf16(a, odd, epi, ctx->plain, ctx->block_x, ctx->stream, e1, e2); break;
+    default: launch_step_f16c(a, odd, epi, ctx->plain, ctx->block_x, ctx->stream, e1, e2); break;
     }
-    if (e1) cudaEventRecord(e2, ctx->stream);
+    if (e2) cudaEventRecord(e3, ctx->stream);
     ctx->launches += 1 + (a.n_edge > 0 ? 1 : 0);
 }
 
@@ -698,6 +775,7 @@ extern "C" lbm_status lbm_get_info(const lbm_ctx *ctx, lbm_info *out)
     out->fluid_cells = ctx->n_fluid;
     out->edge_cells = ctx->n_edge;
     out->bulk_cells = ctx->n_bulk;
+    out->interior_cells = ctx->n_bulk;
     out->launches = ctx->launches;
     out->workspace_bytes = ctx->L.total;
     out->storage = ctx->p.storage;
@@ -719,14 +797,15 @@ extern "C" lbm_status lbm_timing_read(lbm_ctx *ctx, lbm_timing_report *out, int3
     CK(cudaStreamSynchronize(ctx->stream));
     std::memset(out, 0, sizeof(*out));
     for (size_t k = 0; k < ctx->ev_kind.size(); ++k) {
-        float a = 0.f, b = 0.f;
-        CK(cudaEventElapsedTime(&a, ctx->ev_pool[3 * k], ctx->ev_pool[3 * k + 1]));
-        CK(cudaEventElapsedTime(&b, ctx->ev_pool[3 * k + 1], ctx->ev_pool[3 * k + 2]));
+        float a = 0.f, b = 0.f, c = 0.f;
+        CK(cudaEventElapsedTime(&a, ctx->ev_pool[4 * k], ctx->ev_pool[4 * k + 1]));
+        CK(cudaEventElapsedTime(&b, ctx->ev_pool[4 * k + 1], ctx->ev_pool[4 * k + 2]));
+        CK(cudaEventElapsedTime(&c, ctx->ev_pool[4 * k + 2], ctx->ev_pool[4 * k + 3]));
         const int kind = ctx->ev_kind[k];
         out->bulk_ms[kind] += a;
         out->bulk_n[kind] += 1;
-        out->edge_ms += b;
-        out->edge_n += 1;
+        out->rowend_ms += b;
+        out->edge_ms += c;
     }
     out->steps = (int64_t)ctx->ev_kind.size();
     if (reset) {

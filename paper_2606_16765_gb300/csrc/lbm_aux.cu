@@ -9,29 +9,42 @@ namespace lbm {
 // ---------------------------------------------------------------------------
 // cell flags: solid, or edge (some neighbour outside the domain or solid)
 // ---------------------------------------------------------------------------
-__global__ void k_flags(const uint8_t *mask, uint8_t *flags, int nx, int ny, int nz)
+__global__ void k_flags(const uint8_t *mask, uint8_t *flags, int nx, int ny, int nz, int xface_lo, int xface_hi)
 {
     const int64_t n = (int64_t)nx * ny * nz;
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x) {
         const int x = (int)(c % nx), y = (int)((c / nx) % ny), z = (int)(c / ((int64_t)nx * ny));
         if (mask && mask[c]) { flags[c] = CELL_SOLID; continue; }
+        bool solid_nbr = false;
+        if (mask) {
+            for (int dz = -1; dz <= 1; ++dz)
+                for (int dy = -1; dy <= 1; ++dy)
+                    for (int dx = -1; dx <= 1; ++dx) {
+                        const int xx = x + dx, yy = y + dy, zz = z + dz;
+                        if (xx < 0 || yy < 0 || zz < 0 || xx >= nx || yy >= ny || zz >= nz) continue;
+                        if (mask[xx + (int64_t)nx * (yy + (int64_t)ny * zz)]) solid_nbr = true;
+                    }
+        }
+        const bool yz_face = y == 0 || z == 0 || y == ny - 1 || z == nz - 1;
+        const bool x_face = x == 0 || x == nx - 1;
         uint8_t fl = 0;
-        if (x == 0 || y == 0 || z == 0 || x == nx - 1 || y == ny - 1 || z == nz - 1) {
+        if (solid_nbr || yz_face) {
             fl = CELL_EDGE;
-        } else if (mask) {
-            for (int dz = -1; dz <= 1 && !fl; ++dz)
-                for (int dy = -1; dy <= 1 && !fl; ++dy)
-                    for (int dx = -1; dx <= 1; ++dx)
-                        if (mask[c + dx + (int64_t)nx * (dy + (int64_t)ny * dz)]) { fl = CELL_EDGE; break; }
+        } else if (x_face) {
+            // only the links through one non-periodic x face need a rule
+            const bool ok = nx >= 2 && (x == 0 ? xface_lo : xface_hi);
+            fl = ok ? CELL_XFACE : CELL_EDGE;
         }
         flags[c] = fl;
     }
 }
 
-void launch_flags(const uint8_t *mask, uint8_t *flags, int nx, int ny, int nz, cudaStream_t s)
+void launch_flags(const uint8_t *mask, uint8_t *flags, int nx, int ny, int nz, bool xface_lo, bool xface_hi,
+                  cudaStream_t s)
 {
-    k_flags<<<1216, 256, 0, s>>>(mask, flags, nx, ny, nz);
+    k_flags<<<1216, 256, 0, s>>>(mask, flags, nx, ny, nz, xface_lo, xface_hi);
 }
+
 
 // ---------------------------------------------------------------------------
 // SplitMix64 (Steele, Lea & Flood 2014; Vigna's reference constants):
@@ -270,7 +283,8 @@ void launch_aux(int storage, AuxOp op, const StepArgs &a, bool odd, const AuxArg
     case 0: launch_aux_t<double>(op, a, odd, x, s); break;
     case 1: launch_aux_t<float>(op, a, odd, x, s); break;
     case 2: launch_aux_t<__half>(op, a, odd, x, s); break;
-    default: launch_aux_t<__nv_bfloat16>(op, a, odd, x, s); break;
+    case 3: launch_aux_t<__nv_bfloat16>(op, a, odd, x, s); break;
+    default: launch_aux_t<F16C>(op, a, odd, x, s); break;
     }
 }
 
@@ -280,10 +294,41 @@ void launch_mean_out(const double *msum, int64_t n, double inv_samples, bool f32
     else k_mean_out<double><<<grid_for(n, 256), 256, 0, s>>>(msum, n, inv_samples, (double *)out);
 }
 
+// FP32 snapshot box mean: one thread per half-resolution cell, 16-byte loads
+// of the (u, v, w, p) records (consecutive threads read consecutive pairs).
+__global__ void k_halfres_f4(const float4 *in, int nx, int ny, int nz, float4 *out)
+{
+    const int hx = (nx + 1) / 2, hy = (ny + 1) / 2, hz = (nz + 1) / 2;
+    const int64_t nh = (int64_t)hx * hy * hz;
+    for (int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; h < nh; h += (int64_t)gridDim.x * blockDim.x) {
+        const int X = (int)(h % hx), Y = (int)((h / hx) % hy), Z = (int)(h / ((int64_t)hx * hy));
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+        int cnt = 0;
+        for (int dz = 0; dz < 2; ++dz) {
+            const int z = 2 * Z + dz;
+            if (z >= nz) continue;
+            for (int dy = 0; dy < 2; ++dy) {
+                const int y = 2 * Y + dy;
+                if (y >= ny) continue;
+                const int64_t row = (int64_t)nx * (y + (int64_t)ny * z);
+                for (int dx = 0; dx < 2; ++dx) {
+                    const int x = 2 * X + dx;
+                    if (x >= nx) continue;
+                    const float4 v = in[row + x];
+                    acc.x += v.x; acc.y += v.y; acc.z += v.z; acc.w += v.w;
+                    ++cnt;
+                }
+            }
+        }
+        const float r = 1.0f / (float)cnt;
+        out[h] = make_float4(acc.x * r, acc.y * r, acc.z * r, acc.w * r);
+    }
+}
+
 void launch_halfres(const void *in, int nx, int ny, int nz, bool f32, void *out, cudaStream_t s)
 {
     const int64_t nh = (int64_t)((nx + 1) / 2) * ((ny + 1) / 2) * ((nz + 1) / 2);
-    if (f32) k_halfres<float><<<grid_for(nh, 256), 256, 0, s>>>((const float *)in, nx, ny, nz, (float *)out);
+    if (f32) k_halfres_f4<<<grid_for(nh, 256), 256, 0, s>>>((const float4 *)in, nx, ny, nz, (float4 *)out);
     else k_halfres<double><<<grid_for(nh, 256), 256, 0, s>>>((const double *)in, nx, ny, nz, (double *)out);
 }
 

@@ -30,12 +30,15 @@ __host__ __device__ constexpr double w_of(int i) { return tw(i % 3) * tw((i / 3)
 // Moments of t about the mean in one dimension: order 0 -> 1, 1 -> 0, 2 -> 1/3.
 __host__ __device__ constexpr double zw(int a) { return a == 0 ? 1.0 : (a == 1 ? 0.0 : 1.0 / 3.0); }
 
-// cell flag bits
-enum : uint8_t { CELL_SOLID = 1, CELL_EDGE = 2 };
+// cell classes: solid, edge (boundary-aware kernel), x-face (an inlet or
+// outlet plane cell whose only boundary links cross that x face; handled by
+// the row-end variant of the bulk kernel); 0 = bulk
+enum : uint8_t { CELL_SOLID = 1, CELL_EDGE = 2, CELL_XFACE = 4 };
 // face kinds (lbm_face)
 enum { FACE_WALL = 0, FACE_PERIODIC = 1, FACE_INLET = 2, FACE_OUTLET = 3 };
-// link kinds of the cell a population comes from (pull view)
-enum { LINK_FLUID = 0, LINK_WALL = 1, LINK_SOLID = 2, LINK_INLET = 3, LINK_OUTLET = 4 };
+// link kinds of the cell a population comes from (pull view); LINK_WRAP is a
+// fluid neighbour reached through a periodic face
+enum { LINK_FLUID = 0, LINK_WALL = 1, LINK_SOLID = 2, LINK_INLET = 3, LINK_OUTLET = 4, LINK_WRAP = 5 };
 // device status bits
 enum { STATUS_UNSTABLE = 1 };
 
@@ -64,6 +67,33 @@ template <> struct Store<__nv_bfloat16> {
     static __device__ __forceinline__ void st(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
 };
 
+// 16-bit custom float for shifted populations: sign, 4 exponent bits (bias
+// 15), 11 mantissa bits; normal range 2^-14 .. 2 - 2^-11, subnormal step
+// 2^-25.  Shifted populations of a stable flow stay well inside (-1, 1), so
+// one exponent bit of IEEE binary16 is traded for one more mantissa bit.
+// Encoding scales by 2^-112 so that the FP32 exponent field becomes the
+// 4-bit field, then rounds the 12 dropped mantissa bits to nearest-even;
+// magnitudes beyond the range (and non-finite values) saturate.
+struct F16C {
+    uint16_t bits;
+};
+template <> struct Store<F16C> {
+    using R = float;
+    static __device__ __forceinline__ float ld(const F16C *p)
+    {
+        const uint32_t b = p->bits;
+        return __uint_as_float(((b & 0x8000u) << 16) | ((b & 0x7FFFu) << 12)) * 0x1p112f;
+    }
+    static __device__ __forceinline__ void st(F16C *p, float v)
+    {
+        const uint32_t u = __float_as_uint(v * 0x1p-112f);
+        const uint32_t mag = u & 0x7FFFFFFFu;
+        uint32_t r = mag >= 0x7F800000u ? 0x7FFFu : (mag + 0x7FFu + ((mag >> 12) & 1u)) >> 12;
+        r = r > 0x7FFFu ? 0x7FFFu : r;
+        p->bits = (uint16_t)(((u >> 16) & 0x8000u) | r);
+    }
+};
+
 // ---------------------------------------------------------------------------
 // launch arguments shared by the step kernels (plain data, passed by value)
 // ---------------------------------------------------------------------------
@@ -71,7 +101,7 @@ struct StepArgs {
     void *pdf;              // 27 slots of `slot` elements each
     int64_t slot;
     const uint8_t *flags;   // per cell: CELL_SOLID / CELL_EDGE
-    const uint32_t *edge;   // edge-cell list
+    const uint4 *edge;      // edge-cell records {cell, link codes 0-8, 9-17, 18-26}
     int64_t n_edge;
     int nx, ny, nz;
     int64_t nxy, n;
@@ -79,6 +109,12 @@ struct StepArgs {
     int galilean;
     int face_x_lo, face_x_hi, face_y, face_z;
     double u_in, rho_in, rho_out;
+    // FP32 copies of the rates and boundary constants, so that FP32 kernels
+    // never touch the FP64 pipe
+    float w1f, w2f, w3f, u_in_f, rho_in_f, rho_out_f;
+    // byte offsets of the bulk accesses relative to the cell's slot-0 address:
+    // index 0/1 = even gather/scatter, 2/3 = odd gather/scatter
+    int64_t boff[4][27];
     void *ub;               // outlet plane velocity [nz*ny][3] (compute type)
     double *msum;           // mean sums [4][n] when this step is sampled, else null
     float *snap;            // full-resolution float4 target when snapshotting, else null
@@ -87,6 +123,11 @@ struct StepArgs {
     double *fout;           // force row of this step (3 doubles)
     int *status;            // latched device conditions
 };
+
+// A parameter in the compute type: the FP32 copy for float kernels.
+template <class R> __device__ __forceinline__ R pick(double d, float f);
+template <> __device__ __forceinline__ float pick<float>(double, float f) { return f; }
+template <> __device__ __forceinline__ double pick<double>(double d, float) { return d; }
 
 // ---------------------------------------------------------------------------
 // link classification (Sec. 3.1: velocity inlet, outflow, no-slip lateral
@@ -125,12 +166,13 @@ template <class R>
 __device__ __forceinline__ R boundary_value(const StepArgs &a, int kind, int i, R own, R ubx, R uby, R ubz)
 {
     const R w = R(w_of(i));
-    if (kind == LINK_INLET) return own + R(6) * w * R(a.rho_in) * (R(cx_of(i)) * R(a.u_in));
+    if (kind == LINK_INLET)
+        return own + R(6) * w * pick<R>(a.rho_in, a.rho_in_f) * (R(cx_of(i)) * pick<R>(a.u_in, a.u_in_f));
     if (kind == LINK_OUTLET) {
         const R cu = R(cx_of(i)) * ubx + R(cy_of(i)) * uby + R(cz_of(i)) * ubz;
         const R uu = ubx * ubx + uby * uby + ubz * ubz;
         // shifted form: -(own + w) + 2 w rho_out (1 + 4.5 cu^2 - 1.5 uu) - w
-        return -own + R(2) * w * (R(a.rho_out) * (R(1) + R(4.5) * cu * cu - R(1.5) * uu) - R(1));
+        return -own + R(2) * w * (pick<R>(a.rho_out, a.rho_out_f) * (R(1) + R(4.5) * cu * cu - R(1.5) * uu) - R(1));
     }
     return own;
 }
@@ -212,50 +254,108 @@ __device__ __forceinline__ void chimera_inverse(R *f, R ux, R uy, R uz)
             inv_line<R>(f[xi + 3 * yi], f[xi + 3 * yi + 9], f[xi + 3 * yi + 18], uz, R(tw(xi) * tw(yi)));
 }
 
+template <class R>
 struct Rates {
-    double w1, w2, w3;
+    R w1, w2, w3;
     int galilean;
 };
+
+template <class R>
+__device__ __forceinline__ Rates<R> rates_of(const StepArgs &a)
+{
+    return Rates<R>{pick<R>(a.w1, a.w1f), pick<R>(a.w2, a.w2f), pick<R>(a.w3, a.w3f), a.galilean};
+}
 
 // Cumulant collision of one cell, in place on the shifted populations f[27].
 // Returns the pre-collision density deviation and velocity.
 // PLAIN: every cumulant of order >= 3 relaxes to zero (omega_higher = 1).
 template <class R, bool PLAIN>
-__device__ __forceinline__ void collide(R *f, const Rates &rt, R &drho_out, R &ux, R &uy, R &uz)
+__device__ __forceinline__ void collide(R *f, const Rates<R> &rt, R &drho_out, R &ux, R &uy, R &uz)
 {
-    // macroscopic quantities (the weights carry no mass flux)
-    R drho = R(0), jx = R(0), jy = R(0), jz = R(0);
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        drho += f[i];
-        if (cx_of(i) == 1) jx += f[i];
-        if (cx_of(i) == -1) jx -= f[i];
-        if (cy_of(i) == 1) jy += f[i];
-        if (cy_of(i) == -1) jy -= f[i];
-        if (cz_of(i) == 1) jz += f[i];
-        if (cz_of(i) == -1) jz -= f[i];
-    }
-    const R rho = R(1) + drho;
-    const R ir = R(1) / rho;
-    ux = jx * ir;
-    uy = jy * ir;
-    uz = jz * ir;
-    drho_out = drho;
-
-    chimera_forward<R>(f, ux, uy, uz);
     R *m = f;
     const R third = R(1.0 / 3.0), ninth = R(1.0 / 9.0), t27 = R(1.0 / 27.0);
-
-    // second order: normalised deviations from the rest values (1/3 on the diagonal)
-    const R d200 = (m[MI(2, 0, 0)] - drho * third) * ir;
-    const R d020 = (m[MI(0, 2, 0)] - drho * third) * ir;
-    const R d002 = (m[MI(0, 0, 2)] - drho * third) * ir;
-    const R k110 = m[MI(1, 1, 0)] * ir, k101 = m[MI(1, 0, 1)] * ir, k011 = m[MI(0, 1, 1)] * ir;
+    R drho, rho, ir, d200, d020, d002, k110, k101, k011;
+    if (PLAIN) {
+        // Only density, momentum and the six second moments enter the
+        // relaxation when every higher cumulant is reset: take them as raw
+        // moments of the shifted populations by partial sums over x, y, z.
+        // (The weights carry no momentum and no off-diagonal second moment;
+        // their diagonal second moment 1/3 is the rest offset.)
+        R A0[9], A1[9], A2[9];   // per (y, z) line: sum f, sum cx f, sum cx^2 f
+#pragma unroll
+        for (int l = 0; l < 9; ++l) {
+            A2[l] = f[3 * l + 2] + f[3 * l];
+            A0[l] = A2[l] + f[3 * l + 1];
+            A1[l] = f[3 * l + 2] - f[3 * l];
+        }
+        R B00[3], B01[3], B02[3], B10[3], B11[3], B20[3];   // per z plane
+#pragma unroll
+        for (int zi = 0; zi < 3; ++zi) {
+            const int lm = 3 * zi, l0 = 3 * zi + 1, lp = 3 * zi + 2;
+            B02[zi] = A0[lp] + A0[lm];
+            B00[zi] = B02[zi] + A0[l0];
+            B01[zi] = A0[lp] - A0[lm];
+            B10[zi] = A1[lm] + A1[l0] + A1[lp];
+            B11[zi] = A1[lp] - A1[lm];
+            B20[zi] = A2[lm] + A2[l0] + A2[lp];
+        }
+        const R M002 = B00[2] + B00[0];
+        const R M000 = M002 + B00[1];
+        const R M001 = B00[2] - B00[0];
+        const R M010 = B01[0] + B01[1] + B01[2];
+        const R M011 = B01[2] - B01[0];
+        const R M020 = B02[0] + B02[1] + B02[2];
+        const R M100 = B10[0] + B10[1] + B10[2];
+        const R M101 = B10[2] - B10[0];
+        const R M110 = B11[0] + B11[1] + B11[2];
+        const R M200 = B20[0] + B20[1] + B20[2];
+        drho = M000;
+        rho = R(1) + drho;
+        ir = R(1) / rho;
+        ux = M100 * ir;
+        uy = M010 * ir;
+        uz = M001 * ir;
+        // central second moments minus their rest values: kappa_ab - delta_ab/3
+        d200 = ((M200 - M100 * ux) - drho * third) * ir;
+        d020 = ((M020 - M010 * uy) - drho * third) * ir;
+        d002 = ((M002 - M001 * uz) - drho * third) * ir;
+        k110 = (M110 - M100 * uy) * ir;
+        k101 = (M101 - M100 * uz) * ir;
+        k011 = (M011 - M010 * uz) * ir;
+    } else {
+        // macroscopic quantities (the weights carry no mass flux)
+        R jx = R(0), jy = R(0), jz = R(0);
+        drho = R(0);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            drho += f[i];
+            if (cx_of(i) == 1) jx += f[i];
+            if (cx_of(i) == -1) jx -= f[i];
+            if (cy_of(i) == 1) jy += f[i];
+            if (cy_of(i) == -1) jy -= f[i];
+            if (cz_of(i) == 1) jz += f[i];
+            if (cz_of(i) == -1) jz -= f[i];
+        }
+        rho = R(1) + drho;
+        ir = R(1) / rho;
+        ux = jx * ir;
+        uy = jy * ir;
+        uz = jz * ir;
+        chimera_forward<R>(f, ux, uy, uz);
+        // second order: normalised deviations from the rest values (1/3 on the diagonal)
+        d200 = (m[MI(2, 0, 0)] - drho * third) * ir;
+        d020 = (m[MI(0, 2, 0)] - drho * third) * ir;
+        d002 = (m[MI(0, 0, 2)] - drho * third) * ir;
+        k110 = m[MI(1, 1, 0)] * ir;
+        k101 = m[MI(1, 0, 1)] * ir;
+        k011 = m[MI(0, 1, 1)] * ir;
+    }
+    drho_out = drho;
 
     // relaxation of second order (shear rate on deviators and off-diagonals,
     // bulk rate on the trace), with the Galilean correction built from the
     // velocity-derivative estimates implied by the non-equilibrium moments
-    const R w1 = R(rt.w1), w2 = R(rt.w2);
+    const R w1 = rt.w1, w2 = rt.w2;
     const R Dxy = d200 - d020, Dxz = d200 - d002, dTr = d200 + d020 + d002;
     const R dxu = -R(0.5) * w1 * (R(2) * d200 - d020 - d002) - R(0.5) * w2 * dTr;
     const R dyv = dxu + R(1.5) * w1 * Dxy;
@@ -285,7 +385,7 @@ __device__ __forceinline__ void collide(R *f, const Rates &rt, R &drho_out, R &u
         s122 = s212 = s221 = R(0);
         e222s = R(0);
     } else {
-        const R w3 = R(rt.w3), r3 = R(1) - w3;
+        const R w3 = rt.w3, r3 = R(1) - w3;
         // third order: cumulants equal central moments
         const R k111 = m[MI(1, 1, 1)] * ir;
         const R k210 = m[MI(2, 1, 0)] * ir, k201 = m[MI(2, 0, 1)] * ir, k120 = m[MI(1, 2, 0)] * ir;

@@ -11,13 +11,15 @@ namespace lbm {
 
 // fused step (bulk + edge kernels) for one storage type
 void launch_step_f64(const StepArgs &a, bool odd, bool epi, bool plain, int block_x, cudaStream_t s,
-                    cudaEvent_t mid);
+                    cudaEvent_t ev_interior, cudaEvent_t ev_bulk);
 void launch_step_f32(const StepArgs &a, bool odd, bool epi, bool plain, int block_x, cudaStream_t s,
-                    cudaEvent_t mid);
+                    cudaEvent_t ev_interior, cudaEvent_t ev_bulk);
 void launch_step_f16(const StepArgs &a, bool odd, bool epi, bool plain, int block_x, cudaStream_t s,
-                    cudaEvent_t mid);
+                    cudaEvent_t ev_interior, cudaEvent_t ev_bulk);
 void launch_step_bf16(const StepArgs &a, bool odd, bool epi, bool plain, int block_x, cudaStream_t s,
-                    cudaEvent_t mid);
+                    cudaEvent_t ev_interior, cudaEvent_t ev_bulk);
+void launch_step_f16c(const StepArgs &a, bool odd, bool epi, bool plain, int block_x, cudaStream_t s,
+                      cudaEvent_t ev_interior, cudaEvent_t ev_bulk);
 
 enum AuxOp { AUX_NOISE, AUX_GATHER, AUX_SET, AUX_MACROS, AUX_TOTALS };
 
@@ -33,7 +35,8 @@ struct AuxArgs {
     int nblocks = 0;
 };
 
-void launch_flags(const uint8_t *mask, uint8_t *flags, int nx, int ny, int nz, cudaStream_t s);
+void launch_flags(const uint8_t *mask, uint8_t *flags, int nx, int ny, int nz, bool xface_lo, bool xface_hi,
+                  cudaStream_t s);
 void launch_aux(int storage, AuxOp op, const StepArgs &a, bool odd, const AuxArgs &x, cudaStream_t s);
 void launch_mean_out(const double *msum, int64_t n, double inv_samples, bool f32, void *out, cudaStream_t s);
 void launch_halfres(const void *in, int nx, int ny, int nz, bool f32, void *out, cudaStream_t s);

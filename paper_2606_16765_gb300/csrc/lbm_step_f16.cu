@@ -5,8 +5,8 @@
 
 namespace lbm {
 void launch_step_f16(const StepArgs &a, bool odd, bool epi, bool plain, int block_x, cudaStream_t s,
-                    cudaEvent_t mid)
+                    cudaEvent_t ev_interior, cudaEvent_t ev_bulk)
 {
-    launch_step_t<__half>(a, odd, epi, plain, block_x, s, mid);
+    launch_step_t<__half>(a, odd, epi, plain, block_x, s, ev_interior, ev_bulk);
 }
 }  // namespace lbm

@@ -16,9 +16,9 @@ import numpy as np
 _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "lib", "liblbm.so")
 
 LBM_OK, LBM_ERR_ARG, LBM_ERR_CUDA, LBM_ERR_OOM, LBM_ERR_UNSTABLE, LBM_ERR_TIMEOUT, LBM_ERR_STATE, LBM_ERR_IO = range(8)
-LBM_F64, LBM_F32, LBM_F16S, LBM_BF16S = range(4)
+LBM_F64, LBM_F32, LBM_F16S, LBM_BF16S, LBM_F16C = range(5)
 LBM_FACE_WALL, LBM_FACE_PERIODIC, LBM_FACE_INLET, LBM_FACE_OUTLET = range(4)
-STORAGE = {"f64": LBM_F64, "f32": LBM_F32, "f16s": LBM_F16S, "bf16s": LBM_BF16S}
+STORAGE = {"f64": LBM_F64, "f32": LBM_F32, "f16s": LBM_F16S, "bf16s": LBM_BF16S, "f16c": LBM_F16C}
 FACES = {"wall": LBM_FACE_WALL, "periodic": LBM_FACE_PERIODIC, "inlet": LBM_FACE_INLET, "outlet": LBM_FACE_OUTLET}
 
 
@@ -44,12 +44,13 @@ class lbm_params(C.Structure):
 class lbm_info(C.Structure):
     _fields_ = [("cells", C.c_int64), ("fluid_cells", C.c_int64), ("edge_cells", C.c_int64),
                 ("bulk_cells", C.c_int64), ("launches", C.c_int64), ("workspace_bytes", C.c_uint64),
-                ("storage", C.c_int32), ("block_x", C.c_int32), ("omega1", C.c_double)]
+                ("storage", C.c_int32), ("block_x", C.c_int32), ("omega1", C.c_double),
+                ("interior_cells", C.c_int64)]
 
 
 class lbm_timing_report(C.Structure):
     _fields_ = [("steps", C.c_int64), ("bulk_ms", C.c_double * 4), ("bulk_n", C.c_int64 * 4),
-                ("edge_ms", C.c_double), ("edge_n", C.c_int64)]
+                ("rowend_ms", C.c_double), ("edge_ms", C.c_double)]
 
 
 class LBMError(RuntimeError):
@@ -73,7 +74,7 @@ def lib():
         G, P = C.POINTER(lbm_grid), C.POINTER(lbm_params)
         sig = {
             "lbm_params_default": (None, [P]),
-            "lbm_workspace_bytes": (C.c_size_t, [G, P]),
+            "lbm_workspace_bytes": (C.c_size_t, [G, _vp, P]),
             "lbm_create": (C.c_int, [G, _vp, P, _vp, C.POINTER(_vp)]),
             "lbm_create_in": (C.c_int, [G, _vp, P, _vp, _vp, C.c_size_t, C.POINTER(_vp)]),
             "lbm_destroy": (C.c_int, [_vp]),
@@ -129,8 +130,8 @@ def lbm_params_default() -> lbm_params:
     return p
 
 
-def lbm_workspace_bytes(grid: lbm_grid, p: lbm_params) -> int:
-    return int(lib().lbm_workspace_bytes(C.byref(grid), C.byref(p)))
+def lbm_workspace_bytes(grid: lbm_grid, mask, p: lbm_params) -> int:
+    return int(lib().lbm_workspace_bytes(C.byref(grid), _ptr(mask) if mask is not None else None, C.byref(p)))
 
 
 def lbm_create(grid, mask, p, stream=None):
@@ -269,16 +270,16 @@ class Solver:
         self.shape = (grid[2], grid[1], grid[0])
         self.n = int(np.prod(grid))
         self._torch = torch
-        nbytes = lbm_workspace_bytes(self.grid, self.p)
-        if nbytes == 0:
-            raise LBMError(LBM_ERR_ARG, "invalid grid or parameters")
-        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
-        self.stream = torch.cuda.current_stream()
         m = None
         if mask is not None:
             m = np.ascontiguousarray(mask, dtype=np.uint8)
             assert m.shape == self.shape, (m.shape, self.shape)
         self._mask = m
+        nbytes = lbm_workspace_bytes(self.grid, m, self.p)
+        if nbytes == 0:
+            raise LBMError(LBM_ERR_ARG, "invalid grid or parameters")
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        self.stream = torch.cuda.current_stream()
         self.h = lbm_create_in(self.grid, m, self.p, self.stream.cuda_stream, self.workspace, nbytes)
 
     def close(self):
