@@ -227,6 +227,51 @@ def run_e2e(args, storage, d):
     return dict(seconds=t1 - t0, fluid=info.fluid_cells, h2d=mask.nbytes, d2h=mean.nbytes)
 
 
+def run_batch(steps, warmup, storage="f16s", n=32):
+    """32 seeded channels on uneven grids {128,192,256} x {64,96,128}^2, Re
+    log-uniform in [1e3, 1e4] on the channel height, stepped together by the
+    batched driver (graph-captured chunks, autotuned block shape), with the
+    FP64 time average every 10 steps and the obstacle force every step."""
+    import torch
+    from paper_2606_16765_gb300 import inputs as I
+    from paper_2606_16765_gb300.lbm import Batch
+
+    chans = I.batch_channels(0, n=n)
+    total = warmup + steps + 40
+    ms = []
+    for d in chans:
+        ms.append(dict(grid=d["grid"], mask=d["mask"], storage=storage, re=d["re"], u_in=d["u_in"],
+                       l_ref=d["l_ref"], mean_start=0, mean_end=10 ** 9, mean_every=10,
+                       force_every=1, force_capacity=total + 64))
+    b = Batch(ms)
+    bx, by, tune_ms = b.autotune(trials=2)
+    b.run(warmup)
+    b.sync()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    i0 = b.info()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    b.run(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    b.sync()
+    i1 = b.info()
+    t = e0.elapsed_time(e1)
+    ups = i1.lattice_updates - i0.lattice_updates
+    cells = sum(int((d["mask"] == 0).sum()) for d in chans)
+    out = {"value": ups / (t / 1e3) / 1e6, "unit": "MLUPS", "storage": storage, "members": n,
+           "fluid_cells": cells, "steps": int(i1.t - i0.t), "ms_per_step": t / max(1, i1.t - i0.t),
+           "block": [bx, by], "graph_captures": int(i1.graph_captures),
+           "graph_launches": int(i1.graph_launches - i0.graph_launches),
+           "gpu_launches": int(i1.kernel_launches - i0.kernel_launches),
+           "bytes_per_update": 54 * BYTES_PER_POP[storage]}
+    out["hbm_gbs"] = out["value"] * 1e6 * out["bytes_per_update"] / 1e9
+    b.close()
+    torch.cuda.empty_cache()
+    return out
+
+
 def cpu_baseline(d, seconds=12.0, box=(128, 96, 96)):
     """FP64 oracle on the host cores, on a sub-box of the same channel around
     the obstacle, stepped until ~`seconds` of CPU work."""
@@ -325,6 +370,7 @@ def main():
     ap.add_argument("--block-x", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -397,6 +443,8 @@ def main():
                 "interior_kernel_gbs": b2 * r2["info"].interior_cells / (t2 / 1e3) / 1e9,
                 "interior_kernel_frac": b2 * r2["info"].interior_cells / (t2 / 1e3) / 1e9 / peak,
                 "clocks": r2["clocks"]}
+        if not args.no_batch:
+            line["batch"] = run_batch(args.steps, 20)
         if not args.no_e2e:
             e = run_e2e(args, args.storage, d)
             line["e2e"] = {"value": e["fluid"] * K / e["seconds"] / 1e6, "unit": "MLUPS",

@@ -85,8 +85,9 @@ typedef struct {
     int32_t snap_halfres;   /* 1: 2x2x2 box mean (Sec. 3.1: half resolution)    */
     int32_t force_every;    /* record the obstacle force every n steps (0: off) */
     int64_t force_capacity; /* rows kept on the device between host flushes     */
-    int32_t block_x;        /* threads per block along x (0: library default)   */
-    int32_t reserved[7];
+    int32_t block_x;        /* threads per block along x, multiple of 32 (0: 128) */
+    int32_t block_y;        /* rows per block (0: 1); block_x * block_y <= 256   */
+    int32_t reserved[6];
 } lbm_params;
 
 /* Fill *p with the defaults listed above (re = 1000, u_in = 0.05, l_ref = 1,
@@ -202,6 +203,73 @@ lbm_status lbm_timing_read(lbm_ctx *ctx, lbm_timing_report *out, int32_t reset);
 /* Checkpoint: pdfs, time step, outlet plane, accumulators, force rows. */
 lbm_status lbm_save(lbm_ctx *ctx, const char *path);
 lbm_status lbm_load(lbm_ctx *ctx, const char *path);
+
+/* ------------------------------------------------------------------------
+ * Batches: many independent lattices (e.g. generated geometries on uneven
+ * grids at different Re, Sec. 2-3.1) stepped together.  Every step is one
+ * bulk launch and one edge launch over all unfinished members (blocks are
+ * numbered member after member); a chunk of steps is captured once as a CUDA
+ * graph on the batch's own stream and replayed.  Step-dependent work (time
+ * average sampling, force rows) is driven by a device step counter.
+ *
+ * Members are ordinary contexts owned by the batch: read them with the
+ * lbm_read_* / lbm_get_* calls through lbm_batch_member; do not step them
+ * directly.  Requirements: one storage for all members; the same
+ * omega_higher == 1 choice; no snapshots; if any member averages, all share
+ * one even mean_every and each mean_start is a multiple of it (the chunk
+ * length is mean_every, else 2); force_capacity must hold every recorded row.
+ * ------------------------------------------------------------------------ */
+typedef struct lbm_batch lbm_batch;
+
+lbm_status lbm_batch_create(int32_t n, const lbm_grid *grids, const uint8_t *const *masks,
+                            const lbm_params *params, void *cuda_stream, lbm_batch **out);
+lbm_status lbm_batch_destroy(lbm_batch *b);
+
+/* Last step of every member: member g runs t_end[g] steps (rounded up to a
+ * multiple of the chunk length). */
+lbm_status lbm_batch_set_end(lbm_batch *b, const int64_t *t_end);
+
+/* t_end[g] = ceil(n_ft * nx_g / u_in_g): n_ft flow-through times. */
+lbm_status lbm_batch_set_flowthroughs(lbm_batch *b, double n_ft);
+
+/* Advance every unfinished member by n steps (rounded up to whole chunks,
+ * stopping members at their end).  Asynchronous on the caller's stream. */
+lbm_status lbm_batch_run(lbm_batch *b, int64_t n);
+
+/* Run until every member reached its end. */
+lbm_status lbm_batch_run_to_end(lbm_batch *b);
+
+/* Wait for the batch; report latched device conditions of any member. */
+lbm_status lbm_batch_sync(lbm_batch *b);
+
+/* Borrow member g's context (valid until lbm_batch_destroy). */
+lbm_status lbm_batch_member(lbm_batch *b, int32_t g, lbm_ctx **ctx);
+
+typedef struct {
+    int64_t t;               /* steps taken by the batch                           */
+    int64_t chunk;           /* steps per captured graph                          */
+    int32_t members, live;   /* members, members not yet at their end             */
+    int32_t block_x, block_y;
+    int64_t graph_captures, graph_launches, kernel_launches;
+    int64_t lattice_updates; /* fluid cell updates performed so far               */
+} lbm_batch_info;
+
+lbm_status lbm_batch_get_info(const lbm_batch *b, lbm_batch_info *out);
+
+/* Autotuner.  Times each candidate block shape (block_x, block_y) for
+ * `trials` chunks (batch) or steps (context) on the real lattices, picks the
+ * fastest, and resets the lattices to rest (t = 0, accumulators cleared), so
+ * call it before the run.  With the environment variable LBM_AUTOTUNE_CACHE
+ * set to a file path, results are read from / written to that JSON file,
+ * keyed by device, storage, collision variant and grid sizes. */
+lbm_status lbm_batch_autotune(lbm_batch *b, int32_t trials, int32_t *best_block_x, int32_t *best_block_y,
+                              double *best_ms);
+lbm_status lbm_autotune(lbm_ctx *ctx, int32_t trials, int32_t *best_block_x, int32_t *best_block_y,
+                        double *best_ms);
+
+/* Return a context to rest: f = w, t = 0, accumulators, forces and
+ * snapshots cleared, instability latch reset. */
+lbm_status lbm_reset(lbm_ctx *ctx);
 
 /* Totals of a caller-owned population array, allocating nothing.
  *

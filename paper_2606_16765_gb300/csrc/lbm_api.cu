@@ -2,7 +2,9 @@
 // creation (cell flags, edge-cell list, device memory layout), the time loop
 // with its epilogue schedule (time average, snapshots, obstacle force), read
 // and write of the state, checkpoints.
+#include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -96,7 +98,7 @@ struct lbm_ctx {
     int64_t t = 0;
     double w1 = 0;
     bool plain = true;
-    int block_x = 128;
+    int block_x = 128, block_y = 1;
     int64_t msamples = 0;
     std::vector<char> snap_taken;
     std::vector<double> force_host;   // flushed rows (deviation part)
@@ -193,6 +195,8 @@ static std::string validate(const lbm_grid *g, const lbm_params *p)
     if (p->mean_every < 0 || p->snap_count < 0 || p->force_every < 0) return "negative schedule";
     if (p->snap_count > 0 && p->snap_every < 1) return "snap_every must be >= 1";
     if (p->block_x != 0 && (p->block_x % 32 != 0 || p->block_x > 256)) return "block_x must be a multiple of 32, <= 256";
+    if (p->block_y < 0 || (p->block_x ? p->block_x : 128) * (p->block_y ? p->block_y : 1) > 256)
+        return "block_x * block_y must be <= 256";
     return "";
 }
 
@@ -244,6 +248,7 @@ static lbm_status create_impl(const lbm_grid *g, const uint8_t *mask, const lbm_
     ctx->w1 = p->omega1 > 0 ? p->omega1 : 1.0 / (3.0 * p->u_in * p->l_ref / p->re + 0.5);
     ctx->plain = (p->omega_higher == 1.0);
     ctx->block_x = p->block_x ? p->block_x : 128;
+    ctx->block_y = p->block_y ? p->block_y : 1;
     ctx->force_cap = ctx->p.force_capacity;
     ctx->snap_taken.assign(std::max<int64_t>(0, p->snap_count), 0);
     const Layout &L = ctx->L;
@@ -428,11 +433,11 @@ static void step_launch(lbm_ctx *ctx, const StepArgs &a, bool odd, bool epi)
         }
     }
     switch (ctx->p.storage) {
-    case LBM_F64: launch_step_f64(a, odd, epi, ctx->plain, ctx->block_x, ctx->stream, e1, e2); break;
-    case LBM_F32: launch_step_f32(a, odd, epi, ctx->plain, ctx->block_x, ctx->stream, e1, e2); break;
-    case LBM_F16S: launch_step_f16(a, odd, epi, ctx->plain, ctx->block_x, ctx->stream, e1, e2); break;
-    case LBM_BF16S: launch_step_bf16(a, odd, epi, ctx->plain, ctx->block_x, ctx->stream, e1, e2); break;
-    default: launch_step_f16c(a, odd, epi, ctx->plain, ctx->block_x, ctx->stream, e1, e2); break;
+    case LBM_F64: launch_step_f64(a, odd, epi, ctx->plain, ctx->block_x, ctx->block_y, ctx->stream, e1, e2); break;
+    case LBM_F32: launch_step_f32(a, odd, epi, ctx->plain, ctx->block_x, ctx->block_y, ctx->stream, e1, e2); break;
+    case LBM_F16S: launch_step_f16(a, odd, epi, ctx->plain, ctx->block_x, ctx->block_y, ctx->stream, e1, e2); break;
+    case LBM_BF16S: launch_step_bf16(a, odd, epi, ctx->plain, ctx->block_x, ctx->block_y, ctx->stream, e1, e2); break;
+    default: launch_step_f16c(a, odd, epi, ctx->plain, ctx->block_x, ctx->block_y, ctx->stream, e1, e2); break;
     }
     if (e2) cudaEventRecord(e3, ctx->stream);
     ctx->launches += 1 + (a.n_edge > 0 ? 1 : 0);
@@ -813,6 +818,524 @@ extern "C" lbm_status lbm_timing_read(lbm_ctx *ctx, lbm_timing_report *out, int3
         ctx->ev_used = 0;
     }
     return LBM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// reset to rest
+// ---------------------------------------------------------------------------
+extern "C" lbm_status lbm_reset(lbm_ctx *ctx)
+{
+    if (!ctx) return LBM_ERR_ARG;
+    const Layout &L = ctx->L;
+    const lbm_params &p = ctx->p;
+    cudaStream_t s = ctx->stream;
+    CK(cudaStreamSynchronize(s));
+    CK(cudaMemsetAsync(ctx->base + L.pdf, 0, (size_t)Q * L.slot * storage_bytes(p.storage), s));
+    CK(cudaMemsetAsync(ctx->base + L.ub, 0, (size_t)3 * ctx->g.ny * ctx->g.nz * (p.storage == LBM_F64 ? 8 : 4), s));
+    if (p.mean_every > 0) CK(cudaMemsetAsync(ctx->base + L.msum, 0, (size_t)4 * L.n * 8, s));
+    if (p.force_every > 0) CK(cudaMemsetAsync(ctx->base + L.force, 0, (size_t)ctx->force_cap * 3 * 8, s));
+    CK(cudaMemsetAsync(ctx->base + L.fcount, 0, sizeof(unsigned), s));
+    CK(cudaMemsetAsync(ctx->base + L.status, 0, sizeof(int), s));
+    CK(cudaStreamSynchronize(s));
+    ctx->t = 0;
+    ctx->msamples = 0;
+    ctx->force_host.clear();
+    ctx->force_rows_dev = 0;
+    std::fill(ctx->snap_taken.begin(), ctx->snap_taken.end(), 0);
+    ctx->unstable = false;
+    ctx->ev_kind.clear();
+    ctx->ev_used = 0;
+    return LBM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// autotuner cache: a flat JSON object {"key": [block_x, block_y, ms], ...}
+// ---------------------------------------------------------------------------
+namespace {
+const int TUNE_CAND[][2] = {{64, 1}, {128, 1}, {256, 1}, {64, 2}, {128, 2}, {32, 4}, {32, 8}};
+constexpr int N_TUNE_CAND = 7;
+
+std::string tune_key(const std::string &what)
+{
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceProp pr;
+    std::string name = cudaGetDeviceProperties(&pr, dev) == cudaSuccess ? pr.name : "gpu";
+    for (char &ch : name)
+        if (ch == '"' || ch == ' ') ch = '_';
+    return name + "|" + what;
+}
+
+bool tune_lookup(const std::string &key, int *bx, int *by, double *ms)
+{
+    const char *path = std::getenv("LBM_AUTOTUNE_CACHE");
+    if (!path) return false;
+    FILE *fp = std::fopen(path, "rb");
+    if (!fp) return false;
+    std::string text;
+    char buf[4096];
+    size_t r;
+    while ((r = std::fread(buf, 1, sizeof buf, fp)) > 0) text.append(buf, r);
+    std::fclose(fp);
+    const std::string pat = "\"" + key + "\": [";
+    const size_t pos = text.find(pat);
+    if (pos == std::string::npos) return false;
+    return std::sscanf(text.c_str() + pos + pat.size(), "%d, %d, %lf", bx, by, ms) == 3;
+}
+
+void tune_store(const std::string &key, int bx, int by, double ms)
+{
+    const char *path = std::getenv("LBM_AUTOTUNE_CACHE");
+    if (!path) return;
+    std::vector<std::string> entries;
+    if (FILE *fp = std::fopen(path, "rb")) {
+        std::string text;
+        char buf[4096];
+        size_t r;
+        while ((r = std::fread(buf, 1, sizeof buf, fp)) > 0) text.append(buf, r);
+        std::fclose(fp);
+        size_t pos = 0;
+        while ((pos = text.find('"', pos)) != std::string::npos) {
+            const size_t end = text.find(']', pos);
+            if (end == std::string::npos) break;
+            std::string e = text.substr(pos, end - pos + 1);
+            if (e.compare(0, key.size() + 2, "\"" + key + "\"") != 0) entries.push_back(e);
+            pos = end + 1;
+        }
+    }
+    char line[512];
+    std::snprintf(line, sizeof line, "\"%s\": [%d, %d, %.6f]", key.c_str(), bx, by, ms);
+    entries.push_back(line);
+    const std::string tmp = std::string(path) + ".tmp";
+    if (FILE *fp = std::fopen(tmp.c_str(), "wb")) {
+        std::fputs("{\n", fp);
+        for (size_t k = 0; k < entries.size(); ++k)
+            std::fprintf(fp, "  %s%s\n", entries[k].c_str(), k + 1 < entries.size() ? "," : "");
+        std::fputs("}\n", fp);
+        std::fclose(fp);
+        std::rename(tmp.c_str(), path);
+    }
+}
+}  // namespace
+
+extern "C" lbm_status lbm_autotune(lbm_ctx *ctx, int32_t trials, int32_t *best_bx, int32_t *best_by, double *best_ms)
+{
+    if (!ctx || trials < 2) return ctx ? fail(ctx, LBM_ERR_ARG, "autotune needs trials >= 2") : LBM_ERR_ARG;
+    char what[256];
+    std::snprintf(what, sizeof what, "ctx|s%d|p%d|%dx%dx%d", ctx->p.storage, (int)ctx->plain, ctx->g.nx, ctx->g.ny,
+                  ctx->g.nz);
+    const std::string key = tune_key(what);
+    int bx = 0, by = 0;
+    double ms = 0;
+    if (!tune_lookup(key, &bx, &by, &ms)) {
+        cudaEvent_t e0, e1;
+        CK(cudaEventCreate(&e0));
+        CK(cudaEventCreate(&e1));
+        double best = 1e300;
+        const int64_t nt = trials + (trials & 1);
+        for (int c = 0; c < N_TUNE_CAND; ++c) {
+            ctx->block_x = TUNE_CAND[c][0];
+            ctx->block_y = TUNE_CAND[c][1];
+            lbm_status st = lbm_step(ctx, 2);        // warm-up
+            if (st == LBM_OK) {
+                cudaEventRecord(e0, ctx->stream);
+                st = lbm_step(ctx, nt);
+                cudaEventRecord(e1, ctx->stream);
+            }
+            if (st != LBM_OK || cudaEventSynchronize(e1) != cudaSuccess) {
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                return st != LBM_OK ? st : fail(ctx, LBM_ERR_CUDA, "autotune timing failed");
+            }
+            float t = 0.f;
+            cudaEventElapsedTime(&t, e0, e1);
+            if (t / nt < best) { best = t / nt; bx = ctx->block_x; by = ctx->block_y; }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        ms = best;
+        tune_store(key, bx, by, ms);
+    }
+    ctx->block_x = bx;
+    ctx->block_y = by;
+    if (best_bx) *best_bx = bx;
+    if (best_by) *best_by = by;
+    if (best_ms) *best_ms = ms;
+    return lbm_reset(ctx);
+}
+
+// ---------------------------------------------------------------------------
+// batches
+// ---------------------------------------------------------------------------
+struct lbm_batch {
+    std::vector<lbm_ctx *> members;
+    std::vector<int64_t> t_end;
+    int64_t t = 0;
+    int64_t chunk = 2;
+    int64_t mean_every = 0;
+    int storage = LBM_F32;
+    bool plain = true;
+    int block_x = 128, block_y = 1;
+    cudaStream_t user = nullptr, own = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    BatchMember *d_mem = nullptr;
+    int64_t *d_bbegin = nullptr, *d_ebegin = nullptr, *d_t = nullptr;
+    std::vector<int> live;              // members in the current table
+    BatchLaunch launch{};
+    cudaGraphExec_t graph = nullptr;
+    int64_t captures = 0, graph_launches = 0, kernel_launches = 0, updates = 0;
+    std::string err;
+};
+
+#define BCK(call)                                                                        \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess) {                                                         \
+            b->err = std::string(#call) + ": " + cudaGetErrorString(e_);                 \
+            g_err = b->err;                                                              \
+            return LBM_ERR_CUDA;                                                         \
+        }                                                                                \
+    } while (0)
+
+static lbm_status batch_fail(lbm_batch *b, lbm_status s, const std::string &m)
+{
+    if (b) b->err = m;
+    g_err = m;
+    return s;
+}
+
+extern "C" lbm_status lbm_batch_destroy(lbm_batch *b)
+{
+    if (!b) return LBM_ERR_ARG;
+    if (b->own) cudaStreamSynchronize(b->own);
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    if (b->d_mem) cudaFree(b->d_mem);
+    if (b->d_bbegin) cudaFree(b->d_bbegin);
+    if (b->d_ebegin) cudaFree(b->d_ebegin);
+    if (b->d_t) cudaFree(b->d_t);
+    if (b->ev_in) cudaEventDestroy(b->ev_in);
+    if (b->ev_out) cudaEventDestroy(b->ev_out);
+    if (b->own) cudaStreamDestroy(b->own);
+    for (lbm_ctx *c : b->members) lbm_destroy(c);
+    delete b;
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_batch_create(int32_t n, const lbm_grid *grids, const uint8_t *const *masks,
+                                       const lbm_params *params, void *cuda_stream, lbm_batch **out)
+{
+    if (!out || n < 1 || !grids || !params) return batch_fail(nullptr, LBM_ERR_ARG, "bad batch arguments");
+    *out = nullptr;
+    const lbm_params &p0 = params[0];
+    int64_t me = 0;
+    for (int g = 0; g < n; ++g) {
+        const lbm_params &p = params[g];
+        if (p.storage != p0.storage) return batch_fail(nullptr, LBM_ERR_ARG, "batch members need one storage");
+        if ((p.omega_higher == 1.0) != (p0.omega_higher == 1.0))
+            return batch_fail(nullptr, LBM_ERR_ARG, "batch members need the same omega_higher == 1 choice");
+        if (p.snap_count > 0) return batch_fail(nullptr, LBM_ERR_ARG, "batch members take no snapshots");
+        if (p.mean_every > 0) {
+            if (me && p.mean_every != me) return batch_fail(nullptr, LBM_ERR_ARG, "batch members need one mean_every");
+            me = p.mean_every;
+        }
+    }
+    if (me % 2 != 0) return batch_fail(nullptr, LBM_ERR_ARG, "mean_every must be even in a batch");
+    for (int g = 0; g < n; ++g)
+        if (params[g].mean_every > 0 && params[g].mean_start % me != 0)
+            return batch_fail(nullptr, LBM_ERR_ARG, "mean_start must be a multiple of mean_every in a batch");
+    lbm_batch *b = new lbm_batch();
+    b->user = static_cast<cudaStream_t>(cuda_stream);
+    b->mean_every = me;
+    b->chunk = me > 0 ? me : 2;
+    b->storage = p0.storage;
+    b->plain = p0.omega_higher == 1.0;
+    b->block_x = p0.block_x ? p0.block_x : 128;
+    b->block_y = p0.block_y ? p0.block_y : 1;
+    for (int g = 0; g < n; ++g) {
+        lbm_ctx *c = nullptr;
+        lbm_status st = lbm_create(&grids[g], masks ? masks[g] : nullptr, &params[g], cuda_stream, &c);
+        if (st != LBM_OK) {
+            const std::string m = "member " + std::to_string(g) + ": " + g_err;
+            lbm_batch_destroy(b);
+            return batch_fail(nullptr, st, m);
+        }
+        b->members.push_back(c);
+        b->t_end.push_back(INT64_MAX / 4);
+    }
+    lbm_status st = LBM_OK;
+    if (cudaStreamCreateWithFlags(&b->own, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming) != cudaSuccess ||
+        cudaMalloc(&b->d_mem, sizeof(BatchMember) * n) != cudaSuccess ||
+        cudaMalloc(&b->d_bbegin, sizeof(int64_t) * (n + 1)) != cudaSuccess ||
+        cudaMalloc(&b->d_ebegin, sizeof(int64_t) * (n + 1)) != cudaSuccess ||
+        cudaMalloc(&b->d_t, sizeof(int64_t)) != cudaSuccess ||
+        cudaMemset(b->d_t, 0, sizeof(int64_t)) != cudaSuccess)
+        st = LBM_ERR_CUDA;
+    if (st != LBM_OK) {
+        cudaGetLastError();
+        lbm_batch_destroy(b);
+        return batch_fail(nullptr, st, "batch device set-up failed");
+    }
+    *out = b;
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_batch_member(lbm_batch *b, int32_t g, lbm_ctx **ctx)
+{
+    if (!b || !ctx || g < 0 || g >= (int32_t)b->members.size()) return LBM_ERR_ARG;
+    *ctx = b->members[g];
+    return LBM_OK;
+}
+
+static int64_t round_chunk(const lbm_batch *b, int64_t v) { return (v + b->chunk - 1) / b->chunk * b->chunk; }
+
+extern "C" lbm_status lbm_batch_set_end(lbm_batch *b, const int64_t *t_end)
+{
+    if (!b || !t_end) return LBM_ERR_ARG;
+    for (size_t g = 0; g < b->members.size(); ++g) {
+        if (t_end[g] < 0) return batch_fail(b, LBM_ERR_ARG, "negative end step");
+        const lbm_ctx *c = b->members[g];
+        const int64_t te = round_chunk(b, t_end[g]);
+        if (c->p.force_every > 0 && te / c->p.force_every + 1 > c->force_cap)
+            return batch_fail(b, LBM_ERR_ARG, "force_capacity of member " + std::to_string(g) + " is too small");
+        b->t_end[g] = te;
+    }
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_batch_set_flowthroughs(lbm_batch *b, double n_ft)
+{
+    if (!b || !(n_ft >= 0)) return LBM_ERR_ARG;
+    std::vector<int64_t> te(b->members.size());
+    for (size_t g = 0; g < b->members.size(); ++g) {
+        const lbm_ctx *c = b->members[g];
+        if (!(c->p.u_in > 0)) return batch_fail(b, LBM_ERR_ARG, "flow-through time needs u_in > 0");
+        const double steps = n_ft * c->g.nx / c->p.u_in;
+        te[g] = (int64_t)std::ceil(steps * (1.0 - 1e-12));   // integral counts stay integral
+    }
+    return lbm_batch_set_end(b, te.data());
+}
+
+// Build the member table of the live members and capture one chunk as a graph.
+static lbm_status batch_rebuild(lbm_batch *b, const std::vector<int> &live)
+{
+    std::vector<BatchMember> mem(live.size());
+    std::vector<int64_t> bb(live.size() + 1, 0), eb(live.size() + 1, 0);
+    for (size_t k = 0; k < live.size(); ++k) {
+        lbm_ctx *c = b->members[live[k]];
+        BatchMember &M = mem[k];
+        std::memset(&M, 0, sizeof(M));
+        M.a = c->args();
+        M.a.fpart = c->at<double>(c->L.fpart);
+        M.msum = c->p.mean_every > 0 ? c->at<double>(c->L.msum) : nullptr;
+        M.mean_start = c->p.mean_start;
+        M.mean_end = c->p.mean_end;
+        M.mean_every = c->p.mean_every;
+        M.force = c->p.force_every > 0 ? c->at<double>(c->L.force) : nullptr;
+        M.force_every = c->p.force_every > 0 ? c->p.force_every : 1;
+        M.gx = (c->g.nx + b->block_x - 1) / b->block_x;
+        M.gy = (c->g.ny + b->block_y - 1) / b->block_y;
+        bb[k + 1] = bb[k] + (int64_t)M.gx * M.gy * c->g.nz;
+        eb[k + 1] = eb[k] + (c->n_edge + EDGE_BLOCK - 1) / EDGE_BLOCK;
+    }
+    if (bb.back() >= (int64_t(1) << 31) || eb.back() >= (int64_t(1) << 31))
+        return batch_fail(b, LBM_ERR_ARG, "batch too large for one launch");
+    BCK(cudaMemcpyAsync(b->d_mem, mem.data(), sizeof(BatchMember) * mem.size(), cudaMemcpyHostToDevice, b->own));
+    BCK(cudaMemcpyAsync(b->d_bbegin, bb.data(), sizeof(int64_t) * bb.size(), cudaMemcpyHostToDevice, b->own));
+    BCK(cudaMemcpyAsync(b->d_ebegin, eb.data(), sizeof(int64_t) * eb.size(), cudaMemcpyHostToDevice, b->own));
+    BCK(cudaStreamSynchronize(b->own));
+    b->launch = BatchLaunch{b->d_mem, b->d_bbegin, b->d_ebegin, (int)live.size(), bb.back(), eb.back(), b->d_t,
+                            b->block_x, b->block_y};
+    if (b->graph) {
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+    }
+    cudaGraph_t graph;
+    BCK(cudaStreamBeginCapture(b->own, cudaStreamCaptureModeThreadLocal));
+    for (int64_t k = 0; k < b->chunk; ++k) {
+        const bool odd = (k & 1) != 0;
+        const bool epi = b->mean_every > 0 && k == 0;   // chunks start at multiples of mean_every
+        switch (b->storage) {
+        case LBM_F64: launch_batch_step_f64(b->launch, odd, epi, b->plain, b->own); break;
+        case LBM_F32: launch_batch_step_f32(b->launch, odd, epi, b->plain, b->own); break;
+        case LBM_F16S: launch_batch_step_f16(b->launch, odd, epi, b->plain, b->own); break;
+        case LBM_BF16S: launch_batch_step_bf16(b->launch, odd, epi, b->plain, b->own); break;
+        default: launch_batch_step_f16c(b->launch, odd, epi, b->plain, b->own); break;
+        }
+    }
+    const cudaError_t ce = cudaStreamEndCapture(b->own, &graph);
+    if (ce != cudaSuccess) return batch_fail(b, LBM_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
+    const cudaError_t ie = cudaGraphInstantiate(&b->graph, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) return batch_fail(b, LBM_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ie));
+    b->live = live;
+    b->captures++;
+    return LBM_OK;
+}
+
+// Bring the member contexts' host bookkeeping to batch time t.
+static void batch_sync_members(lbm_batch *b)
+{
+    for (size_t g = 0; g < b->members.size(); ++g) {
+        lbm_ctx *c = b->members[g];
+        const int64_t tm = std::min(b->t, b->t_end[g]);
+        c->t = tm;
+        const lbm_params &p = c->p;
+        if (p.mean_every > 0) {
+            const int64_t hi = std::min(tm, p.mean_end);
+            c->msamples = hi > p.mean_start ? (hi - p.mean_start + p.mean_every - 1) / p.mean_every : 0;
+        }
+        if (p.force_every > 0) {
+            c->force_host.clear();
+            c->force_rows_dev = (tm + p.force_every - 1) / p.force_every;
+        }
+    }
+}
+
+extern "C" lbm_status lbm_batch_run(lbm_batch *b, int64_t nsteps)
+{
+    if (!b || nsteps < 0) return LBM_ERR_ARG;
+    for (lbm_ctx *c : b->members)
+        if (c->unstable) return batch_fail(b, LBM_ERR_STATE, "a member is unstable; steps refused");
+    const int64_t target = b->t + round_chunk(b, nsteps);
+    BCK(cudaEventRecord(b->ev_in, b->user));
+    BCK(cudaStreamWaitEvent(b->own, b->ev_in, 0));
+    while (b->t < target) {
+        std::vector<int> live;
+        int64_t seg_end = target;
+        for (size_t g = 0; g < b->members.size(); ++g)
+            if (b->t < b->t_end[g]) {
+                live.push_back((int)g);
+                seg_end = std::min(seg_end, b->t_end[g]);
+            }
+        if (live.empty()) break;
+        if (!b->graph || live != b->live) {
+            lbm_status st = batch_rebuild(b, live);
+            if (st != LBM_OK) return st;
+        }
+        const int64_t chunks = (seg_end - b->t) / b->chunk;
+        for (int64_t k = 0; k < chunks; ++k) BCK(cudaGraphLaunch(b->graph, b->own));
+        int64_t cells = 0;
+        for (int g : live) cells += b->members[g]->n_fluid;
+        b->updates += cells * (seg_end - b->t);
+        b->graph_launches += chunks;
+        b->kernel_launches += chunks * b->chunk * (2 + (b->launch.edge_blocks > 0 ? 1 : 0));
+        b->t = seg_end;
+    }
+    BCK(cudaEventRecord(b->ev_out, b->own));
+    BCK(cudaStreamWaitEvent(b->user, b->ev_out, 0));
+    batch_sync_members(b);
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_batch_run_to_end(lbm_batch *b)
+{
+    if (!b) return LBM_ERR_ARG;
+    int64_t te = 0;
+    for (int64_t v : b->t_end) te = std::max(te, v);
+    if (te >= INT64_MAX / 4) return batch_fail(b, LBM_ERR_STATE, "member ends not set");
+    return te > b->t ? lbm_batch_run(b, te - b->t) : LBM_OK;
+}
+
+extern "C" lbm_status lbm_batch_sync(lbm_batch *b)
+{
+    if (!b) return LBM_ERR_ARG;
+    BCK(cudaStreamSynchronize(b->own));
+    for (size_t g = 0; g < b->members.size(); ++g) {
+        const lbm_status st = lbm_sync(b->members[g]);
+        if (st != LBM_OK) return batch_fail(b, st, "member " + std::to_string(g) + ": " + b->members[g]->err);
+    }
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_batch_get_info(const lbm_batch *b, lbm_batch_info *out)
+{
+    if (!b || !out) return LBM_ERR_ARG;
+    std::memset(out, 0, sizeof(*out));
+    out->t = b->t;
+    out->chunk = b->chunk;
+    out->members = (int32_t)b->members.size();
+    for (size_t g = 0; g < b->members.size(); ++g) out->live += b->t < b->t_end[g];
+    out->block_x = b->block_x;
+    out->block_y = b->block_y;
+    out->graph_captures = b->captures;
+    out->graph_launches = b->graph_launches;
+    out->kernel_launches = b->kernel_launches;
+    out->lattice_updates = b->updates;
+    return LBM_OK;
+}
+
+static lbm_status batch_reset(lbm_batch *b)
+{
+    BCK(cudaStreamSynchronize(b->own));
+    for (lbm_ctx *c : b->members) {
+        const lbm_status st = lbm_reset(c);
+        if (st != LBM_OK) return st;
+    }
+    BCK(cudaMemset(b->d_t, 0, sizeof(int64_t)));
+    b->t = 0;
+    b->updates = 0;
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_batch_autotune(lbm_batch *b, int32_t trials, int32_t *best_bx, int32_t *best_by,
+                                         double *best_ms)
+{
+    if (!b || trials < 1) return LBM_ERR_ARG;
+    int64_t cells = 0;
+    for (lbm_ctx *c : b->members) cells += c->L.n;
+    char what[256];
+    std::snprintf(what, sizeof what, "batch|s%d|p%d|n%zu|cells%lld", b->storage, (int)b->plain, b->members.size(),
+                  (long long)cells);
+    const std::string key = tune_key(what);
+    int bx = 0, by = 0;
+    double ms = 0;
+    if (!tune_lookup(key, &bx, &by, &ms)) {
+        std::vector<int64_t> saved = b->t_end;
+        std::vector<int64_t> big(b->members.size(), INT64_MAX / 4);
+        b->t_end = big;
+        cudaEvent_t e0, e1;
+        BCK(cudaEventCreate(&e0));
+        BCK(cudaEventCreate(&e1));
+        double best = 1e300;
+        for (int c = 0; c < N_TUNE_CAND; ++c) {
+            b->block_x = TUNE_CAND[c][0];
+            b->block_y = TUNE_CAND[c][1];
+            b->graph_launches = 0;
+            lbm_status st = lbm_batch_run(b, b->chunk);          // capture + warm-up
+            if (st == LBM_OK) {
+                cudaEventRecord(e0, b->user);
+                st = lbm_batch_run(b, (int64_t)trials * b->chunk);
+                cudaEventRecord(e1, b->user);
+            }
+            if (st != LBM_OK || cudaEventSynchronize(e1) != cudaSuccess) {
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                b->t_end = saved;
+                return st != LBM_OK ? st : batch_fail(b, LBM_ERR_CUDA, "autotune timing failed");
+            }
+            float t = 0.f;
+            cudaEventElapsedTime(&t, e0, e1);
+            const double per = t / ((double)trials * b->chunk);
+            if (per < best) { best = per; bx = b->block_x; by = b->block_y; }
+            if (b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        b->t_end = saved;
+        ms = best;
+        tune_store(key, bx, by, ms);
+    }
+    b->block_x = bx;
+    b->block_y = by;
+    if (b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }
+    b->live.clear();
+    b->graph_launches = b->kernel_launches = 0;
+    if (best_bx) *best_bx = bx;
+    if (best_by) *best_by = by;
+    if (best_ms) *best_ms = ms;
+    return batch_reset(b);
 }
 
 extern "C" const char *lbm_last_error(const lbm_ctx *ctx)

@@ -124,6 +124,28 @@ struct StepArgs {
     int *status;            // latched device conditions
 };
 
+// Member of a batched launch (device memory): the static arguments of the
+// member lattice plus its schedule.
+struct BatchMember {
+    StepArgs a;             // static fields (msum/snap/fout of `a` unused)
+    double *msum;           // mean sums (null: no time average)
+    int64_t mean_start, mean_end, mean_every;
+    double *force;          // force rows indexed by t / force_every (null: off)
+    int64_t force_every;
+    int32_t gx, gy;         // bulk blocks along x and y per z plane
+};
+
+// One batched step: device member table and block numbering.
+struct BatchLaunch {
+    const BatchMember *mem;
+    const int64_t *bulk_begin;  // nm + 1 entries (first bulk block per member)
+    const int64_t *edge_begin;  // nm + 1 entries (first edge block per member)
+    int nm;
+    int64_t bulk_blocks, edge_blocks;
+    int64_t *t;                 // device step counter
+    int block_x, block_y;
+};
+
 // A parameter in the compute type: the FP32 copy for float kernels.
 template <class R> __device__ __forceinline__ R pick(double d, float f);
 template <> __device__ __forceinline__ float pick<float>(double, float f) { return f; }

@@ -10,16 +10,21 @@
 namespace lbm {
 
 // fused step (bulk + edge kernels) for one storage type
-void launch_step_f64(const StepArgs &a, bool odd, bool epi, bool plain, int block_x, cudaStream_t s,
-                    cudaEvent_t ev_interior, cudaEvent_t ev_bulk);
-void launch_step_f32(const StepArgs &a, bool odd, bool epi, bool plain, int block_x, cudaStream_t s,
-                    cudaEvent_t ev_interior, cudaEvent_t ev_bulk);
-void launch_step_f16(const StepArgs &a, bool odd, bool epi, bool plain, int block_x, cudaStream_t s,
-                    cudaEvent_t ev_interior, cudaEvent_t ev_bulk);
-void launch_step_bf16(const StepArgs &a, bool odd, bool epi, bool plain, int block_x, cudaStream_t s,
-                    cudaEvent_t ev_interior, cudaEvent_t ev_bulk);
-void launch_step_f16c(const StepArgs &a, bool odd, bool epi, bool plain, int block_x, cudaStream_t s,
-                      cudaEvent_t ev_interior, cudaEvent_t ev_bulk);
+void launch_step_f64(const StepArgs &a, bool odd, bool epi, bool plain, int block_x, int block_y,
+                    cudaStream_t s, cudaEvent_t ev_interior, cudaEvent_t ev_bulk);
+void launch_batch_step_f64(const BatchLaunch &L, bool odd, bool epi, bool plain, cudaStream_t s);
+void launch_step_f32(const StepArgs &a, bool odd, bool epi, bool plain, int block_x, int block_y,
+                    cudaStream_t s, cudaEvent_t ev_interior, cudaEvent_t ev_bulk);
+void launch_batch_step_f32(const BatchLaunch &L, bool odd, bool epi, bool plain, cudaStream_t s);
+void launch_step_f16(const StepArgs &a, bool odd, bool epi, bool plain, int block_x, int block_y,
+                    cudaStream_t s, cudaEvent_t ev_interior, cudaEvent_t ev_bulk);
+void launch_batch_step_f16(const BatchLaunch &L, bool odd, bool epi, bool plain, cudaStream_t s);
+void launch_step_bf16(const StepArgs &a, bool odd, bool epi, bool plain, int block_x, int block_y,
+                    cudaStream_t s, cudaEvent_t ev_interior, cudaEvent_t ev_bulk);
+void launch_batch_step_bf16(const BatchLaunch &L, bool odd, bool epi, bool plain, cudaStream_t s);
+void launch_step_f16c(const StepArgs &a, bool odd, bool epi, bool plain, int block_x, int block_y,
+                    cudaStream_t s, cudaEvent_t ev_interior, cudaEvent_t ev_bulk);
+void launch_batch_step_f16c(const BatchLaunch &L, bool odd, bool epi, bool plain, cudaStream_t s);
 
 enum AuxOp { AUX_NOISE, AUX_GATHER, AUX_SET, AUX_MACROS, AUX_TOTALS };
 

@@ -19,18 +19,32 @@
 
 namespace lbm {
 
-template <class R>
-__device__ __forceinline__ void epilogue(const StepArgs &a, int64_t c, R drho, R ux, R uy, R uz)
+// Per-step outputs of the epilogues (null when not produced this step).
+struct StepOut {
+    double *msum;           // mean sums [4][n]
+    float *snap;            // full-resolution float4 snapshot target
+    double *fpart;          // force partials per edge block
+    unsigned int *fcount;   // arrival counter of the force reduction
+    double *fout;           // force row of this step
+};
+
+__device__ __forceinline__ StepOut step_out(const StepArgs &a)
 {
-    if (a.msum) {
-        a.msum[c] += (double)drho;
-        a.msum[a.n + c] += (double)ux;
-        a.msum[2 * a.n + c] += (double)uy;
-        a.msum[3 * a.n + c] += (double)uz;
+    return StepOut{a.msum, a.snap, a.fpart, a.fcount, a.fout};
+}
+
+template <class R>
+__device__ __forceinline__ void epilogue(const StepArgs &a, const StepOut &o, int64_t c, R drho, R ux, R uy, R uz)
+{
+    if (o.msum) {
+        o.msum[c] += (double)drho;
+        o.msum[a.n + c] += (double)ux;
+        o.msum[2 * a.n + c] += (double)uy;
+        o.msum[3 * a.n + c] += (double)uz;
     }
-    if (a.snap) {
+    if (o.snap) {
         float4 v = make_float4((float)ux, (float)uy, (float)uz, (float)(drho * R(1.0 / 3.0)));
-        reinterpret_cast<float4 *>(a.snap)[c] = v;
+        reinterpret_cast<float4 *>(o.snap)[c] = v;
     }
 }
 
@@ -43,14 +57,11 @@ __device__ __forceinline__ void epilogue(const StepArgs &a, int64_t c, R drho, R
 // the x face to the cell's own slot, like the edge kernel; every other warp
 // runs the plain gather/scatter.
 template <class S, bool ODD, bool EPI, bool PLAIN>
-__global__ void __launch_bounds__(256) k_step_bulk(StepArgs a)
+__device__ __forceinline__ void bulk_cell(const StepArgs &a, const StepOut &o, int x, int y, int z)
 {
     using T = Store<S>;
     using R = typename T::R;
-    const int x = (int)(blockIdx.x * blockDim.x + threadIdx.x);
-    if (x >= a.nx) return;
-    const int y = (int)blockIdx.y;
-    const int64_t c = (int64_t)x + (int64_t)a.nx * ((int64_t)y + (int64_t)a.ny * blockIdx.z);
+    const int64_t c = (int64_t)x + (int64_t)a.nx * ((int64_t)y + (int64_t)a.ny * z);
     const uint8_t fl = a.flags[c];
     if (fl != 0 && fl != CELL_XFACE) return;   // solid or edge cell
     // warp-uniform: does this warp hold x = 0 or x = nx - 1?
@@ -62,7 +73,7 @@ __global__ void __launch_bounds__(256) k_step_bulk(StepArgs a)
     const int hi_kind = a.face_x_hi == FACE_OUTLET ? LINK_OUTLET : LINK_WALL;
     S *p = static_cast<S *>(a.pdf);
     R *ub = static_cast<R *>(a.ub);
-    const int64_t pl = 3 * ((int64_t)y + (int64_t)a.ny * blockIdx.z);
+    const int64_t pl = 3 * ((int64_t)y + (int64_t)a.ny * z);
     const char *q = reinterpret_cast<const char *>(p) + c * (int64_t)sizeof(S);
     const int64_t *gof = a.boff[ODD ? 2 : 0], *sof = a.boff[ODD ? 3 : 1];
     R f[Q];
@@ -85,7 +96,7 @@ __global__ void __launch_bounds__(256) k_step_bulk(StepArgs a)
     R drho, ux, uy, uz;
     collide<R, PLAIN>(f, rates_of<R>(a), drho, ux, uy, uz);
     check_density(drho, a.status);
-    if (EPI) epilogue<R>(a, c, drho, ux, uy, uz);
+    if (EPI) epilogue<R>(a, o, c, drho, ux, uy, uz);
     // the outlet condition of the next (odd) step uses this step's velocity
     if (!ODD && hi && a.face_x_hi == FACE_OUTLET) {
         ub[pl] = ux;
@@ -111,10 +122,21 @@ __global__ void __launch_bounds__(256) k_step_bulk(StepArgs a)
     }
 }
 
+// Single-grid bulk kernel: grid (ceil(nx / blockDim.x), ceil(ny / blockDim.y), nz).
+template <class S, bool ODD, bool EPI, bool PLAIN>
+__global__ void __launch_bounds__(256) k_step_bulk(StepArgs a)
+{
+    const int x = (int)(blockIdx.x * blockDim.x + threadIdx.x);
+    const int y = (int)(blockIdx.y * blockDim.y + threadIdx.y);
+    if (x >= a.nx || y >= a.ny) return;
+    bulk_cell<S, ODD, EPI, PLAIN>(a, step_out(a), x, y, (int)blockIdx.z);
+}
+
 // Sum a double over the block into partials[blockIdx]; the last block to
 // arrive adds the partials in a fixed order and writes the result, so the
 // value does not depend on block scheduling.
-__device__ __forceinline__ void block_force_reduce(const StepArgs &a, double fx, double fy, double fz)
+__device__ __forceinline__ void block_force_reduce(const StepOut &o, int64_t blk, int64_t nblk, double fx, double fy,
+                                                   double fz)
 {
     __shared__ double sh[3][EDGE_BLOCK / 32];
     __shared__ bool last;
@@ -131,10 +153,10 @@ __device__ __forceinline__ void block_force_reduce(const StepArgs &a, double fx,
         double s[3] = {0, 0, 0};
         for (int w = 0; w < EDGE_BLOCK / 32; ++w)
             for (int d = 0; d < 3; ++d) s[d] += sh[d][w];
-        for (int d = 0; d < 3; ++d) a.fpart[3 * (int64_t)blockIdx.x + d] = s[d];
+        for (int d = 0; d < 3; ++d) o.fpart[3 * blk + d] = s[d];
         __threadfence();
-        const unsigned prev = atomicAdd(a.fcount, 1u);
-        last = (prev == gridDim.x - 1);
+        const unsigned prev = atomicAdd(o.fcount, 1u);
+        last = (prev == (unsigned)(nblk - 1));
     }
     __syncthreads();
     if (!last) return;
@@ -142,8 +164,8 @@ __device__ __forceinline__ void block_force_reduce(const StepArgs &a, double fx,
     // fixed-order tree: each thread sums a strided subset, then a shared tree
     __shared__ double tr[3][EDGE_BLOCK];
     double s[3] = {0, 0, 0};
-    for (int64_t b = threadIdx.x; b < gridDim.x; b += EDGE_BLOCK)
-        for (int d = 0; d < 3; ++d) s[d] += ((volatile double *)a.fpart)[3 * b + d];
+    for (int64_t b = threadIdx.x; b < nblk; b += EDGE_BLOCK)
+        for (int d = 0; d < 3; ++d) s[d] += ((volatile double *)o.fpart)[3 * b + d];
     for (int d = 0; d < 3; ++d) tr[d][threadIdx.x] = s[d];
     __syncthreads();
     for (int h = EDGE_BLOCK / 2; h > 0; h >>= 1) {
@@ -152,8 +174,8 @@ __device__ __forceinline__ void block_force_reduce(const StepArgs &a, double fx,
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        for (int d = 0; d < 3; ++d) a.fout[d] = tr[d][0];
-        *a.fcount = 0u;
+        for (int d = 0; d < 3; ++d) o.fout[d] = tr[d][0];
+        *o.fcount = 0u;
     }
 }
 
@@ -181,13 +203,13 @@ __device__ __forceinline__ int64_t wrapped_neighbour(const StepArgs &a, uint32_t
 // Edge cells: one thread per record of the compact list; the link codes were
 // classified once at creation.
 template <class S, bool ODD, bool PLAIN>
-__global__ void __launch_bounds__(EDGE_BLOCK) k_step_edge(StepArgs a)
+__device__ __forceinline__ void edge_cell(const StepArgs &a, const StepOut &o, int64_t k,
+                                          typename Store<S>::R &fx, typename Store<S>::R &fy,
+                                          typename Store<S>::R &fz)
 {
     using T = Store<S>;
     using R = typename T::R;
-    const int64_t k = (int64_t)blockIdx.x * EDGE_BLOCK + threadIdx.x;
-    R fx = R(0), fy = R(0), fz = R(0);     // this cell's obstacle force
-    if (k < a.n_edge) {
+    {
         const uint4 e = a.edge[k];
         const uint32_t c32 = e.x;
         const int64_t c = c32;
@@ -217,7 +239,7 @@ __global__ void __launch_bounds__(EDGE_BLOCK) k_step_edge(StepArgs a)
         R drho, ux, uy, uz;
         collide<R, PLAIN>(f, rates_of<R>(a), drho, ux, uy, uz);
         check_density(drho, a.status);
-        epilogue<R>(a, c, drho, ux, uy, uz);
+        epilogue<R>(a, o, c, drho, ux, uy, uz);
         // the outlet condition of the next (odd) step uses this step's velocity
         if (!ODD && x == a.nx - 1 && a.face_x_hi == FACE_OUTLET) {
             ub[pl] = ux;
@@ -249,28 +271,135 @@ __global__ void __launch_bounds__(EDGE_BLOCK) k_step_edge(StepArgs a)
             }
         }
     }
-    if (a.fpart) block_force_reduce(a, (double)fx, (double)fy, (double)fz);
+}
+
+// Single-grid edge kernel: one thread per record of the compact list.
+template <class S, bool ODD, bool PLAIN>
+__global__ void __launch_bounds__(EDGE_BLOCK) k_step_edge(StepArgs a)
+{
+    using R = typename Store<S>::R;
+    const int64_t k = (int64_t)blockIdx.x * EDGE_BLOCK + threadIdx.x;
+    const StepOut o = step_out(a);
+    R fx = R(0), fy = R(0), fz = R(0);     // this cell's obstacle force
+    if (k < a.n_edge) edge_cell<S, ODD, PLAIN>(a, o, k, fx, fy, fz);
+    if (o.fpart) block_force_reduce(o, blockIdx.x, gridDim.x, (double)fx, (double)fy, (double)fz);
 }
 
 template <class S, bool ODD, bool EPI, bool PLAIN>
-static void launch_bulk(const StepArgs &a, int block_x, cudaStream_t s, cudaEvent_t ev_interior)
+static void launch_bulk(const StepArgs &a, int block_x, int block_y, cudaStream_t s, cudaEvent_t ev_interior)
 {
-    const dim3 grd((a.nx + block_x - 1) / block_x, a.ny, a.nz);
-    k_step_bulk<S, ODD, EPI, PLAIN><<<grd, block_x, 0, s>>>(a);
+    const dim3 grd((a.nx + block_x - 1) / block_x, (a.ny + block_y - 1) / block_y, a.nz);
+    k_step_bulk<S, ODD, EPI, PLAIN><<<grd, dim3(block_x, block_y), 0, s>>>(a);
     if (ev_interior) cudaEventRecord(ev_interior, s);
 }
 
+// ---------------------------------------------------------------------------
+// batched launches: one bulk and one edge launch per step over every member
+// lattice of a batch.  Blocks are numbered member after member; a block finds
+// its member by binary search over the members' first block numbers.
+// Quantities that depend on the step (time-average sampling, force row) come
+// from the device step counter, so a captured sequence of steps can be
+// replayed unchanged.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int find_member(const int64_t *begin, int nm, int64_t b)
+{
+    int lo = 0, hi = nm - 1;                 // largest m with begin[m] <= b
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (begin[mid] <= b) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ bool samples_at(const BatchMember &B, int64_t t)
+{
+    return B.msum && B.mean_every > 0 && t >= B.mean_start && t < B.mean_end && (t - B.mean_start) % B.mean_every == 0;
+}
+
+template <class S, bool ODD, bool EPI, bool PLAIN>
+__global__ void __launch_bounds__(256) k_batch_bulk(const BatchMember *mem, const int64_t *begin, int nm,
+                                                    const int64_t *tdev)
+{
+    const int m = find_member(begin, nm, blockIdx.x);
+    const BatchMember &B = mem[m];
+    const int64_t local = (int64_t)blockIdx.x - begin[m];
+    const int bx = (int)(local % B.gx);
+    const int64_t r = local / B.gx;
+    const int by = (int)(r % B.gy);
+    const int z = (int)(r / B.gy);
+    const int x = bx * (int)blockDim.x + (int)threadIdx.x;
+    const int y = by * (int)blockDim.y + (int)threadIdx.y;
+    if (x >= B.a.nx || y >= B.a.ny) return;
+    StepOut o{nullptr, nullptr, nullptr, nullptr, nullptr};
+    if (EPI && samples_at(B, *tdev)) o.msum = B.msum;
+    bulk_cell<S, ODD, EPI, PLAIN>(B.a, o, x, y, z);
+}
+
+template <class S, bool ODD, bool PLAIN>
+__global__ void __launch_bounds__(EDGE_BLOCK) k_batch_edge(const BatchMember *mem, const int64_t *begin, int nm,
+                                                           const int64_t *tdev, int epi)
+{
+    using R = typename Store<S>::R;
+    const int m = find_member(begin, nm, blockIdx.x);
+    const BatchMember &B = mem[m];
+    const int64_t lb = (int64_t)blockIdx.x - begin[m], nb = begin[m + 1] - begin[m];
+    const int64_t k = lb * EDGE_BLOCK + threadIdx.x;
+    const int64_t t = *tdev;
+    StepOut o{nullptr, nullptr, nullptr, nullptr, nullptr};
+    if (epi && samples_at(B, t)) o.msum = B.msum;
+    if (B.force && t % B.force_every == 0) {
+        o.fpart = B.a.fpart;
+        o.fcount = B.a.fcount;
+        o.fout = B.force + 3 * (t / B.force_every);
+    }
+    R fx = R(0), fy = R(0), fz = R(0);
+    if (k < B.a.n_edge) edge_cell<S, ODD, PLAIN>(B.a, o, k, fx, fy, fz);
+    if (o.fpart) block_force_reduce(o, lb, nb, (double)fx, (double)fy, (double)fz);
+}
+
+static __global__ void k_batch_tick(int64_t *t)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) *t += 1;
+}
+
 template <class S>
-void launch_step_t(const StepArgs &a, bool odd, bool epi, bool plain, int block_x, cudaStream_t s,
+void launch_batch_step_t(const BatchLaunch &L, bool odd, bool epi, bool plain, cudaStream_t s)
+{
+    const dim3 blk(L.block_x, L.block_y);
+    const unsigned nb = (unsigned)L.bulk_blocks, ne = (unsigned)L.edge_blocks;
+#define LBM_BB(O, E, P) k_batch_bulk<S, O, E, P><<<nb, blk, 0, s>>>(L.mem, L.bulk_begin, L.nm, L.t)
+    if (plain) {
+        if (odd) { if (epi) LBM_BB(true, true, true); else LBM_BB(true, false, true); }
+        else     { if (epi) LBM_BB(false, true, true); else LBM_BB(false, false, true); }
+    } else {
+        if (odd) { if (epi) LBM_BB(true, true, false); else LBM_BB(true, false, false); }
+        else     { if (epi) LBM_BB(false, true, false); else LBM_BB(false, false, false); }
+    }
+#undef LBM_BB
+    if (ne > 0) {
+        if (plain) {
+            if (odd) k_batch_edge<S, true, true><<<ne, EDGE_BLOCK, 0, s>>>(L.mem, L.edge_begin, L.nm, L.t, epi);
+            else     k_batch_edge<S, false, true><<<ne, EDGE_BLOCK, 0, s>>>(L.mem, L.edge_begin, L.nm, L.t, epi);
+        } else {
+            if (odd) k_batch_edge<S, true, false><<<ne, EDGE_BLOCK, 0, s>>>(L.mem, L.edge_begin, L.nm, L.t, epi);
+            else     k_batch_edge<S, false, false><<<ne, EDGE_BLOCK, 0, s>>>(L.mem, L.edge_begin, L.nm, L.t, epi);
+        }
+    }
+    k_batch_tick<<<1, 32, 0, s>>>(L.t);
+}
+
+template <class S>
+void launch_step_t(const StepArgs &a, bool odd, bool epi, bool plain, int block_x, int block_y, cudaStream_t s,
                    cudaEvent_t ev_interior, cudaEvent_t ev_bulk)
 {
     const cudaEvent_t e = ev_interior;
+    const int bx = block_x, by = block_y;
     if (plain) {
-        if (odd) { if (epi) launch_bulk<S, true, true, true>(a, block_x, s, e); else launch_bulk<S, true, false, true>(a, block_x, s, e); }
-        else     { if (epi) launch_bulk<S, false, true, true>(a, block_x, s, e); else launch_bulk<S, false, false, true>(a, block_x, s, e); }
+        if (odd) { if (epi) launch_bulk<S, true, true, true>(a, bx, by, s, e); else launch_bulk<S, true, false, true>(a, bx, by, s, e); }
+        else     { if (epi) launch_bulk<S, false, true, true>(a, bx, by, s, e); else launch_bulk<S, false, false, true>(a, bx, by, s, e); }
     } else {
-        if (odd) { if (epi) launch_bulk<S, true, true, false>(a, block_x, s, e); else launch_bulk<S, true, false, false>(a, block_x, s, e); }
-        else     { if (epi) launch_bulk<S, false, true, false>(a, block_x, s, e); else launch_bulk<S, false, false, false>(a, block_x, s, e); }
+        if (odd) { if (epi) launch_bulk<S, true, true, false>(a, bx, by, s, e); else launch_bulk<S, true, false, false>(a, bx, by, s, e); }
+        else     { if (epi) launch_bulk<S, false, true, false>(a, bx, by, s, e); else launch_bulk<S, false, false, false>(a, bx, by, s, e); }
     }
     if (ev_bulk) cudaEventRecord(ev_bulk, s);
     if (a.n_edge > 0) {

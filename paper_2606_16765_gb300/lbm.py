@@ -37,7 +37,7 @@ class lbm_params(C.Structure):
         ("snap_first", C.c_int64), ("snap_every", C.c_int64), ("snap_count", C.c_int64),
         ("snap_halfres", C.c_int32), ("force_every", C.c_int32),
         ("force_capacity", C.c_int64),
-        ("block_x", C.c_int32), ("reserved", C.c_int32 * 7),
+        ("block_x", C.c_int32), ("block_y", C.c_int32), ("reserved", C.c_int32 * 6),
     ]
 
 
@@ -51,6 +51,12 @@ class lbm_info(C.Structure):
 class lbm_timing_report(C.Structure):
     _fields_ = [("steps", C.c_int64), ("bulk_ms", C.c_double * 4), ("bulk_n", C.c_int64 * 4),
                 ("rowend_ms", C.c_double), ("edge_ms", C.c_double)]
+
+
+class lbm_batch_info(C.Structure):
+    _fields_ = [("t", C.c_int64), ("chunk", C.c_int64), ("members", C.c_int32), ("live", C.c_int32),
+                ("block_x", C.c_int32), ("block_y", C.c_int32), ("graph_captures", C.c_int64),
+                ("graph_launches", C.c_int64), ("kernel_launches", C.c_int64), ("lattice_updates", C.c_int64)]
 
 
 class LBMError(RuntimeError):
@@ -93,6 +99,20 @@ def lib():
             "lbm_get_info": (C.c_int, [_vp, C.POINTER(lbm_info)]),
             "lbm_timing": (C.c_int, [_vp, C.c_int32]),
             "lbm_timing_read": (C.c_int, [_vp, C.POINTER(lbm_timing_report), C.c_int32]),
+            "lbm_batch_create": (C.c_int, [C.c_int32, G, C.POINTER(_vp), P, _vp, C.POINTER(_vp)]),
+            "lbm_batch_destroy": (C.c_int, [_vp]),
+            "lbm_batch_set_end": (C.c_int, [_vp, C.POINTER(_i64)]),
+            "lbm_batch_set_flowthroughs": (C.c_int, [_vp, C.c_double]),
+            "lbm_batch_run": (C.c_int, [_vp, _i64]),
+            "lbm_batch_run_to_end": (C.c_int, [_vp]),
+            "lbm_batch_sync": (C.c_int, [_vp]),
+            "lbm_batch_member": (C.c_int, [_vp, C.c_int32, C.POINTER(_vp)]),
+            "lbm_batch_get_info": (C.c_int, [_vp, C.POINTER(lbm_batch_info)]),
+            "lbm_batch_autotune": (C.c_int, [_vp, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                             C.POINTER(C.c_double)]),
+            "lbm_autotune": (C.c_int, [_vp, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                       C.POINTER(C.c_double)]),
+            "lbm_reset": (C.c_int, [_vp]),
             "lbm_save": (C.c_int, [_vp, C.c_char_p]),
             "lbm_load": (C.c_int, [_vp, C.c_char_p]),
             "lbm_totals_noalloc": (C.c_int, [_vp, C.c_int32, C.c_int64, _vp, C.c_int32, C.c_int32,
@@ -231,6 +251,69 @@ def lbm_totals_noalloc(pdf, storage, slot_stride, mask, grid, stream, out):
                                     C.c_void_p(stream or 0), _ptr(out)), None)
 
 
+def lbm_reset(h):
+    _check(lib().lbm_reset(h), h)
+
+
+def lbm_autotune(h, trials):
+    bx, by, ms = C.c_int32(), C.c_int32(), C.c_double()
+    _check(lib().lbm_autotune(h, int(trials), C.byref(bx), C.byref(by), C.byref(ms)), h)
+    return bx.value, by.value, ms.value
+
+
+def lbm_batch_create(grids, masks, params, stream=None):
+    n = len(grids)
+    G = (lbm_grid * n)(*grids)
+    M = (C.c_void_p * n)(*[(_ptr(m).value if m is not None else None) for m in masks])
+    P = (lbm_params * n)(*params)
+    h = C.c_void_p()
+    _check(lib().lbm_batch_create(n, G, M, P, C.c_void_p(stream or 0), C.byref(h)), None)
+    return h
+
+
+def lbm_batch_destroy(b):
+    _check(lib().lbm_batch_destroy(b), None)
+
+
+def lbm_batch_set_end(b, t_end):
+    arr = (C.c_int64 * len(t_end))(*[int(v) for v in t_end])
+    _check(lib().lbm_batch_set_end(b, arr), None)
+
+
+def lbm_batch_set_flowthroughs(b, n_ft):
+    _check(lib().lbm_batch_set_flowthroughs(b, float(n_ft)), None)
+
+
+def lbm_batch_run(b, n):
+    _check(lib().lbm_batch_run(b, int(n)), None)
+
+
+def lbm_batch_run_to_end(b):
+    _check(lib().lbm_batch_run_to_end(b), None)
+
+
+def lbm_batch_sync(b):
+    _check(lib().lbm_batch_sync(b), None)
+
+
+def lbm_batch_member(b, g):
+    h = C.c_void_p()
+    _check(lib().lbm_batch_member(b, int(g), C.byref(h)), None)
+    return h
+
+
+def lbm_batch_get_info(b) -> lbm_batch_info:
+    out = lbm_batch_info()
+    _check(lib().lbm_batch_get_info(b, C.byref(out)), None)
+    return out
+
+
+def lbm_batch_autotune(b, trials):
+    bx, by, ms = C.c_int32(), C.c_int32(), C.c_double()
+    _check(lib().lbm_batch_autotune(b, int(trials), C.byref(bx), C.byref(by), C.byref(ms)), None)
+    return bx.value, by.value, ms.value
+
+
 def lbm_save(h, path):
     _check(lib().lbm_save(h, os.fsencode(path)), h)
 
@@ -255,50 +338,16 @@ def make_params(**kw) -> lbm_params:
     return p
 
 
-class Solver:
-    """One channel-flow lattice on the current CUDA device.
+class _Lattice:
+    """Read/write methods shared by owned contexts and batch members."""
 
-    grid = (nx, ny, nz); mask: uint8 [nz, ny, nx] (1 = solid) or None;
-    keyword arguments set lbm_params fields (storage='f32', faces=(...), ...).
-    """
-
-    def __init__(self, grid, mask=None, **params):
-        import torch
-
-        self.grid = lbm_grid(*grid)
-        self.p = make_params(**params)
-        self.shape = (grid[2], grid[1], grid[0])
-        self.n = int(np.prod(grid))
-        self._torch = torch
-        m = None
-        if mask is not None:
-            m = np.ascontiguousarray(mask, dtype=np.uint8)
-            assert m.shape == self.shape, (m.shape, self.shape)
-        self._mask = m
-        nbytes = lbm_workspace_bytes(self.grid, m, self.p)
-        if nbytes == 0:
-            raise LBMError(LBM_ERR_ARG, "invalid grid or parameters")
-        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
-        self.stream = torch.cuda.current_stream()
-        self.h = lbm_create_in(self.grid, m, self.p, self.stream.cuda_stream, self.workspace, nbytes)
-
-    def close(self):
-        if getattr(self, "h", None):
-            lbm_destroy(self.h)
-            self.h = None
-
-    def __del__(self):
-        try:
-            self.close()
-        except Exception:
-            pass
+    h = None
+    shape = None
+    p = None
 
     @property
     def t(self):
         return lbm_time(self.h)
-
-    def step(self, n=1):
-        lbm_step(self.h, n)
 
     def sync(self):
         lbm_sync(self.h)
@@ -342,9 +391,6 @@ class Solver:
             lbm_read_forces(self.h, out, n)
         return out
 
-    def init_noise(self, seed, amplitude):
-        lbm_init_noise(self.h, seed, amplitude)
-
     def totals(self):
         out = np.zeros(4)
         lbm_totals(self.h, out)
@@ -352,6 +398,57 @@ class Solver:
 
     def info(self):
         return lbm_get_info(self.h)
+
+
+class Solver(_Lattice):
+    """One channel-flow lattice on the current CUDA device.
+
+    grid = (nx, ny, nz); mask: uint8 [nz, ny, nx] (1 = solid) or None;
+    keyword arguments set lbm_params fields (storage='f32', faces=(...), ...).
+    """
+
+    def __init__(self, grid, mask=None, **params):
+        import torch
+
+        self.grid = lbm_grid(*grid)
+        self.p = make_params(**params)
+        self.shape = (grid[2], grid[1], grid[0])
+        self.n = int(np.prod(grid))
+        self._torch = torch
+        m = None
+        if mask is not None:
+            m = np.ascontiguousarray(mask, dtype=np.uint8)
+            assert m.shape == self.shape, (m.shape, self.shape)
+        self._mask = m
+        nbytes = lbm_workspace_bytes(self.grid, m, self.p)
+        if nbytes == 0:
+            raise LBMError(LBM_ERR_ARG, "invalid grid or parameters")
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        self.stream = torch.cuda.current_stream()
+        self.h = lbm_create_in(self.grid, m, self.p, self.stream.cuda_stream, self.workspace, nbytes)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lbm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, n=1):
+        lbm_step(self.h, n)
+
+    def init_noise(self, seed, amplitude):
+        lbm_init_noise(self.h, seed, amplitude)
+
+    def reset(self):
+        lbm_reset(self.h)
+
+    def autotune(self, trials=10):
+        return lbm_autotune(self.h, trials)
 
     def timing(self, enable=True):
         lbm_timing(self.h, enable)
@@ -364,3 +461,79 @@ class Solver:
 
     def load(self, path):
         lbm_load(self.h, path)
+
+
+class BatchMember(_Lattice):
+    """Borrowed view of one lattice of a Batch (reads only)."""
+
+    def __init__(self, batch, g):
+        self._batch = batch
+        self.h = lbm_batch_member(batch.h, g)
+        d = batch.members[g]
+        self.grid = lbm_grid(*d["grid"])
+        self.shape = (d["grid"][2], d["grid"][1], d["grid"][0])
+        self.p = batch.params[g]
+
+
+class Batch:
+    """Many lattices stepped together (graph-captured batched launches).
+
+    members: list of dicts with keys grid, mask and lbm_params fields.
+    """
+
+    def __init__(self, members):
+        import torch
+
+        self.members = members
+        self.params = []
+        grids, masks = [], []
+        self._masks = []
+        for d in members:
+            kw = {k: v for k, v in d.items() if k not in ("grid", "mask")}
+            self.params.append(make_params(**kw))
+            grids.append(lbm_grid(*d["grid"]))
+            m = d.get("mask")
+            if m is not None:
+                m = np.ascontiguousarray(m, dtype=np.uint8)
+            self._masks.append(m)
+            masks.append(m)
+        self.stream = torch.cuda.current_stream()
+        self.h = lbm_batch_create(grids, masks, self.params, self.stream.cuda_stream)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lbm_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __len__(self):
+        return len(self.members)
+
+    def member(self, g):
+        return BatchMember(self, g)
+
+    def set_end(self, t_end):
+        lbm_batch_set_end(self.h, t_end)
+
+    def set_flowthroughs(self, n_ft):
+        lbm_batch_set_flowthroughs(self.h, n_ft)
+
+    def run(self, n):
+        lbm_batch_run(self.h, n)
+
+    def run_to_end(self):
+        lbm_batch_run_to_end(self.h)
+
+    def sync(self):
+        lbm_batch_sync(self.h)
+
+    def info(self):
+        return lbm_batch_get_info(self.h)
+
+    def autotune(self, trials=4):
+        return lbm_batch_autotune(self.h, trials)

@@ -1,0 +1,142 @@
+"""Batched driver: graph-captured batched launches over uneven grids must give
+exactly what independent contexts give (same kernels per cell, same
+arithmetic order, deterministic force reductions), members must stop at their
+own end, and the autotuners must leave the lattices at rest."""
+import numpy as np
+import pytest
+
+import oracle.lbm as O
+from paper_2606_16765_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2606_16765_gb300 import _build
+    _build.build()
+
+
+def members(storage="f32", mean=True, force=True):
+    out = []
+    for g, (grid, w1) in enumerate([((40, 16, 12), 1.6), ((64, 20, 16), 1.85), ((96, 12, 12), 1.95),
+                                    ((33, 9, 7), 1.3)]):
+        nx, ny, nz = grid
+        mask = I.sphere(grid, (0.3 * nx, 0.5 * (ny - 1), 0.5 * (nz - 1)), 0.22 * ny)
+        d = dict(grid=grid, mask=mask, storage=storage, omega1=w1, u_in=0.05)
+        if mean:
+            d.update(mean_start=4, mean_end=1000, mean_every=2)
+        if force:
+            d.update(force_every=1, force_capacity=4096)
+        out.append(d)
+    return out
+
+
+def independent(d, steps, **extra):
+    from paper_2606_16765_gb300.lbm import Solver
+    kw = {k: v for k, v in d.items() if k not in ("grid", "mask")}
+    kw.update(extra)
+    s = Solver(d["grid"], d["mask"], **kw)
+    s.step(steps)
+    s.sync()
+    return s
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16s"])
+def test_batch_equals_independent_runs(storage):
+    from paper_2606_16765_gb300.lbm import Batch
+    ms = members(storage)
+    b = Batch(ms)
+    b.run(20)
+    b.sync()
+    info = b.info()
+    assert info.t == 20 and info.graph_captures == 1 and info.graph_launches == 10
+    for g, d in enumerate(ms):
+        m = b.member(g)
+        ref = independent(d, 20)
+        assert m.t == 20
+        assert np.array_equal(m.pdfs(), ref.pdfs()), g
+        ma, sa = m.mean()
+        mb, sb = ref.mean()
+        assert sa == sb == 8 and np.array_equal(ma, mb)
+        assert np.array_equal(m.forces(), ref.forces())
+
+
+def test_members_stop_at_their_end():
+    from paper_2606_16765_gb300.lbm import Batch
+    ms = members("f32", mean=False, force=False)
+    b = Batch(ms)
+    ends = [6, 14, 20, 2]
+    b.set_end(ends)
+    b.run_to_end()
+    b.sync()
+    info = b.info()
+    assert info.live == 0 and info.t == 20
+    assert info.graph_captures == 4          # live sets {0,1,2,3}, {0,1,2}, {1,2}, {2}
+    for g, d in enumerate(ms):
+        m = b.member(g)
+        assert m.t == ends[g]
+        assert np.array_equal(m.pdfs(), independent(d, ends[g]).pdfs()), g
+
+
+def test_flowthrough_ends():
+    from paper_2606_16765_gb300.lbm import Batch
+    ms = members("f32", mean=False, force=False)
+    b = Batch(ms)
+    b.set_flowthroughs(0.05)                  # 0.05 * nx / 0.05 = nx steps, rounded to the chunk
+    b.run_to_end()
+    b.sync()
+    for g, d in enumerate(ms):
+        nx = d["grid"][0]
+        assert b.member(g).t == nx + (nx % 2)
+
+
+def test_batch_autotune_resets_to_rest_and_runs_with_the_choice():
+    from paper_2606_16765_gb300.lbm import Batch
+    ms = members("f32")
+    b = Batch(ms)
+    bx, by, ms_step = b.autotune(trials=2)
+    assert bx % 32 == 0 and bx * by <= 256 and ms_step > 0
+    info = b.info()
+    assert info.t == 0 and info.block_x == bx and info.block_y == by
+    w = O.weights()
+    for g in range(len(ms)):
+        f = b.member(g).pdfs()
+        assert np.abs(f - w[:, None, None, None]).max() == 0.0
+    b.run(10)
+    b.sync()
+    for g, d in enumerate(ms):
+        ref = independent(d, 10, block_x=bx, block_y=by)
+        assert np.array_equal(b.member(g).pdfs(), ref.pdfs())
+
+
+def test_single_context_autotune():
+    from paper_2606_16765_gb300.lbm import Solver
+    d = members("f32")[1]
+    s = Solver(d["grid"], d["mask"], storage="f32", omega1=1.8, u_in=0.05, mean_start=0, mean_end=100,
+               mean_every=2, force_every=1)
+    bx, by, t = s.autotune(trials=4)
+    assert bx % 32 == 0 and bx * by <= 256 and t > 0
+    assert s.t == 0 and s.forces().shape == (0, 3)
+    w = O.weights()
+    assert np.abs(s.pdfs() - w[:, None, None, None]).max() == 0.0
+
+
+def test_batch_argument_errors():
+    from paper_2606_16765_gb300.lbm import Batch, LBMError
+    ms = members("f32")
+    ms[1]["storage"] = "f16s"
+    with pytest.raises(LBMError):
+        Batch(ms)
+    ms = members("f32")
+    ms[2]["mean_every"] = 4
+    with pytest.raises(LBMError):
+        Batch(ms)
+    ms = members("f32")
+    ms[0]["snap_count"] = 2
+    ms[0]["snap_every"] = 5
+    with pytest.raises(LBMError):
+        Batch(ms)
