@@ -1,0 +1,93 @@
+/*
+ * fno.h -- C ABI of the Fourier Neural Operator surrogate of the mean flow
+ * (Sec. 4 and the appendix on the baseline models of the paper: an FNO that
+ * maps the obstacle mask and Re to the time-averaged velocity and pressure,
+ * trained with a masked mean square error on the inner region of the
+ * channel, Adam, cosine learning-rate schedule).
+ *
+ * Network, for fields laid out [batch][channel][z][y][x] (x fastest):
+ *   lift      v0 = P x + bP                           (pointwise cin -> width)
+ *   layer l   v_{l+1} = act(K_l v_l + W_l v_l + b_l)  (GELU except after the last)
+ *             K_l v = IDFT_r(R_l . DFT_r(v))          (retained modes only)
+ *   project   y = Q2 GELU(Q1 v_L + bQ1) + bQ2         (width -> hidden -> cout)
+ * DFT_r keeps kx in [0,mx) U [-mx,0), ky in [0,my) U [-my,0), kz in [0,mz)
+ * (z is the real-to-half-complex axis); the inverse is
+ * y(x) = (1/N) Re[sum_k c_kz G(k) exp(+i theta_k . x)], c_0 = 1, c_kz = 2.
+ * R_l holds one complex width x width matrix per retained mode.
+ *
+ * Parameters are one flat FP32 vector, in this order:
+ *   R_0 .. R_{layers-1}, each [K][width_in][width_out][re, im] (K = mz*2my*2mx
+ *   modes, k = (kz*2my + jy)*2mx + jx; first, so that every complex entry is
+ *   8-byte aligned), P_w [width][cin], P_b [width],
+ *   per layer l: W_l_w [width][width], W_l_b [width],
+ *   Q1_w [hidden][width], Q1_b [hidden], Q2_w [cout][hidden], Q2_b [cout].
+ *
+ * Conventions as in lbm.h: every call returns lbm_status; buffers may be
+ * host or device memory; work runs on the stream given at creation.
+ */
+#ifndef GB300_FNO_H
+#define GB300_FNO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#include "lbm.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fno_ctx fno_ctx;
+
+typedef struct {
+    int32_t nx, ny, nz;          /* grid (x streamwise)                            */
+    int32_t cin, width, cout;    /* input channels, co-domain width, outputs        */
+    int32_t mx, my, mz;          /* retained modes (see above), mz < nz/2          */
+    int32_t layers, hidden;      /* Fourier layers, projection hidden width        */
+    int32_t max_batch;           /* largest batch a call may pass                  */
+    int32_t act_bf16;            /* 1: activations stored in BF16 (else FP32)      */
+    int32_t tensor_cores;        /* 1: mode contraction on tensor cores in BF16
+                                    with FP32 accumulation (needs width % 8 == 0) */
+    uint64_t seed;               /* initial parameters                             */
+} fno_config;
+
+/* Defaults of the channel surrogate: 128x64x64 grid, 4 inputs (mask, log10
+ * Re, cos and sin of the angle of attack), width 32, modes 16x8x8, 4 layers,
+ * hidden 128, 4 outputs (u, v, w, p), batch 8, BF16 activations, tensor cores. */
+void fno_config_default(fno_config *c);
+
+lbm_status fno_create(const fno_config *c, void *cuda_stream, fno_ctx **out);
+lbm_status fno_destroy(fno_ctx *f);
+
+/* Number of FP32 parameters (the flat vector above). */
+int64_t fno_num_params(const fno_ctx *f);
+
+lbm_status fno_set_params(fno_ctx *f, const float *src);
+lbm_status fno_get_params(fno_ctx *f, float *dst);
+/* Gradients of the last fno_loss_grad / fno_train_step (same layout). */
+lbm_status fno_get_grads(fno_ctx *f, float *dst);
+
+/* y [batch][cout][N] FP32 from x [batch][cin][N] FP32 (N = nx*ny*nz). */
+lbm_status fno_forward(fno_ctx *f, const float *x, float *y, int32_t batch);
+
+/* Forward and backward of the masked mean square error
+ * sum_{b,c,cell} m (y - t)^2 / (cout * sum m); m [batch][N] FP32 weights.
+ * Stores the gradients; *loss receives the loss (may be NULL). */
+lbm_status fno_loss_grad(fno_ctx *f, const float *x, const float *t, const float *m, int32_t batch,
+                         double *loss);
+
+/* One Adam step (beta1, beta2, eps; bias-corrected; real and imaginary parts
+ * of the spectral weights handled as separate reals) with the stored
+ * gradients at learning rate lr. */
+lbm_status fno_adam_step(fno_ctx *f, float lr, float beta1, float beta2, float eps);
+
+/* fno_loss_grad followed by fno_adam_step with beta1 0.9, beta2 0.999, eps 1e-8. */
+lbm_status fno_train_step(fno_ctx *f, const float *x, const float *t, const float *m, int32_t batch, float lr,
+                          double *loss);
+
+const char *fno_last_error(const fno_ctx *f);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GB300_FNO_H */

@@ -1,0 +1,164 @@
+"""GPU parity of the FNO kernels (forward, backward, Adam) against the FP64
+oracle.  Tolerances: FP32 activations with the FP32 contraction: forward
+<= 1e-5 (max relative), gradients <= 1e-4 (relative L2 per parameter group);
+BF16 tensor-core contraction and/or BF16 activations: forward relative L2
+<= 2e-2, gradients cosine >= 0.999 and relative L2 <= 3e-2 (BF16 keeps 8
+significant bits)."""
+import numpy as np
+import pytest
+
+import oracle.fno as F
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2606_16765_gb300 import _build
+    _build.build()
+
+
+def tiny_cfgs(width=8):
+    ocfg = F.FNOConfig(grid=(8, 6, 10), cin=2, width=width, cout=2, modes=(3, 2, 3), layers=2, hidden=5)
+    gcfg = dict(nx=10, ny=6, nz=8, cin=2, width=width, cout=2, mx=3, my=2, mz=3, layers=2, hidden=5, max_batch=8)
+    return ocfg, gcfg
+
+
+def to_gpu_params(ocfg, p):
+    from paper_2606_16765_gb300 import fno as G
+    d = dict(p)
+    W = ocfg.width
+    for l in range(ocfg.layers):
+        d[f"R{l}"] = p[f"R{l}"].reshape(W, W, -1).transpose(2, 0, 1)      # [i][o][k] -> [k][i][o]
+    return G.flatten(G.make_config(**GCFG_CACHE["g"]), d)
+
+
+GCFG_CACHE = {}
+
+
+def gpu_grads_as_oracle(ocfg, gcfg, flat):
+    from paper_2606_16765_gb300 import fno as G
+    d = G.unflatten(G.make_config(**gcfg), flat)
+    W = ocfg.width
+    mz, my, mx = ocfg.modes
+    for l in range(ocfg.layers):
+        d[f"R{l}"] = d[f"R{l}"].transpose(1, 2, 0).reshape(W, W, mz, 2 * my, 2 * mx)
+    return d
+
+
+def problem(ocfg, B=3, seed=0):
+    r = np.random.Generator(np.random.PCG64(seed))
+    x = r.normal(size=(B, ocfg.cin) + ocfg.grid).astype(np.float32)
+    t = r.normal(size=(B, ocfg.cout) + ocfg.grid).astype(np.float32)
+    m = (r.uniform(size=(B,) + ocfg.grid) < 0.6).astype(np.float32)
+    p = F.init_params(ocfg, seed=seed + 1)
+    for k in p:
+        if k.startswith("R"):
+            p[k] = p[k] * 30.0          # make the spectral branch carry real weight
+    return x, t, m, p
+
+
+def run_case(act_bf16, tensor_cores, width=8):
+    from paper_2606_16765_gb300 import fno as G
+    ocfg, gcfg = tiny_cfgs(width)
+    gcfg.update(act_bf16=act_bf16, tensor_cores=tensor_cores)
+    GCFG_CACHE["g"] = gcfg
+    x, t, m, p = problem(ocfg)
+    net = G.FNO(**gcfg)
+    net.set_params(to_gpu_params(ocfg, p))
+    y_gpu = net.forward(x)
+    y_ref, tape = F.forward(p, x.astype(np.float64), ocfg, keep=True)
+    L_gpu = net.loss_grad(x, t, m)
+    L_ref = F.masked_mse(y_ref, t.astype(np.float64), m.astype(np.float64))
+    g_ref = F.backward(p, tape, y_ref, t.astype(np.float64), m.astype(np.float64), ocfg)
+    g_gpu = gpu_grads_as_oracle(ocfg, gcfg, net.grads())
+    return y_gpu, y_ref, L_gpu, L_ref, g_gpu, g_ref
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm((a - b).ravel()) / max(np.linalg.norm(b.ravel()), 1e-300))
+
+
+def cosine(a, b):
+    a, b = np.ravel(a), np.ravel(b)
+    if np.iscomplexobj(a) or np.iscomplexobj(b):
+        a = np.concatenate([np.real(a), np.imag(a)])
+        b = np.concatenate([np.real(b), np.imag(b)])
+    return float(a @ b / max(np.linalg.norm(a) * np.linalg.norm(b), 1e-300))
+
+
+def test_fp32_activations_fp32_contraction_match_oracle():
+    y, yr, L, Lr, g, gr = run_case(act_bf16=0, tensor_cores=0, width=3)
+    assert np.abs(y - yr).max() / np.abs(yr).max() < 1e-5
+    assert abs(L - Lr) / Lr < 1e-5
+    for k in gr:
+        assert rel_l2(g[k], gr[k]) < 1e-4, k
+
+
+@pytest.mark.parametrize("act_bf16", [0, 1])
+def test_tensor_core_contraction_matches_oracle(act_bf16):
+    y, yr, L, Lr, g, gr = run_case(act_bf16=act_bf16, tensor_cores=1, width=8)
+    assert rel_l2(y, yr) < 2e-2
+    assert abs(L - Lr) / Lr < 2e-2
+    for k in gr:
+        assert cosine(g[k], gr[k]) > 0.999, k
+        assert rel_l2(g[k], gr[k]) < 3e-2, k
+
+
+def test_adam_trajectory_matches_oracle():
+    from paper_2606_16765_gb300 import fno as G
+    ocfg, gcfg = tiny_cfgs(3)
+    gcfg.update(act_bf16=0, tensor_cores=0)
+    GCFG_CACHE["g"] = gcfg
+    x, t, m, p = problem(ocfg, seed=3)
+    net = G.FNO(**gcfg)
+    net.set_params(to_gpu_params(ocfg, p))
+    m1 = {k: np.zeros_like(v) for k, v in p.items()}
+    m2 = {k: np.zeros_like(v) for k, v in p.items()}
+    losses = []
+    for step in range(1, 6):
+        Lg = net.train_step(x, t, m, 1e-3)
+        Lr, gr = F.loss_and_grad(p, x.astype(np.float64), t.astype(np.float64), m.astype(np.float64), ocfg)
+        p = F.adam_step(p, gr, m1, m2, step, 1e-3)
+        assert abs(Lg - Lr) / Lr < 1e-4
+        losses.append(Lg)
+    assert losses[-1] < losses[0]
+    pg = gpu_grads_as_oracle(ocfg, gcfg, net.params())
+    for k in p:
+        assert np.abs(pg[k] - p[k]).max() < 1e-5, k
+
+
+def test_full_size_forward_matches_oracle():
+    """128x64x64 grid, width 32, modes 16x8x8, 4 layers, BF16 activations and
+    the tensor-core contraction (the configuration that is timed), batch 1."""
+    from paper_2606_16765_gb300 import fno as G
+    ocfg = F.FNOConfig()
+    gcfg = dict(nx=128, ny=64, nz=64, max_batch=8, act_bf16=1, tensor_cores=1)
+    GCFG_CACHE["g"] = gcfg
+    r = np.random.Generator(np.random.PCG64(11))
+    x = r.normal(size=(1, 4) + ocfg.grid).astype(np.float32)
+    p = F.init_params(ocfg, seed=12)
+    for k in p:
+        if k.startswith("R"):
+            p[k] = p[k] * 30.0
+    net = G.FNO(**gcfg)
+    net.set_params(to_gpu_params(ocfg, p))
+    y = net.forward(x)
+    yr = F.forward(p, x.astype(np.float64), ocfg)
+    assert rel_l2(y, yr) < 2e-2
+
+
+def test_batches_larger_than_max_batch_are_split():
+    from paper_2606_16765_gb300 import fno as G
+    ocfg, gcfg = tiny_cfgs(8)
+    gcfg.update(act_bf16=0, tensor_cores=1, max_batch=4)
+    GCFG_CACHE["g"] = gcfg
+    r = np.random.Generator(np.random.PCG64(21))
+    x = r.normal(size=(10, ocfg.cin) + ocfg.grid).astype(np.float32)
+    net = G.FNO(**gcfg)
+    y_all = net.forward(x)
+    for b in range(10):
+        assert np.array_equal(y_all[b:b + 1], net.forward(x[b:b + 1]))
