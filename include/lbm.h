@@ -226,7 +226,8 @@ lbm_status lbm_batch_create(int32_t n, const lbm_grid *grids, const uint8_t *con
 lbm_status lbm_batch_destroy(lbm_batch *b);
 
 /* Last step of every member: member g runs t_end[g] steps (rounded up to a
- * multiple of the chunk length). */
+ * multiple of the chunk length).  An end at or before the batch's current
+ * step retires the member where it is (e.g. after it became unstable). */
 lbm_status lbm_batch_set_end(lbm_batch *b, const int64_t *t_end);
 
 /* t_end[g] = ceil(n_ft * nx_g / u_in_g): n_ft flow-through times. */
@@ -239,7 +240,8 @@ lbm_status lbm_batch_run(lbm_batch *b, int64_t n);
 /* Run until every member reached its end. */
 lbm_status lbm_batch_run_to_end(lbm_batch *b);
 
-/* Wait for the batch; report latched device conditions of any member. */
+/* Wait for the batch; report latched device conditions of any member.  A
+ * run is refused only while an unstable member is still live. */
 lbm_status lbm_batch_sync(lbm_batch *b);
 
 /* Borrow member g's context (valid until lbm_batch_destroy). */

@@ -1096,7 +1096,8 @@ extern "C" lbm_status lbm_batch_set_end(lbm_batch *b, const int64_t *t_end)
     for (size_t g = 0; g < b->members.size(); ++g) {
         if (t_end[g] < 0) return batch_fail(b, LBM_ERR_ARG, "negative end step");
         const lbm_ctx *c = b->members[g];
-        const int64_t te = round_chunk(b, t_end[g]);
+        // an end at or before the batch time retires the member now
+        const int64_t te = t_end[g] <= b->t ? std::min(b->t, b->t_end[g]) : round_chunk(b, t_end[g]);
         if (c->p.force_every > 0 && te / c->p.force_every + 1 > c->force_cap)
             return batch_fail(b, LBM_ERR_ARG, "force_capacity of member " + std::to_string(g) + " is too small");
         b->t_end[g] = te;
@@ -1196,8 +1197,9 @@ static void batch_sync_members(lbm_batch *b)
 extern "C" lbm_status lbm_batch_run(lbm_batch *b, int64_t nsteps)
 {
     if (!b || nsteps < 0) return LBM_ERR_ARG;
-    for (lbm_ctx *c : b->members)
-        if (c->unstable) return batch_fail(b, LBM_ERR_STATE, "a member is unstable; steps refused");
+    for (size_t g = 0; g < b->members.size(); ++g)
+        if (b->members[g]->unstable && b->t < b->t_end[g])
+            return batch_fail(b, LBM_ERR_STATE, "member " + std::to_string(g) + " is unstable; steps refused");
     const int64_t target = b->t + round_chunk(b, nsteps);
     BCK(cudaEventRecord(b->ev_in, b->user));
     BCK(cudaStreamWaitEvent(b->own, b->ev_in, 0));

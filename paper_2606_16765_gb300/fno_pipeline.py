@@ -1,0 +1,295 @@
+"""Mean-field data set from the batched LBM, FNO training and evaluation.
+
+The pipeline of the paper's Sec. 2 (geometry generation -> LBM simulation,
+mean velocity and pressure after the flow-through times -> scaling -> NN
+training) and the FNO baseline of its appendix (masked MSE on the inner region
+[(0.2,0.25,0.25),(1.8,0.75,0.75)] of the (2,1,1) channel, Adam, cosine
+learning-rate schedule, 50 epochs), run on the 128x64x64 grid the surrogate
+works on:
+
+  1. seeded composite obstacles (5 primitive kinds, angle of attack in
+     [-30, 30] deg), Re log-uniform at the lattice viscosities of the paper's
+     Re 1e3 - 1e4 runs (Re 125 - 1250 on the 64-cell channel height);
+  2. all geometries stepped together by the batched LBM driver to 15
+     flow-through times, the time average taken over flow-through times 5-15;
+  3. inputs (mask, log10 Re - 2, cos and sin of the angle), targets (u, v, w,
+     p) min-max scaled per field on the training set;
+  4. training, evaluation on held-out seeds against the LBM, and the time of an
+     FNO prediction against the LBM run it replaces.
+
+Usage: python -m paper_2606_16765_gb300.fno_pipeline --out report.json [--quick]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import time
+
+import numpy as np
+
+from . import inputs as I
+
+GRID = (128, 64, 64)          # (nx, ny, nz)
+U_IN = 0.05
+
+
+# Re range on the 64-cell channel height: the lattice viscosities of the
+# paper's runs (Re 1e3 - 1e4 on a 512-cell height, nu = U 512 / Re) give
+# Re = 125 - 1250 on 64 cells.
+RE_RANGE = (125.0, 1250.0)
+
+
+def sample(seed, grid=GRID):
+    """Geometry and Re of one sample (deterministic in seed)."""
+    rng = np.random.Generator(np.random.PCG64(70_000 + seed))
+    re = float(math.exp(rng.uniform(math.log(RE_RANGE[0]), math.log(RE_RANGE[1]))))
+    obs = I.composite(seed, grid, size_range=(6.0, 12.0), jitter=2.0)
+    return dict(seed=seed, grid=tuple(grid), mask=obs.mask(), re=re, angle=obs.angle_deg)
+
+
+def features(s):
+    """FNO input channels [4, nz, ny, nx]: mask, log10 Re - 2, cos a, sin a."""
+    m = s["mask"].astype(np.float32)
+    a = math.radians(s["angle"])
+    return np.stack([m, np.full_like(m, math.log10(s["re"]) - 2.0), np.full_like(m, math.cos(a)),
+                     np.full_like(m, math.sin(a))])
+
+
+def simulate(samples, storage="f16c", n_ft=15.0, ft_start=5.0, chunk_ft=1.0, log=print):
+    """Mean (u, v, w, p) [n, 4, nz, ny, nx] of each sample from the batched LBM.
+    Members that become unstable are retired and reported (their targets are
+    NaN)."""
+    from .lbm import Batch, LBMError
+
+    nx = samples[0]["grid"][0]
+    steps_ft = nx / U_IN
+    t_end = int(math.ceil(n_ft * steps_ft))
+    mean_start = int(round(ft_start * steps_ft / 10.0)) * 10
+    members = [dict(grid=s["grid"], mask=s["mask"], storage=storage, re=s["re"], u_in=U_IN,
+                    l_ref=float(s["grid"][1]), mean_start=mean_start, mean_end=t_end, mean_every=10)
+               for s in samples]
+    b = Batch(members)
+    b.set_end([t_end] * len(samples))
+    unstable = set()
+    step = int(math.ceil(chunk_ft * steps_ft / 10.0)) * 10
+    t0 = time.time()
+    while b.info().live > 0:
+        b.run(step)
+        for g in range(len(samples)):
+            if g in unstable:
+                continue
+            try:
+                b.member(g).sync()
+            except LBMError:
+                unstable.add(g)
+        if unstable:
+            ends = [b.info().t if g in unstable else t_end for g in range(len(samples))]
+            b.set_end(ends)
+    if not unstable:
+        b.sync()
+    out = np.full((len(samples), 4) + samples[0]["mask"].shape, np.nan, np.float32)
+    for g in range(len(samples)):
+        if g in unstable:
+            continue
+        m, ns = b.member(g).mean(dtype=np.float32)
+        out[g] = np.moveaxis(m, -1, 0)
+    info = b.info()
+    log(f"  LBM batch of {len(samples)}: {info.t} steps, {info.lattice_updates / 1e9:.1f} G updates in "
+        f"{time.time() - t0:.1f} s, unstable {sorted(unstable)}")
+    b.close()
+    return out, sorted(unstable)
+
+
+def time_lbm_to_end(s, storage="f16c", n_ft=15.0, ft_start=5.0):
+    """Seconds of GPU time for one sample's LBM run alone (15 flow-throughs,
+    averaging included), CUDA events around the batched driver."""
+    import torch
+    from .lbm import Batch
+    nx = s["grid"][0]
+    t_end = int(math.ceil(n_ft * nx / U_IN))
+    mean_start = int(round(ft_start * nx / U_IN / 10.0)) * 10
+    b = Batch([dict(grid=s["grid"], mask=s["mask"], storage=storage, re=s["re"], u_in=U_IN,
+                    l_ref=float(s["grid"][1]), mean_start=mean_start, mean_end=t_end, mean_every=10)])
+    b.set_end([t_end])
+    b.run(10)                                      # capture and warm up
+    b.sync()
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    b.run_to_end()
+    e1.record(st)
+    torch.cuda.synchronize()
+    steps = b.info().t - 10
+    secs = e0.elapsed_time(e1) / 1e3
+    b.close()
+    return secs * t_end / max(1, steps)
+
+
+def region_weights(mask):
+    """Loss weights: inner region of the channel and fluid cells."""
+    nz, ny, nx = mask.shape
+    w = np.zeros(mask.shape, np.float32)
+    w[int(0.25 * nz):int(0.75 * nz), int(0.25 * ny):int(0.75 * ny), int(0.1 * nx):int(0.9 * nx)] = 1.0
+    return w * (mask == 0)
+
+
+def metrics(pred, true, masks):
+    """rel-L2 of stacked (u, v, w) over fluid cells, per field, and the
+    paper's MSE / max MAE / NRMSE / MAPE on min-max scaled fields over the
+    inner region (computed by the caller's scaling)."""
+    rel = []
+    per = {k: [] for k in ("u", "v", "w", "p")}
+    for b in range(pred.shape[0]):
+        fl = masks[b] == 0
+        d = pred[b, :3][:, fl] - true[b, :3][:, fl]
+        rel.append(float(np.linalg.norm(d) / np.linalg.norm(true[b, :3][:, fl])))
+        for c, k in enumerate(("u", "v", "w")):
+            per[k].append(float(np.linalg.norm(pred[b, c][fl] - true[b, c][fl]) / np.linalg.norm(true[b, c][fl])))
+        pp = pred[b, 3][fl] - pred[b, 3][fl].mean()
+        pt = true[b, 3][fl] - true[b, 3][fl].mean()
+        per["p"].append(float(np.linalg.norm(pp - pt) / np.linalg.norm(pt)))
+    return rel, per
+
+
+def run(n_train=512, n_test=64, epochs=50, batch=8, lr=1e-3, storage="f16c", n_ft=15.0, sim_batch=64,
+        out=None, log=print):
+    import torch
+    from .fno import FNO
+
+    dev = torch.device("cuda")
+    report = {"grid": list(GRID), "n_train": n_train, "n_test": n_test, "epochs": epochs, "batch": batch,
+              "lr": lr, "lbm_storage": storage, "flow_throughs": n_ft}
+    train_s = [sample(1000 + k) for k in range(n_train)]
+    test_s = [sample(2000 + k) for k in range(n_test)]
+    # 1-2: data from the LBM
+    t0 = time.time()
+    Y, bad = [], []
+    allS = train_s + test_s
+    for k0 in range(0, len(allS), sim_batch):
+        y, un = simulate(allS[k0:k0 + sim_batch], storage=storage, n_ft=n_ft, ft_start=min(5.0, n_ft / 3.0),
+                         log=log)
+        Y.append(y)
+        bad += [k0 + g for g in un]
+    Y = np.concatenate(Y)
+    report["lbm_seconds"] = time.time() - t0
+    report["unstable_samples"] = bad
+    keep_tr = [k for k in range(n_train) if k not in bad]
+    keep_te = [k for k in range(n_test) if n_train + k not in bad]
+    X = np.stack([features(s) for s in allS])
+    masks = np.stack([s["mask"] for s in allS])
+    # 3: scaling on the training set (fluid cells)
+    lo = np.zeros(4, np.float32)
+    hi = np.zeros(4, np.float32)
+    for c in range(4):
+        vals = np.concatenate([Y[k, c][masks[k] == 0] for k in keep_tr])
+        lo[c], hi[c] = vals.min(), vals.max()
+    Yn = (Y - lo[None, :, None, None, None]) / (hi - lo)[None, :, None, None, None]
+    Yn[np.isnan(Yn)] = 0.0
+    Wt = np.stack([region_weights(m) for m in masks])
+    Xd = torch.from_numpy(X).to(dev)
+    Yd = torch.from_numpy(Yn.astype(np.float32)).to(dev)
+    Wd = torch.from_numpy(Wt).to(dev)
+    # 4: training
+    net = FNO(nx=GRID[0], ny=GRID[1], nz=GRID[2], max_batch=batch)
+    rng = np.random.Generator(np.random.PCG64(0))
+    steps_ep = int(math.ceil(len(keep_tr) / batch))
+    total = epochs * steps_ep
+    losses = []
+    t1 = time.time()
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    step = 0
+    for ep in range(epochs):
+        order = rng.permutation(keep_tr)
+        for j in range(steps_ep):
+            idx = order[j * batch:(j + 1) * batch]
+            if len(idx) < batch:
+                idx = np.concatenate([idx, order[:batch - len(idx)]])
+            it = torch.as_tensor(idx, device=dev)
+            x, y, w = Xd.index_select(0, it).contiguous(), Yd.index_select(0, it).contiguous(), \
+                Wd.index_select(0, it).contiguous()
+            cur = lr * 0.5 * (1.0 + math.cos(math.pi * step / total))
+            L = net.train_step(x, y, w, cur)
+            step += 1
+        losses.append(L)
+        if ep % 10 == 0 or ep == epochs - 1:
+            log(f"  epoch {ep}: loss {L:.3e}")
+    e1.record(st)
+    torch.cuda.synchronize()
+    report["train_seconds"] = e0.elapsed_time(e1) / 1e3
+    report["train_samples_per_s"] = total * batch / report["train_seconds"]
+    report["loss_per_epoch"] = losses
+    # evaluation on the held-out seeds
+    test_idx = [n_train + k for k in keep_te]
+    Xt = Xd[test_idx].contiguous()
+    pred_n = torch.zeros((len(test_idx), 4) + masks.shape[1:], device=dev)
+    net.forward(Xt, pred_n)
+    torch.cuda.synchronize()
+    pred_n = pred_n.cpu().numpy()
+    pred = pred_n * (hi - lo)[None, :, None, None, None] + lo[None, :, None, None, None]
+    true = Y[test_idx]
+    tm = masks[test_idx]
+    rel, per = metrics(pred, true, tm)
+    report["rel_l2_uvw"] = {"median": float(np.median(rel)), "mean": float(np.mean(rel)), "max": float(np.max(rel))}
+    report["rel_l2_per_field_median"] = {k: float(np.median(v)) for k, v in per.items()}
+    # paper's metrics on the scaled fields over the inner region (fluid cells)
+    yn_true = Yn[test_idx]
+    wt = Wt[test_idx][:, None]
+    err = (pred_n - yn_true) * wt
+    cnt = wt.sum() * 4
+    mse = float((err ** 2).sum() / cnt)
+    mae_s = [(np.abs(err[b]).sum() / (wt[b].sum() * 4)) for b in range(len(test_idx))]
+    ref_u = yn_true[:, 0][wt[:, 0] > 0]
+    mape = float(np.mean(np.abs((pred_n[:, 0] - yn_true[:, 0])[wt[:, 0] > 0]) / np.maximum(np.abs(ref_u), 1e-2)) * 100)
+    report["paper_metrics_scaled"] = {"MSE": mse, "max_MAE": float(np.max(mae_s)), "NRMSE": math.sqrt(mse),
+                                      "MAPE_u": mape}
+    # the method without the network: the training-set mean field
+    mean_field = Y[keep_tr].mean(axis=0)
+    rel0, per0 = metrics(np.broadcast_to(mean_field, true.shape), true, tm)
+    report["baseline_train_mean_rel_l2_uvw"] = {"median": float(np.median(rel0)), "mean": float(np.mean(rel0))}
+    # speed: one FNO prediction against the LBM run it replaces
+    xb = Xt[:batch].contiguous() if len(test_idx) >= batch else Xt.repeat(batch, 1, 1, 1, 1)[:batch].contiguous()
+    yb = torch.zeros((batch, 4) + masks.shape[1:], device=dev)
+    for _ in range(3):
+        net.forward(xb, yb)
+    times = []
+    for _ in range(10):
+        e0.record(st)
+        net.forward(xb, yb)
+        e1.record(st)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+    t_fno = float(np.median(times)) / batch
+    t_lbm = [time_lbm_to_end(test_s[k], storage=storage, n_ft=n_ft, ft_start=min(5.0, n_ft / 3.0))
+             for k in keep_te[:3]]
+    report["fno_seconds_per_sample"] = t_fno
+    report["lbm_seconds_per_sample_15ft"] = t_lbm
+    report["speedup_median"] = float(np.median(t_lbm) / t_fno)
+    report["speedup_note"] = ("FNO forward of a batch of 8 divided by 8 (inputs resident) vs one held-out "
+                              "seed's LBM run alone to the end (CUDA events, graph-replayed batched driver)")
+    log(json.dumps({k: report[k] for k in ("rel_l2_uvw", "baseline_train_mean_rel_l2_uvw", "speedup_median",
+                                            "fno_seconds_per_sample", "train_samples_per_s")}))
+    if out:
+        with open(out, "w") as fp:
+            json.dump(report, fp, indent=1)
+    net.close()
+    return report
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--out", default=None)
+    ap.add_argument("--quick", action="store_true", help="small end-to-end check")
+    ap.add_argument("--storage", default="f16c")
+    ap.add_argument("--epochs", type=int, default=50)
+    args = ap.parse_args()
+    if args.quick:
+        run(n_train=16, n_test=8, epochs=2, n_ft=2.0, storage=args.storage, out=args.out, sim_batch=24)
+    else:
+        run(epochs=args.epochs, storage=args.storage, out=args.out)
+
+
+if __name__ == "__main__":
+    main()
