@@ -111,6 +111,224 @@ __global__ void __launch_bounds__(TPB) k_pw_fwd_out(const TI *x, int ci, int co,
     }
 }
 
+__device__ __forceinline__ float4 ld4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
+__device__ __forceinline__ float4 ld4(const __nv_bfloat16 *p)
+{
+    const uint2 u = *reinterpret_cast<const uint2 *>(p);
+    const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&u.x));
+    const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&u.y));
+    return make_float4(a.x, a.y, b.x, b.y);
+}
+
+// Copies `total` floats (a multiple of 4) into shared memory from a
+// contiguous source of which the first `cnt` are valid (zeros after), with
+// eight 4-element loads in flight per thread.
+template <class TI>
+__device__ __forceinline__ void stage4(float *dst, const TI *src, int cnt, int total)
+{
+    const int step = 4 * blockDim.x;
+    for (int k0 = 4 * threadIdx.x; k0 < total; k0 += 8 * step) {
+        float4 v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int k = k0 + u * step;
+            v[u] = k < cnt ? ld4(src + k) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int k = k0 + u * step;
+            if (k < total) *reinterpret_cast<float4 *>(dst + k) = v[u];
+        }
+    }
+}
+
+// Two adjacent cells per thread (N even): loads and stores of pairs, each
+// weight read from shared memory serves both cells.
+__device__ __forceinline__ float2 ld2(const float *p) { return *reinterpret_cast<const float2 *>(p); }
+__device__ __forceinline__ float2 ld2(const __nv_bfloat16 *p)
+{
+    return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(p));
+}
+__device__ __forceinline__ void st2(float *p, float a, float b) { *reinterpret_cast<float2 *>(p) = make_float2(a, b); }
+__device__ __forceinline__ void st2(__nv_bfloat16 *p, float a, float b)
+{
+    *reinterpret_cast<__nv_bfloat162 *>(p) = __floats2bfloat162_rn(a, b);
+}
+
+// y = act(W x + b + extra) for CI inputs (a multiple of 4) held in registers.
+template <class TI, class TO, int CI>
+__global__ void __launch_bounds__(TPB) k_pw_fwd_in2(const TI *x, int co, const float *W, const float *bias,
+                                                    const float *extra, TO *pre, TO *y, int act, int64_t N, int B)
+{
+    extern __shared__ float4 smv[];
+    float *sw = reinterpret_cast<float *>(smv), *sb = sw + co * CI;
+    for (int k = threadIdx.x; k < co * CI; k += blockDim.x) sw[k] = W[k];
+    for (int k = threadIdx.x; k < co; k += blockDim.x) sb[k] = bias[k];
+    __syncthreads();
+    const int64_t half = N / 2;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < (int64_t)B * half;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = idx / half, n = 2 * (idx - b * half);
+        float2 xv[CI];
+#pragma unroll
+        for (int i = 0; i < CI; ++i) xv[i] = ld2(x + (b * CI + i) * N + n);
+        for (int o0 = 0; o0 < co; o0 += 8) {                 // co % 8 == 0
+            float2 e[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) e[u] = extra ? ld2(extra + (b * co + o0 + u) * N + n) : make_float2(0.f, 0.f);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int o = o0 + u;
+                float a0 = sb[o] + e[u].x, a1 = sb[o] + e[u].y;
+                const float4 *w4 = reinterpret_cast<const float4 *>(sw + o * CI);
+#pragma unroll
+                for (int q = 0; q < CI / 4; ++q) {
+                    const float4 w = w4[q];
+                    a0 += w.x * xv[4 * q].x + w.y * xv[4 * q + 1].x + w.z * xv[4 * q + 2].x + w.w * xv[4 * q + 3].x;
+                    a1 += w.x * xv[4 * q].y + w.y * xv[4 * q + 1].y + w.z * xv[4 * q + 2].y + w.w * xv[4 * q + 3].y;
+                }
+                const int64_t off = (b * co + o) * N + n;
+                if (pre) st2(pre + off, a0, a1);
+                st2(y + off, act ? gelu(a0) : a0, act ? gelu(a1) : a1);
+            }
+        }
+    }
+}
+
+// y = W x + b (FP32 out) for co <= 8 outputs and any number of inputs; the
+// weights are transposed in shared memory to [ci][8].
+template <class TI>
+__global__ void __launch_bounds__(TPB) k_pw_fwd_out2(const TI *x, int ci, int co, const float *W, const float *bias,
+                                                     float *y, int64_t N, int B)
+{
+    extern __shared__ float4 smv[];
+    float *swt = reinterpret_cast<float *>(smv);
+    for (int k = threadIdx.x; k < ci * 8; k += blockDim.x) {
+        const int i = k / 8, o = k % 8;
+        swt[k] = o < co ? W[o * ci + i] : 0.f;
+    }
+    __syncthreads();
+    const int64_t half = N / 2;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < (int64_t)B * half;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = idx / half, n = 2 * (idx - b * half);
+        float2 acc[8];
+#pragma unroll
+        for (int o = 0; o < 8; ++o) acc[o] = o < co ? make_float2(bias[o], bias[o]) : make_float2(0.f, 0.f);
+        for (int i0 = 0; i0 < ci; i0 += 8) {                 // ci % 8 == 0
+            float2 xv[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) xv[u] = ld2(x + (b * ci + i0 + u) * N + n);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const float4 wa = reinterpret_cast<const float4 *>(swt)[2 * (i0 + u)];
+                const float4 wb = reinterpret_cast<const float4 *>(swt)[2 * (i0 + u) + 1];
+                const float w[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
+#pragma unroll
+                for (int o = 0; o < 8; ++o) {
+                    acc[o].x += w[o] * xv[u].x;
+                    acc[o].y += w[o] * xv[u].y;
+                }
+            }
+        }
+#pragma unroll
+        for (int o = 0; o < 8; ++o)
+            if (o < co) st2(y + (b * co + o) * N + n, acc[o].x, acc[o].y);
+    }
+}
+
+// gx = (W^T g) * (pre_in ? gelu'(pre_in) : 1) for CI inputs (a multiple of 4).
+template <class TP, int CI>
+__global__ void __launch_bounds__(TPB) k_pw_bwd_in2(const float *g, int co, const float *W, const TP *pre_in,
+                                                    float *gx, int64_t N, int B)
+{
+    extern __shared__ float4 smv[];
+    float *sw = reinterpret_cast<float *>(smv);
+    for (int k = threadIdx.x; k < co * CI; k += blockDim.x) sw[k] = W[k];
+    __syncthreads();
+    const int64_t half = N / 2;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < (int64_t)B * half;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = idx / half, n = 2 * (idx - b * half);
+        float2 acc[CI];
+#pragma unroll
+        for (int i = 0; i < CI; ++i) acc[i] = make_float2(0.f, 0.f);
+        for (int o0 = 0; o0 < co; o0 += 8) {                 // co % 8 == 0
+            float2 gq[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) gq[u] = ld2(g + (b * co + o0 + u) * N + n);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const float2 gv = gq[u];
+                const float4 *w4 = reinterpret_cast<const float4 *>(sw + (o0 + u) * CI);
+#pragma unroll
+                for (int q = 0; q < CI / 4; ++q) {
+                    const float4 w = w4[q];
+                    acc[4 * q].x += w.x * gv.x;     acc[4 * q].y += w.x * gv.y;
+                    acc[4 * q + 1].x += w.y * gv.x; acc[4 * q + 1].y += w.y * gv.y;
+                    acc[4 * q + 2].x += w.z * gv.x; acc[4 * q + 2].y += w.z * gv.y;
+                    acc[4 * q + 3].x += w.w * gv.x; acc[4 * q + 3].y += w.w * gv.y;
+                }
+            }
+        }
+        if (pre_in) {
+#pragma unroll
+            for (int i = 0; i < CI; ++i) {
+                const float2 p = ld2(pre_in + (b * CI + i) * N + n);
+                acc[i].x *= gelu_grad(p.x);
+                acc[i].y *= gelu_grad(p.y);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < CI; ++i) st2(gx + (b * CI + i) * N + n, acc[i].x, acc[i].y);
+    }
+}
+
+// Same for co <= 8 gradient rows and any number of inputs ([ci][8] weights).
+template <class TP>
+__global__ void __launch_bounds__(TPB) k_pw_bwd_out2(const float *g, int co, int ci, const float *W, const TP *pre_in,
+                                                     float *gx, int64_t N, int B)
+{
+    extern __shared__ float4 smv[];
+    float *swt = reinterpret_cast<float *>(smv);
+    for (int k = threadIdx.x; k < ci * 8; k += blockDim.x) {
+        const int i = k / 8, o = k % 8;
+        swt[k] = o < co ? W[o * ci + i] : 0.f;
+    }
+    __syncthreads();
+    const int64_t half = N / 2;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < (int64_t)B * half;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = idx / half, n = 2 * (idx - b * half);
+        float2 gv[8];
+#pragma unroll
+        for (int o = 0; o < 8; ++o) gv[o] = o < co ? ld2(g + (b * co + o) * N + n) : make_float2(0.f, 0.f);
+        for (int i0 = 0; i0 < ci; i0 += 8) {                 // ci % 8 == 0
+            float2 p[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) p[u] = pre_in ? ld2(pre_in + (b * ci + i0 + u) * N + n) : make_float2(0.f, 0.f);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int i = i0 + u;
+                const float4 wa = reinterpret_cast<const float4 *>(swt)[2 * i];
+                const float4 wb = reinterpret_cast<const float4 *>(swt)[2 * i + 1];
+                const float w[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
+                float2 a = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int o = 0; o < 8; ++o) {
+                    a.x += w[o] * gv[o].x;
+                    a.y += w[o] * gv[o].y;
+                }
+                if (pre_in) {
+                    a.x *= gelu_grad(p[u].x);
+                    a.y *= gelu_grad(p[u].y);
+                }
+                st2(gx + (b * ci + i) * N + n, a.x, a.y);
+            }
+        }
+    }
+}
+
 // gx = (W^T g) * (act ? gelu'(pre_in) : 1), ci <= 32 (gx accumulated in registers).
 template <class TP>
 __global__ void __launch_bounds__(TPB) k_pw_bwd_in(const float *g, int co, int ci, const float *W, const TP *pre_in,
@@ -165,63 +383,124 @@ __global__ void __launch_bounds__(TPB) k_pw_bwd_out(const float *g, int co, int 
     }
 }
 
-// gW[o][i] += sum_{b,cell} g[b][o][cell] x[b][i][cell], gb[o] += sum g.  Each
-// block reduces a chunk of cells through shared-memory tiles and adds its
-// partial sums atomically.
+// gW[o][i] += sum_{b,cell} g[b][o][cell] x[b][i][cell], gb[o] += sum g.  A
+// block reduces a chunk of cells: tiles of OUTER_TILE cells are staged in
+// shared memory as rows [channel][cell]; a thread owns four outputs o0..o0+3
+// and four inputs i0 + 8u (u < 4) and walks a range of the tile four cells at
+// a time (float4).  The eight lanes of a quarter warp share o0 (broadcast
+// reads) and take consecutive i0 (rows 68 floats apart: distinct banks).
+// When there are fewer than TPB such units, `groups` threads split the cells
+// of a tile.  Partial sums are added atomically at the end.
 constexpr int OUTER_TILE = 64;
-constexpr int OUTER_LD = OUTER_TILE + 1;           // padded row: no bank conflicts
+constexpr int OUTER_LD = OUTER_TILE + 4;
 constexpr int OUTER_CHUNK = 8192;
-constexpr int OUTER_PAIRS = 20;                     // pairs (o, i) per thread: co * (ci + 1) <= 5120
 
-template <class TX>
+template <class TX, int UPT>
 __global__ void __launch_bounds__(TPB) k_outer(const float *g, int co, const TX *x, int ci, float *gW, float *gb,
-                                               int64_t N, int B)
+                                               int64_t N, int B, int groups)
 {
-    extern __shared__ float sm[];
-    float *sg = sm, *sx = sm + co * OUTER_LD;
-    const int np = co * (ci + 1);                      // pairs (o, i), i = ci is the bias
-    float acc[OUTER_PAIRS];
+    extern __shared__ float4 smv[];
+    const int cop = (co + 3) & ~3, cip = ((ci + 31) / 32) * 32;
+    const int nog = cop / 4, units = nog * (cip / 32) * 8;
+    const int qpg = (OUTER_TILE / 4) / groups;
+    float *sg = reinterpret_cast<float *>(smv);              // [cop][OUTER_LD]
+    float *sx = sg + (size_t)cop * OUTER_LD;                 // [cip][OUTER_LD]
+    float acc[UPT][16], bacc[UPT][4];
 #pragma unroll
-    for (int k = 0; k < OUTER_PAIRS; ++k) acc[k] = 0.f;
+    for (int u = 0; u < UPT; ++u) {
+#pragma unroll
+        for (int k = 0; k < 16; ++k) acc[u][k] = 0.f;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) bacc[u][k] = 0.f;
+    }
     const int64_t total = (int64_t)B * N;
     const int64_t c0 = (int64_t)blockIdx.x * OUTER_CHUNK;
     const int64_t c1 = c0 + OUTER_CHUNK < total ? c0 + OUTER_CHUNK : total;
+    const int jst = threadIdx.x % OUTER_TILE, chst = threadIdx.x / OUTER_TILE;
+    const bool vec = N % OUTER_TILE == 0;                   // whole tiles inside one batch element
+    constexpr int QPR = OUTER_TILE / 4;                     // float4 per staged row
     for (int64_t t0 = c0; t0 < c1; t0 += OUTER_TILE) {
         __syncthreads();
-        for (int k = threadIdx.x; k < (co + ci) * OUTER_TILE; k += blockDim.x) {
-            const int ch = k / OUTER_TILE, j = k % OUTER_TILE;
-            const int64_t cell = t0 + j;
-            float v = 0.f;
-            if (cell < c1) {
-                const int64_t b = cell / N, n = cell - b * N;
-                v = ch < co ? g[(b * co + ch) * N + n] : ldf(x + (b * ci + (ch - co)) * N + n);
+        if (vec) {
+            const int64_t b = t0 / N, n0 = t0 - b * N;
+            const int tot = (cop + cip) * QPR;
+            for (int k0 = threadIdx.x; k0 < tot; k0 += 8 * TPB) {
+                float4 v[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {               // eight loads in flight before any store
+                    const int k = k0 + u * TPB, ch = k / QPR, q = k % QPR;
+                    v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (k < tot) {
+                        if (ch < co) v[u] = ld4(g + (b * co + ch) * N + n0 + 4 * q);
+                        else if (ch >= cop && ch - cop < ci) v[u] = ld4(x + (b * ci + (ch - cop)) * N + n0 + 4 * q);
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int k = k0 + u * TPB;
+                    if (k < tot) *reinterpret_cast<float4 *>(sg + (k / QPR) * OUTER_LD + 4 * (k % QPR)) = v[u];
+                }
             }
-            sm[ch * OUTER_LD + j] = v;
+        } else {
+            const int64_t cell = t0 + jst;
+            const bool cv = cell < c1;
+            const int64_t b = cv ? cell / N : 0, n = cell - b * N;
+            for (int ch = chst; ch < cop + cip; ch += TPB / OUTER_TILE) {
+                float v = 0.f;
+                if (cv) {
+                    if (ch < co) v = g[(b * co + ch) * N + n];
+                    else if (ch >= cop && ch - cop < ci) v = ldf(x + (b * ci + (ch - cop)) * N + n);
+                }
+                sg[ch * OUTER_LD + jst] = v;
+            }
         }
         __syncthreads();
 #pragma unroll
-        for (int k = 0; k < OUTER_PAIRS; ++k) {
-            const int pidx = threadIdx.x + k * TPB;
-            if (pidx < np) {
-                const int o = pidx / (ci + 1), i = pidx % (ci + 1);
-                float s = 0.f;
-                if (i < ci)
-                    for (int j = 0; j < OUTER_TILE; ++j) s += sg[o * OUTER_LD + j] * sx[i * OUTER_LD + j];
-                else
-                    for (int j = 0; j < OUTER_TILE; ++j) s += sg[o * OUTER_LD + j];
-                acc[k] += s;
+        for (int u = 0; u < UPT; ++u) {
+            const int t = threadIdx.x + u * TPB;
+            if (t >= units * groups) break;
+            const int unit = t % units, grp = t / units;
+            const int l8 = unit & 7, rest = unit >> 3;
+            const int o0 = (rest % nog) * 4, i0 = (rest / nog) * 32 + l8;
+            const bool bias = l8 == 0 && rest < nog;
+            for (int q = grp * qpg; q < (grp + 1) * qpg; ++q) {
+                float4 gv[4], xv[4];
+#pragma unroll
+                for (int a = 0; a < 4; ++a) gv[a] = *reinterpret_cast<const float4 *>(sg + (o0 + a) * OUTER_LD + 4 * q);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) xv[c] = *reinterpret_cast<const float4 *>(sx + (i0 + 8 * c) * OUTER_LD + 4 * q);
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c)
+                        acc[u][4 * a + c] += gv[a].x * xv[c].x + gv[a].y * xv[c].y + gv[a].z * xv[c].z + gv[a].w * xv[c].w;
+                if (bias) {
+#pragma unroll
+                    for (int a = 0; a < 4; ++a) bacc[u][a] += gv[a].x + gv[a].y + gv[a].z + gv[a].w;
+                }
             }
         }
     }
 #pragma unroll
-    for (int k = 0; k < OUTER_PAIRS; ++k) {
-        const int pidx = threadIdx.x + k * TPB;
-        if (pidx < np) {
-            const int o = pidx / (ci + 1), i = pidx % (ci + 1);
-            atomicAdd(i < ci ? &gW[o * ci + i] : &gb[o], acc[k]);
+    for (int u = 0; u < UPT; ++u) {
+        const int t = threadIdx.x + u * TPB;
+        if (t >= units * groups) break;
+        const int unit = t % units;
+        const int l8 = unit & 7, rest = unit >> 3;
+        const int o0 = (rest % nog) * 4, i0 = (rest / nog) * 32 + l8;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            if (o0 + a >= co) continue;
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                if (i0 + 8 * c < ci) atomicAdd(&gW[(o0 + a) * ci + i0 + 8 * c], acc[u][4 * a + c]);
+            if (l8 == 0 && rest < nog) atomicAdd(&gb[o0 + a], bacc[u][a]);
         }
     }
 }
+
+int outer_units(int co, int ci) { return ((co + 3) / 4) * ((ci + 31) / 32) * 8; }
+size_t smem_outer(int co, int ci) { return sizeof(float) * (size_t)(((co + 3) & ~3) + ((ci + 31) / 32) * 32) * OUTER_LD; }
 
 // ---------------------------------------------------------------------------
 // truncated DFT: forward stages x -> y -> z, inverse stages z -> y -> x.
@@ -233,57 +512,114 @@ struct Dims {
     int64_t BC;
 };
 
-// rows [R][nx] (real) -> A [R][Kx] (complex)
+constexpr int DFT_RT = 8;                            // rows per warp in the x stages
+constexpr int DFT_ROWS = DFT_RT * (TPB / 32);        // rows per block pass in the x stages
+
+// rows [R][nx] (real) -> A [R][Kx] (complex).  A block stages DFT_ROWS rows
+// in shared memory (padded to nxp, a multiple of 4); lane j of a warp owns
+// mode j (chunks of 32) for the warp's DFT_RT rows, reading the rows four
+// samples at a time (float4 broadcast) against twiddles tw[x][j] held in
+// shared memory (consecutive in j: conflict-free).
 template <class TI>
 __global__ void __launch_bounds__(TPB) k_dftx_fwd(const TI *x, float2 *A, const float2 *twx, Dims d, int64_t R)
 {
-    extern __shared__ float2 smc[];
-    float2 *tw = smc;                                   // [nx][Kx]
-    float *rows = reinterpret_cast<float *>(smc + d.nx * d.Kx);
-    for (int k = threadIdx.x; k < d.nx * d.Kx; k += blockDim.x) tw[k] = twx[k];
-    const int rpb = blockDim.x / d.Kx;                  // rows per group
-    for (int64_t r0 = (int64_t)blockIdx.x * rpb; r0 < R; r0 += (int64_t)gridDim.x * rpb) {
+    extern __shared__ float4 smv[];
+    const int nxp = (d.nx + 3) & ~3, nq = nxp / 4;
+    float2 *tw = reinterpret_cast<float2 *>(smv);                           // [nxp][Kx]
+    float *rows = reinterpret_cast<float *>(tw + (size_t)nxp * d.Kx);      // [DFT_ROWS][nxp]
+    for (int k = threadIdx.x; k < nxp * d.Kx; k += blockDim.x)
+        tw[k] = k < d.nx * d.Kx ? twx[k] : make_float2(0.f, 0.f);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int64_t r0 = (int64_t)blockIdx.x * DFT_ROWS; r0 < R; r0 += (int64_t)gridDim.x * DFT_ROWS) {
+        const int nr = (int)(R - r0 < DFT_ROWS ? R - r0 : DFT_ROWS);
         __syncthreads();
-        for (int k = threadIdx.x; k < rpb * d.nx; k += blockDim.x) {
-            const int64_t r = r0 + k / d.nx;
-            rows[k] = r < R ? ldf(x + r0 * d.nx + k) : 0.f;
+        if (nxp == d.nx) {                                  // rows are one contiguous run
+            stage4(rows, x + r0 * d.nx, nr * d.nx, DFT_ROWS * nxp);
+        } else {
+            for (int k = threadIdx.x; k < DFT_ROWS * nxp; k += blockDim.x) {
+                const int lr = k / nxp, xx = k - lr * nxp;
+                rows[k] = (lr < nr && xx < d.nx) ? ldf(x + (r0 + lr) * d.nx + xx) : 0.f;
+            }
         }
         __syncthreads();
-        const int lr = threadIdx.x / d.Kx, j = threadIdx.x % d.Kx;
-        const int64_t r = r0 + lr;
-        if (lr < rpb && r < R) {
-            float2 acc = make_float2(0.f, 0.f);
-            const float *row = rows + lr * d.nx;
-            for (int xx = 0; xx < d.nx; ++xx) {
-                const float2 t = tw[xx * d.Kx + j];
-                acc.x += row[xx] * t.x;
-                acc.y += row[xx] * t.y;
+        const float4 *rw = reinterpret_cast<const float4 *>(rows) + (size_t)warp * DFT_RT * nq;
+        for (int j0 = 0; j0 < d.Kx; j0 += 32) {
+            const int j = j0 + lane;
+            const int jj = j < d.Kx ? j : d.Kx - 1;
+            float2 acc[DFT_RT];
+#pragma unroll
+            for (int r = 0; r < DFT_RT; ++r) acc[r] = make_float2(0.f, 0.f);
+            for (int q = 0; q < nq; ++q) {
+                const float2 t0 = tw[(4 * q) * d.Kx + jj], t1 = tw[(4 * q + 1) * d.Kx + jj];
+                const float2 t2 = tw[(4 * q + 2) * d.Kx + jj], t3 = tw[(4 * q + 3) * d.Kx + jj];
+#pragma unroll
+                for (int r = 0; r < DFT_RT; ++r) {
+                    const float4 v = rw[r * nq + q];
+                    acc[r].x += v.x * t0.x + v.y * t1.x + v.z * t2.x + v.w * t3.x;
+                    acc[r].y += v.x * t0.y + v.y * t1.y + v.z * t2.y + v.w * t3.y;
+                }
             }
-            A[r * d.Kx + j] = acc;
+            if (j < d.Kx) {
+#pragma unroll
+                for (int r = 0; r < DFT_RT; ++r)
+                    if (warp * DFT_RT + r < nr) A[(r0 + warp * DFT_RT + r) * d.Kx + j] = acc[r];
+            }
         }
     }
 }
 
-// A [S][ny][Kx] -> B [S][Ky][Kx], S = BC*nz slabs
-__global__ void __launch_bounds__(TPB) k_dfty_fwd(const float2 *A, float2 *Bt, const float2 *twy, Dims d, int64_t S)
+// A [S][ny][Kx] -> B [S][Ky][Kx] = sum_y A exp(-i 2 pi ky y / ny), S = BC*nz
+// slabs.  A block stages SB slabs per pass; a warp takes one slab and eight
+// consecutive jy, a lane one jx; twiddles tw[y][jy] (jy padded to kyp, a
+// multiple of 8) are read as float4 broadcasts.
+__global__ void __launch_bounds__(TPB) k_dfty_fwd(const float2 *A, float2 *Bt, const float2 *twy, Dims d, int64_t S,
+                                                  int SB)
 {
-    extern __shared__ float2 smc[];
-    float2 *tw = smc;                                   // [ny][Ky]
-    float2 *slab = smc + d.ny * d.Ky;                   // [ny][Kx]
-    for (int k = threadIdx.x; k < d.ny * d.Ky; k += blockDim.x) tw[k] = twy[k];
-    for (int64_t s = blockIdx.x; s < S; s += gridDim.x) {
+    extern __shared__ float4 smv[];
+    const int kyp = (d.Ky + 7) & ~7, cps = kyp / 8;
+    const int slab_n = d.ny * d.Kx;
+    float2 *tw = reinterpret_cast<float2 *>(smv);                           // [ny][kyp]
+    float2 *slab = tw + (size_t)d.ny * kyp;                                 // [SB][ny][Kx]
+    for (int k = threadIdx.x; k < d.ny * kyp; k += blockDim.x) {
+        const int y = k / kyp, jy = k - y * kyp;
+        tw[k] = jy < d.Ky ? twy[y * d.Ky + jy] : make_float2(0.f, 0.f);
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int64_t s0 = (int64_t)blockIdx.x * SB; s0 < S; s0 += (int64_t)gridDim.x * SB) {
+        const int ns = (int)(S - s0 < SB ? S - s0 : SB);
         __syncthreads();
-        for (int k = threadIdx.x; k < d.ny * d.Kx; k += blockDim.x) slab[k] = A[s * d.ny * d.Kx + k];
+        stage4(reinterpret_cast<float *>(slab), reinterpret_cast<const float *>(A + s0 * slab_n), 2 * ns * slab_n,
+               2 * SB * slab_n);
         __syncthreads();
-        for (int o = threadIdx.x; o < d.Ky * d.Kx; o += blockDim.x) {
-            const int jy = o / d.Kx, jx = o % d.Kx;
-            float2 acc = make_float2(0.f, 0.f);
-            for (int y = 0; y < d.ny; ++y) {
-                const float2 v = cmul(slab[y * d.Kx + jx], tw[y * d.Ky + jy]);
-                acc.x += v.x;
-                acc.y += v.y;
+        for (int task = warp; task < ns * cps; task += TPB / 32) {
+            const int sb = task / cps, jc = task - sb * cps;
+            const float2 *sl = slab + (size_t)sb * slab_n;
+            for (int jx0 = 0; jx0 < d.Kx; jx0 += 32) {
+                const int jx = jx0 + lane;
+                const int jj = jx < d.Kx ? jx : d.Kx - 1;
+                float2 acc[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) acc[q] = make_float2(0.f, 0.f);
+                for (int y = 0; y < d.ny; ++y) {
+                    const float2 v = sl[y * d.Kx + jj];
+                    const float4 *t4 = reinterpret_cast<const float4 *>(tw + y * kyp + jc * 8);
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const float4 t = t4[u];
+                        acc[2 * u].x += v.x * t.x - v.y * t.y;
+                        acc[2 * u].y += v.x * t.y + v.y * t.x;
+                        acc[2 * u + 1].x += v.x * t.z - v.y * t.w;
+                        acc[2 * u + 1].y += v.x * t.w + v.y * t.z;
+                    }
+                }
+                if (jx < d.Kx) {
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        const int jy = jc * 8 + q;
+                        if (jy < d.Ky) Bt[((s0 + sb) * d.Ky + jy) * d.Kx + jx] = acc[q];
+                    }
+                }
             }
-            Bt[s * d.Ky * d.Kx + o] = acc;
         }
     }
 }
@@ -346,62 +682,134 @@ __global__ void __launch_bounds__(TPB) k_dftz_inv(const float2 *Sp, float2 *Ht, 
     }
 }
 
-// H [S][Ky][Kx] -> I [S][ny][Kx] = sum_jy H exp(+i 2 pi ky y / ny)
-__global__ void __launch_bounds__(TPB) k_dfty_inv(const float2 *Ht, float2 *It, const float2 *twy, Dims d, int64_t S)
+// H [S][Ky][Kx] -> I [S][ny][Kx] = sum_jy H exp(+i 2 pi ky y / ny).  A warp
+// takes one slab and eight consecutive y, a lane one jx; the twiddles are
+// transposed into twT[jy][y] (y padded to nyp) so that eight y are two
+// float4 broadcasts.
+__global__ void __launch_bounds__(TPB) k_dfty_inv(const float2 *Ht, float2 *It, const float2 *twy, Dims d, int64_t S,
+                                                  int SB)
 {
-    extern __shared__ float2 smc[];
-    float2 *tw = smc;                                   // [ny][Ky]
-    float2 *slab = smc + d.ny * d.Ky;                   // [Ky][Kx]
-    for (int k = threadIdx.x; k < d.ny * d.Ky; k += blockDim.x) tw[k] = twy[k];
-    for (int64_t s = blockIdx.x; s < S; s += gridDim.x) {
+    extern __shared__ float4 smv[];
+    const int nyp = (d.ny + 7) & ~7, cps = nyp / 8;
+    const int slab_n = d.Ky * d.Kx;
+    float2 *tw = reinterpret_cast<float2 *>(smv);                           // [Ky][nyp]
+    float2 *slab = tw + (size_t)d.Ky * nyp;                                 // [SB][Ky][Kx]
+    for (int k = threadIdx.x; k < d.Ky * nyp; k += blockDim.x) {
+        const int jy = k / nyp, y = k - jy * nyp;
+        tw[k] = y < d.ny ? twy[y * d.Ky + jy] : make_float2(0.f, 0.f);
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int64_t s0 = (int64_t)blockIdx.x * SB; s0 < S; s0 += (int64_t)gridDim.x * SB) {
+        const int ns = (int)(S - s0 < SB ? S - s0 : SB);
         __syncthreads();
-        for (int k = threadIdx.x; k < d.Ky * d.Kx; k += blockDim.x) slab[k] = Ht[s * d.Ky * d.Kx + k];
+        stage4(reinterpret_cast<float *>(slab), reinterpret_cast<const float *>(Ht + s0 * slab_n), 2 * ns * slab_n,
+               2 * SB * slab_n);
         __syncthreads();
-        for (int o = threadIdx.x; o < d.ny * d.Kx; o += blockDim.x) {
-            const int y = o / d.Kx, jx = o % d.Kx;
-            float2 acc = make_float2(0.f, 0.f);
-            for (int jy = 0; jy < d.Ky; ++jy) {
-                const float2 v = cmulc(slab[jy * d.Kx + jx], tw[y * d.Ky + jy]);
-                acc.x += v.x;
-                acc.y += v.y;
+        for (int task = warp; task < ns * cps; task += TPB / 32) {
+            const int sb = task / cps, yc = task - sb * cps;
+            const float2 *sl = slab + (size_t)sb * slab_n;
+            for (int jx0 = 0; jx0 < d.Kx; jx0 += 32) {
+                const int jx = jx0 + lane;
+                const int jj = jx < d.Kx ? jx : d.Kx - 1;
+                float2 acc[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) acc[q] = make_float2(0.f, 0.f);
+                for (int jy = 0; jy < d.Ky; ++jy) {
+                    const float2 v = sl[jy * d.Kx + jj];
+                    const float4 *t4 = reinterpret_cast<const float4 *>(tw + jy * nyp + yc * 8);
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {               // v conj(t)
+                        const float4 t = t4[u];
+                        acc[2 * u].x += v.x * t.x + v.y * t.y;
+                        acc[2 * u].y += v.y * t.x - v.x * t.y;
+                        acc[2 * u + 1].x += v.x * t.z + v.y * t.w;
+                        acc[2 * u + 1].y += v.y * t.z - v.x * t.w;
+                    }
+                }
+                if (jx < d.Kx) {
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        const int y = yc * 8 + q;
+                        if (y < d.ny) It[((s0 + sb) * d.ny + y) * d.Kx + jx] = acc[q];
+                    }
+                }
             }
-            It[s * d.ny * d.Kx + o] = acc;
         }
     }
 }
 
 // I [R][Kx] -> out [R][nx] = Re sum_jx I exp(+i 2 pi kx x / nx); mode 0: store,
-// mode 1: add to out; then, if pre is given, multiply by gelu'(pre).
+// mode 1: add to out; then, if pre is given, multiply by gelu'(pre).  The
+// twiddles are transposed into twT[j][x] (x padded to a multiple of 128) so
+// that lane l reads x = l + 32u (u < 4) conflict-free; a warp takes DFT_RT
+// rows and reads their coefficients two modes at a time (float4 broadcast).
 template <class TP>
 __global__ void __launch_bounds__(TPB) k_dftx_inv(const float2 *It, float *out, const float2 *twx, Dims d, int64_t R,
                                                   int accumulate, const TP *pre)
 {
-    extern __shared__ float2 smc[];
-    float2 *tw = smc;                                   // [nx][Kx]
-    float2 *rows = smc + d.nx * d.Kx;                   // [rpb][Kx]
-    for (int k = threadIdx.x; k < d.nx * d.Kx; k += blockDim.x) tw[k] = twx[k];
-    const int rpb = 8;
-    for (int64_t r0 = (int64_t)blockIdx.x * rpb; r0 < R; r0 += (int64_t)gridDim.x * rpb) {
+    extern __shared__ float4 smv[];
+    const int ldx = (d.nx + 127) & ~127, kh = d.Kx / 2;
+    float2 *tw = reinterpret_cast<float2 *>(smv);                           // [Kx][ldx]
+    float4 *rows = reinterpret_cast<float4 *>(tw + (size_t)d.Kx * ldx);    // [DFT_ROWS][Kx/2]
+    for (int k = threadIdx.x; k < d.Kx * ldx; k += blockDim.x) {
+        const int j = k / ldx, xx = k - j * ldx;
+        tw[k] = xx < d.nx ? twx[xx * d.Kx + j] : make_float2(0.f, 0.f);
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int64_t r0 = (int64_t)blockIdx.x * DFT_ROWS; r0 < R; r0 += (int64_t)gridDim.x * DFT_ROWS) {
+        const int nr = (int)(R - r0 < DFT_ROWS ? R - r0 : DFT_ROWS);
         __syncthreads();
-        for (int k = threadIdx.x; k < rpb * d.Kx; k += blockDim.x) {
-            const int64_t r = r0 + k / d.Kx;
-            rows[k] = r < R ? It[r0 * d.Kx + k] : make_float2(0.f, 0.f);
-        }
+        stage4(reinterpret_cast<float *>(rows), reinterpret_cast<const float *>(It + r0 * d.Kx), 2 * nr * d.Kx,
+               2 * DFT_ROWS * d.Kx);
         __syncthreads();
-        for (int o = threadIdx.x; o < rpb * d.nx; o += blockDim.x) {
-            const int lr = o / d.nx, xx = o % d.nx;
-            const int64_t r = r0 + lr;
-            if (r >= R) continue;
-            float acc = 0.f;
-            const float2 *row = rows + lr * d.Kx;
-            for (int j = 0; j < d.Kx; ++j) {
-                const float2 t = tw[xx * d.Kx + j];
-                acc += row[j].x * t.x + row[j].y * t.y;     // Re(I conj(t))
+        const float4 *rw = rows + (size_t)warp * DFT_RT * kh;
+        for (int xc = 0; xc < d.nx; xc += 128) {
+            float acc[DFT_RT][4];
+#pragma unroll
+            for (int r = 0; r < DFT_RT; ++r)
+#pragma unroll
+                for (int u = 0; u < 4; ++u) acc[r][u] = 0.f;
+            for (int jp = 0; jp < kh; ++jp) {
+                float2 ta[4], tb[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    ta[u] = tw[(2 * jp) * ldx + xc + lane + 32 * u];
+                    tb[u] = tw[(2 * jp + 1) * ldx + xc + lane + 32 * u];
+                }
+#pragma unroll
+                for (int r = 0; r < DFT_RT; ++r) {
+                    const float4 v = rw[r * kh + jp];               // modes 2jp, 2jp+1 of row r
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        acc[r][u] += v.x * ta[u].x + v.y * ta[u].y + v.z * tb[u].x + v.w * tb[u].y;
+                }
             }
-            const int64_t off = r * d.nx + xx;
-            float v = accumulate ? out[off] + acc : acc;
-            if (pre) v *= gelu_grad(ldf(pre + off));
-            out[off] = v;
+            // epilogue four rows at a time: all loads of a group before its stores
+#pragma unroll
+            for (int r4 = 0; r4 < DFT_RT; r4 += 4) {
+                float prev[4][4], pv[4][4];
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int xx = xc + lane + 32 * u;
+                        const bool ok = warp * DFT_RT + r4 + r < nr && xx < d.nx;
+                        const int64_t off = (r0 + warp * DFT_RT + r4 + r) * d.nx + xx;
+                        prev[r][u] = ok && accumulate ? out[off] : 0.f;
+                        pv[r][u] = ok && pre ? ldf(pre + off) : 0.f;
+                    }
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int xx = xc + lane + 32 * u;
+                        if (warp * DFT_RT + r4 + r >= nr || xx >= d.nx) continue;
+                        const int64_t off = (r0 + warp * DFT_RT + r4 + r) * d.nx + xx;
+                        float v = acc[r4 + r][u] + prev[r][u];
+                        if (pre) v *= gelu_grad(pv[r][u]);
+                        out[off] = v;
+                    }
+            }
         }
     }
 }
@@ -598,6 +1006,45 @@ __global__ void k_adam(float *p, const float *g, float *m1, float *m2, int64_t n
     }
 }
 
+// shared memory of the transform stages (independent of the batch)
+size_t smem_dftx_fwd(const Dims &d)
+{
+    const size_t nxp = (d.nx + 3) & ~3;
+    return sizeof(float2) * nxp * d.Kx + sizeof(float) * DFT_ROWS * nxp;
+}
+size_t smem_dftx_inv(const Dims &d)
+{
+    const size_t ldx = (d.nx + 127) & ~127;
+    return sizeof(float2) * ((size_t)d.Kx * ldx + (size_t)DFT_ROWS * d.Kx);
+}
+int dfty_fwd_slabs(const Dims &d) { return std::max(1, (TPB / 32) / ((d.Ky + 7) / 8)); }
+int dfty_inv_slabs(const Dims &d) { return std::max(1, (TPB / 32) / ((d.ny + 7) / 8)); }
+size_t smem_dfty_fwd(const Dims &d)
+{
+    const size_t kyp = (d.Ky + 7) & ~7;
+    return sizeof(float2) * ((size_t)d.ny * kyp + (size_t)dfty_fwd_slabs(d) * d.ny * d.Kx);
+}
+size_t smem_dfty_inv(const Dims &d)
+{
+    const size_t nyp = (d.ny + 7) & ~7;
+    return sizeof(float2) * ((size_t)d.Ky * nyp + (size_t)dfty_inv_slabs(d) * d.Ky * d.Kx);
+}
+
+bool set_smem_limits(size_t bytes)
+{
+    const int b = (int)bytes;
+    const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    return cudaFuncSetAttribute(k_dftx_fwd<float>, a, b) == cudaSuccess &&
+           cudaFuncSetAttribute(k_dftx_fwd<__nv_bfloat16>, a, b) == cudaSuccess &&
+           cudaFuncSetAttribute(k_dftx_inv<float>, a, b) == cudaSuccess &&
+           cudaFuncSetAttribute(k_dftx_inv<__nv_bfloat16>, a, b) == cudaSuccess &&
+           cudaFuncSetAttribute(k_dfty_fwd, a, b) == cudaSuccess && cudaFuncSetAttribute(k_dfty_inv, a, b) == cudaSuccess &&
+           cudaFuncSetAttribute(k_outer<float, 1>, a, b) == cudaSuccess &&
+           cudaFuncSetAttribute(k_outer<float, 2>, a, b) == cudaSuccess &&
+           cudaFuncSetAttribute(k_outer<__nv_bfloat16, 1>, a, b) == cudaSuccess &&
+           cudaFuncSetAttribute(k_outer<__nv_bfloat16, 2>, a, b) == cudaSuccess;
+}
+
 bool on_device(const void *p)
 {
     cudaPointerAttributes at;
@@ -708,16 +1155,17 @@ extern "C" lbm_status fno_create(const fno_config *cfg, void *stream, fno_ctx **
         return bad("modes must satisfy 2mx <= nx, 2my <= ny, mz <= nz/2, mz <= 16");
     if (c.tensor_cores && c.width % 8 != 0) return bad("tensor-core contraction needs width % 8 == 0");
     if (2 * c.mx > 256) return bad("2mx must be <= 256");
-    const size_t smx = sizeof(float2) * c.nx * 2 * c.mx + sizeof(float) * (256 / (2 * c.mx)) * c.nx;
-    const size_t smi = sizeof(float2) * (c.nx * 2 * c.mx + 8 * 2 * c.mx);
-    const size_t smy = sizeof(float2) * (c.ny * 2 * c.my + c.ny * 2 * c.mx);
-    const int outer_ch = std::max(std::max(c.hidden + c.width, c.cout + c.hidden), std::max(2 * c.width, c.width + c.cin));
-    const size_t smo = sizeof(float) * outer_ch * (OUTER_TILE + 1);
-    if (smx > 48 * 1024 || smi > 48 * 1024 || smy > 48 * 1024 || smo > 48 * 1024)
+    const Dims d0{c.nx, c.ny, c.nz, 2 * c.mx, 2 * c.my, c.mz, 1};
+    const size_t sm_max = 160 * 1024;
+    if (smem_dftx_fwd(d0) > sm_max || smem_dftx_inv(d0) > sm_max || smem_dfty_fwd(d0) > sm_max ||
+        smem_dfty_inv(d0) > sm_max)
         return bad("grid x modes too large for the shared-memory twiddle tables");
-    if ((int64_t)c.hidden * (c.width + 1) > OUTER_PAIRS * TPB || (int64_t)c.cout * (c.hidden + 1) > OUTER_PAIRS * TPB ||
-        (int64_t)c.width * (c.width + 1) > OUTER_PAIRS * TPB)
+    if (outer_units(c.hidden, c.width) > 2 * TPB || outer_units(c.cout, c.hidden) > 2 * TPB ||
+        outer_units(c.width, c.width) > 2 * TPB || outer_units(c.width, c.cin) > 2 * TPB)
         return bad("layer too wide for the gradient reduction");
+    if (smem_outer(c.hidden, c.width) > sm_max || smem_outer(c.cout, c.hidden) > sm_max)
+        return bad("layer too wide for the gradient reduction tiles");
+    if (!set_smem_limits(sm_max)) return bad("cannot raise the shared-memory limit of the FNO kernels");
     fno_ctx *f = new fno_ctx();
     f->c = c;
     f->s = static_cast<cudaStream_t>(stream);
@@ -867,24 +1315,41 @@ template <class T>
 void pw_fwd(fno_ctx *f, const T *x, int ci, int co, int64_t oW, int64_t ob, const float *extra, T *pre, void *y,
             bool y_is_float, int act, int B)
 {
-    const size_t sm = sizeof(float) * (co * ci + co);
+    const bool pairs = f->N % 2 == 0;
+    const int64_t units = pairs ? (int64_t)B * f->N / 2 : (int64_t)B * f->N;
+    const float *W = f->params + oW, *bias = f->params + ob;
     if (ci <= 32 && !y_is_float) {
-        k_pw_fwd_in<T, T><<<grid_for((int64_t)B * f->N), TPB, sm, f->s>>>(x, ci, co, f->params + oW, f->params + ob, extra,
-                                                                        pre, static_cast<T *>(y), act, f->N, B);
+        const size_t sm = sizeof(float) * (co * ci + co);
+        T *yt = static_cast<T *>(y);
+        if (pairs && ci == 32 && co % 8 == 0)
+            k_pw_fwd_in2<T, T, 32><<<grid_for(units), TPB, sm, f->s>>>(x, co, W, bias, extra, pre, yt, act, f->N, B);
+        else if (pairs && ci == 4 && co % 8 == 0)
+            k_pw_fwd_in2<T, T, 4><<<grid_for(units), TPB, sm, f->s>>>(x, co, W, bias, extra, pre, yt, act, f->N, B);
+        else
+            k_pw_fwd_in<T, T><<<grid_for(units), TPB, sm, f->s>>>(x, ci, co, W, bias, extra, pre, yt, act, f->N, B);
+    } else if (pairs && ci % 8 == 0) {
+        k_pw_fwd_out2<T><<<grid_for(units), TPB, sizeof(float) * ci * 8, f->s>>>(x, ci, co, W, bias,
+                                                                                static_cast<float *>(y), f->N, B);
     } else {
-        k_pw_fwd_out<T><<<grid_for((int64_t)B * f->N), TPB, sm, f->s>>>(x, ci, co, f->params + oW, f->params + ob,
-                                                                      static_cast<float *>(y), f->N, B);
+        k_pw_fwd_out<T><<<grid_for(units), TPB, sizeof(float) * (co * ci + co), f->s>>>(x, ci, co, W, bias,
+                                                                                       static_cast<float *>(y), f->N, B);
     }
 }
 
 template <class T>
 void pw_bwd_input(fno_ctx *f, const float *g, int co, int ci, int64_t oW, const T *pre_in, float *gx, int B)
 {
-    const size_t sm = sizeof(float) * co * ci;
-    if (ci <= 32)
-        k_pw_bwd_in<T><<<grid_for((int64_t)B * f->N), TPB, sm, f->s>>>(g, co, ci, f->params + oW, pre_in, gx, f->N, B);
+    const bool pairs = f->N % 2 == 0;
+    const int64_t units = pairs ? (int64_t)B * f->N / 2 : (int64_t)B * f->N;
+    const float *W = f->params + oW;
+    if (pairs && ci == 32 && co % 8 == 0)
+        k_pw_bwd_in2<T, 32><<<grid_for(units), TPB, sizeof(float) * co * ci, f->s>>>(g, co, W, pre_in, gx, f->N, B);
+    else if (ci <= 32)
+        k_pw_bwd_in<T><<<grid_for(units), TPB, sizeof(float) * co * ci, f->s>>>(g, co, ci, W, pre_in, gx, f->N, B);
+    else if (pairs && ci % 8 == 0)
+        k_pw_bwd_out2<T><<<grid_for(units), TPB, sizeof(float) * ci * 8, f->s>>>(g, co, ci, W, pre_in, gx, f->N, B);
     else
-        k_pw_bwd_out<T><<<grid_for((int64_t)B * f->N), TPB, sm, f->s>>>(g, co, ci, f->params + oW, pre_in, gx, f->N, B);
+        k_pw_bwd_out<T><<<grid_for(units), TPB, sizeof(float) * co * ci, f->s>>>(g, co, ci, W, pre_in, gx, f->N, B);
 }
 
 template <class T>
@@ -892,8 +1357,14 @@ void outer(fno_ctx *f, const float *g, int co, const T *x, int ci, int64_t oW, i
 {
     const int64_t total = (int64_t)B * f->N;
     const int nb = (int)((total + OUTER_CHUNK - 1) / OUTER_CHUNK);
-    const size_t sm = sizeof(float) * (co + ci) * OUTER_LD;
-    k_outer<T><<<nb, TPB, sm, f->s>>>(g, co, x, ci, f->grads + oW, f->grads + ob, f->N, B);
+    const int units = outer_units(co, ci);
+    int groups = 1;
+    while (units * groups * 2 <= TPB && groups * 2 <= OUTER_TILE / 4) groups *= 2;
+    const size_t sm = smem_outer(co, ci);
+    if (units <= TPB)
+        k_outer<T, 1><<<nb, TPB, sm, f->s>>>(g, co, x, ci, f->grads + oW, f->grads + ob, f->N, B, groups);
+    else
+        k_outer<T, 2><<<nb, TPB, sm, f->s>>>(g, co, x, ci, f->grads + oW, f->grads + ob, f->N, B, groups);
 }
 
 Dims dims(const fno_ctx *f, int B)
@@ -907,12 +1378,12 @@ void dft_fwd(fno_ctx *f, const T *x, float2 *S, const float *scale, int B)
 {
     const Dims d = dims(f, B);
     const int64_t R = d.BC * d.nz * d.ny;
-    const int rpb = TPB / d.Kx;
-    const size_t smx = sizeof(float2) * d.nx * d.Kx + sizeof(float) * rpb * d.nx;
-    k_dftx_fwd<T><<<(int)std::min<int64_t>((R + rpb - 1) / rpb, 152 * 8), TPB, smx, f->s>>>(x, f->stA, f->twx, d, R);
+    k_dftx_fwd<T><<<(int)std::min<int64_t>((R + DFT_ROWS - 1) / DFT_ROWS, 152 * 8), TPB, smem_dftx_fwd(d), f->s>>>(
+        x, f->stA, f->twx, d, R);
     const int64_t Sl = d.BC * d.nz;
-    const size_t smy = sizeof(float2) * (d.ny * d.Ky + d.ny * d.Kx);
-    k_dfty_fwd<<<(int)std::min<int64_t>(Sl, 152 * 8), TPB, smy, f->s>>>(f->stA, f->stB, f->twy, d, Sl);
+    const int SB = dfty_fwd_slabs(d);
+    k_dfty_fwd<<<(int)std::min<int64_t>((Sl + SB - 1) / SB, 152 * 8), TPB, smem_dfty_fwd(d), f->s>>>(f->stA, f->stB,
+                                                                                                  f->twy, d, Sl, SB);
     k_dftz_fwd<<<grid_for(d.BC * d.Ky * d.Kx), TPB, 0, f->s>>>(f->stB, S, f->twz, scale, d);
 }
 
@@ -924,12 +1395,12 @@ void dft_inv(fno_ctx *f, const float2 *S, float *out, const float *scale, int ac
     const Dims d = dims(f, B);
     k_dftz_inv<<<grid_for(d.BC * d.Ky * d.Kx), TPB, 0, f->s>>>(S, f->stB, f->twz, scale, d);
     const int64_t Sl = d.BC * d.nz;
-    const size_t smy = sizeof(float2) * (d.ny * d.Ky + d.Ky * d.Kx);
-    k_dfty_inv<<<(int)std::min<int64_t>(Sl, 152 * 8), TPB, smy, f->s>>>(f->stB, f->stA, f->twy, d, Sl);
+    const int SB = dfty_inv_slabs(d);
+    k_dfty_inv<<<(int)std::min<int64_t>((Sl + SB - 1) / SB, 152 * 8), TPB, smem_dfty_inv(d), f->s>>>(f->stB, f->stA,
+                                                                                                  f->twy, d, Sl, SB);
     const int64_t R = d.BC * d.nz * d.ny;
-    const size_t smx = sizeof(float2) * (d.nx * d.Kx + 8 * d.Kx);
-    k_dftx_inv<TP><<<(int)std::min<int64_t>((R + 7) / 8, 152 * 8), TPB, smx, f->s>>>(f->stA, out, f->twx, d, R, accumulate,
-                                                                                    pre);
+    k_dftx_inv<TP><<<(int)std::min<int64_t>((R + DFT_ROWS - 1) / DFT_ROWS, 152 * 8), TPB, smem_dftx_inv(d), f->s>>>(
+        f->stA, out, f->twx, d, R, accumulate, pre);
 }
 
 void contract(fno_ctx *f, const float2 *Vin, int64_t oR, float2 *Gout, bool adj, int B)
