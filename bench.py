@@ -272,6 +272,24 @@ def run_batch(steps, warmup, storage="f16s", n=32):
     return out
 
 
+def run_fno(batch=8, reps=10):
+    """FNO surrogate at 128x64x64 (4 Fourier layers, width 32, modes 16x8x8,
+    BF16 activations, tensor-core mode contraction): forward and training-step
+    time for a batch of 8 with inputs resident, and the LBM run it replaces
+    (one held-out geometry of the surrogate's data set alone to 15
+    flow-through times, CUDA events).  Prediction accuracy comes from the
+    trained pipeline (paper_2606_16765_gb300.fno_pipeline), not from here."""
+    from paper_2606_16765_gb300 import fno_pipeline as P
+
+    r = P.time_fno(batch=batch, reps=reps)
+    t_lbm = P.time_lbm_to_end(P.sample(2000))
+    fwd = r["forward_ms_per_batch"]
+    return {"grid": list(P.GRID), "batch": batch, "forward_ms_per_batch": fwd,
+            "forward_ms_per_sample": fwd / batch, "train_step_ms": r["train_step_ms"],
+            "train_samples_per_s": batch / (r["train_step_ms"] / 1e3), "lbm_15ft_seconds_one_sample": t_lbm,
+            "speedup_vs_lbm": t_lbm / (fwd / batch / 1e3), "dtype": "bf16 activations, fp32 accumulation"}
+
+
 def cpu_baseline(d, seconds=12.0, box=(128, 96, 96)):
     """FP64 oracle on the host cores, on a sub-box of the same channel around
     the obstacle, stepped until ~`seconds` of CPU work."""
@@ -371,6 +389,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-fno", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -445,6 +464,8 @@ def main():
                 "clocks": r2["clocks"]}
         if not args.no_batch:
             line["batch"] = run_batch(args.steps, 20)
+        if not args.no_fno:
+            line["fno"] = run_fno()
         if not args.no_e2e:
             e = run_e2e(args, args.storage, d)
             line["e2e"] = {"value": e["fluid"] * K / e["seconds"] / 1e6, "unit": "MLUPS",

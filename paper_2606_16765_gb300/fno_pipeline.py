@@ -126,6 +126,40 @@ def time_lbm_to_end(s, storage="f16c", n_ft=15.0, ft_start=5.0):
     return secs * t_end / max(1, steps)
 
 
+def time_fno(batch=8, reps=10, warmup=3):
+    """Forward and training-step time (ms) of the default surrogate for one
+    batch of random inputs resident on the device (CUDA events)."""
+    import torch
+    from .fno import FNO
+
+    nx, ny, nz = GRID
+    net = FNO(nx=nx, ny=ny, nz=nz, max_batch=batch)
+    g = torch.Generator(device="cuda").manual_seed(0)
+    x = torch.rand((batch, 4, nz, ny, nx), device="cuda", generator=g)
+    t = torch.rand((batch, 4, nz, ny, nx), device="cuda", generator=g)
+    w = torch.ones((batch, nz, ny, nx), device="cuda")
+    y = torch.zeros((batch, 4, nz, ny, nx), device="cuda")
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    fwd = timed(lambda: net.forward(x, y))
+    train = timed(lambda: net.train_step(x, t, w, 1e-6))
+    net.close()
+    torch.cuda.empty_cache()
+    return {"batch": batch, "forward_ms_per_batch": fwd, "train_step_ms": train}
+
+
 def region_weights(mask):
     """Loss weights: inner region of the channel and fluid cells."""
     nz, ny, nx = mask.shape
@@ -289,8 +323,11 @@ def main():
     ap.add_argument("--quick", action="store_true", help="small end-to-end check")
     ap.add_argument("--storage", default="f16c")
     ap.add_argument("--epochs", type=int, default=50)
+    ap.add_argument("--time", action="store_true", help="only time forward and training step (random inputs)")
     args = ap.parse_args()
-    if args.quick:
+    if args.time:
+        print(json.dumps(time_fno()))
+    elif args.quick:
         run(n_train=16, n_test=8, epochs=2, n_ft=2.0, storage=args.storage, out=args.out, sim_batch=24)
     else:
         run(epochs=args.epochs, storage=args.storage, out=args.out)

@@ -1,0 +1,31 @@
+"""Host post-processing of the force record: Strouhal number and drag
+coefficient against closed forms."""
+import numpy as np
+import pytest
+
+from paper_2606_16765_gb300 import wake
+
+
+@pytest.mark.parametrize("f", [0.0031, 0.0123, 0.041])
+def test_dominant_frequency_of_a_noisy_sinusoid(f):
+    t = np.arange(12000)
+    x = 2.0 + np.sin(2 * np.pi * f * t + 0.7) + 0.3 * np.random.default_rng(1).normal(size=t.size)
+    # bin width 1/12000; the parabolic refinement lands well inside one bin
+    assert abs(wake.dominant_frequency(x) - f) < 0.15 / len(t)
+
+
+def test_strouhal_scales_with_sampling_interval_and_geometry():
+    t = np.arange(4000)
+    lift = np.cos(2 * np.pi * 0.002 * t * 5)          # sampled every 5 steps: 0.002 cycles per step
+    assert abs(wake.strouhal(lift, 16.0, 0.05, every=5) - 0.002 * 16 / 0.05) < 2e-3
+
+
+def test_drag_coefficient_closed_form():
+    fx = np.full(100, 0.8)
+    # C_d = 2 F / (rho U^2 D H)
+    assert wake.drag_coefficient(fx, 16.0, 128.0, 0.05) == pytest.approx(2 * 0.8 / (0.0025 * 16 * 128))
+
+
+def test_short_signal_is_rejected():
+    with pytest.raises(ValueError):
+        wake.dominant_frequency(np.ones(4))
