@@ -44,10 +44,11 @@ def measured_peaks():
 
 
 def kernel_source_hash():
+    """Hash of the LBM kernel sources (the FNO sources do not enter)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2606_16765_gb300", "csrc")
     for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh", ".h")):
+        if name.startswith("lbm") and name.endswith((".cu", ".cuh", ".h")):
             h.update(open(os.path.join(csrc, name), "rb").read())
     return h.hexdigest()[:16]
 

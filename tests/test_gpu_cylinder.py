@@ -1,0 +1,89 @@
+"""Cylinder channel 256x128x128 (spanwise cylinder D = 16 at x = 64, FP32
+AA pdfs): the obstacle force record against the FP64 oracle, and the wake
+measures (Strouhal number of the lift, drag coefficient) over 20,000 steps.
+
+  * Force trend: a half-size copy of the channel (128x64x64, D = 8) at the
+    shear rate of the Re = 3900 case, first 60 steps from rest; F(t) of the
+    FP32 step against the oracle's, max deviation <= 1e-5 of max |F_x| per
+    step (the same bound as the velocities).
+  * Wake: the full-size channel at Re = 200 on D (laminar shedding; the plain
+    operator's stable range, see below), seeded 1e-4 noise to break the
+    symmetry, FP64 mean from step 10,000, force every step.  St from the lift
+    spectrum of steps 10,000-20,000 must lie in [0.15, 0.30] and C_d in
+    [0.8, 3.0] (a confined cylinder, blockage D/H = 1/8).
+  * Re = 3900 itself (omega1 = 1.99877) is outside the plain operator's stable
+    range: the step latches the instability, and further steps are refused.
+"""
+import numpy as np
+import pytest
+
+import oracle.lbm as O
+from paper_2606_16765_gb300 import inputs as I
+from paper_2606_16765_gb300 import wake
+from tests import cases as K
+
+pytestmark = pytest.mark.gpu
+
+U = 0.05
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2606_16765_gb300 import _build
+    _build.build()
+
+
+def test_cylinder_force_record_matches_oracle():
+    grid = (128, 64, 64)
+    mask = I.cylinder_z(grid, (32.0, 31.5), 8.0)
+    w1 = O.omega_from_re(3900.0, U, 16.0)            # the Re = 3900 shear rate
+    c = K.case(grid, mask, omega1=w1, u_in=U)
+    L = K.run_oracle(c, 60)
+    Fr = L.forces()
+    s = K.make_solver(c, "f32", force_every=1)
+    s.step(60)
+    s.sync()
+    F = s.forces()
+    assert F.shape == Fr.shape == (60, 3)
+    scale = np.abs(Fr[:, 0]).max()
+    err = np.abs(F - Fr).max() / scale
+    print(f"cylinder force record, 60 steps: max |F - F_oracle| / max |Fx| = {err:.2e}")
+    assert err <= 1e-5
+
+
+def test_cylinder_wake_strouhal_and_drag():
+    from paper_2606_16765_gb300.lbm import Solver
+    grid = (256, 128, 128)
+    D = 16.0
+    mask = I.cylinder_z(grid, (64.0, 63.5), D)
+    s = Solver(grid, mask, storage="f32", re=200.0, u_in=U, l_ref=D, mean_start=10000, mean_end=20000,
+               mean_every=1, force_every=1, force_capacity=20000)
+    s.init_noise(7, 1e-4)
+    for _ in range(20):
+        s.step(1000)
+    s.sync()
+    F = s.forces()
+    assert F.shape == (20000, 3) and np.isfinite(F).all()
+    st = wake.strouhal(F[10000:, 1], D, U)
+    cd = wake.drag_coefficient(F[10000:, 0], D, grid[2], U)
+    m, ns = s.mean(halfres=True, dtype=np.float32)
+    print(f"cylinder Re 200: St = {st:.4f}, C_d = {cd:.4f}, mean samples {ns}, "
+          f"lift rms {F[10000:, 1].std():.4e}")
+    assert ns == 10000
+    assert 0.15 <= st <= 0.30
+    assert 0.8 <= cd <= 3.0
+
+
+def test_cylinder_re3900_latches_instability():
+    from paper_2606_16765_gb300.lbm import LBMError, Solver
+    grid = (256, 128, 128)
+    mask = I.cylinder_z(grid, (64.0, 63.5), 16.0)
+    s = Solver(grid, mask, storage="f32", re=3900.0, u_in=U, l_ref=16.0)
+    s.step(2000)
+    with pytest.raises(LBMError):
+        s.sync()
+    with pytest.raises(LBMError):
+        s.step(1)
