@@ -11,7 +11,7 @@ import numpy as np
 
 from . import build as _build
 
-FACE_WALL, FACE_PERIODIC, FACE_INLET, FACE_OUTLET = 0, 1, 2, 3
+FACE_WALL, FACE_PERIODIC, FACE_INLET, FACE_OUTLET, FACE_OUTFLOW = 0, 1, 2, 3, 4
 Q = 27
 
 
@@ -90,7 +90,7 @@ def params(nx, ny, nz, omega1, omega2=1.0, omega3=1.0, galilean=1, u_in=0.0,
            rho_in=1.0, rho_out=1.0, faces=("inlet", "outlet", "wall", "wall"),
            mean=(0, 0, 0)):
     kinds = {"wall": FACE_WALL, "periodic": FACE_PERIODIC,
-             "inlet": FACE_INLET, "outlet": FACE_OUTLET}
+             "inlet": FACE_INLET, "outlet": FACE_OUTLET, "outflow": FACE_OUTFLOW}
     p = OracleParams()
     p.nx, p.ny, p.nz = nx, ny, nz
     p.face_x_lo, p.face_x_hi, p.face_y, p.face_z = (kinds[f] for f in faces)

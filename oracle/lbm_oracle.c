@@ -61,8 +61,9 @@ void oracle_weights(double *w)
 
 /* ---- parameters ------------------------------------------------------ */
 
-/* Face kinds. */
-enum { FACE_WALL = 0, FACE_PERIODIC = 1, FACE_INLET = 2, FACE_OUTLET = 3 };
+/* Face kinds.  x high: FACE_OUTLET is the pressure outlet (anti-bounce-back
+ * at rho_out), FACE_OUTFLOW the convective extrapolation outflow. */
+enum { FACE_WALL = 0, FACE_PERIODIC = 1, FACE_INLET = 2, FACE_OUTLET = 3, FACE_OUTFLOW = 4 };
 
 typedef struct {
     int32_t nx, ny, nz;
@@ -433,7 +434,7 @@ static int in_sample_window(const oracle_params *p, int64_t t)
 
 /* Classification of the cell a link comes from / goes to (Sec. 3.1: velocity
  * inlet, outflow, no-slip lateral walls; obstacle bounce-back Sec. 3.2). */
-enum { SRC_FLUID = 0, SRC_WALL = 1, SRC_INLET = 2, SRC_OUTLET = 3 };
+enum { SRC_FLUID = 0, SRC_WALL = 1, SRC_INLET = 2, SRC_OUTLET = 3, SRC_OUTFLOW = 4 };
 
 static int classify(const oracle_lbm *o, int x, int y, int z, int64_t *cell)
 {
@@ -453,6 +454,7 @@ static int classify(const oracle_lbm *o, int x, int y, int z, int64_t *cell)
         x += p->nx;
     } else if (x >= p->nx) {
         if (p->face_x_hi == FACE_OUTLET) return SRC_OUTLET;
+        if (p->face_x_hi == FACE_OUTFLOW) return SRC_OUTFLOW;
         if (p->face_x_hi == FACE_WALL) return SRC_WALL;
         x -= p->nx;
     }
@@ -521,6 +523,26 @@ void oracle_lbm_step(oracle_lbm *o, int nsteps)
         o->force[3 * o->t + 1] = fy;
         o->force[3 * o->t + 2] = fz;
 
+        /* 3a. the outflow condition needs the pre-collision populations of
+         *     the outlet plane and of the plane next to it; streaming
+         *     overwrites f, so keep copies of both planes */
+        const int64_t P = (int64_t)p->ny * p->nz;
+        double *fo = NULL, *fi = NULL;
+        if (p->face_x_hi == FACE_OUTFLOW) {
+            fo = (double *)malloc(sizeof(double) * Q * P);
+            fi = (double *)malloc(sizeof(double) * Q * P);
+            for (int64_t yz = 0; yz < P; ++yz) {
+                const int64_t co = (int64_t)(p->nx - 1) + (int64_t)p->nx * yz;
+                /* an obstacle cell (or no cell) next to the outlet: the
+                 * outlet cell extrapolates from itself */
+                const int64_t ci = (p->nx >= 2 && !o->solid[co - 1]) ? co - 1 : co;
+                for (int i = 0; i < Q; ++i) {
+                    fo[i * P + yz] = o->f[i * n + co];
+                    fi[i * P + yz] = o->f[i * n + ci];
+                }
+            }
+        }
+
         /* 3. pull streaming with boundary rules: for fluid cell x and
          *    direction i the incoming value comes from x - c_i */
 #pragma omp parallel for schedule(static)
@@ -546,6 +568,17 @@ void oracle_lbm_step(oracle_lbm *o, int nsteps)
                             /* bounce-back from a wall moving with the inlet
                              * velocity (u_in, 0, 0) */
                             v = o->post[inv * n + c] + 6.0 * weight(i) * p->rho_in * (cx * p->u_in);
+                        } else if (kind == SRC_OUTFLOW) {
+                            /* convective outflow (Geier et al. 2015, App. F):
+                             * the missing population is carried out of the
+                             * domain at the speed of sound, first-order
+                             * upwind in time and space from the pre-collision
+                             * values of this cell and of its inner neighbour:
+                             * f_i(x_b, t+1) = c_s f_i(x_b - e_x, t)
+                             *                 + (1 - c_s) f_i(x_b, t) */
+                            const int64_t yz = (int64_t)y + (int64_t)p->ny * z;
+                            const double cs = sqrt(1.0 / 3.0);
+                            v = cs * fi[i * P + yz] + (1.0 - cs) * fo[i * P + yz];
                         } else {
                             /* pressure outlet: anti-bounce-back against the
                              * even part of the equilibrium at rho_out and the
@@ -559,6 +592,8 @@ void oracle_lbm_step(oracle_lbm *o, int nsteps)
                         o->f[i * n + c] = v;
                     }
                 }
+        free(fo);
+        free(fi);
         o->t++;
     }
 }

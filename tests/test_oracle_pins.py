@@ -3,7 +3,8 @@
 Each test checks the oracle against something other than itself: lattice
 isotropy, the product equilibrium's closed-form moments, the textbook
 set-partition moment/cumulant relation, exact conservation, the BGK and
-identity special cases, the textbook boundary rules on one step, the exact
+identity special cases, the textbook boundary rules on one step, the
+non-reflection of the convective outflow, the exact
 Navier-Stokes decay of a Taylor-Green vortex (with and without a uniform
 drift), the analytic Poiseuille profile and mirror symmetry.
 """
@@ -340,6 +341,72 @@ def test_pressure_outlet_rule():
         uu = (ub ** 2).sum(-1)
         exp = -f[OPP[i], :, :, nx - 1] + 2 * w[i] * (1 + 4.5 * cu ** 2 - 1.5 * uu)
         assert np.allclose(g[i, :, :, nx - 1], exp, atol=2e-15, rtol=0)
+
+
+def test_outflow_keeps_uniform_flow():
+    """Convective outflow: a uniform stream f_eq(1, (U, 0, 0)) through the
+    moving-wall inlet and the outflow face is a fixed point of the step
+    (extrapolating a uniform field returns it; the inlet term is the odd part
+    of that equilibrium)."""
+    nx, ny, nz = 12, 4, 3
+    U = 0.05
+    L = O.Lattice(O.params(nx, ny, nz, 1.7, u_in=U, faces=("inlet", "outflow", "periodic", "periodic")))
+    fe = np.asarray(O.equilibrium(1.0, U, 0.0, 0.0))
+    f0 = np.broadcast_to(fe[:, None, None, None], (Q, nz, ny, nx)).copy()
+    L.set_f(f0)
+    L.step(50)
+    assert np.abs(L.get_f() - f0).max() < 1e-14
+
+
+def pulse_reflection(outlet):
+    """Amplitude of what a Gaussian density pulse sends back from the x-high
+    face, relative to the incoming half of the pulse (1-D channel, wall at
+    x = 0, the reflection sampled while it is well separated from the wave
+    the wall sends back)."""
+    nx, x0, sig, A = 160, 60, 4.0, 1e-3
+    L = O.Lattice(O.params(nx, 1, 1, 1.95, u_in=0.0, faces=("wall", outlet, "periodic", "periodic")))
+    x = np.arange(nx)
+    rho = 1 + A * np.exp(-(x - x0) ** 2 / (2 * sig ** 2))
+    f = np.zeros((Q, 1, 1, nx))
+    for k in range(nx):
+        f[:, 0, 0, k] = O.equilibrium(rho[k], 0.0, 0.0, 0.0)
+    L.set_f(f)
+    L.step(240)                      # the right-going half reaches x = 159 near t = 172
+    r, _ = L.macros()
+    return np.abs(r[0, 0, 100:] - 1).max() / (A / 2)
+
+
+def test_outflow_does_not_reflect_sound():
+    """Characteristic property of the convective outflow: a sound pulse
+    leaves the domain.  A wall (pressure antinode) and the fixed-density
+    anti-bounce-back outlet (pressure node) both send it back at full
+    strength, up to the viscous decay they share."""
+    wall, abb, out = pulse_reflection("wall"), pulse_reflection("outlet"), pulse_reflection("outflow")
+    assert abb > 0.9 * wall
+    assert out < 0.02 * wall
+
+
+def test_outflow_keeps_a_low_viscosity_channel_bounded():
+    """At the lattice viscosity of the thinnest batch members (nu = 3.3e-4),
+    a channel from rest with the anti-bounce-back outlet diverges within a
+    few hundred steps; with the convective outflow it stays bounded (the
+    start-up pressure wave leaves through the face)."""
+    nu = 3.3e-4
+    w1 = 1.0 / (3 * nu + 0.5)
+
+    def run(outlet, steps):
+        L = O.Lattice(O.params(64, 32, 2, w1, u_in=0.05, faces=("inlet", outlet, "wall", "periodic")))
+        worst = 0.0
+        for _ in range(steps // 100):
+            L.step(100)
+            r, _ = L.macros()
+            if not np.isfinite(r).all():
+                return np.inf
+            worst = max(worst, np.abs(r - 1).max())
+        return worst
+
+    assert run("outlet", 600) > 0.5
+    assert run("outflow", 2000) < 0.15
 
 
 # --------------------------------------------------------------------------
