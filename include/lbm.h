@@ -54,12 +54,25 @@ typedef enum {
  * bit more than binary16 for values that never leave (-1, 1). */
 typedef enum { LBM_F64 = 0, LBM_F32 = 1, LBM_F16S = 2, LBM_BF16S = 3, LBM_F16C = 4 } lbm_storage;
 
-/* Boundary kind of a pair of faces (x has a low and a high face). */
+/* Boundary kind of a pair of faces (x has a low and a high face).
+ *
+ * x high, LBM_FACE_OUTFLOW (the default; Sec. 3.1: the outflow "employs
+ * extrapolation"): the convective outflow of Geier et al. 2015 (App. F), the
+ * paper's cited cumulant reference.  For each link of an outlet cell x_b
+ * through the face (cx = -1 and the source not beyond a lateral wall), the
+ * incoming population is f_i(x_b, t+1) = c_s f_i(x_b - e_x, t) +
+ * (1 - c_s) f_i(x_b, t) from pre-collision values, c_s = 1/sqrt(3): waves
+ * leave the domain instead of reflecting.  A solid cell next to the outlet
+ * makes the outlet cell extrapolate from itself.
+ * x high, LBM_FACE_OUTLET: anti-bounce-back at the fixed density rho_out
+ * (a pressure node; it reflects sound, and with lattice viscosities below
+ * about 2.5e-3 the channel diverges from the outlet corners). */
 typedef enum {
     LBM_FACE_WALL = 0,      /* no-slip halfway bounce-back                       */
     LBM_FACE_PERIODIC = 1,  /* wrap-around                                       */
     LBM_FACE_INLET = 2,     /* x low only: bounce-back from a wall moving at u_in */
-    LBM_FACE_OUTLET = 3     /* x high only: anti-bounce-back at rho_out           */
+    LBM_FACE_OUTLET = 3,    /* x high only: anti-bounce-back at rho_out           */
+    LBM_FACE_OUTFLOW = 4    /* x high only: convective extrapolation outflow      */
 } lbm_face;
 
 typedef struct { int32_t nx, ny, nz; } lbm_grid;
@@ -74,7 +87,7 @@ typedef struct {
     double rho_out;         /* outlet density (default 1)                       */
     int32_t storage;        /* lbm_storage (default LBM_F32)                    */
     int32_t galilean_correction; /* 1 (default): corrected diagonal relaxation  */
-    int32_t face_x_lo, face_x_hi, face_y, face_z; /* lbm_face; default inlet/outlet/wall/wall */
+    int32_t face_x_lo, face_x_hi, face_y, face_z; /* lbm_face; default inlet/outflow/wall/wall */
     /* time average (Sec. 2: mean velocity and pressure): steps t with
      * mean_start <= t < mean_end and (t - mean_start) % mean_every == 0 are
      * sampled from the pre-collision state of step t; mean_every = 0: off */

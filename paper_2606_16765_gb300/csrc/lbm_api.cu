@@ -26,7 +26,7 @@ size_t storage_bytes(int s) { return s == LBM_F64 ? 8 : (s == LBM_F32 ? 4 : 2); 
 // Device memory layout of a context (byte offsets into one allocation).
 struct Layout {
     int64_t n = 0, slot = 0, n_half = 0, snap_cells = 0;
-    size_t pdf = 0, flags = 0, edge = 0, ub = 0, msum = 0, snaps = 0, stage = 0, force = 0,
+    size_t pdf = 0, flags = 0, edge = 0, ub = 0, ob = 0, msum = 0, snaps = 0, stage = 0, force = 0,
            fpart = 0, fcount = 0, tpart = 0, tout = 0, status = 0, total = 0;
     int tot_blocks = 0;
 };
@@ -55,6 +55,7 @@ Layout make_layout(const lbm_grid &g, const lbm_params &p, int64_t n_solid)
     L.flags = take((size_t)L.n);
     L.edge = take((size_t)edge_bound(g, n_solid) * 16);
     L.ub = take((size_t)3 * g.ny * g.nz * rsz);
+    L.ob = take(p.face_x_hi == LBM_FACE_OUTFLOW ? (size_t)18 * g.ny * g.nz * rsz : 0);
     L.msum = take(p.mean_every > 0 ? (size_t)4 * L.n * 8 : 0);
     L.snaps = take(p.snap_count > 0 ? (size_t)p.snap_count * 4 * L.snap_cells * 4 : 0);
     L.stage = take(p.snap_count > 0 && p.snap_halfres ? (size_t)4 * L.n * 4 : 0);
@@ -141,6 +142,7 @@ struct lbm_ctx {
         }
         a.u_in_f = (float)a.u_in; a.rho_in_f = (float)a.rho_in; a.rho_out_f = (float)a.rho_out;
         a.ub = base + L.ub;
+        a.ob = base + L.ob;
         a.fcount = at<unsigned>(L.fcount);
         a.status = at<int>(L.status);
         return a;
@@ -170,7 +172,7 @@ extern "C" void lbm_params_default(lbm_params *p)
     p->omega1 = 0.0; p->omega_bulk = 1.0; p->omega_higher = 1.0;
     p->rho_in = 1.0; p->rho_out = 1.0;
     p->storage = LBM_F32; p->galilean_correction = 1;
-    p->face_x_lo = LBM_FACE_INLET; p->face_x_hi = LBM_FACE_OUTLET;
+    p->face_x_lo = LBM_FACE_INLET; p->face_x_hi = LBM_FACE_OUTFLOW;
     p->face_y = LBM_FACE_WALL; p->face_z = LBM_FACE_WALL;
     p->force_capacity = 65536;
 }
@@ -184,8 +186,9 @@ static std::string validate(const lbm_grid *g, const lbm_params *p)
     if (p->storage < LBM_F64 || p->storage > LBM_F16C) return "unknown storage";
     if (p->face_x_lo != LBM_FACE_INLET && p->face_x_lo != LBM_FACE_WALL && p->face_x_lo != LBM_FACE_PERIODIC)
         return "face_x_lo must be inlet, wall or periodic";
-    if (p->face_x_hi != LBM_FACE_OUTLET && p->face_x_hi != LBM_FACE_WALL && p->face_x_hi != LBM_FACE_PERIODIC)
-        return "face_x_hi must be outlet, wall or periodic";
+    if (p->face_x_hi != LBM_FACE_OUTLET && p->face_x_hi != LBM_FACE_OUTFLOW && p->face_x_hi != LBM_FACE_WALL &&
+        p->face_x_hi != LBM_FACE_PERIODIC)
+        return "face_x_hi must be outflow, outlet, wall or periodic";
     if ((p->face_x_lo == LBM_FACE_PERIODIC) != (p->face_x_hi == LBM_FACE_PERIODIC))
         return "periodic x needs both x faces periodic";
     if ((p->face_y != LBM_FACE_WALL && p->face_y != LBM_FACE_PERIODIC) ||
@@ -314,7 +317,7 @@ static lbm_status create_impl(const lbm_grid *g, const uint8_t *mask, const lbm_
             if (p->face_x_lo == LBM_FACE_WALL) return LINK_WALL;
             sx += nx; wrapped = true;
         } else if (sx >= nx) {
-            if (p->face_x_hi == LBM_FACE_OUTLET) return LINK_OUTLET;
+            if (p->face_x_hi == LBM_FACE_OUTLET || p->face_x_hi == LBM_FACE_OUTFLOW) return LINK_OUTLET;
             if (p->face_x_hi == LBM_FACE_WALL) return LINK_WALL;
             sx -= nx; wrapped = true;
         }

@@ -34,8 +34,9 @@ __host__ __device__ constexpr double zw(int a) { return a == 0 ? 1.0 : (a == 1 ?
 // outlet plane cell whose only boundary links cross that x face; handled by
 // the row-end variant of the bulk kernel); 0 = bulk
 enum : uint8_t { CELL_SOLID = 1, CELL_EDGE = 2, CELL_XFACE = 4 };
-// face kinds (lbm_face)
-enum { FACE_WALL = 0, FACE_PERIODIC = 1, FACE_INLET = 2, FACE_OUTLET = 3 };
+// face kinds (lbm_face): x high is either the anti-bounce-back pressure
+// outlet or the convective extrapolation outflow
+enum { FACE_WALL = 0, FACE_PERIODIC = 1, FACE_INLET = 2, FACE_OUTLET = 3, FACE_OUTFLOW = 4 };
 // link kinds of the cell a population comes from (pull view); LINK_WRAP is a
 // fluid neighbour reached through a periodic face
 enum { LINK_FLUID = 0, LINK_WALL = 1, LINK_SOLID = 2, LINK_INLET = 3, LINK_OUTLET = 4, LINK_WRAP = 5 };
@@ -116,6 +117,9 @@ struct StepArgs {
     // index 0/1 = even gather/scatter, 2/3 = odd gather/scatter
     int64_t boff[4][27];
     void *ub;               // outlet plane velocity [nz*ny][3] (compute type)
+    void *ob;               // outflow planes (compute type): [9][nz*ny] pre-collision
+                            // populations with cx = -1 of the outlet cells, then
+                            // [9][nz*ny] of the cells next to them (x = nx - 2)
     double *msum;           // mean sums [4][n] when this step is sampled, else null
     float *snap;            // full-resolution float4 target when snapshotting, else null
     double *fpart;          // force partials per edge block when recorded, else null
@@ -171,7 +175,7 @@ __device__ __forceinline__ int classify(const StepArgs &a, int sx, int sy, int s
         if (a.face_x_lo == FACE_WALL) return LINK_WALL;
         sx += a.nx;
     } else if (sx >= a.nx) {
-        if (a.face_x_hi == FACE_OUTLET) return LINK_OUTLET;
+        if (a.face_x_hi == FACE_OUTLET || a.face_x_hi == FACE_OUTFLOW) return LINK_OUTLET;
         if (a.face_x_hi == FACE_WALL) return LINK_WALL;
         sx -= a.nx;
     }
@@ -183,13 +187,16 @@ __device__ __forceinline__ int classify(const StepArgs &a, int sx, int sy, int s
 // whose own slot holds `own` (the post-collision population of the opposite
 // direction).  Halfway bounce-back for walls and obstacles, bounce-back from
 // a wall moving with (u_in, 0, 0) at the inlet, anti-bounce-back against the
-// even part of the equilibrium at rho_out with velocity ub at the outlet.
+// even part of the equilibrium at rho_out with velocity ub at the pressure
+// outlet.  With the convective outflow the own slot already holds the
+// extrapolated value (written after the previous step by k_outflow).
 template <class R>
 __device__ __forceinline__ R boundary_value(const StepArgs &a, int kind, int i, R own, R ubx, R uby, R ubz)
 {
     const R w = R(w_of(i));
     if (kind == LINK_INLET)
         return own + R(6) * w * pick<R>(a.rho_in, a.rho_in_f) * (R(cx_of(i)) * pick<R>(a.u_in, a.u_in_f));
+    if (kind == LINK_OUTLET && a.face_x_hi == FACE_OUTFLOW) return own;
     if (kind == LINK_OUTLET) {
         const R cu = R(cx_of(i)) * ubx + R(cy_of(i)) * uby + R(cz_of(i)) * ubz;
         const R uu = ubx * ubx + uby * uby + ubz * ubz;
@@ -197,6 +204,20 @@ __device__ __forceinline__ R boundary_value(const StepArgs &a, int kind, int i, 
         return -own + R(2) * w * (pick<R>(a.rho_out, a.rho_out_f) * (R(1) + R(4.5) * cu * cu - R(1.5) * uu) - R(1));
     }
     return own;
+}
+
+// Convective outflow: the cells of the outlet plane (x = nx - 1) and of the
+// plane next to it record their pre-collision populations with cx = -1
+// (directions 3k, k < 9) every step; k_outflow extrapolates from them after
+// the step.
+template <class R>
+__device__ __forceinline__ void record_outflow_planes(const StepArgs &a, int x, int64_t yz, const R *f)
+{
+    if (a.face_x_hi != FACE_OUTFLOW || x < a.nx - 2) return;
+    const int64_t P = (int64_t)a.ny * a.nz;
+    R *pl = static_cast<R *>(a.ob) + (x == a.nx - 1 ? 0 : 9 * P) + yz;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) pl[k * P] = f[3 * k];
 }
 
 // ---------------------------------------------------------------------------

@@ -93,6 +93,7 @@ __device__ __forceinline__ void bulk_cell(const StepArgs &a, const StepOut &o, i
 #pragma unroll
         for (int i = 0; i < Q; ++i) f[i] = T::ld(reinterpret_cast<const S *>(q + gof[i]));
     }
+    record_outflow_planes<R>(a, x, (int64_t)y + (int64_t)a.ny * z, f);
     R drho, ux, uy, uz;
     collide<R, PLAIN>(f, rates_of<R>(a), drho, ux, uy, uz);
     check_density(drho, a.status);
@@ -236,6 +237,7 @@ __device__ __forceinline__ void edge_cell(const StepArgs &a, const StepOut &o, i
                 f[i] = T::ld(p + (int64_t)i * a.slot + c);
             }
         }
+        record_outflow_planes<R>(a, x, (int64_t)yz, f);
         R drho, ux, uy, uz;
         collide<R, PLAIN>(f, rates_of<R>(a), drho, ux, uy, uz);
         check_density(drho, a.status);
@@ -283,6 +285,52 @@ __global__ void __launch_bounds__(EDGE_BLOCK) k_step_edge(StepArgs a)
     R fx = R(0), fy = R(0), fz = R(0);     // this cell's obstacle force
     if (k < a.n_edge) edge_cell<S, ODD, PLAIN>(a, o, k, fx, fy, fz);
     if (o.fpart) block_force_reduce(o, blockIdx.x, gridDim.x, (double)fx, (double)fy, (double)fz);
+}
+
+// Convective outflow (after every step): each fluid outlet cell gets, for its
+// links through the x-high face (cx = -1 and the source cell not beyond a
+// lateral wall), f_i = c_s f_i(x_b - e_x) + (1 - c_s) f_i(x_b) from the
+// pre-collision populations its step recorded, written into its own slot i:
+// the place where the next step, of either parity, reads that link.  A solid
+// (or missing) inner neighbour makes the cell extrapolate from itself.
+template <class S>
+__device__ __forceinline__ void outflow_cell(const StepArgs &a, int64_t yz)
+{
+    using T = Store<S>;
+    using R = typename T::R;
+    const int64_t P = (int64_t)a.ny * a.nz;
+    const int64_t c = (int64_t)(a.nx - 1) + (int64_t)a.nx * yz;
+    if (a.flags[c] & CELL_SOLID) return;
+    const int y = (int)(yz % a.ny), z = (int)(yz / a.ny);
+    const R *own = static_cast<const R *>(a.ob) + yz;
+    const bool inner = a.nx >= 2 && !(a.flags[c - 1] & CELL_SOLID);
+    const R *in = inner ? own + 9 * P : own;
+    const R cs = R(0.57735026918962576451), cs1 = R(1) - cs;
+    S *p = static_cast<S *>(a.pdf);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        const int i = 3 * k;
+        const int sy = y - cy_of(i), sz = z - cz_of(i);
+        if ((sy < 0 || sy >= a.ny) && a.face_y != FACE_PERIODIC) continue;   // wall link
+        if ((sz < 0 || sz >= a.nz) && a.face_z != FACE_PERIODIC) continue;
+        T::st(p + (int64_t)i * a.slot + c, cs * in[k * P] + cs1 * own[k * P]);
+    }
+}
+
+template <class S>
+__global__ void __launch_bounds__(256) k_outflow(StepArgs a)
+{
+    const int64_t P = (int64_t)a.ny * a.nz;
+    for (int64_t yz = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; yz < P; yz += (int64_t)gridDim.x * blockDim.x)
+        outflow_cell<S>(a, yz);
+}
+
+template <class S>
+static void launch_outflow(const StepArgs &a, cudaStream_t s)
+{
+    if (a.face_x_hi != FACE_OUTFLOW) return;
+    const int64_t P = (int64_t)a.ny * a.nz;
+    k_outflow<S><<<(unsigned)std::min<int64_t>((P + 255) / 256, 1024), 256, 0, s>>>(a);
 }
 
 template <class S, bool ODD, bool EPI, bool PLAIN>
@@ -357,8 +405,16 @@ __global__ void __launch_bounds__(EDGE_BLOCK) k_batch_edge(const BatchMember *me
     if (o.fpart) block_force_reduce(o, lb, nb, (double)fx, (double)fy, (double)fz);
 }
 
-static __global__ void k_batch_tick(int64_t *t)
+// End of a batched step: the convective outflow of every member with that
+// outlet (block m serves member m), then the step counter advances.
+template <class S>
+__global__ void __launch_bounds__(256) k_batch_tail(const BatchMember *mem, int nm, int64_t *t)
 {
+    const StepArgs &a = mem[blockIdx.x].a;
+    if (a.face_x_hi == FACE_OUTFLOW) {
+        const int64_t P = (int64_t)a.ny * a.nz;
+        for (int64_t yz = threadIdx.x; yz < P; yz += blockDim.x) outflow_cell<S>(a, yz);
+    }
     if (threadIdx.x == 0 && blockIdx.x == 0) *t += 1;
 }
 
@@ -385,7 +441,7 @@ void launch_batch_step_t(const BatchLaunch &L, bool odd, bool epi, bool plain, c
             else     k_batch_edge<S, false, false><<<ne, EDGE_BLOCK, 0, s>>>(L.mem, L.edge_begin, L.nm, L.t, epi);
         }
     }
-    k_batch_tick<<<1, 32, 0, s>>>(L.t);
+    k_batch_tail<S><<<(unsigned)L.nm, 256, 0, s>>>(L.mem, L.nm, L.t);
 }
 
 template <class S>
@@ -412,6 +468,7 @@ void launch_step_t(const StepArgs &a, bool odd, bool epi, bool plain, int block_
             else     k_step_edge<S, false, false><<<eg, EDGE_BLOCK, 0, s>>>(a);
         }
     }
+    launch_outflow<S>(a, s);
 }
 
 }  // namespace lbm

@@ -17,9 +17,10 @@ _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "lib", "lib
 
 LBM_OK, LBM_ERR_ARG, LBM_ERR_CUDA, LBM_ERR_OOM, LBM_ERR_UNSTABLE, LBM_ERR_TIMEOUT, LBM_ERR_STATE, LBM_ERR_IO = range(8)
 LBM_F64, LBM_F32, LBM_F16S, LBM_BF16S, LBM_F16C = range(5)
-LBM_FACE_WALL, LBM_FACE_PERIODIC, LBM_FACE_INLET, LBM_FACE_OUTLET = range(4)
+LBM_FACE_WALL, LBM_FACE_PERIODIC, LBM_FACE_INLET, LBM_FACE_OUTLET, LBM_FACE_OUTFLOW = range(5)
 STORAGE = {"f64": LBM_F64, "f32": LBM_F32, "f16s": LBM_F16S, "bf16s": LBM_BF16S, "f16c": LBM_F16C}
-FACES = {"wall": LBM_FACE_WALL, "periodic": LBM_FACE_PERIODIC, "inlet": LBM_FACE_INLET, "outlet": LBM_FACE_OUTLET}
+FACES = {"wall": LBM_FACE_WALL, "periodic": LBM_FACE_PERIODIC, "inlet": LBM_FACE_INLET, "outlet": LBM_FACE_OUTLET,
+         "outflow": LBM_FACE_OUTFLOW}
 
 
 class lbm_grid(C.Structure):

@@ -17,16 +17,23 @@ from __future__ import annotations
 import numpy as np
 
 
-def dominant_frequency(signal, dt=1.0):
+def dominant_frequency(signal, dt=1.0, band=None):
     """Frequency (cycles per unit of dt) of the largest non-zero periodogram
-    peak of a real signal."""
+    peak of a real signal, optionally searched only inside band = (lo, hi)."""
     x = np.asarray(signal, dtype=np.float64)
     n = len(x)
     if n < 8:
         raise ValueError("signal too short")
     w = np.hanning(n)
     p = np.abs(np.fft.rfft((x - x.mean()) * w)) ** 2
-    k = int(np.argmax(p[1:])) + 1
+    freq = np.arange(len(p)) / (n * dt)
+    sel = np.ones(len(p), bool)
+    sel[0] = False
+    if band is not None:
+        sel &= (freq >= band[0]) & (freq <= band[1])
+    if not sel.any():
+        raise ValueError("no frequency bin inside the band")
+    k = int(np.argmax(np.where(sel, p, -1.0)))
     shift = 0.0
     if 1 <= k < len(p) - 1 and p[k - 1] > 0 and p[k + 1] > 0:
         a, b, c = np.log(p[k - 1]), np.log(p[k]), np.log(p[k + 1])
@@ -36,10 +43,13 @@ def dominant_frequency(signal, dt=1.0):
     return (k + shift) / (n * dt)
 
 
-def strouhal(lift, d, u, every=1):
+def strouhal(lift, d, u, every=1, st_band=None):
     """St of a lift record sampled every `every` steps, diameter d and inlet
-    speed u in lattice units."""
-    return dominant_frequency(lift, dt=float(every)) * d / u
+    speed u in lattice units; st_band = (lo, hi) limits the search to a range
+    of St (e.g. to keep a channel's acoustic modes, St = d c_s / (2 H u) and
+    above, out of a shedding measurement)."""
+    band = None if st_band is None else (st_band[0] * u / d, st_band[1] * u / d)
+    return dominant_frequency(lift, dt=float(every), band=band) * d / u
 
 
 def drag_coefficient(fx, d, span, u, rho=1.0):

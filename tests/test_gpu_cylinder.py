@@ -4,15 +4,18 @@ measures (Strouhal number of the lift, drag coefficient) over 20,000 steps.
 
   * Force trend: a half-size copy of the channel (128x64x64, D = 8) at the
     shear rate of the Re = 3900 case, first 60 steps from rest; F(t) of the
-    FP32 step against the oracle's, max deviation <= 1e-5 of max |F_x| per
-    step (the same bound as the velocities).
-  * Wake: the full-size channel at Re = 200 on D (laminar shedding; the plain
-    operator's stable range, see below), seeded 1e-4 noise to break the
-    symmetry, FP64 mean from step 10,000, force every step.  St from the lift
-    spectrum of steps 10,000-20,000 must lie in [0.15, 0.30] and C_d in
-    [0.8, 3.0] (a confined cylinder, blockage D/H = 1/8).
-  * Re = 3900 itself (omega1 = 1.99877) is outside the plain operator's stable
-    range: the step latches the instability, and further steps are refused.
+    FP32 step against the oracle's, max deviation <= 1e-5 of max |F_x|.
+  * Re = 3900 on D (omega1 = 1.99877), 20,000 steps from rest with the FP64
+    mean every step from step 10,000 and the force every step.  The lift of
+    steps 10,000-20,000 also carries the channel's transverse acoustic mode
+    (period 2H / c_s = 443 steps, St = 0.72), excited by the impulsive start
+    and weakly damped at this viscosity.  So the shedding frequency is
+    searched for St < 0.5, and it must lie in [0.15, 0.30] (0.21 for an
+    unconfined cylinder at this Re).  C_d must lie in [0.8, 2.5] (blockage
+    D/H = 1/8).  With the anti-bounce-back pressure outlet the same channel
+    diverges near the outlet corners within 1000 steps.
+  * Re = 200 (laminar shedding), seeded 1e-4 noise to break the symmetry,
+    the same measures.
 """
 import numpy as np
 import pytest
@@ -54,34 +57,41 @@ def test_cylinder_force_record_matches_oracle():
     assert err <= 1e-5
 
 
-def test_cylinder_wake_strouhal_and_drag():
+def cylinder_run(re, steps=20000, noise=None, faces=None):
     from paper_2606_16765_gb300.lbm import Solver
     grid = (256, 128, 128)
     D = 16.0
     mask = I.cylinder_z(grid, (64.0, 63.5), D)
-    s = Solver(grid, mask, storage="f32", re=200.0, u_in=U, l_ref=D, mean_start=10000, mean_end=20000,
-               mean_every=1, force_every=1, force_capacity=20000)
-    s.init_noise(7, 1e-4)
+    extra = {} if faces is None else {"faces": faces}
+    s = Solver(grid, mask, storage="f32", re=re, u_in=U, l_ref=D, mean_start=steps // 2, mean_end=steps,
+               mean_every=1, force_every=1, force_capacity=steps, **extra)
+    if noise:
+        s.init_noise(noise, 1e-4)
+    return s, grid, D
+
+
+@pytest.mark.parametrize("re,noise", [(3900.0, None), (200.0, 7)])
+def test_cylinder_wake_strouhal_and_drag(re, noise):
+    s, grid, D = cylinder_run(re, noise=noise)
     for _ in range(20):
         s.step(1000)
     s.sync()
     F = s.forces()
     assert F.shape == (20000, 3) and np.isfinite(F).all()
-    st = wake.strouhal(F[10000:, 1], D, U)
+    st = wake.strouhal(F[10000:, 1], D, U, st_band=(0.05, 0.5))
+    st_all = wake.strouhal(F[10000:, 1], D, U)
     cd = wake.drag_coefficient(F[10000:, 0], D, grid[2], U)
     m, ns = s.mean(halfres=True, dtype=np.float32)
-    print(f"cylinder Re 200: St = {st:.4f}, C_d = {cd:.4f}, mean samples {ns}, "
-          f"lift rms {F[10000:, 1].std():.4e}")
-    assert ns == 10000
+    print(f"cylinder Re {re:.0f}: St = {st:.4f} (unbanded peak {st_all:.4f}), C_d = {cd:.4f}, "
+          f"mean samples {ns}, lift rms {F[10000:, 1].std():.4e}")
+    assert ns == 10000 and np.isfinite(m).all()
     assert 0.15 <= st <= 0.30
-    assert 0.8 <= cd <= 3.0
+    assert 0.8 <= cd <= 2.5
 
 
-def test_cylinder_re3900_latches_instability():
-    from paper_2606_16765_gb300.lbm import LBMError, Solver
-    grid = (256, 128, 128)
-    mask = I.cylinder_z(grid, (64.0, 63.5), 16.0)
-    s = Solver(grid, mask, storage="f32", re=3900.0, u_in=U, l_ref=16.0)
+def test_cylinder_re3900_with_pressure_outlet_latches_instability():
+    from paper_2606_16765_gb300.lbm import LBMError
+    s, _, _ = cylinder_run(3900.0, steps=2000, faces=("inlet", "outlet", "wall", "wall"))
     s.step(2000)
     with pytest.raises(LBMError):
         s.sync()

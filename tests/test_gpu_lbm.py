@@ -78,6 +78,42 @@ def test_sphere_channel_200_steps(sphere64, storage):
     assert np.abs(F - Fr).max() <= TOL_U[storage] * np.abs(Fr[:, 0]).max() * 10
 
 
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+def test_sphere_channel_outflow_200_steps(storage):
+    """The same channel with the convective outflow on the x-high face."""
+    d = I.sphere_channel_64()
+    w1 = O.omega_from_re(d["re"], d["u_in"], d["l_ref"])
+    c = K.case(d["grid"], d["mask"], omega1=w1, u_in=d["u_in"], faces=("inlet", "outflow", "wall", "wall"))
+    L = K.run_oracle(c, 200)
+    rho_r, u_r = L.macros()
+    s = K.make_solver(c, storage)
+    s.step(200)
+    s.sync()
+    rho, u = s.macros()
+    fluid = c["mask"] == 0
+    eu, er = K.rel_u_err(u, u_r, fluid), K.rho_err(rho, rho_r, fluid)
+    print(f"outflow {storage}: rel u err {eu:.3e}  rho err {er:.3e}")
+    assert eu <= TOL_U[storage] and er <= TOL_U[storage]
+
+
+def test_outflow_keeps_low_viscosity_channel_stable():
+    """An empty 128x64x128 channel at nu = 3.3e-4 (the thinnest member of the
+    32-channel batch): with the anti-bounce-back outlet it diverges within
+    400 steps; with the convective outflow it runs 4000 steps."""
+    from paper_2606_16765_gb300.lbm import LBMError, Solver
+    nu = 3.3e-4
+    s = Solver((128, 64, 128), None, storage="f32", omega1=1.0 / (3 * nu + 0.5), u_in=0.05)
+    s.step(4000)
+    s.sync()
+    rho, u = s.macros()
+    assert np.isfinite(rho).all() and np.abs(rho - 1).max() < 0.2
+    a = Solver((128, 64, 128), None, storage="f32", omega1=1.0 / (3 * nu + 0.5), u_in=0.05,
+               faces=("inlet", "outlet", "wall", "wall"))
+    a.step(1000)
+    with pytest.raises(LBMError):
+        a.sync()
+
+
 def test_bf16s_runs_and_is_reported(sphere64):
     """BF16-shifted storage (8-bit mantissa) is reported, not gated."""
     c = sphere64["case"]
@@ -97,6 +133,8 @@ def box_cases():
     g = (37, 13, 11)                     # ragged: not a multiple of the block
     obs = I.sphere(g, (9.0, 6.0, 5.0), 3.0)
     wall_obs = I.voxelize(g, [I.Primitive("rectangle", (20.0, 1.0, 5.0), (4.0, 4.0, 20.0))])  # touches y=0 and both z walls
+    # solid cells in the outlet plane and next to it (the outflow's inner neighbour)
+    outlet_obs = I.voxelize(g, [I.Primitive("rectangle", (35.5, 6.0, 5.0), (2.0, 4.0, 4.0))])
     return {
         "channel_obstacle": K.case(g, obs, omega1=1.7, noise=(11, 2e-3)),
         "obstacle_on_walls": K.case(g, wall_obs, omega1=1.9, noise=(12, 2e-3)),
@@ -108,9 +146,17 @@ def box_cases():
         "no_galilean": K.case(g, obs, omega1=1.8, galilean=0, noise=(17, 2e-3)),
         "thin_slab": K.case((16, 1, 3), None, omega1=1.4, faces=("inlet", "outlet", "periodic", "wall"), noise=(18, 2e-3)),
         "single_cell": K.case((1, 1, 1), None, omega1=1.1, faces=("periodic",) * 4, u_in=0.0, noise=(19, 5e-3)),
+        # convective outflow on the x-high face
+        "outflow_obstacle": K.case(g, obs, omega1=1.9, faces=OUTFLOW, noise=(20, 2e-3)),
+        "outflow_solid_at_outlet": K.case(g, outlet_obs, omega1=1.8, faces=OUTFLOW, noise=(21, 2e-3)),
+        "outflow_periodic_yz": K.case(g, obs, omega1=1.7, faces=("inlet", "outflow", "periodic", "periodic"),
+                                      noise=(22, 2e-3)),
+        "outflow_nx2": K.case((2, 5, 4), None, omega1=1.5, faces=OUTFLOW, noise=(23, 2e-3)),
+        "outflow_nx1": K.case((1, 3, 3), None, omega1=1.5, faces=OUTFLOW, noise=(24, 2e-3)),
     }
 
 
+OUTFLOW = ("inlet", "outflow", "wall", "wall")
 BOXES = box_cases()
 
 
@@ -243,7 +289,7 @@ def test_library_owned_memory_matches_workspace():
     d = I.sphere_channel_64()
     c = K.case(d["grid"], d["mask"], omega1=1.9, noise=(3, 1e-3))
     a = K.make_solver(c, "f32")
-    p = B.make_params(storage="f32", omega1=1.9, u_in=0.05)
+    p = B.make_params(storage="f32", omega1=1.9, u_in=0.05, faces=c["faces"])
     h = B.lbm_create(B.lbm_grid(*d["grid"]), d["mask"], p, torch.cuda.current_stream().cuda_stream)
     B.lbm_init_noise(h, 3, 1e-3)
     a.step(7)
@@ -311,7 +357,7 @@ def oracle_cell_after(mask, grid, faces, omega1, u_in, seed, amp, cell, steps):
     w = O.weights()
     f = w[:, None] + amp * I.pdf_noise(seed, gcell)
     f[:, sub.reshape(-1) != 0] = w[:, None]
-    sub_faces = ("inlet" if x0 == 0 else "wall", "outlet" if x1 == nx else "wall", "wall", "wall")
+    sub_faces = ("inlet" if x0 == 0 else "wall", faces[1] if x1 == nx else "wall", "wall", "wall")
     p = O.params(*sg, omega1, u_in=u_in, faces=sub_faces)
     L = O.Lattice(p, sub)
     L.set_f(f.reshape(27, *sub.shape))
@@ -328,7 +374,8 @@ def test_full_size_channel_sampled_cells(storage):
     w1 = O.omega_from_re(d["re"], d["u_in"], d["l_ref"])
     from paper_2606_16765_gb300.lbm import Solver
     seed, amp = 77, 1e-3
-    s = Solver(grid, mask, storage=storage, omega1=w1, u_in=d["u_in"])
+    faces = ("inlet", "outflow", "wall", "wall")
+    s = Solver(grid, mask, storage=storage, omega1=w1, u_in=d["u_in"], faces=faces)
     s.init_noise(seed, amp)
     rng = np.random.default_rng(0)
     n = nx * ny * nz
@@ -352,7 +399,7 @@ def test_full_size_channel_sampled_cells(storage):
         s.step(1)
         got = s.cells(pick)
         for j, c in enumerate(pick):
-            ref = oracle_cell_after(mask, grid, ("inlet", "outlet", "wall", "wall"), w1, d["u_in"], seed, amp, c, steps)
+            ref = oracle_cell_after(mask, grid, faces, w1, d["u_in"], seed, amp, c, steps)
             err = np.abs(got[j] - ref).max()
             assert err <= tol, (storage, steps, int(c), err)
     s.sync()

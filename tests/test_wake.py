@@ -29,3 +29,10 @@ def test_drag_coefficient_closed_form():
 def test_short_signal_is_rejected():
     with pytest.raises(ValueError):
         wake.dominant_frequency(np.ones(4))
+
+
+def test_band_limited_peak_ignores_a_stronger_mode_outside_the_band():
+    t = np.arange(10000)
+    x = 5 * np.sin(2 * np.pi * 0.00225 * t) + np.sin(2 * np.pi * 0.0006 * t)
+    assert wake.strouhal(x, 16.0, 0.05) == pytest.approx(0.00225 * 16 / 0.05, abs=0.01)
+    assert wake.strouhal(x, 16.0, 0.05, st_band=(0.1, 0.5)) == pytest.approx(0.0006 * 16 / 0.05, abs=0.01)
