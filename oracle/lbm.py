@@ -59,6 +59,8 @@ def lib():
         L.oracle_lbm_macros.argtypes = [C.c_void_p, dp, dp]
         L.oracle_lbm_means.argtypes = [C.c_void_p, dp]
         L.oracle_lbm_means.restype = C.c_int64
+        L.oracle_lbm_stats.argtypes = [C.c_void_p, dp]
+        L.oracle_lbm_stats.restype = C.c_int64
         L.oracle_lbm_forces.argtypes = [C.c_void_p, dp]
         L.oracle_lbm_step.argtypes = [C.c_void_p, C.c_int]
         L.oracle_lbm_totals.argtypes = [C.c_void_p, dp]
@@ -196,6 +198,13 @@ class Lattice:
     def means(self):
         out = np.zeros(self.shape + (4,))
         s = lib().oracle_lbm_means(self.h, _dp(out))
+        return out, s
+
+    def stats(self):
+        """Velocity covariances [..., 6] (xx, yy, zz, xy, xz, yz) over the
+        averaging samples, and the sample count."""
+        out = np.zeros(self.shape + (6,))
+        s = lib().oracle_lbm_stats(self.h, _dp(out))
         return out, s
 
     def forces(self):

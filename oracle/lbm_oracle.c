@@ -353,6 +353,7 @@ typedef struct {
     double *post;        /* post-collision */
     double *rho, *u;     /* pre-collision macros of the last step (u[3*cell + d]) */
     double *msum;        /* 4*n mean sums: rho-1, ux, uy, uz */
+    double *qsum;        /* 6*n sums of velocity products: uxux, uyuy, uzuz, uxuy, uxuz, uyuz */
     int64_t msamples;
     double *force;       /* 3 per step */
     int64_t force_cap;
@@ -376,6 +377,7 @@ oracle_lbm *oracle_lbm_create(const oracle_params *p, const uint8_t *solid)
     o->rho = (double *)calloc(o->n, sizeof(double));
     o->u = (double *)calloc(3 * o->n, sizeof(double));
     o->msum = (double *)calloc(4 * o->n, sizeof(double));
+    o->qsum = (double *)calloc(6 * o->n, sizeof(double));
     for (int i = 0; i < Q; ++i) {
         double w = weight(i);
         for (int64_t c = 0; c < o->n; ++c) { o->f[i * o->n + c] = w; o->post[i * o->n + c] = w; }
@@ -389,7 +391,7 @@ void oracle_lbm_destroy(oracle_lbm *o)
 {
     if (!o) return;
     free(o->solid); free(o->f); free(o->post); free(o->rho); free(o->u);
-    free(o->msum); free(o->force); free(o);
+    free(o->msum); free(o->qsum); free(o->force); free(o);
 }
 
 void oracle_lbm_set_f(oracle_lbm *o, const double *f) { memcpy(o->f, f, sizeof(double) * Q * o->n); }
@@ -411,6 +413,25 @@ void oracle_lbm_macros(const oracle_lbm *o, double *rho, double *u)
 }
 
 /* Mean fields: (ux, uy, uz, p) per cell, p = (rho - 1)/3; solid cells 0. */
+/* Velocity covariances over the same samples as the means (Reynolds
+ * stresses, the turbulence statistics of Sec. 3.3): per cell
+ * <ux ux> - <ux><ux>, <uy uy> - ..., <uz uz> - ..., <ux uy> - <ux><uy>,
+ * <ux uz> - ..., <uy uz> - ... .  Returns the sample count. */
+int64_t oracle_lbm_stats(const oracle_lbm *o, double *out)
+{
+    const double s = o->msamples > 0 ? 1.0 / (double)o->msamples : 0.0;
+    for (int64_t c = 0; c < o->n; ++c) {
+        const double mx = o->msum[4 * c + 1] * s, my = o->msum[4 * c + 2] * s, mz = o->msum[4 * c + 3] * s;
+        out[6 * c + 0] = o->qsum[6 * c + 0] * s - mx * mx;
+        out[6 * c + 1] = o->qsum[6 * c + 1] * s - my * my;
+        out[6 * c + 2] = o->qsum[6 * c + 2] * s - mz * mz;
+        out[6 * c + 3] = o->qsum[6 * c + 3] * s - mx * my;
+        out[6 * c + 4] = o->qsum[6 * c + 4] * s - mx * mz;
+        out[6 * c + 5] = o->qsum[6 * c + 5] * s - my * mz;
+    }
+    return o->msamples;
+}
+
 int64_t oracle_lbm_means(const oracle_lbm *o, double *out)
 {
     for (int64_t c = 0; c < o->n; ++c) {
@@ -484,6 +505,12 @@ void oracle_lbm_step(oracle_lbm *o, int nsteps)
                 o->msum[4 * c + 1] += v[0];
                 o->msum[4 * c + 2] += v[1];
                 o->msum[4 * c + 3] += v[2];
+                o->qsum[6 * c + 0] += v[0] * v[0];
+                o->qsum[6 * c + 1] += v[1] * v[1];
+                o->qsum[6 * c + 2] += v[2] * v[2];
+                o->qsum[6 * c + 3] += v[0] * v[1];
+                o->qsum[6 * c + 4] += v[0] * v[2];
+                o->qsum[6 * c + 5] += v[1] * v[2];
             }
         }
         if (sample) o->msamples++;

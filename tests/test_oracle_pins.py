@@ -530,3 +530,29 @@ def test_force_vanishes_at_rest_and_means_average_macros():
     m, s = L2.means()
     assert s == 3
     assert np.abs(m - acc / 3).max() < 1e-15
+
+
+def test_velocity_covariances_equal_those_of_the_sampled_series():
+    """The Reynolds-stress accumulators (sums of velocity products over the
+    averaging samples) give the two-pass covariance of the velocity series
+    sampled step by step (numpy, centred first), per cell and component
+    pair."""
+    nx, ny, nz = 16, 8, 8
+    solid = I.sphere((nx, ny, nz), (6.0, 3.5, 3.5), 2.0)
+    L = O.Lattice(O.params(nx, ny, nz, 1.8, u_in=0.05, mean=(3, 40, 4)), solid)
+    L.set_f(L.get_f() + 2e-3 * I.pdf_noise(5, np.arange(nx * ny * nz)).reshape(27, nz, ny, nx)
+            * (solid == 0))
+    series = []
+    for t in range(41):
+        if 3 <= t < 40 and (t - 3) % 4 == 0:
+            series.append(L.macros()[1])
+        L.step(1)
+    U = np.stack(series)                         # [samples, nz, ny, nx, 3]
+    D = U - U.mean(0)
+    pairs = [(0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2)]
+    ref = np.stack([(D[..., a] * D[..., b]).mean(0) for a, b in pairs], -1)
+    st, n = L.stats()
+    assert n == len(series) == 10
+    fl = solid == 0
+    assert np.abs(st - ref)[fl].max() < 1e-15
+    assert np.abs(ref[fl]).max() > 1e-8          # the flow does fluctuate
