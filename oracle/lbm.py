@@ -61,6 +61,8 @@ def lib():
         L.oracle_lbm_means.restype = C.c_int64
         L.oracle_lbm_stats.argtypes = [C.c_void_p, dp]
         L.oracle_lbm_stats.restype = C.c_int64
+        L.oracle_lbm_set_q.argtypes = [C.c_void_p, C.c_void_p]
+        L.oracle_lbm_set_q.restype = None
         L.oracle_lbm_forces.argtypes = [C.c_void_p, dp]
         L.oracle_lbm_step.argtypes = [C.c_void_p, C.c_int]
         L.oracle_lbm_totals.argtypes = [C.c_void_p, dp]
@@ -199,6 +201,15 @@ class Lattice:
         out = np.zeros(self.shape + (4,))
         s = lib().oracle_lbm_means(self.h, _dp(out))
         return out, s
+
+    def set_q(self, q):
+        """Wall distances [27, nz, ny, nx] of the links x -> x + c_j into
+        obstacle cells (interpolated bounce-back), or None for halfway."""
+        if q is None:
+            lib().oracle_lbm_set_q(self.h, None)
+        else:
+            q = np.ascontiguousarray(q, dtype=np.float64)
+            lib().oracle_lbm_set_q(self.h, q.ctypes.data)
 
     def stats(self):
         """Velocity covariances [..., 6] (xx, yy, zz, xy, xz, yz) over the

@@ -355,6 +355,9 @@ typedef struct {
     double *msum;        /* 4*n mean sums: rho-1, ux, uy, uz */
     double *qsum;        /* 6*n sums of velocity products: uxux, uyuy, uzuz, uxuy, uxuz, uyuz */
     int64_t msamples;
+    double *q;           /* wall distances q[j*n + cell] of links x -> x + c_j into
+                            obstacle cells (fraction of the link in the fluid), or
+                            NULL for halfway bounce-back everywhere */
     double *force;       /* 3 per step */
     int64_t force_cap;
     int64_t t;
@@ -391,10 +394,78 @@ void oracle_lbm_destroy(oracle_lbm *o)
 {
     if (!o) return;
     free(o->solid); free(o->f); free(o->post); free(o->rho); free(o->u);
-    free(o->msum); free(o->qsum); free(o->force); free(o);
+    free(o->msum); free(o->qsum); free(o->q); free(o->force); free(o);
 }
 
 void oracle_lbm_set_f(oracle_lbm *o, const double *f) { memcpy(o->f, f, sizeof(double) * Q * o->n); }
+
+/* Wall distances for the interpolated bounce-back on obstacle links (Sec.
+ * 3.2): q[j*n + cell] in (0, 1] for each link from a fluid cell into an
+ * obstacle cell along c_j; other entries are ignored.  NULL restores
+ * halfway bounce-back (q = 1/2 on every link). */
+void oracle_lbm_set_q(oracle_lbm *o, const double *q)
+{
+    free(o->q);
+    o->q = NULL;
+    if (!q) return;
+    o->q = (double *)malloc(sizeof(double) * Q * o->n);
+    memcpy(o->q, q, sizeof(double) * Q * o->n);
+}
+
+/* A fluid cell at (x, y, z), reached through periodic faces if needed (a
+ * wall, inlet or outlet face ends the interpolation stencil). */
+static int inner_fluid(const oracle_lbm *o, int x, int y, int z, int64_t *cell)
+{
+    const oracle_params *p = &o->p;
+    if (x < 0 || x >= p->nx) {
+        if (p->face_x_lo != FACE_PERIODIC) return 0;
+        x = ((x % p->nx) + p->nx) % p->nx;
+    }
+    if (y < 0 || y >= p->ny) {
+        if (p->face_y != FACE_PERIODIC) return 0;
+        y = ((y % p->ny) + p->ny) % p->ny;
+    }
+    if (z < 0 || z >= p->nz) {
+        if (p->face_z != FACE_PERIODIC) return 0;
+        z = ((z % p->nz) + p->nz) % p->nz;
+    }
+    *cell = cell_of(o, x, y, z);
+    return !o->solid[*cell];
+}
+
+/* Population returned into pull direction i of fluid cell c = (x, y, z) whose
+ * link to x - c_i ends in an obstacle at fraction q of the link (Bouzidi,
+ * Firdaouss & Lallemand 2001): j = 26 - i heads into the wall; x1 = x + c_i
+ * and x2 = x + 2 c_i are the cells behind.  Quadratic interpolation when x1
+ * and x2 are fluid cells (inside, or across periodic faces), linear when only
+ * x1 is, halfway bounce-back otherwise (for q = 1/2 all three coincide):
+ *   q <  1/2: q(1+2q) f*_j(x) + (1-4q^2) f*_j(x1) - q(1-2q) f*_j(x2)
+ *             [linear: 2q f*_j(x) + (1-2q) f*_j(x1)]
+ *   q >= 1/2: f*_j(x)/(q(2q+1)) + (2q-1)/q f*_i(x) - (2q-1)/(2q+1) f*_i(x1)
+ *             [linear: f*_j(x)/(2q) + (2q-1)/(2q) f*_i(x)]                   */
+static double interpolated_bounce_back(const oracle_lbm *o, int64_t c, int x, int y, int z, int i)
+{
+    const int64_t n = o->n;
+    const int j = Q - 1 - i;
+    int cx, cy, cz;
+    velocity(i, &cx, &cy, &cz);
+    const double a0 = o->post[j * n + c];
+    const double q = o->q[j * n + c];
+    int64_t x1 = -1, x2 = -1;
+    const int v1 = inner_fluid(o, x + cx, y + cy, z + cz, &x1);
+    const int v2 = v1 && inner_fluid(o, x + 2 * cx, y + 2 * cy, z + 2 * cz, &x2);
+    if (!v1) return a0;
+    if (q < 0.5) {
+        if (v2)
+            return q * (1.0 + 2.0 * q) * a0 + (1.0 - 4.0 * q * q) * o->post[j * n + x1]
+                 - q * (1.0 - 2.0 * q) * o->post[j * n + x2];
+        return 2.0 * q * a0 + (1.0 - 2.0 * q) * o->post[j * n + x1];
+    }
+    if (v2)
+        return a0 / (q * (2.0 * q + 1.0)) + (2.0 * q - 1.0) / q * o->post[i * n + c]
+             - (2.0 * q - 1.0) / (2.0 * q + 1.0) * o->post[i * n + x1];
+    return a0 / (2.0 * q) + (2.0 * q - 1.0) / (2.0 * q) * o->post[i * n + c];
+}
 void oracle_lbm_get_f(const oracle_lbm *o, double *f) { memcpy(f, o->f, sizeof(double) * Q * o->n); }
 int64_t oracle_lbm_time(const oracle_lbm *o) { return o->t; }
 void oracle_lbm_set_time(oracle_lbm *o, int64_t t) { o->t = t; }
@@ -516,8 +587,10 @@ void oracle_lbm_step(oracle_lbm *o, int nsteps)
         if (sample) o->msamples++;
 
         /* 2. momentum exchange on obstacle links: every post-collision
-         *    population that heads into an obstacle cell and bounces back
-         *    hands 2 c_i f*_i to the body (walls are not part of the body) */
+         *    population f*_i that heads into an obstacle cell and the
+         *    population returned into the opposite direction hand
+         *    c_i (f*_i + f_returned) to the body, 2 c_i f*_i for halfway
+         *    bounce-back (walls are not part of the body) */
         if (o->t >= o->force_cap) {
             int64_t cap = o->force_cap * 2;
             while (cap <= o->t) cap *= 2;
@@ -543,7 +616,8 @@ void oracle_lbm_step(oracle_lbm *o, int nsteps)
                         }
                         if (!o->solid[cell_of(o, xx, yy, zz)]) continue;
                         double fs = o->post[i * n + c];
-                        fx += 2.0 * cx * fs; fy += 2.0 * cy * fs; fz += 2.0 * cz * fs;
+                        double back = o->q ? interpolated_bounce_back(o, c, x, y, z, Q - 1 - i) : fs;
+                        fx += cx * (fs + back); fy += cy * (fs + back); fz += cz * (fs + back);
                     }
                 }
         o->force[3 * o->t + 0] = fx;
@@ -589,8 +663,13 @@ void oracle_lbm_step(oracle_lbm *o, int nsteps)
                             v = o->post[i * n + src];
                         } else if (kind == SRC_WALL) {
                             /* halfway bounce-back: the population that left
-                             * towards the wall comes back reversed */
-                            v = o->post[inv * n + c];
+                             * towards the wall comes back reversed; on
+                             * obstacle links with wall distances, the
+                             * interpolated bounce-back */
+                            if (o->q && src >= 0 && o->solid[src])
+                                v = interpolated_bounce_back(o, c, x, y, z, i);
+                            else
+                                v = o->post[inv * n + c];
                         } else if (kind == SRC_INLET) {
                             /* bounce-back from a wall moving with the inlet
                              * velocity (u_in, 0, 0) */

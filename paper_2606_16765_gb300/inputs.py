@@ -117,6 +117,61 @@ def voxelize(grid, prims, out=None) -> np.ndarray:
     return m
 
 
+def link_wall_distances(grid, prims, mask=None, iters=40):
+    """Wall distances of the links from fluid cells into obstacle cells (for
+    the interpolated bounce-back): for each fluid cell x and direction c_j
+    with x + c_j solid, q = |x_w - x| / |c_j| in (0, 1), x_w the crossing of
+    the segment x -> x + c_j with the surface of the union of primitives
+    (bisection of the inside test, `iters` halvings).  Directions are indexed
+    i = (cx+1) + 3(cy+1) + 9(cz+1); cells are x + nx (y + ny z).
+
+    Returns (cell, direction, q) arrays of the links (int64, int8, float64).
+    Links leaving the grid are not obstacle links and are not listed."""
+    nx, ny, nz = grid
+    m = voxelize(grid, prims) if mask is None else mask
+    solid = np.argwhere(m != 0)                      # [k, (z, y, x)]
+    cells, dirs, qs = [], [], []
+    for j in range(27):
+        cx, cy, cz = j % 3 - 1, (j // 3) % 3 - 1, j // 9 - 1
+        if cx == 0 and cy == 0 and cz == 0:
+            continue
+        # fluid cells x with x + c_j solid: x = s - c_j for solid s
+        z, y, x = solid[:, 0] - cz, solid[:, 1] - cy, solid[:, 2] - cx
+        ok = (x >= 0) & (x < nx) & (y >= 0) & (y < ny) & (z >= 0) & (z < nz)
+        z, y, x = z[ok], y[ok], x[ok]
+        ok = m[z, y, x] == 0
+        z, y, x = z[ok], y[ok], x[ok]
+        if len(x) == 0:
+            continue
+        lo = np.zeros(len(x))                        # outside at 0
+        hi = np.ones(len(x))                         # inside at 1
+        X0, Y0, Z0 = x.astype(np.float64), y.astype(np.float64), z.astype(np.float64)
+        for _ in range(iters):
+            mid = 0.5 * (lo + hi)
+            X, Y, Z = X0 + mid * cx, Y0 + mid * cy, Z0 + mid * cz
+            ins = np.zeros(len(x), bool)
+            for pr in prims:
+                ins |= pr.inside(X, Y, Z)
+            hi = np.where(ins, mid, hi)
+            lo = np.where(ins, lo, mid)
+        cells.append(x + nx * (y + ny * z))
+        dirs.append(np.full(len(x), j, np.int8))
+        qs.append(0.5 * (lo + hi))
+    if not cells:
+        return np.zeros(0, np.int64), np.zeros(0, np.int8), np.zeros(0)
+    return (np.concatenate(cells).astype(np.int64), np.concatenate(dirs), np.concatenate(qs))
+
+
+def dense_wall_distances(grid, links):
+    """[27, nz, ny, nx] array of q (1/2 where no obstacle link) from the
+    (cell, direction, q) lists of link_wall_distances."""
+    nx, ny, nz = grid
+    q = np.full((27, nx * ny * nz), 0.5)
+    cell, d, v = links
+    q[d.astype(np.int64), cell] = v
+    return q.reshape(27, nz, ny, nx)
+
+
 def sphere(grid, center, radius) -> np.ndarray:
     return voxelize(grid, [Primitive("sphere", tuple(center), (2.0 * radius,))])
 

@@ -69,3 +69,31 @@ def test_batch_channels_shapes():
         assert nx in (128, 192, 256) and ny in (64, 96, 128) and nz in (64, 96, 128)
         assert 1000 <= d["re"] <= 10000
         assert d["mask"].shape == (nz, ny, nx) and d["mask"].sum() > 0
+
+
+def test_link_wall_distances_match_the_sphere_intersection():
+    """Bisection wall distances of the fluid-to-obstacle links against the
+    closed-form intersection of each link segment with the sphere."""
+    g = (20, 16, 16)
+    C, R = np.array([9.3, 7.6, 8.1]), 3.5
+    cell, d, q = I.link_wall_distances(g, [I.Primitive("sphere", tuple(C), (2 * R,))])
+    m = I.sphere(g, tuple(C), R)
+    nx, ny = g[0], g[1]
+    X, Y, Z = cell % nx, (cell // nx) % ny, cell // (nx * ny)
+    cv = np.array([[j % 3 - 1, (j // 3) % 3 - 1, j // 9 - 1] for j in range(27)], float)
+    V = cv[d.astype(int)]
+    P = np.stack([X, Y, Z], 1).astype(float)
+    assert (m.reshape(-1)[cell] == 0).all()
+    tgt = P + V
+    assert (m[tgt[:, 2].astype(int), tgt[:, 1].astype(int), tgt[:, 0].astype(int)] == 1).all()
+    a, b, c = (V * V).sum(1), 2 * ((P - C) * V).sum(1), ((P - C) ** 2).sum(1) - R * R
+    s = (-b - np.sqrt(b * b - 4 * a * c)) / (2 * a)
+    assert np.abs(s - q).max() < 1e-10
+    # every fluid-to-solid link is listed once
+    n_links = 0
+    for j in range(27):
+        if j == 13:
+            continue
+        sh = np.roll(np.roll(np.roll(m, -int(cv[j, 2]), 0), -int(cv[j, 1]), 1), -int(cv[j, 0]), 2)
+        n_links += int(((m == 0) & (sh == 1)).sum())
+    assert len(cell) == n_links

@@ -556,3 +556,73 @@ def test_velocity_covariances_equal_those_of_the_sampled_series():
     fl = solid == 0
     assert np.abs(st - ref)[fl].max() < 1e-15
     assert np.abs(ref[fl]).max() > 1e-8          # the flow does fluctuate
+
+
+# --------------------------------------------------------------------------
+# interpolated bounce-back (wall distances q, Sec. 3.2)
+# --------------------------------------------------------------------------
+def test_interpolated_bounce_back_at_half_link_is_halfway_bounce_back():
+    """With q = 1/2 on every link the quadratic and linear interpolations
+    reduce to halfway bounce-back: same populations and force record."""
+    nx, ny, nz = 14, 9, 7
+    solid = I.sphere((nx, ny, nz), (6.0, 4.0, 3.0), 2.5)
+    p = O.params(nx, ny, nz, 1.6, u_in=0.05, faces=("inlet", "outflow", "wall", "periodic"))
+    f = random_field((nz, ny, nx), 21)
+    A = O.Lattice(p, solid)
+    A.set_f(f)
+    A.step(5)
+    B = O.Lattice(p, solid)
+    B.set_f(f)
+    B.set_q(np.full((Q, nz, ny, nx), 0.5))
+    B.step(5)
+    fl = solid == 0
+    assert np.abs(A.get_f() - B.get_f())[:, fl].max() < 1e-15
+    assert np.abs(A.forces() - B.forces()).max() < 1e-15
+
+
+def shear_wave_rate_error(q, w1, use_q):
+    """Decay of u_x = U sin(pi (y - y1) / H) between plane walls at y1 = 1 - q
+    and y2 = ny - 2 + q (solid rows y = 0 and ny - 1, the walls at distance
+    q from the outermost fluid cells): an exact Navier-Stokes solution whose
+    amplitude falls as exp(-nu (pi / H)^2 t).  Returns the relative error of
+    the fitted rate."""
+    nx, ny, nz = 2, 20, 2
+    solid = np.zeros((nz, ny, nx), np.uint8)
+    solid[:, 0, :] = 1
+    solid[:, ny - 1, :] = 1
+    y1, y2 = 1 - q, ny - 2 + q
+    H = y2 - y1
+    L = O.Lattice(O.params(nx, ny, nz, w1, u_in=0.0, faces=("periodic",) * 4), solid)
+    y = np.arange(ny)
+    ux = 1e-3 * np.sin(np.pi * (y - y1) / H)
+    f = np.zeros((Q, nz, ny, nx))
+    for k in range(ny):
+        f[:, :, k, :] = np.asarray(O.equilibrium(1.0, ux[k], 0.0, 0.0))[:, None, None]
+    L.set_f(f)
+    if use_q:
+        qa = np.full((Q, nz, ny, nx), 0.5)
+        qa[CV[:, 1] == -1, :, 1, :] = q
+        qa[CV[:, 1] == 1, :, ny - 2, :] = q
+        L.set_q(qa)
+    nu = (1 / w1 - 0.5) / 3
+    rate = nu * (np.pi / H) ** 2
+    T = int(0.7 / rate)
+    prof = np.sin(np.pi * (y[1:-1] - y1) / H)
+    amp = []
+    for t in (T // 5, T):
+        L.step(t - L.t)
+        _, u = L.macros()
+        amp.append(u[0, 1:-1, 0, 0] @ prof / (prof @ prof))
+    return -np.log(amp[1] / amp[0]) / (T - T // 5) / rate - 1
+
+
+@pytest.mark.parametrize("q", [0.25, 0.75])
+@pytest.mark.parametrize("w1", [1.2, 1.7])
+def test_interpolated_bounce_back_puts_the_wall_at_q(q, w1):
+    """The shear wave between walls a quarter (or three quarters) of a link
+    from the outermost fluid cells decays at the rate of the true width with
+    the interpolated bounce-back (within 0.5 %); halfway bounce-back, which
+    puts the walls at half a link, is off by the (H_halfway / H)^2 factor
+    (about 5 %)."""
+    assert abs(shear_wave_rate_error(q, w1, True)) < 5e-3
+    assert abs(shear_wave_rate_error(q, w1, False)) > 4e-2
