@@ -100,7 +100,9 @@ typedef struct {
     int64_t force_capacity; /* rows kept on the device between host flushes     */
     int32_t block_x;        /* threads per block along x, multiple of 32 (0: 128) */
     int32_t block_y;        /* rows per block (0: 1); block_x * block_y <= 256   */
-    int32_t reserved[6];
+    int32_t stats;          /* 1: also accumulate the velocity products of the
+                               averaged samples (lbm_read_stats)                */
+    int32_t reserved[5];
 } lbm_params;
 
 /* Fill *p with the defaults listed above (re = 1000, u_in = 0.05, l_ref = 1,
@@ -145,6 +147,34 @@ int64_t lbm_time(const lbm_ctx *ctx);
  * samples (may be NULL) receives the sample count. */
 lbm_status lbm_read_mean(lbm_ctx *ctx, int32_t dtype, int32_t halfres, void *dst,
                          int64_t *samples);
+
+/* Interpolated bounce-back on obstacle links (Sec. 3.2: a quadratic
+ * bounce-back with wall distances).  Link k runs from fluid cell cell[k]
+ * along direction dir[k] (index (cx+1) + 3(cy+1) + 9(cz+1)) into an obstacle
+ * cell inside the grid; q[k] in (0, 1] is the fraction of the link on the
+ * fluid side of the wall.  After every step the population returned into the
+ * opposite direction becomes the quadratic interpolation of Bouzidi,
+ * Firdaouss & Lallemand (2001) from the post-collision populations of the
+ * cell and of the two cells behind it (x - c, x - 2c; linear when only the
+ * first is a fluid cell, halfway bounce-back when neither is; periodic faces
+ * are crossed, other faces end the stencil), and the obstacle force becomes
+ * the momentum exchange c (f* + f_returned).  Links not listed keep halfway
+ * bounce-back; n = 0 restores it everywhere; a repeated link takes its last
+ * entry.  Host arrays; the list is copied to device memory the context owns
+ * (kept across lbm_reset and lbm_load).  LBM_ERR_ARG for a link that is not
+ * fluid -> obstacle or q outside (0, 1]; LBM_ERR_STATE on a batch member (use
+ * lbm_batch_set_wall_distances).  Stepped by an extra kernel after each step
+ * (for batches, in the end-of-step kernel that also runs the outflow). */
+lbm_status lbm_set_wall_distances(lbm_ctx *ctx, int64_t n, const int64_t *cell, const int8_t *dir,
+                                  const double *q);
+
+/* Turbulence statistics (Sec. 3.3 validates turbulent fluctuations): the
+ * velocity covariances over the same samples as the time average, per cell
+ * <ux ux> - <ux>^2, <uy uy> - <uy>^2, <uz uz> - <uz>^2, <ux uy> - <ux><uy>,
+ * <ux uz> - <ux><uz>, <uy uz> - <uy><uz>, cell-major [z][y][x][6], from FP64
+ * running sums; solid cells give 0.  Needs params.stats = 1 and a time
+ * average (LBM_ERR_STATE otherwise).  dtype 0 = double, 1 = float. */
+lbm_status lbm_read_stats(lbm_ctx *ctx, int32_t dtype, void *dst, int64_t *samples);
 
 /* Snapshot k (0 <= k < snap_count) as float [z][y][x][4] (ux, uy, uz, p) at
  * full or half resolution (params.snap_halfres); LBM_ERR_STATE if not taken. */
@@ -256,6 +286,11 @@ lbm_status lbm_batch_run_to_end(lbm_batch *b);
 /* Wait for the batch; report latched device conditions of any member.  A
  * run is refused only while an unstable member is still live. */
 lbm_status lbm_batch_sync(lbm_batch *b);
+
+/* Wall distances of member g (as lbm_set_wall_distances); the next run
+ * captures the step sequence again. */
+lbm_status lbm_batch_set_wall_distances(lbm_batch *b, int32_t g, int64_t n, const int64_t *cell,
+                                        const int8_t *dir, const double *q);
 
 /* Borrow member g's context (valid until lbm_batch_destroy). */
 lbm_status lbm_batch_member(lbm_batch *b, int32_t g, lbm_ctx **ctx);

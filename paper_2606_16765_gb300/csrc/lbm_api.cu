@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -30,6 +31,13 @@ struct Layout {
            fpart = 0, fcount = 0, tpart = 0, tout = 0, status = 0, total = 0;
     int tot_blocks = 0;
 };
+
+// Bytes of the time-average sums: [4][n] doubles, plus [6][n] velocity
+// products with turbulence statistics on.
+size_t msum_bytes(const lbm_params &p, int64_t n)
+{
+    return p.mean_every > 0 ? (size_t)(p.stats ? 10 : 4) * n * 8 : 0;
+}
 
 // Upper bound of the edge-cell count: every cell on a domain face, plus the
 // (at most 26) fluid neighbours of each solid cell.
@@ -56,7 +64,7 @@ Layout make_layout(const lbm_grid &g, const lbm_params &p, int64_t n_solid)
     L.edge = take((size_t)edge_bound(g, n_solid) * 16);
     L.ub = take((size_t)3 * g.ny * g.nz * rsz);
     L.ob = take(p.face_x_hi == LBM_FACE_OUTFLOW ? (size_t)18 * g.ny * g.nz * rsz : 0);
-    L.msum = take(p.mean_every > 0 ? (size_t)4 * L.n * 8 : 0);
+    L.msum = take(msum_bytes(p, L.n));
     L.snaps = take(p.snap_count > 0 ? (size_t)p.snap_count * 4 * L.snap_cells * 4 : 0);
     L.stage = take(p.snap_count > 0 && p.snap_halfres ? (size_t)4 * L.n * 4 : 0);
     const int64_t cap = p.force_capacity > 0 ? p.force_capacity : 65536;
@@ -106,6 +114,12 @@ struct lbm_ctx {
     int64_t force_rows_dev = 0, force_cap = 0;
     double force_w[3] = {0, 0, 0};    // constant w-part of the obstacle force
     bool unstable = false;
+    bool in_batch = false;
+    // interpolated bounce-back links (device, owned by the context)
+    uint4 *qlinks = nullptr;
+    double *qval = nullptr, *qpart = nullptr;
+    unsigned *qcount = nullptr;
+    int64_t n_qlinks = 0;
     std::string err;
     int64_t n_fluid = 0, n_bulk = 0, launches = 0;
     // kernel timing: events recorded per step (start, mid, end) and the step kind
@@ -142,6 +156,12 @@ struct lbm_ctx {
         }
         a.u_in_f = (float)a.u_in; a.rho_in_f = (float)a.rho_in; a.rho_out_f = (float)a.rho_out;
         a.ub = base + L.ub;
+        a.stats = p.stats ? 1 : 0;
+        a.qlinks = qlinks;
+        a.qval = qval;
+        a.n_qlinks = n_qlinks;
+        a.qpart = qpart;
+        a.qcount = qcount;
         a.ob = base + L.ob;
         a.fcount = at<unsigned>(L.fcount);
         a.status = at<int>(L.status);
@@ -357,7 +377,7 @@ static lbm_status create_impl(const lbm_grid *g, const uint8_t *mask, const lbm_
     // state at rest (shifted populations 0), accumulators cleared
     bool ok = cudaMemsetAsync(ctx->base + L.pdf, 0, (size_t)Q * L.slot * storage_bytes(p->storage), s) == cudaSuccess;
     ok = ok && cudaMemsetAsync(ctx->base + L.ub, 0, (size_t)3 * ny * nz * (p->storage == LBM_F64 ? 8 : 4), s) == cudaSuccess;
-    if (p->mean_every > 0) ok = ok && cudaMemsetAsync(ctx->base + L.msum, 0, (size_t)4 * n * 8, s) == cudaSuccess;
+    if (p->mean_every > 0) ok = ok && cudaMemsetAsync(ctx->base + L.msum, 0, msum_bytes(*p, n), s) == cudaSuccess;
     if (p->snap_count > 0) {
         ok = ok && cudaMemsetAsync(ctx->base + L.snaps, 0, (size_t)p->snap_count * 4 * L.snap_cells * 4, s) == cudaSuccess;
         if (p->snap_halfres) ok = ok && cudaMemsetAsync(ctx->base + L.stage, 0, (size_t)4 * n * 4, s) == cudaSuccess;
@@ -391,6 +411,10 @@ extern "C" lbm_status lbm_destroy(lbm_ctx *ctx)
     if (!ctx) return LBM_ERR_ARG;
     cudaStreamSynchronize(ctx->stream);
     for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
+    cudaFree(ctx->qlinks);
+    cudaFree(ctx->qval);
+    cudaFree(ctx->qpart);
+    cudaFree(ctx->qcount);
     if (ctx->owns && ctx->base) cudaFree(ctx->base);
     delete ctx;
     return LBM_OK;
@@ -443,7 +467,21 @@ static void step_launch(lbm_ctx *ctx, const StepArgs &a, bool odd, bool epi)
     default: launch_step_f16c(a, odd, epi, ctx->plain, ctx->block_x, ctx->block_y, ctx->stream, e1, e2); break;
     }
     if (e2) cudaEventRecord(e3, ctx->stream);
-    ctx->launches += 1 + (a.n_edge > 0 ? 1 : 0);
+    ctx->launches += 1 + (a.n_edge > 0 ? 1 : 0) + (a.face_x_hi == FACE_OUTFLOW ? 1 : 0) + (a.n_qlinks > 0 ? 1 : 0);
+}
+
+// Outflow planes of the state before a step of parity `odd` (the convective
+// outflow extrapolates from them after that step).
+static void outflow_record(const lbm_ctx *c, const StepArgs &a, bool odd, cudaStream_t s)
+{
+    if (c->p.face_x_hi != LBM_FACE_OUTFLOW) return;
+    switch (c->p.storage) {
+    case LBM_F64: launch_outflow_record_f64(a, odd, s); break;
+    case LBM_F32: launch_outflow_record_f32(a, odd, s); break;
+    case LBM_F16S: launch_outflow_record_f16(a, odd, s); break;
+    case LBM_BF16S: launch_outflow_record_bf16(a, odd, s); break;
+    default: launch_outflow_record_f16c(a, odd, s); break;
+    }
 }
 
 extern "C" lbm_status lbm_step(lbm_ctx *ctx, int64_t nsteps)
@@ -453,6 +491,7 @@ extern "C" lbm_status lbm_step(lbm_ctx *ctx, int64_t nsteps)
     const lbm_params &p = ctx->p;
     const Layout &L = ctx->L;
     const StepArgs base = ctx->args();
+    if (nsteps > 0) outflow_record(ctx, base, (ctx->t & 1) != 0, ctx->stream);
     for (int64_t k = 0; k < nsteps; ++k) {
         const int64_t t = ctx->t;
         StepArgs a = base;
@@ -563,6 +602,96 @@ extern "C" lbm_status lbm_read_mean(lbm_ctx *ctx, int32_t dtype, int32_t halfres
     return produce(ctx, dst, 4 * es * nh, [&](void *o) {
         launch_halfres(full.p, ctx->g.nx, ctx->g.ny, ctx->g.nz, f32, o, ctx->stream);
     });
+}
+
+// ---------------------------------------------------------------------------
+// interpolated bounce-back: wall distances of obstacle links
+// ---------------------------------------------------------------------------
+extern "C" lbm_status lbm_set_wall_distances(lbm_ctx *ctx, int64_t n, const int64_t *cell, const int8_t *dir,
+                                             const double *q)
+{
+    if (!ctx || n < 0 || (n > 0 && (!cell || !dir || !q))) return ctx ? fail(ctx, LBM_ERR_ARG, "bad wall-distance arguments") : LBM_ERR_ARG;
+    if (ctx->in_batch) return fail(ctx, LBM_ERR_STATE, "set a batch member's wall distances with lbm_batch_set_wall_distances");
+    const lbm_grid &g = ctx->g;
+    const int64_t N = ctx->L.n;
+    std::vector<uint8_t> flags(N);
+    CK(cudaStreamSynchronize(ctx->stream));
+    CK(cudaMemcpy(flags.data(), ctx->base + ctx->L.flags, N, cudaMemcpyDeviceToHost));
+    const lbm_params &p = ctx->p;
+    // a fluid cell at (x, y, z), reached through periodic faces if needed
+    auto inner_fluid = [&](int x, int y, int z, int64_t &c) {
+        if (x < 0 || x >= g.nx) {
+            if (p.face_x_lo != LBM_FACE_PERIODIC) return false;
+            x = ((x % g.nx) + g.nx) % g.nx;
+        }
+        if (y < 0 || y >= g.ny) {
+            if (p.face_y != LBM_FACE_PERIODIC) return false;
+            y = ((y % g.ny) + g.ny) % g.ny;
+        }
+        if (z < 0 || z >= g.nz) {
+            if (p.face_z != LBM_FACE_PERIODIC) return false;
+            z = ((z % g.nz) + g.nz) % g.nz;
+        }
+        c = (int64_t)x + (int64_t)g.nx * ((int64_t)y + (int64_t)g.ny * z);
+        return !(flags[c] & CELL_SOLID);
+    };
+    std::map<int64_t, std::pair<uint4, double>> recs;    // keyed by cell * 27 + j: the last entry wins
+    for (int64_t k = 0; k < n; ++k) {
+        const int64_t c = cell[k];
+        const int j = dir[k];
+        if (c < 0 || c >= N || j < 0 || j >= Q || j == 13 || !(q[k] > 0.0 && q[k] <= 1.0))
+            return fail(ctx, LBM_ERR_ARG, "wall distance " + std::to_string(k) + ": cell, direction or q out of range");
+        const int x = (int)(c % g.nx), y = (int)((c / g.nx) % g.ny), z = (int)(c / ((int64_t)g.nx * g.ny));
+        const int cx = cx_of(j), cy = cy_of(j), cz = cz_of(j);
+        const int sx = x + cx, sy = y + cy, sz = z + cz;
+        const bool inside = sx >= 0 && sx < g.nx && sy >= 0 && sy < g.ny && sz >= 0 && sz < g.nz;
+        if ((flags[c] & CELL_SOLID) || !inside ||
+            !(flags[(int64_t)sx + (int64_t)g.nx * ((int64_t)sy + (int64_t)g.ny * sz)] & CELL_SOLID))
+            return fail(ctx, LBM_ERR_ARG, "wall distance " + std::to_string(k) +
+                                              ": not a link from a fluid cell into an obstacle cell");
+        int64_t x1 = -1, x2 = -1;
+        const bool v1 = inner_fluid(x - cx, y - cy, z - cz, x1);
+        const bool v2 = v1 && inner_fluid(x - 2 * cx, y - 2 * cy, z - 2 * cz, x2);
+        const int mode = v1 ? (v2 ? 2 : 1) : 0;
+        const int i = Q - 1 - j;                            // returning (pull) direction
+        recs[c * Q + j] = {make_uint4((uint32_t)c, (uint32_t)(v1 ? x1 : c), (uint32_t)(v2 ? x2 : c),
+                                      (uint32_t)(i | (mode << 8))), q[k]};
+    }
+    std::vector<uint4> L;
+    std::vector<double> V;
+    for (const auto &kv : recs)
+        if ((kv.second.first.w >> 8) != 0) {               // mode 0: halfway bounce-back, nothing to do
+            L.push_back(kv.second.first);
+            V.push_back(kv.second.second);
+        }
+    cudaFree(ctx->qlinks); cudaFree(ctx->qval); cudaFree(ctx->qpart); cudaFree(ctx->qcount);
+    ctx->qlinks = nullptr; ctx->qval = nullptr; ctx->qpart = nullptr; ctx->qcount = nullptr;
+    ctx->n_qlinks = 0;
+    if (L.empty()) return LBM_OK;
+    const int64_t m = (int64_t)L.size(), nb = (m + EDGE_BLOCK - 1) / EDGE_BLOCK;
+    CK(cudaMalloc(&ctx->qlinks, m * sizeof(uint4)));
+    CK(cudaMalloc(&ctx->qval, m * sizeof(double)));
+    CK(cudaMalloc(&ctx->qpart, 3 * sizeof(double) * nb));
+    CK(cudaMalloc(&ctx->qcount, sizeof(unsigned)));
+    CK(cudaMemcpy(ctx->qlinks, L.data(), m * sizeof(uint4), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->qval, V.data(), m * sizeof(double), cudaMemcpyHostToDevice));
+    CK(cudaMemset(ctx->qcount, 0, sizeof(unsigned)));
+    ctx->n_qlinks = m;
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_read_stats(lbm_ctx *ctx, int32_t dtype, void *dst, int64_t *samples)
+{
+    if (!ctx || !dst || (dtype != 0 && dtype != 1)) return ctx ? fail(ctx, LBM_ERR_ARG, "bad read_stats arguments") : LBM_ERR_ARG;
+    if (ctx->p.mean_every <= 0 || !ctx->p.stats) return fail(ctx, LBM_ERR_STATE, "turbulence statistics not enabled");
+    lbm_status st = lbm_sync(ctx);
+    if (st != LBM_OK && st != LBM_ERR_UNSTABLE) return st;
+    if (samples) *samples = ctx->msamples;
+    const bool f32 = dtype == 1;
+    const int64_t n = ctx->L.n;
+    const double inv = ctx->msamples > 0 ? 1.0 / (double)ctx->msamples : 0.0;
+    const double *msum = ctx->at<double>(ctx->L.msum);
+    return produce(ctx, dst, 6 * (f32 ? 4 : 8) * n, [&](void *o) { launch_stats_out(msum, n, inv, f32, o, ctx->stream); });
 }
 
 extern "C" lbm_status lbm_read_snapshot(lbm_ctx *ctx, int32_t k, float *dst)
@@ -715,7 +844,7 @@ extern "C" lbm_status lbm_save(lbm_ctx *ctx, const char *path)
     const size_t es = storage_bytes(ctx->p.storage);
     const size_t pdf_bytes = (size_t)Q * L.slot * es;
     const size_t ub_bytes = (size_t)3 * ctx->g.ny * ctx->g.nz * (ctx->p.storage == LBM_F64 ? 8 : 4);
-    const size_t ms_bytes = ctx->p.mean_every > 0 ? (size_t)4 * L.n * 8 : 0;
+    const size_t ms_bytes = msum_bytes(ctx->p, L.n);
     std::vector<char> buf(pdf_bytes + ub_bytes + ms_bytes);
     CK(cudaStreamSynchronize(ctx->stream));
     CK(cudaMemcpy(buf.data(), ctx->base + L.pdf, pdf_bytes, cudaMemcpyDeviceToHost));
@@ -752,7 +881,7 @@ extern "C" lbm_status lbm_load(lbm_ctx *ctx, const char *path)
     const size_t es = storage_bytes(ctx->p.storage);
     const size_t pdf_bytes = (size_t)Q * L.slot * es;
     const size_t ub_bytes = (size_t)3 * ctx->g.ny * ctx->g.nz * (ctx->p.storage == LBM_F64 ? 8 : 4);
-    const size_t ms_bytes = ctx->p.mean_every > 0 ? (size_t)4 * L.n * 8 : 0;
+    const size_t ms_bytes = msum_bytes(ctx->p, L.n);
     std::vector<char> buf(pdf_bytes + ub_bytes + ms_bytes);
     std::vector<double> frows(3 * h.force_rows);
     std::vector<char> taken(h.snap_count);
@@ -835,7 +964,7 @@ extern "C" lbm_status lbm_reset(lbm_ctx *ctx)
     CK(cudaStreamSynchronize(s));
     CK(cudaMemsetAsync(ctx->base + L.pdf, 0, (size_t)Q * L.slot * storage_bytes(p.storage), s));
     CK(cudaMemsetAsync(ctx->base + L.ub, 0, (size_t)3 * ctx->g.ny * ctx->g.nz * (p.storage == LBM_F64 ? 8 : 4), s));
-    if (p.mean_every > 0) CK(cudaMemsetAsync(ctx->base + L.msum, 0, (size_t)4 * L.n * 8, s));
+    if (p.mean_every > 0) CK(cudaMemsetAsync(ctx->base + L.msum, 0, msum_bytes(p, L.n), s));
     if (p.force_every > 0) CK(cudaMemsetAsync(ctx->base + L.force, 0, (size_t)ctx->force_cap * 3 * 8, s));
     CK(cudaMemsetAsync(ctx->base + L.fcount, 0, sizeof(unsigned), s));
     CK(cudaMemsetAsync(ctx->base + L.status, 0, sizeof(int), s));
@@ -982,7 +1111,7 @@ struct lbm_batch {
     cudaStream_t user = nullptr, own = nullptr;
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     BatchMember *d_mem = nullptr;
-    int64_t *d_bbegin = nullptr, *d_ebegin = nullptr, *d_t = nullptr;
+    int64_t *d_bbegin = nullptr, *d_ebegin = nullptr, *d_qbegin = nullptr, *d_t = nullptr;
     std::vector<int> live;              // members in the current table
     BatchLaunch launch{};
     cudaGraphExec_t graph = nullptr;
@@ -1015,6 +1144,7 @@ extern "C" lbm_status lbm_batch_destroy(lbm_batch *b)
     if (b->d_mem) cudaFree(b->d_mem);
     if (b->d_bbegin) cudaFree(b->d_bbegin);
     if (b->d_ebegin) cudaFree(b->d_ebegin);
+    if (b->d_qbegin) cudaFree(b->d_qbegin);
     if (b->d_t) cudaFree(b->d_t);
     if (b->ev_in) cudaEventDestroy(b->ev_in);
     if (b->ev_out) cudaEventDestroy(b->ev_out);
@@ -1062,6 +1192,7 @@ extern "C" lbm_status lbm_batch_create(int32_t n, const lbm_grid *grids, const u
             lbm_batch_destroy(b);
             return batch_fail(nullptr, st, m);
         }
+        c->in_batch = true;
         b->members.push_back(c);
         b->t_end.push_back(INT64_MAX / 4);
     }
@@ -1072,6 +1203,7 @@ extern "C" lbm_status lbm_batch_create(int32_t n, const lbm_grid *grids, const u
         cudaMalloc(&b->d_mem, sizeof(BatchMember) * n) != cudaSuccess ||
         cudaMalloc(&b->d_bbegin, sizeof(int64_t) * (n + 1)) != cudaSuccess ||
         cudaMalloc(&b->d_ebegin, sizeof(int64_t) * (n + 1)) != cudaSuccess ||
+        cudaMalloc(&b->d_qbegin, sizeof(int64_t) * (n + 1)) != cudaSuccess ||
         cudaMalloc(&b->d_t, sizeof(int64_t)) != cudaSuccess ||
         cudaMemset(b->d_t, 0, sizeof(int64_t)) != cudaSuccess)
         st = LBM_ERR_CUDA;
@@ -1081,6 +1213,22 @@ extern "C" lbm_status lbm_batch_create(int32_t n, const lbm_grid *grids, const u
         return batch_fail(nullptr, st, "batch device set-up failed");
     }
     *out = b;
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_batch_set_wall_distances(lbm_batch *b, int32_t g, int64_t n, const int64_t *cell,
+                                                   const int8_t *dir, const double *q)
+{
+    if (!b || g < 0 || g >= (int32_t)b->members.size()) return LBM_ERR_ARG;
+    lbm_ctx *c = b->members[g];
+    c->in_batch = false;
+    const lbm_status st = lbm_set_wall_distances(c, n, cell, dir, q);
+    c->in_batch = true;
+    if (st != LBM_OK) return batch_fail(b, st, "member " + std::to_string(g) + ": " + c->err);
+    if (b->graph) {                                     // the member table changes: capture again
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+    }
     return LBM_OK;
 }
 
@@ -1125,7 +1273,7 @@ extern "C" lbm_status lbm_batch_set_flowthroughs(lbm_batch *b, double n_ft)
 static lbm_status batch_rebuild(lbm_batch *b, const std::vector<int> &live)
 {
     std::vector<BatchMember> mem(live.size());
-    std::vector<int64_t> bb(live.size() + 1, 0), eb(live.size() + 1, 0);
+    std::vector<int64_t> bb(live.size() + 1, 0), eb(live.size() + 1, 0), qb(live.size() + 1, 0);
     for (size_t k = 0; k < live.size(); ++k) {
         lbm_ctx *c = b->members[live[k]];
         BatchMember &M = mem[k];
@@ -1142,6 +1290,7 @@ static lbm_status batch_rebuild(lbm_batch *b, const std::vector<int> &live)
         M.gy = (c->g.ny + b->block_y - 1) / b->block_y;
         bb[k + 1] = bb[k] + (int64_t)M.gx * M.gy * c->g.nz;
         eb[k + 1] = eb[k] + (c->n_edge + EDGE_BLOCK - 1) / EDGE_BLOCK;
+        qb[k + 1] = qb[k] + (c->n_qlinks + EDGE_BLOCK - 1) / EDGE_BLOCK;
     }
     if (bb.back() >= (int64_t(1) << 31) || eb.back() >= (int64_t(1) << 31))
         return batch_fail(b, LBM_ERR_ARG, "batch too large for one launch");
@@ -1149,8 +1298,16 @@ static lbm_status batch_rebuild(lbm_batch *b, const std::vector<int> &live)
     BCK(cudaMemcpyAsync(b->d_bbegin, bb.data(), sizeof(int64_t) * bb.size(), cudaMemcpyHostToDevice, b->own));
     BCK(cudaMemcpyAsync(b->d_ebegin, eb.data(), sizeof(int64_t) * eb.size(), cudaMemcpyHostToDevice, b->own));
     BCK(cudaStreamSynchronize(b->own));
+    int out_chunks = 0;
+    for (int g : live) {
+        const lbm_ctx *c = b->members[g];
+        if (c->p.face_x_hi == LBM_FACE_OUTFLOW)
+            out_chunks = std::max<int>(out_chunks, (int)std::min<int64_t>(((int64_t)c->g.ny * c->g.nz + 255) / 256, 64));
+    }
+    BCK(cudaMemcpyAsync(b->d_qbegin, qb.data(), sizeof(int64_t) * qb.size(), cudaMemcpyHostToDevice, b->own));
+    BCK(cudaStreamSynchronize(b->own));
     b->launch = BatchLaunch{b->d_mem, b->d_bbegin, b->d_ebegin, (int)live.size(), bb.back(), eb.back(), b->d_t,
-                            b->block_x, b->block_y};
+                            b->block_x, b->block_y, out_chunks, b->d_qbegin, qb.back()};
     if (b->graph) {
         cudaGraphExecDestroy(b->graph);
         b->graph = nullptr;
@@ -1206,6 +1363,8 @@ extern "C" lbm_status lbm_batch_run(lbm_batch *b, int64_t nsteps)
     const int64_t target = b->t + round_chunk(b, nsteps);
     BCK(cudaEventRecord(b->ev_in, b->user));
     BCK(cudaStreamWaitEvent(b->own, b->ev_in, 0));
+    for (size_t g = 0; g < b->members.size(); ++g)
+        if (b->t < b->t_end[g]) outflow_record(b->members[g], b->members[g]->args(), (b->t & 1) != 0, b->own);
     while (b->t < target) {
         std::vector<int> live;
         int64_t seg_end = target;
@@ -1225,7 +1384,9 @@ extern "C" lbm_status lbm_batch_run(lbm_batch *b, int64_t nsteps)
         for (int g : live) cells += b->members[g]->n_fluid;
         b->updates += cells * (seg_end - b->t);
         b->graph_launches += chunks;
-        b->kernel_launches += chunks * b->chunk * (2 + (b->launch.edge_blocks > 0 ? 1 : 0));
+        b->kernel_launches += chunks * b->chunk *
+                              (2 + (b->launch.edge_blocks > 0 ? 1 : 0) + (b->launch.out_chunks > 0 ? 1 : 0) +
+                               (b->launch.q_blocks > 0 ? 1 : 0));
         b->t = seg_end;
     }
     BCK(cudaEventRecord(b->ev_out, b->own));

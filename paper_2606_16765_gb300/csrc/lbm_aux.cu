@@ -226,6 +226,24 @@ __global__ void k_mean_out(const double *msum, int64_t n, double inv_samples, T 
     }
 }
 
+// Velocity covariances from the running sums: msum [4][n] means then [6][n]
+// products (xx, yy, zz, xy, xz, yz) -> out [n][6].
+template <class T>
+__global__ void k_stats_out(const double *msum, int64_t n, double inv_samples, T *out)
+{
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x) {
+        const double mx = msum[n + c] * inv_samples, my = msum[2 * n + c] * inv_samples,
+                     mz = msum[3 * n + c] * inv_samples;
+        const double *q = msum + 4 * n + c;
+        out[6 * c + 0] = (T)(q[0] * inv_samples - mx * mx);
+        out[6 * c + 1] = (T)(q[n] * inv_samples - my * my);
+        out[6 * c + 2] = (T)(q[2 * n] * inv_samples - mz * mz);
+        out[6 * c + 3] = (T)(q[3 * n] * inv_samples - mx * my);
+        out[6 * c + 4] = (T)(q[4 * n] * inv_samples - mx * mz);
+        out[6 * c + 5] = (T)(q[5 * n] * inv_samples - my * mz);
+    }
+}
+
 // 2x2x2 box mean of a [z][y][x][4] field; a trailing odd cell is a block of its own.
 template <class T>
 __global__ void k_halfres(const T *in, int nx, int ny, int nz, T *out)
@@ -292,6 +310,12 @@ void launch_mean_out(const double *msum, int64_t n, double inv_samples, bool f32
 {
     if (f32) k_mean_out<float><<<grid_for(n, 256), 256, 0, s>>>(msum, n, inv_samples, (float *)out);
     else k_mean_out<double><<<grid_for(n, 256), 256, 0, s>>>(msum, n, inv_samples, (double *)out);
+}
+
+void launch_stats_out(const double *msum, int64_t n, double inv_samples, bool f32, void *out, cudaStream_t s)
+{
+    if (f32) k_stats_out<float><<<grid_for(n, 256), 256, 0, s>>>(msum, n, inv_samples, (float *)out);
+    else k_stats_out<double><<<grid_for(n, 256), 256, 0, s>>>(msum, n, inv_samples, (double *)out);
 }
 
 // FP32 snapshot box mean: one thread per half-resolution cell, 16-byte loads

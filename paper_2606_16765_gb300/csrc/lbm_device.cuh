@@ -119,8 +119,19 @@ struct StepArgs {
     void *ub;               // outlet plane velocity [nz*ny][3] (compute type)
     void *ob;               // outflow planes (compute type): [9][nz*ny] pre-collision
                             // populations with cx = -1 of the outlet cells, then
-                            // [9][nz*ny] of the cells next to them (x = nx - 2)
-    double *msum;           // mean sums [4][n] when this step is sampled, else null
+                            // [9][nz*ny] of the cells next to them (x = nx - 2),
+                            // recorded between steps by k_outflow
+    double *msum;           // mean sums [4][n] (+ [6][n] velocity products when
+                            // `stats`) when this step is sampled, else null
+    int stats;              // accumulate velocity products with the means
+    // interpolated bounce-back on obstacle links (after the step, k_qbb):
+    // records {cell, x1 = cell + c_i, x2 = cell + 2 c_i, i | mode << 8} with i
+    // the returning (pull) direction, mode 1 linear / 2 quadratic; q per link
+    const uint4 *qlinks;
+    const double *qval;
+    int64_t n_qlinks;
+    double *qpart;          // force partials per q-link block
+    unsigned int *qcount;   // arrival counter of that reduction
     float *snap;            // full-resolution float4 target when snapshotting, else null
     double *fpart;          // force partials per edge block when recorded, else null
     unsigned int *fcount;   // arrival counter of the last-block reduction
@@ -148,6 +159,9 @@ struct BatchLaunch {
     int64_t bulk_blocks, edge_blocks;
     int64_t *t;                 // device step counter
     int block_x, block_y;
+    int out_chunks;             // outflow: blocks per member along its outlet plane (0: none)
+    const int64_t *q_begin;     // nm + 1 entries (first wall-distance block per member)
+    int64_t q_blocks;           // wall-distance blocks in all (0: none)
 };
 
 // A parameter in the compute type: the FP32 copy for float kernels.
@@ -204,20 +218,6 @@ __device__ __forceinline__ R boundary_value(const StepArgs &a, int kind, int i, 
         return -own + R(2) * w * (pick<R>(a.rho_out, a.rho_out_f) * (R(1) + R(4.5) * cu * cu - R(1.5) * uu) - R(1));
     }
     return own;
-}
-
-// Convective outflow: the cells of the outlet plane (x = nx - 1) and of the
-// plane next to it record their pre-collision populations with cx = -1
-// (directions 3k, k < 9) every step; k_outflow extrapolates from them after
-// the step.
-template <class R>
-__device__ __forceinline__ void record_outflow_planes(const StepArgs &a, int x, int64_t yz, const R *f)
-{
-    if (a.face_x_hi != FACE_OUTFLOW || x < a.nx - 2) return;
-    const int64_t P = (int64_t)a.ny * a.nz;
-    R *pl = static_cast<R *>(a.ob) + (x == a.nx - 1 ? 0 : 9 * P) + yz;
-#pragma unroll
-    for (int k = 0; k < 9; ++k) pl[k * P] = f[3 * k];
 }
 
 // ---------------------------------------------------------------------------

@@ -13,18 +13,23 @@ namespace lbm {
 void launch_step_f64(const StepArgs &a, bool odd, bool epi, bool plain, int block_x, int block_y,
                     cudaStream_t s, cudaEvent_t ev_interior, cudaEvent_t ev_bulk);
 void launch_batch_step_f64(const BatchLaunch &L, bool odd, bool epi, bool plain, cudaStream_t s);
+void launch_outflow_record_f64(const StepArgs &a, bool odd, cudaStream_t s);
 void launch_step_f32(const StepArgs &a, bool odd, bool epi, bool plain, int block_x, int block_y,
                     cudaStream_t s, cudaEvent_t ev_interior, cudaEvent_t ev_bulk);
 void launch_batch_step_f32(const BatchLaunch &L, bool odd, bool epi, bool plain, cudaStream_t s);
+void launch_outflow_record_f32(const StepArgs &a, bool odd, cudaStream_t s);
 void launch_step_f16(const StepArgs &a, bool odd, bool epi, bool plain, int block_x, int block_y,
                     cudaStream_t s, cudaEvent_t ev_interior, cudaEvent_t ev_bulk);
 void launch_batch_step_f16(const BatchLaunch &L, bool odd, bool epi, bool plain, cudaStream_t s);
+void launch_outflow_record_f16(const StepArgs &a, bool odd, cudaStream_t s);
 void launch_step_bf16(const StepArgs &a, bool odd, bool epi, bool plain, int block_x, int block_y,
                     cudaStream_t s, cudaEvent_t ev_interior, cudaEvent_t ev_bulk);
 void launch_batch_step_bf16(const BatchLaunch &L, bool odd, bool epi, bool plain, cudaStream_t s);
+void launch_outflow_record_bf16(const StepArgs &a, bool odd, cudaStream_t s);
 void launch_step_f16c(const StepArgs &a, bool odd, bool epi, bool plain, int block_x, int block_y,
                     cudaStream_t s, cudaEvent_t ev_interior, cudaEvent_t ev_bulk);
 void launch_batch_step_f16c(const BatchLaunch &L, bool odd, bool epi, bool plain, cudaStream_t s);
+void launch_outflow_record_f16c(const StepArgs &a, bool odd, cudaStream_t s);
 
 enum AuxOp { AUX_NOISE, AUX_GATHER, AUX_SET, AUX_MACROS, AUX_TOTALS };
 
@@ -44,6 +49,7 @@ void launch_flags(const uint8_t *mask, uint8_t *flags, int nx, int ny, int nz, b
                   cudaStream_t s);
 void launch_aux(int storage, AuxOp op, const StepArgs &a, bool odd, const AuxArgs &x, cudaStream_t s);
 void launch_mean_out(const double *msum, int64_t n, double inv_samples, bool f32, void *out, cudaStream_t s);
+void launch_stats_out(const double *msum, int64_t n, double inv_samples, bool f32, void *out, cudaStream_t s);
 void launch_halfres(const void *in, int nx, int ny, int nz, bool f32, void *out, cudaStream_t s);
 
 }  // namespace lbm

@@ -41,6 +41,16 @@ __device__ __forceinline__ void epilogue(const StepArgs &a, const StepOut &o, in
         o.msum[a.n + c] += (double)ux;
         o.msum[2 * a.n + c] += (double)uy;
         o.msum[3 * a.n + c] += (double)uz;
+        if (a.stats) {
+            const double x = (double)ux, y = (double)uy, z = (double)uz;
+            double *q = o.msum + 4 * a.n + c;
+            q[0] += x * x;
+            q[a.n] += y * y;
+            q[2 * a.n] += z * z;
+            q[3 * a.n] += x * y;
+            q[4 * a.n] += x * z;
+            q[5 * a.n] += y * z;
+        }
     }
     if (o.snap) {
         float4 v = make_float4((float)ux, (float)uy, (float)uz, (float)(drho * R(1.0 / 3.0)));
@@ -93,7 +103,6 @@ __device__ __forceinline__ void bulk_cell(const StepArgs &a, const StepOut &o, i
 #pragma unroll
         for (int i = 0; i < Q; ++i) f[i] = T::ld(reinterpret_cast<const S *>(q + gof[i]));
     }
-    record_outflow_planes<R>(a, x, (int64_t)y + (int64_t)a.ny * z, f);
     R drho, ux, uy, uz;
     collide<R, PLAIN>(f, rates_of<R>(a), drho, ux, uy, uz);
     check_density(drho, a.status);
@@ -137,7 +146,7 @@ __global__ void __launch_bounds__(256) k_step_bulk(StepArgs a)
 // arrive adds the partials in a fixed order and writes the result, so the
 // value does not depend on block scheduling.
 __device__ __forceinline__ void block_force_reduce(const StepOut &o, int64_t blk, int64_t nblk, double fx, double fy,
-                                                   double fz)
+                                                   double fz, bool add = false)
 {
     __shared__ double sh[3][EDGE_BLOCK / 32];
     __shared__ bool last;
@@ -175,7 +184,7 @@ __device__ __forceinline__ void block_force_reduce(const StepOut &o, int64_t blk
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        for (int d = 0; d < 3; ++d) o.fout[d] = tr[d][0];
+        for (int d = 0; d < 3; ++d) o.fout[d] = add ? o.fout[d] + tr[d][0] : tr[d][0];
         *o.fcount = 0u;
     }
 }
@@ -237,7 +246,6 @@ __device__ __forceinline__ void edge_cell(const StepArgs &a, const StepOut &o, i
                 f[i] = T::ld(p + (int64_t)i * a.slot + c);
             }
         }
-        record_outflow_planes<R>(a, x, (int64_t)yz, f);
         R drho, ux, uy, uz;
         collide<R, PLAIN>(f, rates_of<R>(a), drho, ux, uy, uz);
         check_density(drho, a.status);
@@ -287,14 +295,22 @@ __global__ void __launch_bounds__(EDGE_BLOCK) k_step_edge(StepArgs a)
     if (o.fpart) block_force_reduce(o, blockIdx.x, gridDim.x, (double)fx, (double)fy, (double)fz);
 }
 
-// Convective outflow (after every step): each fluid outlet cell gets, for its
-// links through the x-high face (cx = -1 and the source cell not beyond a
-// lateral wall), f_i = c_s f_i(x_b - e_x) + (1 - c_s) f_i(x_b) from the
-// pre-collision populations its step recorded, written into its own slot i:
-// the place where the next step, of either parity, reads that link.  A solid
-// (or missing) inner neighbour makes the cell extrapolate from itself.
+// Convective outflow, between steps (one thread per outlet column y, z).
+// fix: each fluid outlet cell x_b gets, for its links through the x-high face
+// (cx = -1, the source not beyond a lateral wall),
+//     f_i = c_s f_i(x_b - e_x) + (1 - c_s) f_i(x_b)
+// from the pre-collision populations of the step just taken (recorded by the
+// previous call), written into its own slot i: where the next step, of
+// either parity, reads that link.  A solid (or missing) inner neighbour makes
+// the cell extrapolate from itself.
+// record: the populations with cx = -1 that the next step (parity next_odd)
+// will gather, of the outlet cell (all such links of an outlet cell are
+// boundary links: its own slot) and of the cell next to it (own slot for an
+// even step or a boundary link; slot 26 - i of the source for an odd step).
+// The fix only writes outlet-cell slots of cx = -1, which the inner cell's
+// gather never reads.
 template <class S>
-__device__ __forceinline__ void outflow_cell(const StepArgs &a, int64_t yz)
+__device__ __forceinline__ void outflow_cell(const StepArgs &a, int64_t yz, bool fix, bool next_odd)
 {
     using T = Store<S>;
     using R = typename T::R;
@@ -302,35 +318,128 @@ __device__ __forceinline__ void outflow_cell(const StepArgs &a, int64_t yz)
     const int64_t c = (int64_t)(a.nx - 1) + (int64_t)a.nx * yz;
     if (a.flags[c] & CELL_SOLID) return;
     const int y = (int)(yz % a.ny), z = (int)(yz / a.ny);
-    const R *own = static_cast<const R *>(a.ob) + yz;
+    R *own = static_cast<R *>(a.ob) + yz;
+    R *in = own + 9 * P;
     const bool inner = a.nx >= 2 && !(a.flags[c - 1] & CELL_SOLID);
-    const R *in = inner ? own + 9 * P : own;
-    const R cs = R(0.57735026918962576451), cs1 = R(1) - cs;
     S *p = static_cast<S *>(a.pdf);
+    if (fix) {
+        const R cs = R(0.57735026918962576451), cs1 = R(1) - cs;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            const int i = 3 * k;
+            const int sy = y - cy_of(i), sz = z - cz_of(i);
+            if ((sy < 0 || sy >= a.ny) && a.face_y != FACE_PERIODIC) continue;   // wall link
+            if ((sz < 0 || sz >= a.nz) && a.face_z != FACE_PERIODIC) continue;
+            const R g = cs * (inner ? in[k * P] : own[k * P]) + cs1 * own[k * P];
+            T::st(p + (int64_t)i * a.slot + c, g);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 9; ++k) own[k * P] = T::ld(p + (int64_t)(3 * k) * a.slot + c);
+    if (!inner) return;
+    const int64_t ci = c - 1;
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
         const int i = 3 * k;
-        const int sy = y - cy_of(i), sz = z - cz_of(i);
-        if ((sy < 0 || sy >= a.ny) && a.face_y != FACE_PERIODIC) continue;   // wall link
-        if ((sz < 0 || sz >= a.nz) && a.face_z != FACE_PERIODIC) continue;
-        T::st(p + (int64_t)i * a.slot + c, cs * in[k * P] + cs1 * own[k * P]);
+        int64_t src = -1;
+        if (next_odd) {
+            int sy = y - cy_of(i), sz = z - cz_of(i);
+            bool ok = true;
+            if (sy < 0 || sy >= a.ny) { ok = a.face_y == FACE_PERIODIC; sy = sy < 0 ? sy + a.ny : sy - a.ny; }
+            if (sz < 0 || sz >= a.nz) { ok = ok && a.face_z == FACE_PERIODIC; sz = sz < 0 ? sz + a.nz : sz - a.nz; }
+            if (ok) {
+                const int64_t s = (int64_t)(a.nx - 1) + (int64_t)a.nx * ((int64_t)sy + (int64_t)a.ny * sz);
+                if (!(a.flags[s] & CELL_SOLID)) src = s;
+            }
+        }
+        in[k * P] = src >= 0 ? T::ld(p + (int64_t)(Q - 1 - i) * a.slot + src) : T::ld(p + (int64_t)i * a.slot + ci);
     }
 }
 
 template <class S>
-__global__ void __launch_bounds__(256) k_outflow(StepArgs a)
+__global__ void __launch_bounds__(256) k_outflow(StepArgs a, int fix, int next_odd)
 {
     const int64_t P = (int64_t)a.ny * a.nz;
     for (int64_t yz = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; yz < P; yz += (int64_t)gridDim.x * blockDim.x)
-        outflow_cell<S>(a, yz);
+        outflow_cell<S>(a, yz, fix != 0, next_odd != 0);
 }
 
 template <class S>
-static void launch_outflow(const StepArgs &a, cudaStream_t s)
+static void launch_outflow(const StepArgs &a, bool fix, bool next_odd, cudaStream_t s)
 {
     if (a.face_x_hi != FACE_OUTFLOW) return;
     const int64_t P = (int64_t)a.ny * a.nz;
-    k_outflow<S><<<(unsigned)std::min<int64_t>((P + 255) / 256, 1024), 256, 0, s>>>(a);
+    k_outflow<S><<<(unsigned)std::min<int64_t>((P + 255) / 256, 1024), 256, 0, s>>>(a, fix ? 1 : 0, next_odd ? 1 : 0);
+}
+
+// Interpolated bounce-back (Bouzidi, Firdaouss & Lallemand 2001), after the
+// step: for an obstacle link of fluid cell x (pull direction i, j = 26 - i
+// heading into the wall at fraction q of the link, x1 = x + c_i and
+// x2 = x + 2 c_i behind it) the own slot i holds f*_j(x), the halfway
+// bounce-back value, and f*_j(x1), f*_j(x2), f*_i(x), f*_i(x1) sit where
+// the next step gathers them: for a next odd step slot i of x1 / x2 and slot
+// j of x / x1, for a next even step slot j of x / x1 and slot i of x1 / x2.
+// None of those slots belongs to an obstacle link, so the links are updated
+// in place without ordering.  The returned population replaces own slot i;
+// the momentum exchange gains c_j (f_returned - f*_j) over the halfway value
+// recorded by the edge kernel.
+template <class S>
+__device__ __forceinline__ void qbb_link(const StepArgs &a, int64_t k, bool next_odd, typename Store<S>::R &fx,
+                                         typename Store<S>::R &fy, typename Store<S>::R &fz)
+{
+    using T = Store<S>;
+    using R = typename T::R;
+    S *p = static_cast<S *>(a.pdf);
+    const uint4 e = a.qlinks[k];
+    const int i = (int)(e.w & 0xFFu), mode = (int)(e.w >> 8), j = Q - 1 - i;
+    const int64_t x = e.x, x1 = e.y, x2 = e.z;
+    const int64_t si = (int64_t)i * a.slot, sj = (int64_t)j * a.slot;
+    const R q = R(a.qval[k]);
+    const R a0 = T::ld(p + si + x);
+    R ret;
+    if (q < R(0.5)) {
+        const R a1 = T::ld(p + (next_odd ? si + x1 : sj + x));
+        if (mode == 2) {
+            const R a2 = T::ld(p + (next_odd ? si + x2 : sj + x1));
+            ret = q * (R(1) + R(2) * q) * a0 + (R(1) - R(4) * q * q) * a1 - q * (R(1) - R(2) * q) * a2;
+        } else {
+            ret = R(2) * q * a0 + (R(1) - R(2) * q) * a1;
+        }
+    } else {
+        const R b0 = T::ld(p + (next_odd ? sj + x : si + x1));
+        if (mode == 2) {
+            const R b1 = T::ld(p + (next_odd ? sj + x1 : si + x2));
+            ret = a0 / (q * (R(2) * q + R(1))) + (R(2) * q - R(1)) / q * b0 -
+                  (R(2) * q - R(1)) / (R(2) * q + R(1)) * b1;
+        } else {
+            ret = a0 / (R(2) * q) + (R(2) * q - R(1)) / (R(2) * q) * b0;
+        }
+    }
+    T::st(p + si + x, ret);
+    const R dv = ret - a0;
+    fx += R(cx_of(j)) * dv;
+    fy += R(cy_of(j)) * dv;
+    fz += R(cz_of(j)) * dv;
+}
+
+template <class S>
+__global__ void __launch_bounds__(EDGE_BLOCK) k_qbb(StepArgs a, int next_odd)
+{
+    using R = typename Store<S>::R;
+    const int64_t k = (int64_t)blockIdx.x * EDGE_BLOCK + threadIdx.x;
+    R fx = R(0), fy = R(0), fz = R(0);
+    if (k < a.n_qlinks) qbb_link<S>(a, k, next_odd != 0, fx, fy, fz);
+    if (a.fout) {
+        StepOut o{nullptr, nullptr, a.qpart, a.qcount, a.fout};
+        block_force_reduce(o, blockIdx.x, gridDim.x, (double)fx, (double)fy, (double)fz, true);
+    }
+}
+
+template <class S>
+static void launch_qbb(const StepArgs &a, bool next_odd, cudaStream_t s)
+{
+    if (a.n_qlinks <= 0) return;
+    k_qbb<S><<<(unsigned)((a.n_qlinks + EDGE_BLOCK - 1) / EDGE_BLOCK), EDGE_BLOCK, 0, s>>>(a, next_odd ? 1 : 0);
 }
 
 template <class S, bool ODD, bool EPI, bool PLAIN>
@@ -406,15 +515,41 @@ __global__ void __launch_bounds__(EDGE_BLOCK) k_batch_edge(const BatchMember *me
 }
 
 // End of a batched step: the convective outflow of every member with that
-// outlet (block m serves member m), then the step counter advances.
+// outlet (grid x = member, grid y splits its outlet plane) ...
 template <class S>
-__global__ void __launch_bounds__(256) k_batch_tail(const BatchMember *mem, int nm, int64_t *t)
+__global__ void __launch_bounds__(256) k_batch_outflow(const BatchMember *mem, int nm, int fix, int next_odd)
 {
     const StepArgs &a = mem[blockIdx.x].a;
-    if (a.face_x_hi == FACE_OUTFLOW) {
-        const int64_t P = (int64_t)a.ny * a.nz;
-        for (int64_t yz = threadIdx.x; yz < P; yz += blockDim.x) outflow_cell<S>(a, yz);
+    if (a.face_x_hi != FACE_OUTFLOW) return;
+    const int64_t P = (int64_t)a.ny * a.nz;
+    for (int64_t yz = (int64_t)blockIdx.y * blockDim.x + threadIdx.x; yz < P; yz += (int64_t)gridDim.y * blockDim.x)
+        outflow_cell<S>(a, yz, fix != 0, next_odd != 0);
+}
+
+// ... then the interpolated bounce-back of the members with wall distances
+// (blocks numbered member after member, as for the edge kernel), each
+// member's force correction reduced over its blocks in a fixed order and
+// added to its force row of this step.
+template <class S>
+__global__ void __launch_bounds__(EDGE_BLOCK) k_batch_qbb(const BatchMember *mem, const int64_t *begin, int nm,
+                                                         const int64_t *tdev, int next_odd)
+{
+    using R = typename Store<S>::R;
+    const int m = find_member(begin, nm, blockIdx.x);
+    const BatchMember &B = mem[m];
+    const int64_t lb = (int64_t)blockIdx.x - begin[m], nb = begin[m + 1] - begin[m];
+    const int64_t k = lb * EDGE_BLOCK + threadIdx.x;
+    R fx = R(0), fy = R(0), fz = R(0);
+    if (k < B.a.n_qlinks) qbb_link<S>(B.a, k, next_odd != 0, fx, fy, fz);
+    const int64_t t = *tdev;
+    if (B.force && t % B.force_every == 0) {
+        StepOut o{nullptr, nullptr, B.a.qpart, B.a.qcount, B.force + 3 * (t / B.force_every)};
+        block_force_reduce(o, lb, nb, (double)fx, (double)fy, (double)fz, true);
     }
+}
+
+static __global__ void k_batch_tick(int64_t *t)
+{
     if (threadIdx.x == 0 && blockIdx.x == 0) *t += 1;
 }
 
@@ -441,7 +576,11 @@ void launch_batch_step_t(const BatchLaunch &L, bool odd, bool epi, bool plain, c
             else     k_batch_edge<S, false, false><<<ne, EDGE_BLOCK, 0, s>>>(L.mem, L.edge_begin, L.nm, L.t, epi);
         }
     }
-    k_batch_tail<S><<<(unsigned)L.nm, 256, 0, s>>>(L.mem, L.nm, L.t);
+    if (L.q_blocks > 0)
+        k_batch_qbb<S><<<(unsigned)L.q_blocks, EDGE_BLOCK, 0, s>>>(L.mem, L.q_begin, L.nm, L.t, odd ? 0 : 1);
+    if (L.out_chunks > 0)
+        k_batch_outflow<S><<<dim3((unsigned)L.nm, (unsigned)L.out_chunks), 256, 0, s>>>(L.mem, L.nm, 1, odd ? 0 : 1);
+    k_batch_tick<<<1, 32, 0, s>>>(L.t);
 }
 
 template <class S>
@@ -468,7 +607,15 @@ void launch_step_t(const StepArgs &a, bool odd, bool epi, bool plain, int block_
             else     k_step_edge<S, false, false><<<eg, EDGE_BLOCK, 0, s>>>(a);
         }
     }
-    launch_outflow<S>(a, s);
+    launch_qbb<S>(a, !odd, s);
+    launch_outflow<S>(a, true, !odd, s);
+}
+
+// Record-only outflow pass for the state before a step of parity `odd`.
+template <class S>
+void launch_outflow_record_t(const StepArgs &a, bool odd, cudaStream_t s)
+{
+    launch_outflow<S>(a, false, odd, s);
 }
 
 }  // namespace lbm

@@ -14,4 +14,9 @@ void launch_batch_step_bf16(const BatchLaunch &L, bool odd, bool epi, bool plain
 {
     launch_batch_step_t<__nv_bfloat16>(L, odd, epi, plain, s);
 }
+
+void launch_outflow_record_bf16(const StepArgs &a, bool odd, cudaStream_t s)
+{
+    launch_outflow_record_t<__nv_bfloat16>(a, odd, s);
+}
 }  // namespace lbm

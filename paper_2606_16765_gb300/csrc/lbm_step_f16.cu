@@ -14,4 +14,9 @@ void launch_batch_step_f16(const BatchLaunch &L, bool odd, bool epi, bool plain,
 {
     launch_batch_step_t<__half>(L, odd, epi, plain, s);
 }
+
+void launch_outflow_record_f16(const StepArgs &a, bool odd, cudaStream_t s)
+{
+    launch_outflow_record_t<__half>(a, odd, s);
+}
 }  // namespace lbm

@@ -14,4 +14,9 @@ void launch_batch_step_f16c(const BatchLaunch &L, bool odd, bool epi, bool plain
 {
     launch_batch_step_t<F16C>(L, odd, epi, plain, s);
 }
+
+void launch_outflow_record_f16c(const StepArgs &a, bool odd, cudaStream_t s)
+{
+    launch_outflow_record_t<F16C>(a, odd, s);
+}
 }  // namespace lbm

@@ -14,4 +14,9 @@ void launch_batch_step_f32(const BatchLaunch &L, bool odd, bool epi, bool plain,
 {
     launch_batch_step_t<float>(L, odd, epi, plain, s);
 }
+
+void launch_outflow_record_f32(const StepArgs &a, bool odd, cudaStream_t s)
+{
+    launch_outflow_record_t<float>(a, odd, s);
+}
 }  // namespace lbm

@@ -14,4 +14,9 @@ void launch_batch_step_f64(const BatchLaunch &L, bool odd, bool epi, bool plain,
 {
     launch_batch_step_t<double>(L, odd, epi, plain, s);
 }
+
+void launch_outflow_record_f64(const StepArgs &a, bool odd, cudaStream_t s)
+{
+    launch_outflow_record_t<double>(a, odd, s);
+}
 }  // namespace lbm

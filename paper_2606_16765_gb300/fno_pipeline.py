@@ -8,8 +8,11 @@ learning-rate schedule, 50 epochs), run on the 128x64x64 grid the surrogate
 works on:
 
   1. seeded composite obstacles (5 primitive kinds, angle of attack in
-     [-30, 30] deg), Re log-uniform at the lattice viscosities of the paper's
-     Re 1e3 - 1e4 runs (Re 125 - 1250 on the 64-cell channel height);
+     [-30, 30] deg), Re log-uniform in a range on the 64-cell channel height:
+     by default [125, 1250], the lattice viscosities of the paper's Re 1e3 -
+     1e4 runs on a 512-cell height (whose fields the paper downsamples to
+     this grid); --re-range 1000,10000 puts the paper's Re on the coarse grid
+     itself (lattice viscosity down to 3.2e-4);
   2. all geometries stepped together by the batched LBM driver to 15
      flow-through times, the time average taken over flow-through times 5-15;
   3. inputs (mask, log10 Re - 2, cos and sin of the angle), targets (u, v, w,
@@ -34,25 +37,26 @@ GRID = (128, 64, 64)          # (nx, ny, nz)
 U_IN = 0.05
 
 
-# Re range on the 64-cell channel height: the lattice viscosities of the
-# paper's runs (Re 1e3 - 1e4 on a 512-cell height, nu = U 512 / Re) give
-# Re = 125 - 1250 on 64 cells.
+# Default Re range on the 64-cell channel height: the lattice viscosities
+# nu = U 512 / Re of the paper's Re 1e3 - 1e4 runs on a 512-cell height.
 RE_RANGE = (125.0, 1250.0)
 
 
-def sample(seed, grid=GRID):
+def sample(seed, grid=GRID, re_range=RE_RANGE):
     """Geometry and Re of one sample (deterministic in seed)."""
     rng = np.random.Generator(np.random.PCG64(70_000 + seed))
-    re = float(math.exp(rng.uniform(math.log(RE_RANGE[0]), math.log(RE_RANGE[1]))))
+    re = float(math.exp(rng.uniform(math.log(re_range[0]), math.log(re_range[1]))))
     obs = I.composite(seed, grid, size_range=(6.0, 12.0), jitter=2.0)
-    return dict(seed=seed, grid=tuple(grid), mask=obs.mask(), re=re, angle=obs.angle_deg)
+    return dict(seed=seed, grid=tuple(grid), mask=obs.mask(), re=re, angle=obs.angle_deg, prims=obs.prims)
 
 
-def features(s):
-    """FNO input channels [4, nz, ny, nx]: mask, log10 Re - 2, cos a, sin a."""
+def features(s, re_range=RE_RANGE):
+    """FNO input channels [4, nz, ny, nx]: mask, log10 Re centred on the
+    range (log10 of Re over the geometric mean of its ends), cos a, sin a."""
     m = s["mask"].astype(np.float32)
     a = math.radians(s["angle"])
-    return np.stack([m, np.full_like(m, math.log10(s["re"]) - 2.0), np.full_like(m, math.cos(a)),
+    re_c = 0.5 * (math.log10(re_range[0]) + math.log10(re_range[1]))
+    return np.stack([m, np.full_like(m, math.log10(s["re"]) - re_c), np.full_like(m, math.cos(a)),
                      np.full_like(m, math.sin(a))])
 
 
@@ -70,6 +74,8 @@ def simulate(samples, storage="f16c", n_ft=15.0, ft_start=5.0, chunk_ft=1.0, log
                     l_ref=float(s["grid"][1]), mean_start=mean_start, mean_end=t_end, mean_every=10)
                for s in samples]
     b = Batch(members)
+    for g, s in enumerate(samples):                 # interpolated bounce-back on the obstacle links
+        b.set_wall_distances(g, I.link_wall_distances(s["grid"], s["prims"], s["mask"]))
     b.set_end([t_end] * len(samples))
     unstable = set()
     step = int(math.ceil(chunk_ft * steps_ft / 10.0)) * 10
@@ -111,6 +117,7 @@ def time_lbm_to_end(s, storage="f16c", n_ft=15.0, ft_start=5.0):
     mean_start = int(round(ft_start * nx / U_IN / 10.0)) * 10
     b = Batch([dict(grid=s["grid"], mask=s["mask"], storage=storage, re=s["re"], u_in=U_IN,
                     l_ref=float(s["grid"][1]), mean_start=mean_start, mean_end=t_end, mean_every=10)])
+    b.set_wall_distances(0, I.link_wall_distances(s["grid"], s["prims"], s["mask"]))
     b.set_end([t_end])
     b.run(10)                                      # capture and warm up
     b.sync()
@@ -186,15 +193,15 @@ def metrics(pred, true, cells):
 
 
 def run(n_train=512, n_test=64, epochs=50, batch=8, lr=1e-3, storage="f16c", n_ft=15.0, sim_batch=64,
-        out=None, log=print):
+        out=None, log=print, full_region=True, re_range=RE_RANGE):
     import torch
     from .fno import FNO
 
     dev = torch.device("cuda")
     report = {"grid": list(GRID), "n_train": n_train, "n_test": n_test, "epochs": epochs, "batch": batch,
-              "lr": lr, "lbm_storage": storage, "flow_throughs": n_ft}
-    train_s = [sample(1000 + k) for k in range(n_train)]
-    test_s = [sample(2000 + k) for k in range(n_test)]
+              "lr": lr, "lbm_storage": storage, "flow_throughs": n_ft, "re_range": list(re_range)}
+    train_s = [sample(1000 + k, re_range=re_range) for k in range(n_train)]
+    test_s = [sample(2000 + k, re_range=re_range) for k in range(n_test)]
     # 1-2: data from the LBM
     t0 = time.time()
     Y, bad = [], []
@@ -209,7 +216,7 @@ def run(n_train=512, n_test=64, epochs=50, batch=8, lr=1e-3, storage="f16c", n_f
     report["unstable_samples"] = bad
     keep_tr = [k for k in range(n_train) if k not in bad]
     keep_te = [k for k in range(n_test) if n_train + k not in bad]
-    X = np.stack([features(s) for s in allS])
+    X = np.stack([features(s, re_range) for s in allS])
     masks = np.stack([s["mask"] for s in allS])
     # 3: scaling on the training set (fluid cells)
     lo = np.zeros(4, np.float32)
@@ -222,51 +229,55 @@ def run(n_train=512, n_test=64, epochs=50, batch=8, lr=1e-3, storage="f16c", n_f
     Wt = np.stack([region_weights(m) for m in masks])
     Xd = torch.from_numpy(X).to(dev)
     Yd = torch.from_numpy(Yn.astype(np.float32)).to(dev)
-    Wd = torch.from_numpy(Wt).to(dev)
-    # 4: training
-    net = FNO(nx=GRID[0], ny=GRID[1], nz=GRID[2], max_batch=batch)
-    rng = np.random.Generator(np.random.PCG64(0))
-    steps_ep = int(math.ceil(len(keep_tr) / batch))
-    total = epochs * steps_ep
-    losses = []
-    t1 = time.time()
-    st = torch.cuda.current_stream()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(st)
-    step = 0
-    for ep in range(epochs):
-        order = rng.permutation(keep_tr)
-        for j in range(steps_ep):
-            idx = order[j * batch:(j + 1) * batch]
-            if len(idx) < batch:
-                idx = np.concatenate([idx, order[:batch - len(idx)]])
-            it = torch.as_tensor(idx, device=dev)
-            x, y, w = Xd.index_select(0, it).contiguous(), Yd.index_select(0, it).contiguous(), \
-                Wd.index_select(0, it).contiguous()
-            cur = lr * 0.5 * (1.0 + math.cos(math.pi * step / total))
-            L = net.train_step(x, y, w, cur)
-            step += 1
-        losses.append(L)
-        if ep % 10 == 0 or ep == epochs - 1:
-            log(f"  epoch {ep}: loss {L:.3e}")
-    e1.record(st)
-    torch.cuda.synchronize()
-    report["train_seconds"] = e0.elapsed_time(e1) / 1e3
-    report["train_samples_per_s"] = total * batch / report["train_seconds"]
-    report["loss_per_epoch"] = losses
-    # evaluation on the held-out seeds
+    # 4: training (the paper's masked loss on the inner region), evaluation
     test_idx = [n_train + k for k in keep_te]
-    Xt = Xd[test_idx].contiguous()
-    pred_n = torch.zeros((len(test_idx), 4) + masks.shape[1:], device=dev)
-    net.forward(Xt, pred_n)
-    torch.cuda.synchronize()
-    pred_n = pred_n.cpu().numpy()
-    pred = pred_n * (hi - lo)[None, :, None, None, None] + lo[None, :, None, None, None]
-    true = Y[test_idx]
     tm = masks[test_idx]
+    true = Y[test_idx]
     inner = Wt[test_idx] > 0                        # fluid cells of the loss region
+    fluid = tm == 0
+
+    def train(weights, tag):
+        Wd = torch.from_numpy(weights).to(dev)
+        net = FNO(nx=GRID[0], ny=GRID[1], nz=GRID[2], max_batch=batch)
+        rng = np.random.Generator(np.random.PCG64(0))
+        steps_ep = int(math.ceil(len(keep_tr) / batch))
+        total = epochs * steps_ep
+        losses = []
+        st = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        step = 0
+        for ep in range(epochs):
+            order = rng.permutation(keep_tr)
+            for j in range(steps_ep):
+                idx = order[j * batch:(j + 1) * batch]
+                if len(idx) < batch:
+                    idx = np.concatenate([idx, order[:batch - len(idx)]])
+                it = torch.as_tensor(idx, device=dev)
+                x, y, w = Xd.index_select(0, it).contiguous(), Yd.index_select(0, it).contiguous(), \
+                    Wd.index_select(0, it).contiguous()
+                cur = lr * 0.5 * (1.0 + math.cos(math.pi * step / total))
+                L = net.train_step(x, y, w, cur)
+                step += 1
+            losses.append(L)
+            if ep % 10 == 0 or ep == epochs - 1:
+                log(f"  [{tag}] epoch {ep}: loss {L:.3e}")
+        e1.record(st)
+        torch.cuda.synchronize()
+        secs = e0.elapsed_time(e1) / 1e3
+        pred_n = torch.zeros((len(test_idx), 4) + masks.shape[1:], device=dev)
+        net.forward(Xd[test_idx].contiguous(), pred_n)
+        torch.cuda.synchronize()
+        pred_n = pred_n.cpu().numpy()
+        return net, pred_n, losses, secs, total
+
+    net, pred_n, losses, secs, total = train(Wt, "inner-region loss")
+    report["train_seconds"] = secs
+    report["train_samples_per_s"] = total * batch / secs
+    report["loss_per_epoch"] = losses
+    pred = pred_n * (hi - lo)[None, :, None, None, None] + lo[None, :, None, None, None]
     rel, per = metrics(pred, true, inner)
-    rel_all, _ = metrics(pred, true, tm == 0)
+    rel_all, _ = metrics(pred, true, fluid)
     report["rel_l2_uvw"] = {"median": float(np.median(rel)), "mean": float(np.mean(rel)), "max": float(np.max(rel)),
                             "cells": "fluid cells of the inner loss region"}
     report["rel_l2_per_field_median"] = {k: float(np.median(v)) for k, v in per.items()}
@@ -285,11 +296,26 @@ def run(n_train=512, n_test=64, epochs=50, batch=8, lr=1e-3, storage="f16c", n_f
     # the method without the network: the training-set mean field
     mean_field = Y[keep_tr].mean(axis=0)
     rel0, _ = metrics(np.broadcast_to(mean_field, true.shape), true, inner)
-    rel0a, _ = metrics(np.broadcast_to(mean_field, true.shape), true, tm == 0)
+    rel0a, _ = metrics(np.broadcast_to(mean_field, true.shape), true, fluid)
     report["baseline_train_mean_rel_l2_uvw"] = {"median": float(np.median(rel0)), "mean": float(np.mean(rel0)),
                                                 "all_fluid_median": float(np.median(rel0a))}
+    if full_region:
+        # the same network trained with the loss on every fluid cell
+        net2, pred2_n, losses2, _, _ = train((masks == 0).astype(np.float32), "all-fluid loss")
+        net2.close()
+        pred2 = pred2_n * (hi - lo)[None, :, None, None, None] + lo[None, :, None, None, None]
+        r2, _ = metrics(pred2, true, fluid)
+        r2i, _ = metrics(pred2, true, inner)
+        report["all_fluid_loss_model"] = {"rel_l2_uvw_all_fluid": {"median": float(np.median(r2)),
+                                                                   "mean": float(np.mean(r2))},
+                                          "rel_l2_uvw_inner": {"median": float(np.median(r2i))},
+                                          "final_loss": losses2[-1]}
+    xb_src = Xd[test_idx].contiguous()
     # speed: one FNO prediction against the LBM run it replaces
-    xb = Xt[:batch].contiguous() if len(test_idx) >= batch else Xt.repeat(batch, 1, 1, 1, 1)[:batch].contiguous()
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    xb = xb_src[:batch].contiguous() if len(test_idx) >= batch else \
+        xb_src.repeat(batch, 1, 1, 1, 1)[:batch].contiguous()
     yb = torch.zeros((batch, 4) + masks.shape[1:], device=dev)
     for _ in range(3):
         net.forward(xb, yb)
@@ -309,7 +335,8 @@ def run(n_train=512, n_test=64, epochs=50, batch=8, lr=1e-3, storage="f16c", n_f
     report["speedup_note"] = ("FNO forward of a batch of 8 divided by 8 (inputs resident) vs one held-out "
                               "seed's LBM run alone to the end (CUDA events, graph-replayed batched driver)")
     log(json.dumps({k: report[k] for k in ("rel_l2_uvw", "rel_l2_uvw_all_fluid", "baseline_train_mean_rel_l2_uvw",
-                                            "speedup_median", "fno_seconds_per_sample", "train_samples_per_s")}))
+                                            "all_fluid_loss_model", "speedup_median", "fno_seconds_per_sample",
+                                            "train_samples_per_s") if k in report}))
     if out:
         with open(out, "w") as fp:
             json.dump(report, fp, indent=1)
@@ -324,13 +351,15 @@ def main():
     ap.add_argument("--storage", default="f16c")
     ap.add_argument("--epochs", type=int, default=50)
     ap.add_argument("--time", action="store_true", help="only time forward and training step (random inputs)")
+    ap.add_argument("--re-range", default=None, help="lo,hi Re on the 64-cell channel height")
     args = ap.parse_args()
+    rr = RE_RANGE if args.re_range is None else tuple(float(v) for v in args.re_range.split(","))
     if args.time:
         print(json.dumps(time_fno()))
     elif args.quick:
-        run(n_train=16, n_test=8, epochs=2, n_ft=2.0, storage=args.storage, out=args.out, sim_batch=24)
+        run(n_train=16, n_test=8, epochs=2, n_ft=2.0, storage=args.storage, out=args.out, sim_batch=24, re_range=rr)
     else:
-        run(epochs=args.epochs, storage=args.storage, out=args.out)
+        run(epochs=args.epochs, storage=args.storage, out=args.out, re_range=rr)
 
 
 if __name__ == "__main__":

@@ -38,7 +38,7 @@ class lbm_params(C.Structure):
         ("snap_first", C.c_int64), ("snap_every", C.c_int64), ("snap_count", C.c_int64),
         ("snap_halfres", C.c_int32), ("force_every", C.c_int32),
         ("force_capacity", C.c_int64),
-        ("block_x", C.c_int32), ("block_y", C.c_int32), ("reserved", C.c_int32 * 6),
+        ("block_x", C.c_int32), ("block_y", C.c_int32), ("stats", C.c_int32), ("reserved", C.c_int32 * 5),
     ]
 
 
@@ -89,6 +89,9 @@ def lib():
             "lbm_sync": (C.c_int, [_vp]),
             "lbm_time": (_i64, [_vp]),
             "lbm_read_mean": (C.c_int, [_vp, C.c_int32, C.c_int32, _vp, C.POINTER(_i64)]),
+            "lbm_read_stats": (C.c_int, [_vp, C.c_int32, _vp, C.POINTER(_i64)]),
+            "lbm_set_wall_distances": (C.c_int, [_vp, _i64, _vp, _vp, _vp]),
+            "lbm_batch_set_wall_distances": (C.c_int, [_vp, C.c_int32, _i64, _vp, _vp, _vp]),
             "lbm_read_snapshot": (C.c_int, [_vp, C.c_int32, _vp]),
             "lbm_read_macros": (C.c_int, [_vp, _vp, _vp]),
             "lbm_read_forces": (C.c_int, [_vp, _vp, _i64, C.POINTER(_i64)]),
@@ -190,6 +193,20 @@ def lbm_time(h):
 def lbm_read_mean(h, dst, dtype, halfres):
     s = C.c_int64()
     _check(lib().lbm_read_mean(h, int(dtype), int(halfres), _ptr(dst), C.byref(s)), h)
+    return s.value
+
+
+def lbm_set_wall_distances(h, cell, direction, q):
+    cell = np.ascontiguousarray(cell, dtype=np.int64)
+    direction = np.ascontiguousarray(direction, dtype=np.int8)
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    n = len(cell)
+    _check(lib().lbm_set_wall_distances(h, n, _ptr(cell), _ptr(direction), _ptr(q)), h)
+
+
+def lbm_read_stats(h, dst, dtype):
+    s = C.c_int64()
+    _check(lib().lbm_read_stats(h, int(dtype), _ptr(dst), C.byref(s)), h)
     return s.value
 
 
@@ -379,6 +396,18 @@ class _Lattice:
         s = lbm_read_mean(self.h, out, 1 if dtype == np.float32 else 0, halfres)
         return out, s
 
+    def set_wall_distances(self, links):
+        """Interpolated bounce-back on the listed obstacle links: (cell,
+        direction, q) arrays as returned by inputs.link_wall_distances."""
+        lbm_set_wall_distances(self.h, *links)
+
+    def stats(self, dtype=np.float64):
+        """Velocity covariances [nz, ny, nx, 6] (xx, yy, zz, xy, xz, yz) over
+        the averaging samples, and the sample count."""
+        out = np.zeros(self.shape + (6,), dtype=dtype)
+        s = lbm_read_stats(self.h, out, 1 if dtype == np.float32 else 0)
+        return out, s
+
     def snapshot(self, k):
         shape = tuple((s + 1) // 2 for s in self.shape) if self.p.snap_halfres else self.shape
         out = np.zeros(shape + (4,), dtype=np.float32)
@@ -523,6 +552,16 @@ class Batch:
 
     def set_flowthroughs(self, n_ft):
         lbm_batch_set_flowthroughs(self.h, n_ft)
+
+    def set_wall_distances(self, g, links):
+        """Interpolated bounce-back for member g: (cell, direction, q) arrays
+        as returned by inputs.link_wall_distances."""
+        cell = np.ascontiguousarray(links[0], dtype=np.int64)
+        direction = np.ascontiguousarray(links[1], dtype=np.int8)
+        q = np.ascontiguousarray(links[2], dtype=np.float64)
+        st = lib().lbm_batch_set_wall_distances(self.h, int(g), len(cell), _ptr(cell), _ptr(direction), _ptr(q))
+        if st != 0:
+            raise LBMError(st, "lbm_batch_set_wall_distances failed")
 
     def run(self, n):
         lbm_batch_run(self.h, n)

@@ -96,6 +96,28 @@ def test_sphere_channel_outflow_200_steps(storage):
     assert eu <= TOL_U[storage] and er <= TOL_U[storage]
 
 
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+def test_velocity_statistics_match_oracle(storage):
+    """Reynolds-stress accumulators (FP64 sums of velocity products over the
+    averaging samples) against the oracle's, over the start-up of the sphere
+    channel from a noisy state (large fluctuations)."""
+    d = I.sphere_channel_64()
+    w1 = O.omega_from_re(d["re"], d["u_in"], d["l_ref"])
+    c = K.case(d["grid"], d["mask"], omega1=w1, u_in=d["u_in"], faces=("inlet", "outflow", "wall", "wall"),
+               mean=(20, 120, 2), noise=(31, 2e-3))
+    L = K.run_oracle(c, 120)
+    ref, n = L.stats()
+    s = K.make_solver(c, storage, stats=1)
+    s.step(120)
+    s.sync()
+    st, ns = s.stats()
+    assert ns == n == 50
+    fl = c["mask"] == 0
+    err = np.abs(st - ref)[fl].max() / np.abs(ref[fl]).max()
+    print(f"stats {storage}: max rel err {err:.3e}, max covariance {np.abs(ref[fl]).max():.3e}")
+    assert err <= {"f64": 1e-8, "f32": 1e-4}[storage]
+
+
 def test_outflow_keeps_low_viscosity_channel_stable():
     """An empty 128x64x128 channel at nu = 3.3e-4 (the thinnest member of the
     32-channel batch): with the anti-bounce-back outlet it diverges within
@@ -405,3 +427,61 @@ def test_full_size_channel_sampled_cells(storage):
     s.sync()
     del s
     torch.cuda.empty_cache()
+
+
+# --------------------------------------------------------------------------
+# interpolated bounce-back with wall distances
+# --------------------------------------------------------------------------
+QBB_CASES = {
+    "sphere_outflow": ((37, 13, 11), [I.Primitive("sphere", (9.3, 6.2, 5.1), (6.6,))],
+                       ("inlet", "outflow", "wall", "wall"), 1.8),
+    "sphere_near_periodic_faces": ((20, 12, 10), [I.Primitive("sphere", (10.4, 1.3, 8.6), (7.0,))],
+                                   ("periodic", "periodic", "periodic", "periodic"), 1.6),
+    "torus_thin_gaps": ((30, 14, 12), [I.Primitive("torus", (12.2, 6.7, 5.4), (8.0, 2.2), 20.0)],
+                        ("inlet", "outflow", "wall", "wall"), 1.9),
+}
+
+
+@pytest.mark.parametrize("name", sorted(QBB_CASES))
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+def test_interpolated_bounce_back_matches_oracle(name, storage):
+    from paper_2606_16765_gb300.lbm import Solver
+    g, prims, faces, w1 = QBB_CASES[name]
+    mask = I.voxelize(g, prims)
+    links = I.link_wall_distances(g, prims, mask)
+    assert len(links[0]) > 0
+    u_in = 0.0 if faces[0] == "periodic" else 0.05
+    c = K.case(g, mask, omega1=w1, u_in=u_in, faces=faces, noise=(41, 2e-3))
+    L = K.run_oracle(c, 0)
+    L.set_q(I.dense_wall_distances(g, links))
+    s = K.make_solver(c, storage, force_every=1)
+    s.set_wall_distances(links)
+    fluid = mask == 0
+    for steps in (1, 1, 5, 13):
+        s.step(steps)
+        L.step(steps)
+        err = np.abs(s.pdfs() - L.get_f())[:, fluid].max()
+        assert err <= (1e-14 if storage == "f64" else 2e-7), (name, storage, L.t, err)
+    F, Fr = s.forces(), L.forces()
+    assert F.shape == Fr.shape
+    ferr = np.abs(F - Fr).max() / max(np.abs(Fr).max(), 1e-30)
+    print(f"qbb {name} {storage}: pdf err {err:.2e}, force err {ferr:.2e}")
+    assert ferr <= (1e-12 if storage == "f64" else 1e-5)
+
+
+def test_wall_distance_argument_errors():
+    from paper_2606_16765_gb300.lbm import LBMError, Solver
+    g = (16, 8, 8)
+    prims = [I.Primitive("sphere", (7.3, 3.6, 4.1), (5.0,))]
+    mask = I.voxelize(g, prims)
+    s = Solver(g, mask, storage="f32", omega1=1.5)
+    cell, d, q = I.link_wall_distances(g, prims, mask)
+    with pytest.raises(LBMError):
+        s.set_wall_distances((cell[:1], np.array([13], np.int8), q[:1]))        # rest direction
+    with pytest.raises(LBMError):
+        s.set_wall_distances((cell[:1], d[:1], np.array([1.5])))               # q out of range
+    far = np.array([0], np.int64)                                             # a corner cell far from the sphere
+    with pytest.raises(LBMError):
+        s.set_wall_distances((far, np.array([26], np.int8), np.array([0.5])))
+    s.set_wall_distances((cell, d, q))
+    s.set_wall_distances((np.zeros(0, np.int64), np.zeros(0, np.int8), np.zeros(0)))   # back to halfway
