@@ -70,6 +70,38 @@ def recorded_traffic(kernel, workload):
     return None
 
 
+def recorded_instructions(kernel):
+    """Warp instructions per interior cell of a bulk kernel from a committed
+    ncu summary (profiles/alu.json), if it was taken on the current kernel
+    sources; the count does not depend on the grid size."""
+    path = os.path.join(ROOT, "profiles", "alu.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        recs = json.load(open(path))
+    except Exception:
+        return None
+    src = kernel_source_hash()
+    for r in recs:
+        if r.get("kernel") == kernel and r.get("source_hash") == src:
+            return r.get("warp_instructions_per_cell")
+    return None
+
+
+def alu_roofline(kernel, cells, ms, clocks):
+    """Issue-rate roofline of a bulk kernel: achieved warp instructions per
+    second against 152 SMs x 4 schedulers x 1 warp instruction per clock at
+    the SM clock sampled during the run (the unit counts of GB300)."""
+    ipc = recorded_instructions(kernel)
+    if ipc is None or not clocks:
+        return None
+    achieved = ipc * cells / (ms / 1e3)
+    peak = 152 * 4 * clocks["sm_mhz"] * 1e6
+    return {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "T warp-instructions/s",
+            "frac": achieved / peak, "warp_instructions_per_cell": ipc, "kernel": kernel,
+            "peak_source": "152 SMs x 4 issue slots x sampled SM clock"}
+
+
 # ---------------------------------------------------------------------------
 # clocks sampled during the timed region
 # ---------------------------------------------------------------------------
@@ -458,6 +490,7 @@ def main():
                      "frac": achieved / peak, "traffic": traffic, "peak_source": peak_kind,
                      "kernel": kname, "bytes_per_launch": bytes_launch,
                      "frac_of_nominal_8000": achieved / NOMINAL_HBM_GBS},
+        "alu_roofline": alu_roofline(kname, info.interior_cells, bulk_ms, res["clocks"]),
         "kernels": {"bulk": per_kind, "edge_ms_per_launch": edge_ms},
         "gpu_launches": int(res["launches"]),
         "clocks": res["clocks"],
@@ -473,6 +506,8 @@ def main():
                 "ms_per_step": r2["ms"] / K,
                 "interior_kernel_gbs": b2 * r2["info"].interior_cells / (t2 / 1e3) / 1e9,
                 "interior_kernel_frac": b2 * r2["info"].interior_cells / (t2 / 1e3) / 1e9 / peak,
+                "alu_roofline": alu_roofline(f"k_step_bulk<{extra},odd={bool(k2 & 1)},epi=False>",
+                                             r2["info"].interior_cells, t2, r2["clocks"]),
                 "clocks": r2["clocks"]}
         if not args.no_batch:
             line["batch"] = run_batch(args.steps, 20)

@@ -6,10 +6,14 @@
 // Kernels:
 //   k_pw_fwd_*   pointwise layers (lift, W path, projection) with fused bias,
 //                spectral-branch add and GELU; pre-activations kept for backward
+//   k_proj_fused inference projection Q2 GELU(Q1 v) without storing the
+//                hidden activations
 //   k_pw_bwd_*   input gradients of pointwise layers with fused GELU'
-//   k_outer      weight/bias gradients sum_{b,cell} gout x
+//   k_outer      weight/bias gradients sum_{b,cell} gout x (k_outer_async:
+//                cp.async double-buffered tiles)
 //   k_dft*       truncated DFT in three separable stages (x, y, z) and the
-//                inverse (z, y, x), FP32 with twiddle tables in shared memory
+//                inverse (z, y, x), FP32 with twiddle tables in shared memory;
+//                the real x stages fold samples x and nx - x
 //   k_contract_tc  per-mode complex channel mixing on tensor cores
 //                (mma.sync m16n8k16 BF16 operands, FP32 accumulation); complex
 //                numbers enter as real 2x2 blocks, the batch is the n8 axis
@@ -192,6 +196,60 @@ __global__ void __launch_bounds__(TPB) k_pw_fwd_in2(const TI *x, int co, const f
                 st2(y + off, act ? gelu(a0) : a0, act ? gelu(a1) : a1);
             }
         }
+    }
+}
+
+// Inference projection y = Q2 GELU(Q1 v + b1) + b2 in one pass (the hidden
+// activations are never stored): CI inputs and co <= 8 outputs in registers,
+// the H hidden units streamed, two adjacent cells per thread.  Shared
+// memory: Q1 [H][CI], b1 [H], Q2 transposed to [H][8] (zero padded).
+template <class TI, int CI>
+__global__ void __launch_bounds__(TPB) k_proj_fused(const TI *v, int H, int co, const float *W1, const float *b1,
+                                                    const float *W2, const float *b2, float *y, int64_t N, int B)
+{
+    extern __shared__ float4 smv[];
+    float *s1 = reinterpret_cast<float *>(smv);
+    float *sb1 = s1 + H * CI;
+    float *s2 = sb1 + ((H + 3) & ~3);
+    for (int k = threadIdx.x; k < H * CI; k += blockDim.x) s1[k] = W1[k];
+    for (int k = threadIdx.x; k < H; k += blockDim.x) sb1[k] = b1[k];
+    for (int k = threadIdx.x; k < H * 8; k += blockDim.x) {
+        const int hh = k / 8, o = k % 8;
+        s2[k] = o < co ? W2[o * H + hh] : 0.f;
+    }
+    __syncthreads();
+    const int64_t half = N / 2;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < (int64_t)B * half;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = idx / half, n = 2 * (idx - b * half);
+        float2 xv[CI];
+#pragma unroll
+        for (int i = 0; i < CI; ++i) xv[i] = ld2(v + (b * CI + i) * N + n);
+        float2 acc[8];
+#pragma unroll
+        for (int o = 0; o < 8; ++o) acc[o] = o < co ? make_float2(b2[o], b2[o]) : make_float2(0.f, 0.f);
+        for (int hh = 0; hh < H; ++hh) {
+            float a0 = sb1[hh], a1 = a0;
+            const float4 *w4 = reinterpret_cast<const float4 *>(s1 + hh * CI);
+#pragma unroll
+            for (int q = 0; q < CI / 4; ++q) {
+                const float4 w = w4[q];
+                a0 += w.x * xv[4 * q].x + w.y * xv[4 * q + 1].x + w.z * xv[4 * q + 2].x + w.w * xv[4 * q + 3].x;
+                a1 += w.x * xv[4 * q].y + w.y * xv[4 * q + 1].y + w.z * xv[4 * q + 2].y + w.w * xv[4 * q + 3].y;
+            }
+            const float g0 = gelu(a0), g1 = gelu(a1);
+            const float4 wa = reinterpret_cast<const float4 *>(s2)[2 * hh];
+            const float4 wb = reinterpret_cast<const float4 *>(s2)[2 * hh + 1];
+            const float w2[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
+#pragma unroll
+            for (int o = 0; o < 8; ++o) {
+                acc[o].x += w2[o] * g0;
+                acc[o].y += w2[o] * g1;
+            }
+        }
+#pragma unroll
+        for (int o = 0; o < 8; ++o)
+            if (o < co) st2(y + (b * co + o) * N + n, acc[o].x, acc[o].y);
     }
 }
 
@@ -499,8 +557,143 @@ __global__ void __launch_bounds__(TPB) k_outer(const float *g, int co, const TX 
     }
 }
 
+// The same reduction when tiles never straddle a batch element (N a multiple
+// of OUTER_TILE): tiles are copied into shared memory by cp.async, two
+// buffers deep, so the copy of tile t+1 runs while tile t is reduced.  The
+// inputs stay in their storage type in shared memory (BF16 rows 72 elements
+// apart: 8-byte reads of eight consecutive rows hit distinct banks).
+template <class TX> struct OuterX;
+template <> struct OuterX<float> {
+    static constexpr int LD = OUTER_TILE + 4;
+    static __device__ __forceinline__ float4 ld(const float *p) { return *reinterpret_cast<const float4 *>(p); }
+};
+template <> struct OuterX<__nv_bfloat16> {
+    static constexpr int LD = OUTER_TILE + 8;
+    static __device__ __forceinline__ float4 ld(const __nv_bfloat16 *p) { return ld4(p); }
+};
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int NG> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(NG) : "memory"); }
+
+template <class TX>
+__host__ __device__ constexpr size_t outer_buf_bytes(int cop, int cip)
+{
+    return sizeof(float) * (size_t)cop * OUTER_LD + sizeof(TX) * (size_t)cip * OuterX<TX>::LD;
+}
+
+template <class TX, int UPT>
+__global__ void __launch_bounds__(TPB) k_outer_async(const float *g, int co, const TX *x, int ci, float *gW, float *gb,
+                                                     int64_t N, int B, int groups)
+{
+    using XR = OuterX<TX>;
+    extern __shared__ float4 smv[];
+    const int cop = (co + 3) & ~3, cip = ((ci + 31) / 32) * 32;
+    const int nog = cop / 4, units = nog * (cip / 32) * 8;
+    const int qpg = (OUTER_TILE / 4) / groups;
+    const size_t buf = outer_buf_bytes<TX>(cop, cip);
+    char *base = reinterpret_cast<char *>(smv);
+    for (size_t k = threadIdx.x; k < 2 * buf / 16; k += TPB) smv[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    __syncthreads();                                        // padding rows stay zero
+    float acc[UPT][16], bacc[UPT][4];
+#pragma unroll
+    for (int u = 0; u < UPT; ++u) {
+#pragma unroll
+        for (int k = 0; k < 16; ++k) acc[u][k] = 0.f;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) bacc[u][k] = 0.f;
+    }
+    const int64_t total = (int64_t)B * N;
+    const int64_t c0 = (int64_t)blockIdx.x * OUTER_CHUNK;
+    const int64_t c1 = c0 + OUTER_CHUNK < total ? c0 + OUTER_CHUNK : total;
+    const int ntile = (int)((c1 - c0) / OUTER_TILE);
+    constexpr int GCH = OUTER_TILE / 4;                     // 16-byte pieces of a gradient row
+    constexpr int PER = 16 / (int)sizeof(TX);               // input elements per 16 bytes
+    constexpr int XCH = OUTER_TILE / PER;
+    auto issue = [&](int t, int bsel) {
+        const int64_t t0 = c0 + (int64_t)t * OUTER_TILE;
+        const int64_t bb = t0 / N, n0 = t0 - bb * N;
+        float *sg = reinterpret_cast<float *>(base + bsel * buf);
+        TX *sx = reinterpret_cast<TX *>(base + bsel * buf + sizeof(float) * (size_t)cop * OUTER_LD);
+        const int ng = co * GCH, nt = ng + ci * XCH;
+        for (int k = threadIdx.x; k < nt; k += TPB) {
+            if (k < ng) {
+                const int ch = k / GCH, q = k % GCH;
+                cp_async16(sg + ch * OUTER_LD + 4 * q, g + (bb * co + ch) * N + n0 + 4 * q);
+            } else {
+                const int kk = k - ng, ch = kk / XCH, q = kk % XCH;
+                cp_async16(sx + ch * XR::LD + PER * q, x + (bb * ci + ch) * N + n0 + PER * q);
+            }
+        }
+        cp_async_commit();
+    };
+    if (ntile > 0) issue(0, 0);
+    for (int t = 0; t < ntile; ++t) {
+        if (t + 1 < ntile) {
+            issue(t + 1, (t + 1) & 1);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncthreads();
+        const float *sg = reinterpret_cast<const float *>(base + (t & 1) * buf);
+        const TX *sx = reinterpret_cast<const TX *>(base + (t & 1) * buf + sizeof(float) * (size_t)cop * OUTER_LD);
+#pragma unroll
+        for (int u = 0; u < UPT; ++u) {
+            const int tt = threadIdx.x + u * TPB;
+            if (tt >= units * groups) break;
+            const int unit = tt % units, grp = tt / units;
+            const int l8 = unit & 7, rest = unit >> 3;
+            const int o0 = (rest % nog) * 4, i0 = (rest / nog) * 32 + l8;
+            const bool bias = l8 == 0 && rest < nog;
+            for (int q = grp * qpg; q < (grp + 1) * qpg; ++q) {
+                float4 gv[4], xv[4];
+#pragma unroll
+                for (int a = 0; a < 4; ++a) gv[a] = *reinterpret_cast<const float4 *>(sg + (o0 + a) * OUTER_LD + 4 * q);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) xv[c] = XR::ld(sx + (i0 + 8 * c) * XR::LD + 4 * q);
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c)
+                        acc[u][4 * a + c] += gv[a].x * xv[c].x + gv[a].y * xv[c].y + gv[a].z * xv[c].z + gv[a].w * xv[c].w;
+                if (bias) {
+#pragma unroll
+                    for (int a = 0; a < 4; ++a) bacc[u][a] += gv[a].x + gv[a].y + gv[a].z + gv[a].w;
+                }
+            }
+        }
+        __syncthreads();                                    // the buffer is refilled two tiles on
+    }
+#pragma unroll
+    for (int u = 0; u < UPT; ++u) {
+        const int tt = threadIdx.x + u * TPB;
+        if (tt >= units * groups) break;
+        const int unit = tt % units;
+        const int l8 = unit & 7, rest = unit >> 3;
+        const int o0 = (rest % nog) * 4, i0 = (rest / nog) * 32 + l8;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            if (o0 + a >= co) continue;
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                if (i0 + 8 * c < ci) atomicAdd(&gW[(o0 + a) * ci + i0 + 8 * c], acc[u][4 * a + c]);
+            if (l8 == 0 && rest < nog) atomicAdd(&gb[o0 + a], bacc[u][a]);
+        }
+    }
+}
+
 int outer_units(int co, int ci) { return ((co + 3) / 4) * ((ci + 31) / 32) * 8; }
-size_t smem_outer(int co, int ci) { return sizeof(float) * (size_t)(((co + 3) & ~3) + ((ci + 31) / 32) * 32) * OUTER_LD; }
+size_t smem_outer(int co, int ci)
+{
+    const int cop = (co + 3) & ~3, cip = ((ci + 31) / 32) * 32;
+    return std::max(sizeof(float) * (size_t)(cop + cip) * OUTER_LD,
+                    2 * std::max(outer_buf_bytes<float>(cop, cip), outer_buf_bytes<__nv_bfloat16>(cop, cip)));
+}
 
 // ---------------------------------------------------------------------------
 // truncated DFT: forward stages x -> y -> z, inverse stages z -> y -> x.
@@ -515,34 +708,59 @@ struct Dims {
 constexpr int DFT_RT = 8;                            // rows per warp in the x stages
 constexpr int DFT_ROWS = DFT_RT * (TPB / 32);        // rows per block pass in the x stages
 
-// rows [R][nx] (real) -> A [R][Kx] (complex).  A block stages DFT_ROWS rows
-// in shared memory (padded to nxp, a multiple of 4); lane j of a warp owns
-// mode j (chunks of 32) for the warp's DFT_RT rows, reading the rows four
-// samples at a time (float4 broadcast) against twiddles tw[x][j] held in
-// shared memory (consecutive in j: conflict-free).
+// rows [R][nx] (real) -> A [R][Kx] (complex), folded: exp(-i t (nx - x)) is
+// the conjugate of exp(-i t x), so with S_p = v[p] + v[nx - p] and
+// D_p = v[p] - v[nx - p] (p = 1 .. (nx-1)/2), S_0 = v[0], D_0 = 0 and, for
+// even nx, S_{nx/2} = v[nx/2], D_{nx/2} = 0:
+//     A_j = sum_{p <= nx/2} S_p cos_pj + i sum_p D_p sin_pj,
+// half the multiply-adds of the plain sum.  A block stages DFT_ROWS rows of
+// (S, D) in shared memory (np_ = nx/2 + 1 entries, padded to a multiple of
+// 4); lane j of a warp owns mode j (chunks of 32) for the warp's DFT_RT rows,
+// reading S and D four entries at a time (float4 broadcast) against the
+// twiddles tw[p][j] (consecutive in j: conflict-free).
 template <class TI>
 __global__ void __launch_bounds__(TPB) k_dftx_fwd(const TI *x, float2 *A, const float2 *twx, Dims d, int64_t R)
 {
     extern __shared__ float4 smv[];
-    const int nxp = (d.nx + 3) & ~3, nq = nxp / 4;
-    float2 *tw = reinterpret_cast<float2 *>(smv);                           // [nxp][Kx]
-    float *rows = reinterpret_cast<float *>(tw + (size_t)nxp * d.Kx);      // [DFT_ROWS][nxp]
-    for (int k = threadIdx.x; k < nxp * d.Kx; k += blockDim.x)
-        tw[k] = k < d.nx * d.Kx ? twx[k] : make_float2(0.f, 0.f);
+    const int h = d.nx / 2, np_ = h + 1, npp = (np_ + 3) & ~3, nq = npp / 4;
+    const int nxp = (d.nx + 3) & ~3;
+    float2 *tw = reinterpret_cast<float2 *>(smv);                           // [npp][Kx]
+    float *sd = reinterpret_cast<float *>(tw + (size_t)npp * d.Kx);        // [DFT_ROWS][2][npp]
+    float *raw = sd + (size_t)DFT_ROWS * 2 * npp;                          // [DFT_ROWS][nxp]
+    for (int k = threadIdx.x; k < npp * d.Kx; k += blockDim.x)
+        tw[k] = k < np_ * d.Kx ? twx[k] : make_float2(0.f, 0.f);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int64_t r0 = (int64_t)blockIdx.x * DFT_ROWS; r0 < R; r0 += (int64_t)gridDim.x * DFT_ROWS) {
         const int nr = (int)(R - r0 < DFT_ROWS ? R - r0 : DFT_ROWS);
         __syncthreads();
         if (nxp == d.nx) {                                  // rows are one contiguous run
-            stage4(rows, x + r0 * d.nx, nr * d.nx, DFT_ROWS * nxp);
+            stage4(raw, x + r0 * d.nx, nr * d.nx, DFT_ROWS * nxp);
         } else {
             for (int k = threadIdx.x; k < DFT_ROWS * nxp; k += blockDim.x) {
                 const int lr = k / nxp, xx = k - lr * nxp;
-                rows[k] = (lr < nr && xx < d.nx) ? ldf(x + (r0 + lr) * d.nx + xx) : 0.f;
+                raw[k] = (lr < nr && xx < d.nx) ? ldf(x + (r0 + lr) * d.nx + xx) : 0.f;
             }
         }
         __syncthreads();
-        const float4 *rw = reinterpret_cast<const float4 *>(rows) + (size_t)warp * DFT_RT * nq;
+        for (int k = threadIdx.x; k < DFT_ROWS * npp; k += blockDim.x) {
+            const int lr = k / npp, pp = k - lr * npp;
+            float sv = 0.f, dv = 0.f;
+            if (pp < np_) {
+                const float *row = raw + (size_t)lr * nxp;
+                const float a = row[pp];
+                if (pp > 0 && pp < d.nx - pp) {
+                    const float b = row[d.nx - pp];
+                    sv = a + b;
+                    dv = a - b;
+                } else {
+                    sv = a;                              // p = 0, or the middle sample of an even row
+                }
+            }
+            sd[(2 * lr) * npp + pp] = sv;
+            sd[(2 * lr + 1) * npp + pp] = dv;
+        }
+        __syncthreads();
+        const float4 *rw = reinterpret_cast<const float4 *>(sd) + (size_t)warp * DFT_RT * 2 * nq;
         for (int j0 = 0; j0 < d.Kx; j0 += 32) {
             const int j = j0 + lane;
             const int jj = j < d.Kx ? j : d.Kx - 1;
@@ -554,9 +772,9 @@ __global__ void __launch_bounds__(TPB) k_dftx_fwd(const TI *x, float2 *A, const 
                 const float2 t2 = tw[(4 * q + 2) * d.Kx + jj], t3 = tw[(4 * q + 3) * d.Kx + jj];
 #pragma unroll
                 for (int r = 0; r < DFT_RT; ++r) {
-                    const float4 v = rw[r * nq + q];
-                    acc[r].x += v.x * t0.x + v.y * t1.x + v.z * t2.x + v.w * t3.x;
-                    acc[r].y += v.x * t0.y + v.y * t1.y + v.z * t2.y + v.w * t3.y;
+                    const float4 sv = rw[(2 * r) * nq + q], dv = rw[(2 * r + 1) * nq + q];
+                    acc[r].x += sv.x * t0.x + sv.y * t1.x + sv.z * t2.x + sv.w * t3.x;
+                    acc[r].y += dv.x * t0.y + dv.y * t1.y + dv.z * t2.y + dv.w * t3.y;
                 }
             }
             if (j < d.Kx) {
@@ -739,21 +957,26 @@ __global__ void __launch_bounds__(TPB) k_dfty_inv(const float2 *Ht, float2 *It, 
 }
 
 // I [R][Kx] -> out [R][nx] = Re sum_jx I exp(+i 2 pi kx x / nx); mode 0: store,
-// mode 1: add to out; then, if pre is given, multiply by gelu'(pre).  The
-// twiddles are transposed into twT[j][x] (x padded to a multiple of 128) so
-// that lane l reads x = l + 32u (u < 4) conflict-free; a warp takes DFT_RT
+// mode 1: add to out; then, if pre is given, multiply by gelu'(pre).
+// Folded: with (c, s) the twiddle of sample p, a_p = sum_j Re(I_j) c_pj and
+// b_p = sum_j Im(I_j) s_pj give out[p] = a_p + b_p and out[nx - p] =
+// a_p - b_p (p = 1 .. (nx-1)/2), out[0] = a_0; the middle sample of an even
+// row, out[nx/2] = sum_j Re(I_j) (-1)^k_j, is a warp reduction.  The
+// twiddles are transposed into twT[j][p] (p padded to a multiple of 64) so
+// that lane l reads p = l + 32u (u < 2) conflict-free; a warp takes DFT_RT
 // rows and reads their coefficients two modes at a time (float4 broadcast).
 template <class TP>
 __global__ void __launch_bounds__(TPB) k_dftx_inv(const float2 *It, float *out, const float2 *twx, Dims d, int64_t R,
                                                   int accumulate, const TP *pre)
 {
     extern __shared__ float4 smv[];
-    const int ldx = (d.nx + 127) & ~127, kh = d.Kx / 2;
-    float2 *tw = reinterpret_cast<float2 *>(smv);                           // [Kx][ldx]
-    float4 *rows = reinterpret_cast<float4 *>(tw + (size_t)d.Kx * ldx);    // [DFT_ROWS][Kx/2]
-    for (int k = threadIdx.x; k < d.Kx * ldx; k += blockDim.x) {
-        const int j = k / ldx, xx = k - j * ldx;
-        tw[k] = xx < d.nx ? twx[xx * d.Kx + j] : make_float2(0.f, 0.f);
+    const int ns = (d.nx + 1) / 2, ldp = (ns + 63) & ~63, kh = d.Kx / 2;
+    const bool mid = (d.nx & 1) == 0;
+    float2 *tw = reinterpret_cast<float2 *>(smv);                           // [Kx][ldp]
+    float4 *rows = reinterpret_cast<float4 *>(tw + (size_t)d.Kx * ldp);    // [DFT_ROWS][Kx/2]
+    for (int k = threadIdx.x; k < d.Kx * ldp; k += blockDim.x) {
+        const int j = k / ldp, pp = k - j * ldp;
+        tw[k] = pp < ns ? twx[pp * d.Kx + j] : make_float2(0.f, 0.f);
     }
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int64_t r0 = (int64_t)blockIdx.x * DFT_ROWS; r0 < R; r0 += (int64_t)gridDim.x * DFT_ROWS) {
@@ -763,52 +986,80 @@ __global__ void __launch_bounds__(TPB) k_dftx_inv(const float2 *It, float *out, 
                2 * DFT_ROWS * d.Kx);
         __syncthreads();
         const float4 *rw = rows + (size_t)warp * DFT_RT * kh;
-        for (int xc = 0; xc < d.nx; xc += 128) {
-            float acc[DFT_RT][4];
+        for (int pc = 0; pc < ns; pc += 64) {
+            float a[DFT_RT][2], b[DFT_RT][2];
 #pragma unroll
             for (int r = 0; r < DFT_RT; ++r)
 #pragma unroll
-                for (int u = 0; u < 4; ++u) acc[r][u] = 0.f;
+                for (int u = 0; u < 2; ++u) a[r][u] = b[r][u] = 0.f;
             for (int jp = 0; jp < kh; ++jp) {
-                float2 ta[4], tb[4];
+                float2 ta[2], tb[2];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    ta[u] = tw[(2 * jp) * ldx + xc + lane + 32 * u];
-                    tb[u] = tw[(2 * jp + 1) * ldx + xc + lane + 32 * u];
+                for (int u = 0; u < 2; ++u) {
+                    ta[u] = tw[(2 * jp) * ldp + pc + lane + 32 * u];
+                    tb[u] = tw[(2 * jp + 1) * ldp + pc + lane + 32 * u];
                 }
 #pragma unroll
                 for (int r = 0; r < DFT_RT; ++r) {
                     const float4 v = rw[r * kh + jp];               // modes 2jp, 2jp+1 of row r
 #pragma unroll
-                    for (int u = 0; u < 4; ++u)
-                        acc[r][u] += v.x * ta[u].x + v.y * ta[u].y + v.z * tb[u].x + v.w * tb[u].y;
+                    for (int u = 0; u < 2; ++u) {
+                        a[r][u] += v.x * ta[u].x + v.z * tb[u].x;
+                        b[r][u] += v.y * ta[u].y + v.w * tb[u].y;
+                    }
                 }
             }
             // epilogue four rows at a time: all loads of a group before its stores
 #pragma unroll
             for (int r4 = 0; r4 < DFT_RT; r4 += 4) {
-                float prev[4][4], pv[4][4];
+                float prev[4][2][2], pv[4][2][2];
 #pragma unroll
                 for (int r = 0; r < 4; ++r)
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const int xx = xc + lane + 32 * u;
-                        const bool ok = warp * DFT_RT + r4 + r < nr && xx < d.nx;
-                        const int64_t off = (r0 + warp * DFT_RT + r4 + r) * d.nx + xx;
-                        prev[r][u] = ok && accumulate ? out[off] : 0.f;
-                        pv[r][u] = ok && pre ? ldf(pre + off) : 0.f;
+                    for (int u = 0; u < 2; ++u) {
+                        const int pp = pc + lane + 32 * u;
+                        const bool ok = warp * DFT_RT + r4 + r < nr && pp < ns;
+                        const int64_t base = (r0 + warp * DFT_RT + r4 + r) * d.nx;
+                        const int64_t o1 = base + pp, o2 = base + (d.nx - pp);
+                        const bool ok2 = ok && pp > 0;
+                        prev[r][u][0] = ok && accumulate ? out[o1] : 0.f;
+                        prev[r][u][1] = ok2 && accumulate ? out[o2] : 0.f;
+                        pv[r][u][0] = ok && pre ? ldf(pre + o1) : 0.f;
+                        pv[r][u][1] = ok2 && pre ? ldf(pre + o2) : 0.f;
                     }
 #pragma unroll
                 for (int r = 0; r < 4; ++r)
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const int xx = xc + lane + 32 * u;
-                        if (warp * DFT_RT + r4 + r >= nr || xx >= d.nx) continue;
-                        const int64_t off = (r0 + warp * DFT_RT + r4 + r) * d.nx + xx;
-                        float v = acc[r4 + r][u] + prev[r][u];
-                        if (pre) v *= gelu_grad(pv[r][u]);
-                        out[off] = v;
+                    for (int u = 0; u < 2; ++u) {
+                        const int pp = pc + lane + 32 * u;
+                        if (warp * DFT_RT + r4 + r >= nr || pp >= ns) continue;
+                        const int64_t base = (r0 + warp * DFT_RT + r4 + r) * d.nx;
+                        float v1 = a[r4 + r][u] + b[r4 + r][u] + prev[r][u][0];
+                        if (pre) v1 *= gelu_grad(pv[r][u][0]);
+                        out[base + pp] = v1;
+                        if (pp > 0) {
+                            float v2 = a[r4 + r][u] - b[r4 + r][u] + prev[r][u][1];
+                            if (pre) v2 *= gelu_grad(pv[r][u][1]);
+                            out[base + d.nx - pp] = v2;
+                        }
                     }
+            }
+        }
+        if (mid) {                                           // out[nx/2] = sum_j Re(I_j) c_(nx/2) j
+            const int hmid = d.nx / 2;
+            const float2 *rows2 = reinterpret_cast<const float2 *>(rows);
+            for (int r = 0; r < DFT_RT; ++r) {
+                const int row = warp * DFT_RT + r;
+                float sum = 0.f;
+                for (int j = lane; j < d.Kx; j += 32) sum += rows2[(size_t)row * d.Kx + j].x * twx[hmid * d.Kx + j].x;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, o);
+                if (lane == 0 && row < nr) {
+                    const int64_t off = (r0 + row) * d.nx + hmid;
+                    float v = accumulate ? out[off] + sum : sum;
+                    if (pre) v *= gelu_grad(ldf(pre + off));
+                    out[off] = v;
+                }
             }
         }
     }
@@ -1009,13 +1260,13 @@ __global__ void k_adam(float *p, const float *g, float *m1, float *m2, int64_t n
 // shared memory of the transform stages (independent of the batch)
 size_t smem_dftx_fwd(const Dims &d)
 {
-    const size_t nxp = (d.nx + 3) & ~3;
-    return sizeof(float2) * nxp * d.Kx + sizeof(float) * DFT_ROWS * nxp;
+    const size_t npp = ((size_t)d.nx / 2 + 1 + 3) & ~(size_t)3, nxp = ((size_t)d.nx + 3) & ~(size_t)3;
+    return sizeof(float2) * npp * d.Kx + sizeof(float) * DFT_ROWS * (2 * npp + nxp);
 }
 size_t smem_dftx_inv(const Dims &d)
 {
-    const size_t ldx = (d.nx + 127) & ~127;
-    return sizeof(float2) * ((size_t)d.Kx * ldx + (size_t)DFT_ROWS * d.Kx);
+    const size_t ldp = (((size_t)d.nx + 1) / 2 + 63) & ~(size_t)63;
+    return sizeof(float2) * ((size_t)d.Kx * ldp + (size_t)DFT_ROWS * d.Kx);
 }
 int dfty_fwd_slabs(const Dims &d) { return std::max(1, (TPB / 32) / ((d.Ky + 7) / 8)); }
 int dfty_inv_slabs(const Dims &d) { return std::max(1, (TPB / 32) / ((d.ny + 7) / 8)); }
@@ -1042,7 +1293,11 @@ bool set_smem_limits(size_t bytes)
            cudaFuncSetAttribute(k_outer<float, 1>, a, b) == cudaSuccess &&
            cudaFuncSetAttribute(k_outer<float, 2>, a, b) == cudaSuccess &&
            cudaFuncSetAttribute(k_outer<__nv_bfloat16, 1>, a, b) == cudaSuccess &&
-           cudaFuncSetAttribute(k_outer<__nv_bfloat16, 2>, a, b) == cudaSuccess;
+           cudaFuncSetAttribute(k_outer<__nv_bfloat16, 2>, a, b) == cudaSuccess &&
+           cudaFuncSetAttribute(k_outer_async<float, 1>, a, b) == cudaSuccess &&
+           cudaFuncSetAttribute(k_outer_async<float, 2>, a, b) == cudaSuccess &&
+           cudaFuncSetAttribute(k_outer_async<__nv_bfloat16, 1>, a, b) == cudaSuccess &&
+           cudaFuncSetAttribute(k_outer_async<__nv_bfloat16, 2>, a, b) == cudaSuccess;
 }
 
 bool on_device(const void *p)
@@ -1361,10 +1616,16 @@ void outer(fno_ctx *f, const float *g, int co, const T *x, int ci, int64_t oW, i
     int groups = 1;
     while (units * groups * 2 <= TPB && groups * 2 <= OUTER_TILE / 4) groups *= 2;
     const size_t sm = smem_outer(co, ci);
-    if (units <= TPB)
+    if (f->N % OUTER_TILE == 0) {                           // whole tiles: double-buffered cp.async copies
+        if (units <= TPB)
+            k_outer_async<T, 1><<<nb, TPB, sm, f->s>>>(g, co, x, ci, f->grads + oW, f->grads + ob, f->N, B, groups);
+        else
+            k_outer_async<T, 2><<<nb, TPB, sm, f->s>>>(g, co, x, ci, f->grads + oW, f->grads + ob, f->N, B, groups);
+    } else if (units <= TPB) {
         k_outer<T, 1><<<nb, TPB, sm, f->s>>>(g, co, x, ci, f->grads + oW, f->grads + ob, f->N, B, groups);
-    else
+    } else {
         k_outer<T, 2><<<nb, TPB, sm, f->s>>>(g, co, x, ci, f->grads + oW, f->grads + ob, f->N, B, groups);
+    }
 }
 
 Dims dims(const fno_ctx *f, int B)
@@ -1418,7 +1679,7 @@ void contract(fno_ctx *f, const float2 *Vin, int64_t oR, float2 *Gout, bool adj,
 }
 
 template <class T>
-lbm_status forward_impl(fno_ctx *f, const float *x, int B)
+lbm_status forward_impl(fno_ctx *f, const float *x, int B, bool keep = true)
 {
     const fno_config &c = f->c;
     const int W = c.width;
@@ -1432,6 +1693,16 @@ lbm_status forward_impl(fno_ctx *f, const float *x, int B)
         dft_inv<T>(f, f->G, f->spec, f->scale_inv, 0, nullptr, B);
         pw_fwd<T>(f, vin, W, W, f->oW_w[l], f->oW_b[l], f->spec, static_cast<T *>(f->pre[l]), f->v[l + 1], false,
                   l < c.layers - 1 ? 1 : 0, B);
+    }
+    const int H = c.hidden;
+    const size_t smf = sizeof(float) * ((size_t)H * 32 + ((H + 3) & ~3) + (size_t)H * 8);
+    if (!keep && W == 32 && f->N % 2 == 0 && smf <= 48 * 1024) {
+        // inference: projection fused, hidden activations not stored
+        const size_t sm = smf;
+        k_proj_fused<T, 32><<<grid_for((int64_t)B * f->N / 2), TPB, sm, f->s>>>(
+            static_cast<T *>(f->v[c.layers]), H, c.cout, f->params + f->oQ1_w, f->params + f->oQ1_b,
+            f->params + f->oQ2_w, f->params + f->oQ2_b, f->y, f->N, B);
+        return LBM_OK;
     }
     pw_fwd<T>(f, static_cast<T *>(f->v[c.layers]), W, c.hidden, f->oQ1_w, f->oQ1_b, nullptr, static_cast<T *>(f->hpre),
               f->h, false, 1, B);
@@ -1488,7 +1759,7 @@ extern "C" lbm_status fno_forward(fno_ctx *f, const float *x, float *y, int32_t 
         const float *xb = x + (int64_t)b0 * c.cin * f->N;
         lbm_status st = stage_input(f, xb, f->xin, (int64_t)B * c.cin * f->N);
         if (st != LBM_OK) return st;
-        st = c.act_bf16 ? forward_impl<__nv_bfloat16>(f, f->xin, B) : forward_impl<float>(f, f->xin, B);
+        st = c.act_bf16 ? forward_impl<__nv_bfloat16>(f, f->xin, B, false) : forward_impl<float>(f, f->xin, B, false);
         if (st != LBM_OK) return st;
         FCK(cudaGetLastError());
         FCK(cudaMemcpyAsync(y + (int64_t)b0 * c.cout * f->N, f->y, (int64_t)B * c.cout * f->N * sizeof(float),

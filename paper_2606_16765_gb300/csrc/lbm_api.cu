@@ -1302,7 +1302,7 @@ static lbm_status batch_rebuild(lbm_batch *b, const std::vector<int> &live)
     for (int g : live) {
         const lbm_ctx *c = b->members[g];
         if (c->p.face_x_hi == LBM_FACE_OUTFLOW)
-            out_chunks = std::max<int>(out_chunks, (int)std::min<int64_t>(((int64_t)c->g.ny * c->g.nz + 255) / 256, 64));
+            out_chunks = std::max<int>(out_chunks, (int)std::min<int64_t>((9 * (int64_t)c->g.ny * c->g.nz + 255) / 256, 256));
     }
     BCK(cudaMemcpyAsync(b->d_qbegin, qb.data(), sizeof(int64_t) * qb.size(), cudaMemcpyHostToDevice, b->own));
     BCK(cudaStreamSynchronize(b->own));

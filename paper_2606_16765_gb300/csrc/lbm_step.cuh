@@ -310,7 +310,7 @@ __global__ void __launch_bounds__(EDGE_BLOCK) k_step_edge(StepArgs a)
 // The fix only writes outlet-cell slots of cx = -1, which the inner cell's
 // gather never reads.
 template <class S>
-__device__ __forceinline__ void outflow_cell(const StepArgs &a, int64_t yz, bool fix, bool next_odd)
+__device__ __forceinline__ void outflow_link(const StepArgs &a, int64_t yz, int k, bool fix, bool next_odd)
 {
     using T = Store<S>;
     using R = typename T::R;
@@ -318,50 +318,42 @@ __device__ __forceinline__ void outflow_cell(const StepArgs &a, int64_t yz, bool
     const int64_t c = (int64_t)(a.nx - 1) + (int64_t)a.nx * yz;
     if (a.flags[c] & CELL_SOLID) return;
     const int y = (int)(yz % a.ny), z = (int)(yz / a.ny);
-    R *own = static_cast<R *>(a.ob) + yz;
+    const int i = 3 * k;                                    // cx = -1
+    R *own = static_cast<R *>(a.ob) + (int64_t)k * P + yz;
     R *in = own + 9 * P;
     const bool inner = a.nx >= 2 && !(a.flags[c - 1] & CELL_SOLID);
     S *p = static_cast<S *>(a.pdf);
-    if (fix) {
-        const R cs = R(0.57735026918962576451), cs1 = R(1) - cs;
-#pragma unroll
-        for (int k = 0; k < 9; ++k) {
-            const int i = 3 * k;
-            const int sy = y - cy_of(i), sz = z - cz_of(i);
-            if ((sy < 0 || sy >= a.ny) && a.face_y != FACE_PERIODIC) continue;   // wall link
-            if ((sz < 0 || sz >= a.nz) && a.face_z != FACE_PERIODIC) continue;
-            const R g = cs * (inner ? in[k * P] : own[k * P]) + cs1 * own[k * P];
-            T::st(p + (int64_t)i * a.slot + c, g);
-        }
+    int sy = y - cy_of(i), sz = z - cz_of(i);
+    bool through_face = true;                              // the link leaves through the x face, not a wall
+    if (sy < 0 || sy >= a.ny) { through_face = a.face_y == FACE_PERIODIC; sy = sy < 0 ? sy + a.ny : sy - a.ny; }
+    if (sz < 0 || sz >= a.nz) { through_face = through_face && a.face_z == FACE_PERIODIC; sz = sz < 0 ? sz + a.nz : sz - a.nz; }
+    R mine;
+    if (fix && through_face) {
+        const R cs = R(0.57735026918962576451);
+        mine = cs * (inner ? *in : *own) + (R(1) - cs) * *own;
+        T::st(p + (int64_t)i * a.slot + c, mine);
+        mine = T::ld(p + (int64_t)i * a.slot + c);         // the stored (rounded) value
+    } else {
+        mine = T::ld(p + (int64_t)i * a.slot + c);
     }
-#pragma unroll
-    for (int k = 0; k < 9; ++k) own[k * P] = T::ld(p + (int64_t)(3 * k) * a.slot + c);
+    *own = mine;                                            // every cx = -1 link of an outlet cell reads its own slot
     if (!inner) return;
-    const int64_t ci = c - 1;
-#pragma unroll
-    for (int k = 0; k < 9; ++k) {
-        const int i = 3 * k;
-        int64_t src = -1;
-        if (next_odd) {
-            int sy = y - cy_of(i), sz = z - cz_of(i);
-            bool ok = true;
-            if (sy < 0 || sy >= a.ny) { ok = a.face_y == FACE_PERIODIC; sy = sy < 0 ? sy + a.ny : sy - a.ny; }
-            if (sz < 0 || sz >= a.nz) { ok = ok && a.face_z == FACE_PERIODIC; sz = sz < 0 ? sz + a.nz : sz - a.nz; }
-            if (ok) {
-                const int64_t s = (int64_t)(a.nx - 1) + (int64_t)a.nx * ((int64_t)sy + (int64_t)a.ny * sz);
-                if (!(a.flags[s] & CELL_SOLID)) src = s;
-            }
-        }
-        in[k * P] = src >= 0 ? T::ld(p + (int64_t)(Q - 1 - i) * a.slot + src) : T::ld(p + (int64_t)i * a.slot + ci);
+    int64_t src = -1;
+    if (next_odd && through_face) {                         // the inner cell's source (nx - 1, y - cy, z - cz)
+        const int64_t s2 = (int64_t)(a.nx - 1) + (int64_t)a.nx * ((int64_t)sy + (int64_t)a.ny * sz);
+        if (!(a.flags[s2] & CELL_SOLID)) src = s2;
     }
+    *in = src >= 0 ? T::ld(p + (int64_t)(Q - 1 - i) * a.slot + src) : T::ld(p + (int64_t)i * a.slot + c - 1);
 }
 
+// One thread per outlet column and direction (nine per column: the plane is
+// strided by nx in memory, so many accesses must be in flight).
 template <class S>
 __global__ void __launch_bounds__(256) k_outflow(StepArgs a, int fix, int next_odd)
 {
     const int64_t P = (int64_t)a.ny * a.nz;
-    for (int64_t yz = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; yz < P; yz += (int64_t)gridDim.x * blockDim.x)
-        outflow_cell<S>(a, yz, fix != 0, next_odd != 0);
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < 9 * P; t += (int64_t)gridDim.x * blockDim.x)
+        outflow_link<S>(a, t % P, (int)(t / P), fix != 0, next_odd != 0);
 }
 
 template <class S>
@@ -369,7 +361,8 @@ static void launch_outflow(const StepArgs &a, bool fix, bool next_odd, cudaStrea
 {
     if (a.face_x_hi != FACE_OUTFLOW) return;
     const int64_t P = (int64_t)a.ny * a.nz;
-    k_outflow<S><<<(unsigned)std::min<int64_t>((P + 255) / 256, 1024), 256, 0, s>>>(a, fix ? 1 : 0, next_odd ? 1 : 0);
+    k_outflow<S><<<(unsigned)std::min<int64_t>((9 * P + 255) / 256, 152 * 16), 256, 0, s>>>(a, fix ? 1 : 0,
+                                                                                          next_odd ? 1 : 0);
 }
 
 // Interpolated bounce-back (Bouzidi, Firdaouss & Lallemand 2001), after the
@@ -522,8 +515,8 @@ __global__ void __launch_bounds__(256) k_batch_outflow(const BatchMember *mem, i
     const StepArgs &a = mem[blockIdx.x].a;
     if (a.face_x_hi != FACE_OUTFLOW) return;
     const int64_t P = (int64_t)a.ny * a.nz;
-    for (int64_t yz = (int64_t)blockIdx.y * blockDim.x + threadIdx.x; yz < P; yz += (int64_t)gridDim.y * blockDim.x)
-        outflow_cell<S>(a, yz, fix != 0, next_odd != 0);
+    for (int64_t t = (int64_t)blockIdx.y * blockDim.x + threadIdx.x; t < 9 * P; t += (int64_t)gridDim.y * blockDim.x)
+        outflow_link<S>(a, t % P, (int)(t / P), fix != 0, next_odd != 0);
 }
 
 // ... then the interpolated bounce-back of the members with wall distances

@@ -21,7 +21,14 @@ def _built():
     _build.build()
 
 
-def tiny_cfgs(width=8):
+def tiny_cfgs(width=8, tiled=False):
+    """tiled: a 16x8x8 grid (1024 cells, whole 64-cell tiles: the gradient
+    reduction takes its cp.async path) instead of 10x6x8 (480 cells)."""
+    if tiled:
+        ocfg = F.FNOConfig(grid=(8, 8, 16), cin=4, width=width, cout=4, modes=(3, 3, 4), layers=2, hidden=16)
+        gcfg = dict(nx=16, ny=8, nz=8, cin=4, width=width, cout=4, mx=4, my=3, mz=3, layers=2, hidden=16,
+                    max_batch=8)
+        return ocfg, gcfg
     ocfg = F.FNOConfig(grid=(8, 6, 10), cin=2, width=width, cout=2, modes=(3, 2, 3), layers=2, hidden=5)
     gcfg = dict(nx=10, ny=6, nz=8, cin=2, width=width, cout=2, mx=3, my=2, mz=3, layers=2, hidden=5, max_batch=8)
     return ocfg, gcfg
@@ -61,9 +68,9 @@ def problem(ocfg, B=3, seed=0):
     return x, t, m, p
 
 
-def run_case(act_bf16, tensor_cores, width=8):
+def run_case(act_bf16, tensor_cores, width=8, tiled=False):
     from paper_2606_16765_gb300 import fno as G
-    ocfg, gcfg = tiny_cfgs(width)
+    ocfg, gcfg = tiny_cfgs(width, tiled)
     gcfg.update(act_bf16=act_bf16, tensor_cores=tensor_cores)
     GCFG_CACHE["g"] = gcfg
     x, t, m, p = problem(ocfg)
@@ -106,6 +113,22 @@ def test_tensor_core_contraction_matches_oracle(act_bf16):
     for k in gr:
         assert cosine(g[k], gr[k]) > 0.999, k
         assert rel_l2(g[k], gr[k]) < 3e-2, k
+
+
+@pytest.mark.parametrize("act_bf16,tensor_cores", [(0, 0), (1, 1)])
+def test_whole_tile_grid_matches_oracle(act_bf16, tensor_cores):
+    """Grid of whole 64-cell tiles (double-buffered gradient reduction),
+    width 32, hidden 16: FP32 to 1e-4, BF16 to the BF16 bounds."""
+    y, yr, L, Lr, g, gr = run_case(act_bf16=act_bf16, tensor_cores=tensor_cores, width=32, tiled=True)
+    if not act_bf16 and not tensor_cores:
+        assert np.abs(y - yr).max() / np.abs(yr).max() < 1e-5
+        for k in gr:
+            assert rel_l2(g[k], gr[k]) < 1e-4, k
+    else:
+        assert rel_l2(y, yr) < 2e-2
+        for k in gr:
+            assert cosine(g[k], gr[k]) > 0.999, k
+            assert rel_l2(g[k], gr[k]) < 3e-2, k
 
 
 def test_adam_trajectory_matches_oracle():
