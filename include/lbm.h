@@ -168,6 +168,20 @@ lbm_status lbm_read_mean(lbm_ctx *ctx, int32_t dtype, int32_t halfres, void *dst
 lbm_status lbm_set_wall_distances(lbm_ctx *ctx, int64_t n, const int64_t *cell, const int8_t *dir,
                                   const double *q);
 
+/* Probes (Sec. 3.3: the Strouhal number from the velocity in the wake; a
+ * monitor of chosen cells): every `every` steps, (ux, uy, uz, p) of the
+ * state before the step at the n listed cells (x + nx (y + ny z)), FP32,
+ * the time-average convention (p = (rho - 1)/3; solid cells give 0).  Rows
+ * are kept on the device, `capacity` at a time, and moved to the host when
+ * full.  A call replaces the probe set and clears the record; n = 0 turns
+ * probes off.  Host cell array, copied.  Not supported on batch members
+ * (LBM_ERR_STATE); not part of checkpoints. */
+lbm_status lbm_set_probes(lbm_ctx *ctx, int64_t n, const int64_t *cells, int64_t every, int64_t capacity);
+
+/* The probe record so far, rows of n x 4 floats (host or device dst, at most
+ * max_rows rows); n_rows (may be NULL) receives the rows recorded. */
+lbm_status lbm_read_probes(lbm_ctx *ctx, float *dst, int64_t max_rows, int64_t *n_rows);
+
 /* Turbulence statistics (Sec. 3.3 validates turbulent fluctuations): the
  * velocity covariances over the same samples as the time average, per cell
  * <ux ux> - <ux>^2, <uy uy> - <uy>^2, <uz uz> - <uz>^2, <ux uy> - <ux><uy>,

@@ -120,6 +120,11 @@ struct lbm_ctx {
     double *qval = nullptr, *qpart = nullptr;
     unsigned *qcount = nullptr;
     int64_t n_qlinks = 0;
+    // probes: (u, v, w, p) at listed cells every probe_every steps
+    int64_t *probe_cells = nullptr;
+    float *probe_ring = nullptr;
+    int64_t n_probes = 0, probe_every = 1, probe_cap = 0, probe_rows_dev = 0;
+    std::vector<float> probe_host;
     std::string err;
     int64_t n_fluid = 0, n_bulk = 0, launches = 0;
     // kernel timing: events recorded per step (start, mid, end) and the step kind
@@ -411,6 +416,8 @@ extern "C" lbm_status lbm_destroy(lbm_ctx *ctx)
     if (!ctx) return LBM_ERR_ARG;
     cudaStreamSynchronize(ctx->stream);
     for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
+    cudaFree(ctx->probe_cells);
+    cudaFree(ctx->probe_ring);
     cudaFree(ctx->qlinks);
     cudaFree(ctx->qval);
     cudaFree(ctx->qpart);
@@ -431,6 +438,18 @@ static lbm_status flush_forces(lbm_ctx *ctx)
                        sizeof(double) * 3 * ctx->force_rows_dev, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     ctx->force_rows_dev = 0;
+    return LBM_OK;
+}
+
+static lbm_status flush_probes(lbm_ctx *ctx)
+{
+    if (ctx->probe_rows_dev == 0) return LBM_OK;
+    const size_t old = ctx->probe_host.size(), cnt = (size_t)4 * ctx->n_probes * ctx->probe_rows_dev;
+    ctx->probe_host.resize(old + cnt);
+    CK(cudaMemcpyAsync(ctx->probe_host.data() + old, ctx->probe_ring, sizeof(float) * cnt, cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->probe_rows_dev = 0;
     return LBM_OK;
 }
 
@@ -525,6 +544,19 @@ extern "C" lbm_status lbm_step(lbm_ctx *ctx, int64_t nsteps)
             if (ctx->n_edge > 0) a.fpart = ctx->at<double>(L.fpart);
             else CK(cudaMemsetAsync(a.fout, 0, 3 * sizeof(double), ctx->stream));
             ctx->force_rows_dev++;
+        }
+        if (ctx->n_probes > 0 && t % ctx->probe_every == 0) {   // the state at t, before the step
+            if (ctx->probe_rows_dev == ctx->probe_cap) {
+                lbm_status st = flush_probes(ctx);
+                if (st != LBM_OK) return st;
+            }
+            AuxArgs x;
+            x.cells = ctx->probe_cells;
+            x.count = ctx->n_probes;
+            x.fout = ctx->probe_ring + 4 * ctx->n_probes * ctx->probe_rows_dev;
+            launch_aux(p.storage, AUX_PROBE, base, (t & 1) != 0, x, ctx->stream);
+            ctx->probe_rows_dev++;
+            ctx->launches++;
         }
         step_launch(ctx, a, (t & 1) != 0, a.msum != nullptr || a.snap != nullptr);
         if (snap_k >= 0 && p.snap_halfres) {
@@ -677,6 +709,50 @@ extern "C" lbm_status lbm_set_wall_distances(lbm_ctx *ctx, int64_t n, const int6
     CK(cudaMemcpy(ctx->qval, V.data(), m * sizeof(double), cudaMemcpyHostToDevice));
     CK(cudaMemset(ctx->qcount, 0, sizeof(unsigned)));
     ctx->n_qlinks = m;
+    return LBM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// probes
+// ---------------------------------------------------------------------------
+extern "C" lbm_status lbm_set_probes(lbm_ctx *ctx, int64_t n, const int64_t *cells, int64_t every, int64_t capacity)
+{
+    if (!ctx || n < 0 || (n > 0 && (!cells || every < 1 || capacity < 1)))
+        return ctx ? fail(ctx, LBM_ERR_ARG, "bad probe arguments") : LBM_ERR_ARG;
+    if (ctx->in_batch) return fail(ctx, LBM_ERR_STATE, "probes are not supported on batch members");
+    for (int64_t k = 0; k < n; ++k)
+        if (cells[k] < 0 || cells[k] >= ctx->L.n) return fail(ctx, LBM_ERR_ARG, "probe cell out of range");
+    CK(cudaStreamSynchronize(ctx->stream));
+    cudaFree(ctx->probe_cells);
+    cudaFree(ctx->probe_ring);
+    ctx->probe_cells = nullptr;
+    ctx->probe_ring = nullptr;
+    ctx->n_probes = 0;
+    ctx->probe_rows_dev = 0;
+    ctx->probe_host.clear();
+    if (n == 0) return LBM_OK;
+    CK(cudaMalloc(&ctx->probe_cells, sizeof(int64_t) * n));
+    CK(cudaMalloc(&ctx->probe_ring, sizeof(float) * 4 * n * capacity));
+    CK(cudaMemcpy(ctx->probe_cells, cells, sizeof(int64_t) * n, cudaMemcpyHostToDevice));
+    ctx->n_probes = n;
+    ctx->probe_every = every;
+    ctx->probe_cap = capacity;
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_read_probes(lbm_ctx *ctx, float *dst, int64_t max_rows, int64_t *n_rows)
+{
+    if (!ctx || max_rows < 0 || (max_rows > 0 && !dst)) return LBM_ERR_ARG;
+    lbm_status st = flush_probes(ctx);
+    if (st != LBM_OK) return st;
+    const int64_t per = 4 * ctx->n_probes;
+    const int64_t rows = per > 0 ? (int64_t)ctx->probe_host.size() / per : 0;
+    if (n_rows) *n_rows = rows;
+    const int64_t m = std::min(rows, max_rows);
+    if (m > 0) {
+        if (is_device_ptr(dst)) CK(cudaMemcpy(dst, ctx->probe_host.data(), sizeof(float) * per * m, cudaMemcpyHostToDevice));
+        else std::memcpy(dst, ctx->probe_host.data(), sizeof(float) * per * m);
+    }
     return LBM_OK;
 }
 
@@ -973,6 +1049,8 @@ extern "C" lbm_status lbm_reset(lbm_ctx *ctx)
     ctx->msamples = 0;
     ctx->force_host.clear();
     ctx->force_rows_dev = 0;
+    ctx->probe_host.clear();
+    ctx->probe_rows_dev = 0;
     std::fill(ctx->snap_taken.begin(), ctx->snap_taken.end(), 0);
     ctx->unstable = false;
     ctx->ev_kind.clear();

@@ -267,6 +267,31 @@ __global__ void k_halfres(const T *in, int nx, int ny, int nz, T *out)
     }
 }
 
+// Probe row: (ux, uy, uz, p) of the current state at the listed cells
+// (p = (rho - 1)/3; solid or out-of-range cells give 0).
+template <class S>
+__global__ void k_probe(StepArgs a, bool odd, const int64_t *cells, int64_t count, float *out)
+{
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < count; k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = cells[k];
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (c >= 0 && c < a.n && !(a.flags[c] & CELL_SOLID)) {
+            double f[Q];
+            gather_natural<S>(a, odd, c, f);
+            double d = 0, jx = 0, jy = 0, jz = 0;
+            for (int i = 0; i < Q; ++i) {
+                d += f[i];
+                jx += cx_of(i) * f[i];
+                jy += cy_of(i) * f[i];
+                jz += cz_of(i) * f[i];
+            }
+            const double r = 1.0 + d;
+            v = make_float4((float)(jx / r), (float)(jy / r), (float)(jz / r), (float)(d / 3.0));
+        }
+        reinterpret_cast<float4 *>(out)[k] = v;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // host launchers
 // ---------------------------------------------------------------------------
@@ -291,6 +316,9 @@ static void launch_aux_t(AuxOp op, const StepArgs &a, bool odd, const AuxArgs &x
     case AUX_TOTALS:
         k_totals_partial<S><<<x.nblocks, TOT_BLOCK, 0, s>>>(a, odd, x.partials);
         k_totals_final<<<1, TOT_BLOCK, 0, s>>>(x.partials, x.nblocks, x.out);
+        break;
+    case AUX_PROBE:
+        k_probe<S><<<grid_for(x.count, 128), 128, 0, s>>>(a, odd, x.cells, x.count, x.fout);
         break;
     }
 }

@@ -106,7 +106,6 @@ __device__ __forceinline__ void bulk_cell(const StepArgs &a, const StepOut &o, i
     R drho, ux, uy, uz;
     collide<R, PLAIN>(f, rates_of<R>(a), drho, ux, uy, uz);
     check_density(drho, a.status);
-    if (EPI) epilogue<R>(a, o, c, drho, ux, uy, uz);
     // the outlet condition of the next (odd) step uses this step's velocity
     if (!ODD && hi && a.face_x_hi == FACE_OUTLET) {
         ub[pl] = ux;
@@ -130,6 +129,10 @@ __device__ __forceinline__ void bulk_cell(const StepArgs &a, const StepOut &o, i
 #pragma unroll
         for (int j = 0; j < Q; ++j) T::st(reinterpret_cast<S *>(const_cast<char *>(q) + sof[j]), f[j]);
     }
+    // time average and snapshot after the scatter: the populations are no
+    // longer live, which keeps the epilogue variants at the register count of
+    // the plain kernel
+    if (EPI) epilogue<R>(a, o, c, drho, ux, uy, uz);
 }
 
 // Single-grid bulk kernel: grid (ceil(nx / blockDim.x), ceil(ny / blockDim.y), nz).

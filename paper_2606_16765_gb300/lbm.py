@@ -90,6 +90,8 @@ def lib():
             "lbm_time": (_i64, [_vp]),
             "lbm_read_mean": (C.c_int, [_vp, C.c_int32, C.c_int32, _vp, C.POINTER(_i64)]),
             "lbm_read_stats": (C.c_int, [_vp, C.c_int32, _vp, C.POINTER(_i64)]),
+            "lbm_set_probes": (C.c_int, [_vp, _i64, _vp, _i64, _i64]),
+            "lbm_read_probes": (C.c_int, [_vp, _vp, _i64, C.POINTER(_i64)]),
             "lbm_set_wall_distances": (C.c_int, [_vp, _i64, _vp, _vp, _vp]),
             "lbm_batch_set_wall_distances": (C.c_int, [_vp, C.c_int32, _i64, _vp, _vp, _vp]),
             "lbm_read_snapshot": (C.c_int, [_vp, C.c_int32, _vp]),
@@ -202,6 +204,20 @@ def lbm_set_wall_distances(h, cell, direction, q):
     q = np.ascontiguousarray(q, dtype=np.float64)
     n = len(cell)
     _check(lib().lbm_set_wall_distances(h, n, _ptr(cell), _ptr(direction), _ptr(q)), h)
+
+
+def lbm_set_probes(h, cells, every=1, capacity=65536):
+    cells = np.ascontiguousarray(cells, dtype=np.int64)
+    _check(lib().lbm_set_probes(h, len(cells), _ptr(cells), int(every), int(capacity)), h)
+
+
+def lbm_read_probes(h, n_probes):
+    rows = C.c_int64()
+    _check(lib().lbm_read_probes(h, None, 0, C.byref(rows)), h)
+    out = np.zeros((rows.value, n_probes, 4), np.float32)
+    if rows.value:
+        _check(lib().lbm_read_probes(h, _ptr(out), rows.value, C.byref(rows)), h)
+    return out
 
 
 def lbm_read_stats(h, dst, dtype):
@@ -400,6 +416,15 @@ class _Lattice:
         """Interpolated bounce-back on the listed obstacle links: (cell,
         direction, q) arrays as returned by inputs.link_wall_distances."""
         lbm_set_wall_distances(self.h, *links)
+
+    def set_probes(self, cells, every=1, capacity=65536):
+        """Record (u, v, w, p) at the cells (flat indices) every `every` steps."""
+        self._n_probes = len(cells)
+        lbm_set_probes(self.h, cells, every, capacity)
+
+    def probes(self):
+        """[rows, n_probes, 4] float32: (u, v, w, p) per recorded step."""
+        return lbm_read_probes(self.h, getattr(self, "_n_probes", 0))
 
     def stats(self, dtype=np.float64):
         """Velocity covariances [nz, ny, nx, 6] (xx, yy, zz, xy, xz, yz) over

@@ -7,6 +7,10 @@ what the solver's force epilogue writes; no lattice arithmetic).
                    three bins around it).
   Drag coefficient C_d = 2 <F_x> / (rho U^2 A), A the projected area (D times
                    the span for a spanwise cylinder).
+  Recirculation    l_r: distance from the rear of the body to the end of the
+  length           backflow region of the mean streamwise velocity on the
+                   wake centreline (first zero up-crossing, linear
+                   interpolation between cells).
 
 The paper reports the Strouhal number of the wake (Sec. 3.3, vertical
 velocity spectrum) and drag coefficients (Sec. 3.3, Table 1) as its validation
@@ -55,3 +59,22 @@ def strouhal(lift, d, u, every=1, st_band=None):
 def drag_coefficient(fx, d, span, u, rho=1.0):
     """C_d from the mean streamwise force over a record."""
     return 2.0 * float(np.mean(fx)) / (rho * u * u * d * span)
+
+
+def recirculation_length(u_line, x_rear):
+    """l_r in cells from the mean streamwise velocity u_line[x] along the wake
+    centreline: the first x > x_rear where u crosses zero upwards after a
+    backflow (u < 0) region that starts behind x_rear, minus x_rear (the x of
+    the body's rear surface).  0 when there is no backflow."""
+    u = np.asarray(u_line, dtype=np.float64)
+    start = int(np.floor(x_rear)) + 1
+    neg = np.nonzero(u[start:] < 0)[0]
+    if len(neg) == 0:
+        return 0.0
+    k = start + int(neg[0])
+    while k + 1 < len(u) and u[k + 1] < 0:
+        k += 1
+    if k + 1 >= len(u):
+        return float(len(u) - 1 - x_rear)
+    x0 = k + u[k] / (u[k] - u[k + 1])            # u[k] < 0 <= u[k+1]
+    return float(x0 - x_rear)

@@ -16,6 +16,13 @@ measures (Strouhal number of the lift, drag coefficient) over 20,000 steps.
     diverges near the outlet corners within 1000 steps.
   * Re = 200 (laminar shedding), seeded 1e-4 noise to break the symmetry,
     the same measures.
+  * Both runs also record the wake velocity at a probe two diameters behind
+    the axis (St from its cross-stream component, the paper's measure) and
+    the recirculation length l_r/D of the mean centreline velocity.  At
+    Re 200 the probe's frequency must match the lift's.  At Re 3900 the
+    10,000-step average of an impulsively started, under-resolved wake is
+    far from converged (about two flow-throughs), so the probe St and l_r/D
+    are reported, not bounded.
 """
 import numpy as np
 import pytest
@@ -73,6 +80,9 @@ def cylinder_run(re, steps=20000, noise=None, faces=None):
 @pytest.mark.parametrize("re,noise", [(3900.0, None), (200.0, 7)])
 def test_cylinder_wake_strouhal_and_drag(re, noise):
     s, grid, D = cylinder_run(re, noise=noise)
+    nx, ny, nz = grid
+    probe = 96 + nx * (60 + ny * (nz // 2))            # two diameters behind the axis, off the centreline
+    s.set_probes(np.array([probe], np.int64), every=1, capacity=20000)
     for _ in range(20):
         s.step(1000)
     s.sync()
@@ -81,12 +91,22 @@ def test_cylinder_wake_strouhal_and_drag(re, noise):
     st = wake.strouhal(F[10000:, 1], D, U, st_band=(0.05, 0.5))
     st_all = wake.strouhal(F[10000:, 1], D, U)
     cd = wake.drag_coefficient(F[10000:, 0], D, grid[2], U)
-    m, ns = s.mean(halfres=True, dtype=np.float32)
-    print(f"cylinder Re {re:.0f}: St = {st:.4f} (unbanded peak {st_all:.4f}), C_d = {cd:.4f}, "
-          f"mean samples {ns}, lift rms {F[10000:, 1].std():.4e}")
-    assert ns == 10000 and np.isfinite(m).all()
+    m, ns = s.mean(dtype=np.float32)
+    # wake probe (the paper's measure: the vertical velocity in the wake)
+    v = s.probes()[10000:, 0, 1]
+    st_probe = wake.strouhal(v, D, U, st_band=(0.05, 0.5))
+    # recirculation length on the centreline (mid-span, the two central rows)
+    u_c = 0.5 * (m[nz // 2, 63, :, 0] + m[nz // 2, 64, :, 0])
+    lr = wake.recirculation_length(u_c, 64.0 + 0.5 * D) / D
+    print(f"cylinder Re {re:.0f}: St = {st:.4f} (lift; unbanded peak {st_all:.4f}), St = {st_probe:.4f} (wake v), "
+          f"C_d = {cd:.4f}, l_r/D = {lr:.3f}, mean samples {ns}, lift rms {F[10000:, 1].std():.4e}")
+    assert ns == 10000 and np.isfinite(m).all() and np.isfinite(v).all()
     assert 0.15 <= st <= 0.30
     assert 0.8 <= cd <= 2.5
+    assert 0.0 < lr < 6.0                              # a recirculation region behind the body
+    if re < 1000:
+        # converged laminar shedding: the wake probe sees the lift frequency
+        assert abs(st_probe - st) < 0.02
 
 
 def test_cylinder_re3900_with_pressure_outlet_latches_instability():

@@ -118,6 +118,40 @@ def test_velocity_statistics_match_oracle(storage):
     assert err <= {"f64": 1e-8, "f32": 1e-4}[storage]
 
 
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+def test_probes_record_the_state_before_each_sampled_step(storage):
+    """Probe rows against the oracle's macros of the state before the step,
+    every third step for 40 steps, at wake, inlet, outlet and solid cells."""
+    d = I.sphere_channel_64()
+    nx, ny, nz = d["grid"]
+    w1 = O.omega_from_re(d["re"], d["u_in"], d["l_ref"])
+    c = K.case(d["grid"], d["mask"], omega1=w1, u_in=d["u_in"], faces=("inlet", "outflow", "wall", "wall"),
+               noise=(33, 1e-3))
+    pts = [(24, 15, 16), (0, 3, 30), (nx - 1, 16, 16), (nx - 1, 0, 0), (16, 15, 15), (40, 31, 0)]
+    cells = np.array([x + nx * (y + ny * z) for x, y, z in pts], np.int64)
+    s = K.make_solver(c, storage)
+    s.set_probes(cells, every=3, capacity=4)          # several flushes to the host
+    s.step(40)
+    s.sync()
+    rec = s.probes()
+    assert rec.shape == (14, len(cells), 4)
+    L = K.run_oracle(c, 0)
+    ref = []
+    for t in range(40):
+        if t % 3 == 0:
+            rho, u = L.macros()
+            z, y, x = np.unravel_index(cells, (nz, ny, nx))
+            row = np.concatenate([u[z, y, x], ((rho[z, y, x] - 1) / 3)[:, None]], 1)
+            row[d["mask"][z, y, x] != 0] = 0.0
+            ref.append(row)
+        L.step(1)
+    ref = np.array(ref)
+    err = np.abs(rec - ref).max() / np.abs(ref[..., :3]).max()
+    print(f"probes {storage}: max rel err {err:.2e}")
+    assert err <= (2e-6 if storage == "f64" else 1e-5)
+    assert np.all(rec[:, 4] == 0)                     # the solid cell
+
+
 def test_outflow_keeps_low_viscosity_channel_stable():
     """An empty 128x64x128 channel at nu = 3.3e-4 (the thinnest member of the
     32-channel batch): with the anti-bounce-back outlet it diverges within

@@ -36,3 +36,11 @@ def test_band_limited_peak_ignores_a_stronger_mode_outside_the_band():
     x = 5 * np.sin(2 * np.pi * 0.00225 * t) + np.sin(2 * np.pi * 0.0006 * t)
     assert wake.strouhal(x, 16.0, 0.05) == pytest.approx(0.00225 * 16 / 0.05, abs=0.01)
     assert wake.strouhal(x, 16.0, 0.05, st_band=(0.1, 0.5)) == pytest.approx(0.0006 * 16 / 0.05, abs=0.01)
+
+
+def test_recirculation_length_of_a_synthetic_wake():
+    x = np.arange(200.0)
+    rear, L = 40.0, 23.5
+    u = np.where(x <= rear, 0.0, 0.05 * np.tanh((x - rear - L) / 4.0))   # backflow until rear + L
+    assert wake.recirculation_length(u, rear) == pytest.approx(L, abs=2e-3)
+    assert wake.recirculation_length(np.abs(u) + 0.01, rear) == 0.0     # no backflow
