@@ -206,6 +206,13 @@ lbm_status lbm_read_forces(lbm_ctx *ctx, double *dst, int64_t max_rows, int64_t 
  * order, direction-major [27][N] doubles. */
 lbm_status lbm_get_pdfs(lbm_ctx *ctx, double *dst);
 
+/* Start from given fields (e.g. a surrogate's prediction of the mean flow):
+ * fields [z][y][x][4] floats (ux, uy, uz, p), host or device; every fluid
+ * cell takes the product-form equilibrium at rho = 1 + 3 p and u (the
+ * equilibrium whose cumulants above second order vanish).  Only at even t
+ * (LBM_ERR_STATE otherwise). */
+lbm_status lbm_init_equilibrium(lbm_ctx *ctx, const float *fields);
+
 /* Overwrite the state with full populations [27][N] (values of solid cells
  * are ignored).  Only at even t (LBM_ERR_STATE otherwise). */
 lbm_status lbm_set_pdfs(lbm_ctx *ctx, const double *src);

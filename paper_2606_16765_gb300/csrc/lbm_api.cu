@@ -853,6 +853,27 @@ extern "C" lbm_status lbm_get_cells(lbm_ctx *ctx, int64_t count, const int64_t *
     });
 }
 
+extern "C" lbm_status lbm_init_equilibrium(lbm_ctx *ctx, const float *fields)
+{
+    if (!ctx || !fields) return LBM_ERR_ARG;
+    if (ctx->t & 1) return fail(ctx, LBM_ERR_STATE, "init_equilibrium needs an even time step");
+    CK(cudaStreamSynchronize(ctx->stream));
+    const int64_t n = ctx->L.n;
+    DevBuf tmp;
+    const float *dsrc = fields;
+    if (!is_device_ptr(fields) || ((uintptr_t)fields & 15) != 0) {
+        CK(tmp.alloc(sizeof(float) * 4 * n));
+        CK(cudaMemcpyAsync(tmp.p, fields, sizeof(float) * 4 * n, cudaMemcpyDefault, ctx->stream));
+        dsrc = (const float *)tmp.p;
+    }
+    AuxArgs x;
+    x.fsrc = dsrc;
+    launch_aux(ctx->p.storage, AUX_EQUILIBRIUM, ctx->args(), false, x, ctx->stream);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(ctx->stream));
+    return LBM_OK;
+}
+
 extern "C" lbm_status lbm_set_pdfs(lbm_ctx *ctx, const double *src)
 {
     if (!ctx || !src) return LBM_ERR_ARG;

@@ -138,6 +138,31 @@ __global__ void k_set(S *pdf, int64_t slot, const uint8_t *flags, int64_t n, con
     }
 }
 
+// Populations at the product-form equilibrium of given fields, per cell
+// (ux, uy, uz, p), rho = 1 + 3 p: f_i = rho phi(cx, ux) phi(cy, uy) phi(cz, uz)
+// with phi(0, u) = 2/3 - u^2 and phi(+-1, u) = (1/3 + u^2 +- u)/2 (the
+// equilibrium whose cumulants above second order vanish); stored shifted,
+// solid cells at rest.  FP64 arithmetic.
+__device__ __forceinline__ double eq_phi(int c, double u)
+{
+    return c == 0 ? 2.0 / 3.0 - u * u : 0.5 * (1.0 / 3.0 + u * u + c * u);
+}
+
+template <class S>
+__global__ void k_equilibrium(S *pdf, int64_t slot, const uint8_t *flags, int64_t n, const float *fields)
+{
+    using T = Store<S>;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x) {
+        const bool solid = flags[c] & CELL_SOLID;
+        const float4 v = reinterpret_cast<const float4 *>(fields)[c];
+        const double ux = v.x, uy = v.y, uz = v.z, rho = 1.0 + 3.0 * (double)v.w;
+        for (int i = 0; i < Q; ++i) {
+            const double f = rho * eq_phi(cx_of(i), ux) * eq_phi(cy_of(i), uy) * eq_phi(cz_of(i), uz);
+            T::st(pdf + i * slot + c, (typename T::R)(solid ? 0.0 : f - w_of(i)));
+        }
+    }
+}
+
 template <class S>
 __global__ void k_macros(StepArgs a, bool odd, double *rho, double *u)
 {
@@ -319,6 +344,9 @@ static void launch_aux_t(AuxOp op, const StepArgs &a, bool odd, const AuxArgs &x
         break;
     case AUX_PROBE:
         k_probe<S><<<grid_for(x.count, 128), 128, 0, s>>>(a, odd, x.cells, x.count, x.fout);
+        break;
+    case AUX_EQUILIBRIUM:
+        k_equilibrium<S><<<grid_for(a.n, 256), 256, 0, s>>>((S *)a.pdf, a.slot, a.flags, a.n, x.fsrc);
         break;
     }
 }

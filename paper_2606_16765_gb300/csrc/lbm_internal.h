@@ -31,7 +31,7 @@ void launch_step_f16c(const StepArgs &a, bool odd, bool epi, bool plain, int blo
 void launch_batch_step_f16c(const BatchLaunch &L, bool odd, bool epi, bool plain, cudaStream_t s);
 void launch_outflow_record_f16c(const StepArgs &a, bool odd, cudaStream_t s);
 
-enum AuxOp { AUX_NOISE, AUX_GATHER, AUX_SET, AUX_MACROS, AUX_TOTALS, AUX_PROBE };
+enum AuxOp { AUX_NOISE, AUX_GATHER, AUX_SET, AUX_MACROS, AUX_TOTALS, AUX_PROBE, AUX_EQUILIBRIUM };
 
 struct AuxArgs {
     uint64_t seed = 0;
@@ -40,6 +40,7 @@ struct AuxArgs {
     int64_t count = 0;
     double *out = nullptr, *out2 = nullptr;
     float *fout = nullptr;
+    const float *fsrc = nullptr;
     int64_t si = 0, sc = 0;
     const double *src = nullptr;
     double *partials = nullptr;

@@ -167,6 +167,45 @@ def time_fno(batch=8, reps=10, warmup=3):
     return {"batch": batch, "forward_ms_per_batch": fwd, "train_step_ms": train}
 
 
+def warm_start_study(samples, ref, inner, start_fields, storage="f16c", windows=(0, 1, 2, 3, 5), width=2.0,
+                     log=print):
+    """How soon an LBM run gives the mean flow, started from rest or from
+    given fields (the FNO's prediction, as equilibrium populations): for each
+    window start s, the time average over flow-through times [s, s + width)
+    against the converged mean `ref` ([n, 4, nz, ny, nx]; rel-L2 of (u, v, w)
+    on the cells `inner`).  Returns {"rest": [...], "fno": [...]} per window
+    and the first window start under 5 %."""
+    from .lbm import Batch
+
+    nx = samples[0]["grid"][0]
+    ft = nx / U_IN
+    out = {}
+    for mode in ("rest", "fno"):
+        errs = []
+        for s0 in windows:
+            t_end = int(math.ceil((s0 + width) * ft / 10.0)) * 10
+            m_start = int(round(s0 * ft / 10.0)) * 10
+            b = Batch([dict(grid=sm["grid"], mask=sm["mask"], storage=storage, re=sm["re"], u_in=U_IN,
+                            l_ref=float(sm["grid"][1]), mean_start=m_start, mean_end=t_end, mean_every=10)
+                       for sm in samples])
+            for g, sm in enumerate(samples):
+                b.set_wall_distances(g, I.link_wall_distances(sm["grid"], sm["prims"], sm["mask"]))
+                if mode == "fno":
+                    b.member(g).init_equilibrium(start_fields[g])
+            b.set_end([t_end] * len(samples))
+            b.run_to_end()
+            b.sync()
+            ms = np.stack([np.moveaxis(b.member(g).mean(dtype=np.float32)[0], -1, 0) for g in range(len(samples))])
+            b.close()
+            rel, _ = metrics(ms, ref, inner)
+            errs.append(float(np.median(rel)))
+            log(f"  warm start [{mode}] window {s0}-{s0 + width} FT: median rel-L2 {errs[-1]:.4f}")
+        first = next((w for w, e in zip(windows, errs) if e < 0.05), None)
+        out[mode] = {"window_start_ft": list(windows), "median_rel_l2": errs, "first_window_under_5pct": first}
+    out["width_ft"] = width
+    return out
+
+
 def region_weights(mask):
     """Loss weights: inner region of the channel and fluid cells."""
     nz, ny, nx = mask.shape
@@ -193,7 +232,7 @@ def metrics(pred, true, cells):
 
 
 def run(n_train=512, n_test=64, epochs=50, batch=8, lr=1e-3, storage="f16c", n_ft=15.0, sim_batch=64,
-        out=None, log=print, full_region=True, re_range=RE_RANGE):
+        out=None, log=print, full_region=True, re_range=RE_RANGE, warm=True):
     import torch
     from .fno import FNO
 
@@ -311,6 +350,14 @@ def run(n_train=512, n_test=64, epochs=50, batch=8, lr=1e-3, storage="f16c", n_f
                                           "rel_l2_uvw_inner": {"median": float(np.median(r2i))},
                                           "final_loss": losses2[-1]}
     xb_src = Xd[test_idx].contiguous()
+    # the FNO as a warm start of the LBM (the solver stays the judge): the
+    # predicted mean field of 8 held-out geometries as the initial state
+    if warm and len(test_idx) >= 8:
+        k8 = list(range(8))
+        pred8 = pred[k8]                                  # lattice units, [8, 4, nz, ny, nx]
+        fields = [np.ascontiguousarray(np.moveaxis(pred8[g], 0, -1), dtype=np.float32) for g in k8]
+        samp8 = [test_s[keep_te[g]] for g in k8]
+        report["warm_start"] = warm_start_study(samp8, true[k8], inner[k8], fields, storage=storage, log=log)
     # speed: one FNO prediction against the LBM run it replaces
     st = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -336,7 +383,7 @@ def run(n_train=512, n_test=64, epochs=50, batch=8, lr=1e-3, storage="f16c", n_f
                               "seed's LBM run alone to the end (CUDA events, graph-replayed batched driver)")
     log(json.dumps({k: report[k] for k in ("rel_l2_uvw", "rel_l2_uvw_all_fluid", "baseline_train_mean_rel_l2_uvw",
                                             "all_fluid_loss_model", "speedup_median", "fno_seconds_per_sample",
-                                            "train_samples_per_s") if k in report}))
+                                            "train_samples_per_s", "warm_start") if k in report}))
     if out:
         with open(out, "w") as fp:
             json.dump(report, fp, indent=1)

@@ -91,6 +91,7 @@ def lib():
             "lbm_read_mean": (C.c_int, [_vp, C.c_int32, C.c_int32, _vp, C.POINTER(_i64)]),
             "lbm_read_stats": (C.c_int, [_vp, C.c_int32, _vp, C.POINTER(_i64)]),
             "lbm_set_probes": (C.c_int, [_vp, _i64, _vp, _i64, _i64]),
+            "lbm_init_equilibrium": (C.c_int, [_vp, _vp]),
             "lbm_read_probes": (C.c_int, [_vp, _vp, _i64, C.POINTER(_i64)]),
             "lbm_set_wall_distances": (C.c_int, [_vp, _i64, _vp, _vp, _vp]),
             "lbm_batch_set_wall_distances": (C.c_int, [_vp, C.c_int32, _i64, _vp, _vp, _vp]),
@@ -393,6 +394,13 @@ class _Lattice:
 
     def set_pdfs(self, f):
         lbm_set_pdfs(self.h, np.ascontiguousarray(f, dtype=np.float64))
+
+    def init_equilibrium(self, fields):
+        """Equilibrium of fields [nz, ny, nx, 4] (ux, uy, uz, p) in every fluid cell."""
+        if hasattr(fields, "data_ptr"):
+            _check(lib().lbm_init_equilibrium(self.h, _ptr(fields.contiguous())), self.h)
+        else:
+            _check(lib().lbm_init_equilibrium(self.h, _ptr(np.ascontiguousarray(fields, dtype=np.float32))), self.h)
 
     def cells(self, idx):
         idx = np.ascontiguousarray(idx, dtype=np.int64)

@@ -152,6 +152,31 @@ def test_probes_record_the_state_before_each_sampled_step(storage):
     assert np.all(rec[:, 4] == 0)                     # the solid cell
 
 
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+def test_equilibrium_initialisation_matches_oracle_equilibrium(storage):
+    """lbm_init_equilibrium against the oracle's product-form equilibrium at
+    rho = 1 + 3 p and u, cell by cell (solid cells at rest)."""
+    from paper_2606_16765_gb300.lbm import Solver
+    g = (13, 7, 5)
+    mask = I.sphere(g, (6.0, 3.0, 2.0), 1.6)
+    r = np.random.default_rng(4)
+    fields = np.concatenate([r.uniform(-0.08, 0.08, (5, 7, 13, 3)), r.uniform(-0.01, 0.01, (5, 7, 13, 1))], -1)
+    fields = fields.astype(np.float32)
+    s = Solver(g, mask, storage=storage, omega1=1.5)
+    s.init_equilibrium(fields)
+    f = s.pdfs()
+    w = O.weights()
+    err = 0.0
+    for z, y, x in np.ndindex(5, 7, 13):
+        if mask[z, y, x]:
+            ref = w
+        else:
+            u = fields[z, y, x].astype(np.float64)
+            ref = np.asarray(O.equilibrium(1.0 + 3.0 * u[3], u[0], u[1], u[2]))
+        err = max(err, np.abs(f[:, z, y, x] - ref).max())
+    assert err <= (1e-15 if storage == "f64" else 1e-8)
+
+
 def test_outflow_keeps_low_viscosity_channel_stable():
     """An empty 128x64x128 channel at nu = 3.3e-4 (the thinnest member of the
     32-channel batch): with the anti-bounce-back outlet it diverges within
@@ -399,10 +424,13 @@ def test_snapshots(halfres):
 # benchmark, on sampled cells that the oracle computes one by one from a
 # neighbourhood of the seeded initial state
 # --------------------------------------------------------------------------
-def oracle_cell_after(mask, grid, faces, omega1, u_in, seed, amp, cell, steps):
+def oracle_cell_after(mask, grid, faces, omega1, u_in, seed, amp, cell, steps, links=None):
+    """The oracle on a box around `cell` large enough that nothing from its
+    fake faces reaches the cell in `steps` steps (streaming moves one cell per
+    step, the interpolated bounce-back reads two cells behind a link)."""
     nx, ny, nz = grid
     z, y, x = np.unravel_index(cell, (nz, ny, nx))
-    R = steps + 1
+    R = 3 * steps + 1
     x0, x1 = max(0, x - R), min(nx, x + R + 1)
     y0, y1 = max(0, y - R), min(ny, y + R + 1)
     z0, z1 = max(0, z - R), min(nz, z + R + 1)
@@ -417,6 +445,14 @@ def oracle_cell_after(mask, grid, faces, omega1, u_in, seed, amp, cell, steps):
     p = O.params(*sg, omega1, u_in=u_in, faces=sub_faces)
     L = O.Lattice(p, sub)
     L.set_f(f.reshape(27, *sub.shape))
+    if links is not None:                              # wall distances of the links inside the box
+        lc, ld, lq = links
+        X, Y, Z = lc % nx, (lc // nx) % ny, lc // (nx * ny)
+        inside = (X >= x0) & (X < x1) & (Y >= y0) & (Y < y1) & (Z >= z0) & (Z < z1)
+        qd = np.full((27, sg[0] * sg[1] * sg[2]), 0.5)
+        local = (X[inside] - x0) + sg[0] * ((Y[inside] - y0) + sg[1] * (Z[inside] - z0))
+        qd[ld[inside].astype(np.int64), local] = lq[inside]
+        L.set_q(qd.reshape(27, sub.shape[0], sub.shape[1], sub.shape[2]))
     L.step(steps)
     return L.get_f()[:, z - z0, y - y0, x - x0]
 
@@ -431,7 +467,9 @@ def test_full_size_channel_sampled_cells(storage):
     from paper_2606_16765_gb300.lbm import Solver
     seed, amp = 77, 1e-3
     faces = ("inlet", "outflow", "wall", "wall")
+    links = I.link_wall_distances(grid, d["obstacle"].prims, mask)
     s = Solver(grid, mask, storage=storage, omega1=w1, u_in=d["u_in"], faces=faces)
+    s.set_wall_distances(links)
     s.init_noise(seed, amp)
     rng = np.random.default_rng(0)
     n = nx * ny * nz
@@ -455,7 +493,7 @@ def test_full_size_channel_sampled_cells(storage):
         s.step(1)
         got = s.cells(pick)
         for j, c in enumerate(pick):
-            ref = oracle_cell_after(mask, grid, faces, w1, d["u_in"], seed, amp, c, steps)
+            ref = oracle_cell_after(mask, grid, faces, w1, d["u_in"], seed, amp, c, steps, links)
             err = np.abs(got[j] - ref).max()
             assert err <= tol, (storage, steps, int(c), err)
     s.sync()
