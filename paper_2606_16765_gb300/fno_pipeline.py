@@ -350,7 +350,7 @@ def run(n_train=512, n_test=64, epochs=50, batch=8, lr=1e-3, storage="f16c", n_f
                                           "rel_l2_uvw_inner": {"median": float(np.median(r2i))},
                                           "final_loss": losses2[-1]}
     xb_src = Xd[test_idx].contiguous()
-    # the FNO as a warm start of the LBM (the solver stays the judge): the
+    # the FNO as a warm start of the LBM (the solver remains the reference): the
     # predicted mean field of 8 held-out geometries as the initial state
     if warm and len(test_idx) >= 8:
         k8 = list(range(8))
