@@ -54,17 +54,19 @@ def drag_coefficient(fx, D):
     return float(np.mean(fx)) / (0.5 * U * U * math.pi * D * D / 4.0)
 
 
-def drag_run(L, re, n_ft=10.0, avg_from_ft=5.0, storage="f32", every=10):
+def drag_run(L, re, n_ft=10.0, avg_from_ft=5.0, storage="f32", every=10, lateral="wall"):
     """C_d at resolution L and Re_s: the mean force over flow-through times
     [avg_from_ft, n_ft) of a run from rest; also the C_d of each flow-through
-    window, to judge convergence."""
+    window, to judge convergence.  lateral = "wall" (no-slip channel walls,
+    the paper's set-up) or "periodic" (y and z wrap around: a sphere in a
+    periodic array of spacing 6 D, free of wall boundary layers)."""
     from .lbm import Solver
 
     grid, D, _, _, mask, links = sphere_channel(L)
     ft = 2 * L / U
     steps = int(round(n_ft * ft / every)) * every
     s = Solver(grid, mask, storage=storage, re=float(re), u_in=U, l_ref=D, force_every=every,
-               force_capacity=steps // every + 1)
+               force_capacity=steps // every + 1, faces=("inlet", "outflow", lateral, lateral))
     try:
         s.set_wall_distances(links)
         t0 = time.time()
@@ -78,8 +80,8 @@ def drag_run(L, re, n_ft=10.0, avg_from_ft=5.0, storage="f32", every=10):
     k0 = int(round(avg_from_ft * rows_per_ft))
     windows = [drag_coefficient(F[int(k * rows_per_ft):int((k + 1) * rows_per_ft), 0], D)
                for k in range(int(n_ft))]
-    return dict(L=L, re_s=re, cd=drag_coefficient(F[k0:, 0], D), cd_per_ft=windows, steps=steps,
-                seconds=sec, links=int(len(links[0])))
+    return dict(L=L, re_s=re, lateral=lateral, cd=drag_coefficient(F[k0:, 0], D), cd_per_ft=windows,
+                steps=steps, seconds=sec, links=int(len(links[0])))
 
 
 def wake_run(L, re=1000.0, n_ft=12.0, mean_from_ft=4.0, storage="f32", probe_every=10, mean_every=10):
@@ -140,15 +142,17 @@ def main(argv=None):
                     help="comma list of L:Re_s drag runs")
     ap.add_argument("--wake", type=int, default=0, help="resolution L of the Re_s = 1000 wake run (0: none)")
     ap.add_argument("--n-ft", type=float, default=10.0)
+    ap.add_argument("--lateral", default="wall", choices=["wall", "periodic"],
+                    help="y/z faces of the drag runs (the wake run always has walls)")
     ap.add_argument("--out", default=None)
     a = ap.parse_args(argv)
     rep = {"drag": [], "wake": None}
     for cs in filter(None, a.cases.split(",")):
         L, re = (int(v) for v in cs.split(":"))
-        r = drag_run(L, re, n_ft=a.n_ft)
+        r = drag_run(L, re, n_ft=a.n_ft, lateral=a.lateral)
         r["paper"] = TABLE1.get(re, {}).get(L)
         rep["drag"].append(r)
-        print(f"L {L} Re_s {re}: C_d {r['cd']:.4f} (paper {r['paper']}), per flow-through "
+        print(f"L {L} Re_s {re} ({a.lateral}): C_d {r['cd']:.4f} (paper {r['paper']}), per flow-through "
               f"{[round(v, 4) for v in r['cd_per_ft']]}, {r['seconds']:.1f} s", flush=True)
         if a.out:
             with open(a.out, "w") as fp:
