@@ -242,6 +242,10 @@ typedef struct {
     int32_t storage, block_x;
     double omega1;           /* shear rate in use                                 */
     int64_t interior_cells;  /* equal to bulk_cells (kept for layout stability)     */
+    int64_t wall_cells;      /* fluid cells in the rows next to no-slip lateral walls,
+                                updated in extra blocks of the edge kernel's
+                                launch (fluid_cells = bulk_cells + wall_cells +
+                                edge_cells) */
 } lbm_info;
 
 lbm_status lbm_get_info(const lbm_ctx *ctx, lbm_info *out);

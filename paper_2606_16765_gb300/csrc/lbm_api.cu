@@ -126,7 +126,7 @@ struct lbm_ctx {
     int64_t n_probes = 0, probe_every = 1, probe_cap = 0, probe_rows_dev = 0;
     std::vector<float> probe_host;
     std::string err;
-    int64_t n_fluid = 0, n_bulk = 0, launches = 0;
+    int64_t n_fluid = 0, n_bulk = 0, n_wall = 0, launches = 0;
     // kernel timing: events recorded per step (start, mid, end) and the step kind
     bool timing = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -143,6 +143,7 @@ struct lbm_ctx {
         a.flags = at<uint8_t>(L.flags);
         a.edge = at<uint4>(L.edge);
         a.n_edge = n_edge;
+        a.n_wall = n_wall;
         a.nx = g.nx; a.ny = g.ny; a.nz = g.nz;
         a.nxy = (int64_t)g.nx * g.ny;
         a.n = L.n;
@@ -313,7 +314,7 @@ static lbm_status create_impl(const lbm_grid *g, const uint8_t *mask, const lbm_
         }
     }
     launch_flags(dmask, ctx->at<uint8_t>(L.flags), g->nx, g->ny, g->nz, p->face_x_lo != LBM_FACE_PERIODIC,
-                 p->face_x_hi != LBM_FACE_PERIODIC, s);
+                 p->face_x_hi != LBM_FACE_PERIODIC, p->face_y == LBM_FACE_WALL, p->face_z == LBM_FACE_WALL, s);
     std::vector<uint8_t> hflags(n);
     if (cudaMemcpyAsync(hflags.data(), ctx->at<uint8_t>(L.flags), n, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess) {
@@ -353,6 +354,7 @@ static lbm_status create_impl(const lbm_grid *g, const uint8_t *mask, const lbm_
         const int x = (int)(c % nx), y = (int)((c / nx) % ny), z = (int)(c / ((int64_t)nx * ny));
         ctx->n_fluid += !(hflags[c] & CELL_SOLID);
         ctx->n_bulk += (hflags[c] == 0 || hflags[c] == CELL_XFACE);
+        ctx->n_wall += hflags[c] == CELL_WALL;
         (void)x;
         if (hflags[c] != CELL_EDGE) continue;
         uint32_t w[3] = {0, 0, 0};
@@ -486,7 +488,8 @@ static void step_launch(lbm_ctx *ctx, const StepArgs &a, bool odd, bool epi)
     default: launch_step_f16c(a, odd, epi, ctx->plain, ctx->block_x, ctx->block_y, ctx->stream, e1, e2); break;
     }
     if (e2) cudaEventRecord(e3, ctx->stream);
-    ctx->launches += 1 + (a.n_edge > 0 ? 1 : 0) + (a.face_x_hi == FACE_OUTFLOW ? 1 : 0) + (a.n_qlinks > 0 ? 1 : 0);
+    ctx->launches += 1 + (a.n_edge > 0 || a.n_wall > 0 ? 1 : 0) + (a.face_x_hi == FACE_OUTFLOW ? 1 : 0) +
+                     (a.n_qlinks > 0 ? 1 : 0);
 }
 
 // Outflow planes of the state before a step of parity `odd` (the convective
@@ -1010,6 +1013,7 @@ extern "C" lbm_status lbm_get_info(const lbm_ctx *ctx, lbm_info *out)
     out->edge_cells = ctx->n_edge;
     out->bulk_cells = ctx->n_bulk;
     out->interior_cells = ctx->n_bulk;
+    out->wall_cells = ctx->n_wall;
     out->launches = ctx->launches;
     out->workspace_bytes = ctx->L.total;
     out->storage = ctx->p.storage;
@@ -1210,7 +1214,7 @@ struct lbm_batch {
     cudaStream_t user = nullptr, own = nullptr;
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     BatchMember *d_mem = nullptr;
-    int64_t *d_bbegin = nullptr, *d_ebegin = nullptr, *d_qbegin = nullptr, *d_t = nullptr;
+    int64_t *d_bbegin = nullptr, *d_ebegin = nullptr, *d_qbegin = nullptr, *d_wbegin = nullptr, *d_t = nullptr;
     std::vector<int> live;              // members in the current table
     BatchLaunch launch{};
     cudaGraphExec_t graph = nullptr;
@@ -1244,6 +1248,7 @@ extern "C" lbm_status lbm_batch_destroy(lbm_batch *b)
     if (b->d_bbegin) cudaFree(b->d_bbegin);
     if (b->d_ebegin) cudaFree(b->d_ebegin);
     if (b->d_qbegin) cudaFree(b->d_qbegin);
+    if (b->d_wbegin) cudaFree(b->d_wbegin);
     if (b->d_t) cudaFree(b->d_t);
     if (b->ev_in) cudaEventDestroy(b->ev_in);
     if (b->ev_out) cudaEventDestroy(b->ev_out);
@@ -1303,6 +1308,7 @@ extern "C" lbm_status lbm_batch_create(int32_t n, const lbm_grid *grids, const u
         cudaMalloc(&b->d_bbegin, sizeof(int64_t) * (n + 1)) != cudaSuccess ||
         cudaMalloc(&b->d_ebegin, sizeof(int64_t) * (n + 1)) != cudaSuccess ||
         cudaMalloc(&b->d_qbegin, sizeof(int64_t) * (n + 1)) != cudaSuccess ||
+        cudaMalloc(&b->d_wbegin, sizeof(int64_t) * (n + 1)) != cudaSuccess ||
         cudaMalloc(&b->d_t, sizeof(int64_t)) != cudaSuccess ||
         cudaMemset(b->d_t, 0, sizeof(int64_t)) != cudaSuccess)
         st = LBM_ERR_CUDA;
@@ -1372,7 +1378,8 @@ extern "C" lbm_status lbm_batch_set_flowthroughs(lbm_batch *b, double n_ft)
 static lbm_status batch_rebuild(lbm_batch *b, const std::vector<int> &live)
 {
     std::vector<BatchMember> mem(live.size());
-    std::vector<int64_t> bb(live.size() + 1, 0), eb(live.size() + 1, 0), qb(live.size() + 1, 0);
+    std::vector<int64_t> bb(live.size() + 1, 0), eb(live.size() + 1, 0), qb(live.size() + 1, 0),
+        wb(live.size() + 1, 0);
     for (size_t k = 0; k < live.size(); ++k) {
         lbm_ctx *c = b->members[live[k]];
         BatchMember &M = mem[k];
@@ -1390,8 +1397,10 @@ static lbm_status batch_rebuild(lbm_batch *b, const std::vector<int> &live)
         bb[k + 1] = bb[k] + (int64_t)M.gx * M.gy * c->g.nz;
         eb[k + 1] = eb[k] + (c->n_edge + EDGE_BLOCK - 1) / EDGE_BLOCK;
         qb[k + 1] = qb[k] + (c->n_qlinks + EDGE_BLOCK - 1) / EDGE_BLOCK;
+        M.wx = (c->g.nx + WALL_BLOCK - 1) / WALL_BLOCK;
+        wb[k + 1] = wb[k] + (c->n_wall > 0 ? (int64_t)M.wx * wall_rows(c->g.ny, c->g.nz) : 0);
     }
-    if (bb.back() >= (int64_t(1) << 31) || eb.back() >= (int64_t(1) << 31))
+    if (bb.back() >= (int64_t(1) << 31) || eb.back() >= (int64_t(1) << 31) || wb.back() >= (int64_t(1) << 31))
         return batch_fail(b, LBM_ERR_ARG, "batch too large for one launch");
     BCK(cudaMemcpyAsync(b->d_mem, mem.data(), sizeof(BatchMember) * mem.size(), cudaMemcpyHostToDevice, b->own));
     BCK(cudaMemcpyAsync(b->d_bbegin, bb.data(), sizeof(int64_t) * bb.size(), cudaMemcpyHostToDevice, b->own));
@@ -1404,9 +1413,10 @@ static lbm_status batch_rebuild(lbm_batch *b, const std::vector<int> &live)
             out_chunks = std::max<int>(out_chunks, (int)std::min<int64_t>((9 * (int64_t)c->g.ny * c->g.nz + 255) / 256, 256));
     }
     BCK(cudaMemcpyAsync(b->d_qbegin, qb.data(), sizeof(int64_t) * qb.size(), cudaMemcpyHostToDevice, b->own));
+    BCK(cudaMemcpyAsync(b->d_wbegin, wb.data(), sizeof(int64_t) * wb.size(), cudaMemcpyHostToDevice, b->own));
     BCK(cudaStreamSynchronize(b->own));
     b->launch = BatchLaunch{b->d_mem, b->d_bbegin, b->d_ebegin, (int)live.size(), bb.back(), eb.back(), b->d_t,
-                            b->block_x, b->block_y, out_chunks, b->d_qbegin, qb.back()};
+                            b->block_x, b->block_y, out_chunks, b->d_qbegin, qb.back(), b->d_wbegin, wb.back()};
     if (b->graph) {
         cudaGraphExecDestroy(b->graph);
         b->graph = nullptr;
@@ -1484,7 +1494,8 @@ extern "C" lbm_status lbm_batch_run(lbm_batch *b, int64_t nsteps)
         b->updates += cells * (seg_end - b->t);
         b->graph_launches += chunks;
         b->kernel_launches += chunks * b->chunk *
-                              (2 + (b->launch.edge_blocks > 0 ? 1 : 0) + (b->launch.out_chunks > 0 ? 1 : 0) +
+                              (2 + (b->launch.edge_blocks + b->launch.w_blocks > 0 ? 1 : 0) +
+                               (b->launch.out_chunks > 0 ? 1 : 0) +
                                (b->launch.q_blocks > 0 ? 1 : 0));
         b->t = seg_end;
     }

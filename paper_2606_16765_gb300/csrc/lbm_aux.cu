@@ -9,7 +9,17 @@ namespace lbm {
 // ---------------------------------------------------------------------------
 // cell flags: solid, or edge (some neighbour outside the domain or solid)
 // ---------------------------------------------------------------------------
-__global__ void k_flags(const uint8_t *mask, uint8_t *flags, int nx, int ny, int nz, int xface_lo, int xface_hi)
+// Cell classes.  A fluid cell is an edge cell when it has an obstacle
+// neighbour or one of its links crosses a periodic face (wrap-around).  A
+// fluid cell whose boundary links all cross one x face (inlet/outlet planes)
+// is an x-face cell, updated by the bulk kernel; one whose boundary links all
+// cross no-slip lateral walls is a wall cell, updated by the wall-row blocks
+// of the edge kernel.
+// Where an x face meets a wall the cells stay edge cells, and so do the wall
+// rows of a grid less than two cells wide in y or z (where the rows y = 0 and
+// y = ny - 1, or z = 0 and z = nz - 1, coincide).
+__global__ void k_flags(const uint8_t *mask, uint8_t *flags, int nx, int ny, int nz, int xface_lo, int xface_hi,
+                        int wall_y, int wall_z)
 {
     const int64_t n = (int64_t)nx * ny * nz;
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x) {
@@ -25,24 +35,24 @@ __global__ void k_flags(const uint8_t *mask, uint8_t *flags, int nx, int ny, int
                         if (mask[xx + (int64_t)nx * (yy + (int64_t)ny * zz)]) solid_nbr = true;
                     }
         }
-        const bool yz_face = y == 0 || z == 0 || y == ny - 1 || z == nz - 1;
+        const bool y_face = y == 0 || y == ny - 1, z_face = z == 0 || z == nz - 1;
         const bool x_face = x == 0 || x == nx - 1;
+        // every face a link of this cell crosses must be non-periodic; a grid
+        // one cell thick in x has both x faces on one cell: edge kernel
+        const bool x_ok = !x_face || (nx >= 2 && (x == 0 ? xface_lo : xface_hi));
+        const bool w_ok = (!y_face || (wall_y && ny >= 2)) && (!z_face || (wall_z && nz >= 2));
         uint8_t fl = 0;
-        if (solid_nbr || yz_face) {
-            fl = CELL_EDGE;
-        } else if (x_face) {
-            // only the links through one non-periodic x face need a rule
-            const bool ok = nx >= 2 && (x == 0 ? xface_lo : xface_hi);
-            fl = ok ? CELL_XFACE : CELL_EDGE;
-        }
+        if (solid_nbr || !x_ok || !w_ok || (x_face && (y_face || z_face))) fl = CELL_EDGE;
+        else if (x_face) fl = CELL_XFACE;
+        else if (y_face || z_face) fl = CELL_WALL;
         flags[c] = fl;
     }
 }
 
 void launch_flags(const uint8_t *mask, uint8_t *flags, int nx, int ny, int nz, bool xface_lo, bool xface_hi,
-                  cudaStream_t s)
+                  bool wall_y, bool wall_z, cudaStream_t s)
 {
-    k_flags<<<1216, 256, 0, s>>>(mask, flags, nx, ny, nz, xface_lo, xface_hi);
+    k_flags<<<1216, 256, 0, s>>>(mask, flags, nx, ny, nz, xface_lo, xface_hi, wall_y, wall_z);
 }
 
 

@@ -19,6 +19,8 @@ namespace lbm {
 constexpr int Q = 27;
 // threads per block of the edge-cell kernel (also sizes the force partials)
 constexpr int EDGE_BLOCK = 128;
+// threads per wall-row block of the edge kernel (one row segment of cells along x)
+constexpr int WALL_BLOCK = 128;
 
 // Velocity components of direction i = (cx+1) + 3(cy+1) + 9(cz+1).
 __host__ __device__ constexpr int cx_of(int i) { return i % 3 - 1; }
@@ -30,10 +32,28 @@ __host__ __device__ constexpr double w_of(int i) { return tw(i % 3) * tw((i / 3)
 // Moments of t about the mean in one dimension: order 0 -> 1, 1 -> 0, 2 -> 1/3.
 __host__ __device__ constexpr double zw(int a) { return a == 0 ? 1.0 : (a == 1 ? 0.0 : 1.0 / 3.0); }
 
-// cell classes: solid, edge (boundary-aware kernel), x-face (an inlet or
+// cell classes: solid; edge (boundary-aware kernel); x-face (an inlet or
 // outlet plane cell whose only boundary links cross that x face; handled by
-// the row-end variant of the bulk kernel); 0 = bulk
-enum : uint8_t { CELL_SOLID = 1, CELL_EDGE = 2, CELL_XFACE = 4 };
+// the row-end variant of the bulk kernel); wall (a cell in a row next to a
+// no-slip lateral wall whose only boundary links cross that wall; handled by
+// the wall-row blocks of the edge kernel); 0 = bulk
+enum : uint8_t { CELL_SOLID = 1, CELL_EDGE = 2, CELL_XFACE = 4, CELL_WALL = 8 };
+// Rows (y, z) next to a lateral wall, numbered y = 0 (nz rows), y = ny - 1
+// (nz rows), then z = 0 and z = nz - 1 for 0 < y < ny - 1 (ny - 2 rows each):
+// distinct rows when ny, nz >= 2 (wall cells exist only then).
+__host__ __device__ constexpr int64_t wall_rows(int ny, int nz)
+{
+    return 2 * (int64_t)nz + 2 * (int64_t)(ny > 2 ? ny - 2 : 0);
+}
+__host__ __device__ inline void wall_row_yz(int64_t r, int ny, int nz, int &y, int &z)
+{
+    if (r < nz) { y = 0; z = (int)r; return; }
+    if (r < 2 * (int64_t)nz) { y = ny - 1; z = (int)(r - nz); return; }
+    const int64_t k = r - 2 * (int64_t)nz, m = ny - 2;
+    if (k < m) { z = 0; y = 1 + (int)k; return; }
+    z = nz - 1; y = 1 + (int)(k - m);
+}
+
 // face kinds (lbm_face): x high is either the anti-bounce-back pressure
 // outlet or the convective extrapolation outflow
 enum { FACE_WALL = 0, FACE_PERIODIC = 1, FACE_INLET = 2, FACE_OUTLET = 3, FACE_OUTFLOW = 4 };
@@ -137,6 +157,7 @@ struct StepArgs {
     unsigned int *fcount;   // arrival counter of the last-block reduction
     double *fout;           // force row of this step (3 doubles)
     int *status;            // latched device conditions
+    int64_t n_wall;         // cells of class CELL_WALL (0: no wall-row blocks)
 };
 
 // Member of a batched launch (device memory): the static arguments of the
@@ -148,6 +169,7 @@ struct BatchMember {
     double *force;          // force rows indexed by t / force_every (null: off)
     int64_t force_every;
     int32_t gx, gy;         // bulk blocks along x and y per z plane
+    int32_t wx;             // wall-row blocks along x (WALL_BLOCK cells each)
 };
 
 // One batched step: device member table and block numbering.
@@ -162,6 +184,8 @@ struct BatchLaunch {
     int out_chunks;             // outflow: blocks per member along its outlet plane (0: none)
     const int64_t *q_begin;     // nm + 1 entries (first wall-distance block per member)
     int64_t q_blocks;           // wall-distance blocks in all (0: none)
+    const int64_t *w_begin;     // nm + 1 entries (first wall-row block per member)
+    int64_t w_blocks;           // wall-row blocks in all (0: none)
 };
 
 // A parameter in the compute type: the FP32 copy for float kernels.

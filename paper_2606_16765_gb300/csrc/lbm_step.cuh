@@ -9,10 +9,13 @@
 // slot i (bounce-back and its inlet/outlet variants), so the set of memory
 // locations a cell reads is exactly the set it writes and cells never race.
 //
-// Cells are split in two classes: bulk cells (all 26 neighbours are in-domain
-// fluid) take the branch-free kernel below with fully coalesced accesses;
-// edge cells (a wall, the inlet/outlet plane, an obstacle or a periodic wrap
-// next to them) go through a compact list and the general kernel.
+// Cells are split in classes: bulk cells (all 26 neighbours are in-domain
+// fluid, or the only boundary links cross one x face) take the branch-free
+// kernel below with fully coalesced accesses; edge cells (an obstacle, a
+// periodic wrap, or both an x face and a wall next to them) go through a
+// compact list and the general kernel; wall cells (rows next to a no-slip
+// lateral wall) take the bulk access pattern in extra blocks of the edge
+// kernel's launch, one block per row segment.
 #pragma once
 
 #include "lbm_device.cuh"
@@ -143,6 +146,54 @@ __global__ void __launch_bounds__(256) k_step_bulk(StepArgs a)
     const int y = (int)(blockIdx.y * blockDim.y + threadIdx.y);
     if (x >= a.nx || y >= a.ny) return;
     bulk_cell<S, ODD, EPI, PLAIN>(a, step_out(a), x, y, (int)blockIdx.z);
+}
+
+// Directions whose component `axis` (0 = x, 1 = y, 2 = z) equals `sign`, as
+// a 27-bit mask.
+__host__ __device__ constexpr uint32_t dir_mask(int axis, int sign)
+{
+    uint32_t m = 0;
+    for (int i = 0; i < Q; ++i)
+        if ((axis == 0 ? cx_of(i) : (axis == 1 ? cy_of(i) : cz_of(i))) == sign) m |= 1u << i;
+    return m;
+}
+
+// Wall cells (class CELL_WALL): the bulk update with halfway bounce-back on
+// the links that cross a lateral wall.  In the odd step such a link gathers
+// the cell's own slot i (written by the previous step with the post-collision
+// population 26 - i) and the population heading into the wall returns into
+// the own slot; the even step is local, as for every cell.  A row's cells
+// share y and z, so the wall mask is uniform over a block.  The epilogue
+// checks its targets at run time (EPI = true) like the edge kernel's.
+template <class S, bool ODD, bool EPI, bool PLAIN>
+__device__ __forceinline__ void wall_cell(const StepArgs &a, const StepOut &o, int x, int y, int z)
+{
+    using T = Store<S>;
+    using R = typename T::R;
+    const int64_t c = (int64_t)x + (int64_t)a.nx * ((int64_t)y + (int64_t)a.ny * z);
+    if (a.flags[c] != CELL_WALL) return;
+    const char *q = reinterpret_cast<const char *>(a.pdf) + c * (int64_t)sizeof(S);
+    const int64_t *gof = a.boff[ODD ? 2 : 0], *sof = a.boff[ODD ? 3 : 1];
+    // bit i: the link of pull direction i (from x - c_i) crosses a wall
+    const uint32_t wmask = (y == 0 ? dir_mask(1, 1) : 0u) | (y == a.ny - 1 ? dir_mask(1, -1) : 0u) |
+                           (z == 0 ? dir_mask(2, 1) : 0u) | (z == a.nz - 1 ? dir_mask(2, -1) : 0u);
+    R f[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const int64_t off = (ODD && ((wmask >> i) & 1u)) ? a.boff[0][i] : gof[i];
+        f[i] = T::ld(reinterpret_cast<const S *>(q + off));
+    }
+    R drho, ux, uy, uz;
+    collide<R, PLAIN>(f, rates_of<R>(a), drho, ux, uy, uz);
+    check_density(drho, a.status);
+#pragma unroll
+    for (int j = 0; j < Q; ++j) {
+        // population j heads to x + c_j = x - c_i, i = 26 - j
+        const int i = Q - 1 - j;
+        const int64_t off = (ODD && ((wmask >> i) & 1u)) ? a.boff[0][i] : sof[j];
+        T::st(reinterpret_cast<S *>(const_cast<char *>(q) + off), f[j]);
+    }
+    if (EPI) epilogue<R>(a, o, c, drho, ux, uy, uz);
 }
 
 // Sum a double over the block into partials[blockIdx]; the last block to
@@ -286,16 +337,31 @@ __device__ __forceinline__ void edge_cell(const StepArgs &a, const StepOut &o, i
     }
 }
 
-// Single-grid edge kernel: one thread per record of the compact list.
+static_assert(WALL_BLOCK == EDGE_BLOCK, "wall-row blocks run in the edge kernel's launch");
+
+// Single-grid edge kernel: blocks [0, eblocks) take one record of the compact
+// list per thread; the blocks after them take the wall rows, block b covering
+// cells [(b % wx) WALL_BLOCK, ...) of wall row b / wx (they have no obstacle
+// links and stay out of the force reduction).
 template <class S, bool ODD, bool PLAIN>
-__global__ void __launch_bounds__(EDGE_BLOCK) k_step_edge(StepArgs a)
+__global__ void __launch_bounds__(EDGE_BLOCK) k_step_edge(StepArgs a, int eblocks, int wx)
 {
     using R = typename Store<S>::R;
-    const int64_t k = (int64_t)blockIdx.x * EDGE_BLOCK + threadIdx.x;
     const StepOut o = step_out(a);
+    if ((int)blockIdx.x >= eblocks) {
+        const int64_t b = (int64_t)blockIdx.x - eblocks, r = b / wx;
+        const int x = (int)(b - r * wx) * WALL_BLOCK + (int)threadIdx.x;
+        if (x < a.nx) {
+            int y, z;
+            wall_row_yz(r, a.ny, a.nz, y, z);
+            wall_cell<S, ODD, true, PLAIN>(a, o, x, y, z);
+        }
+        return;
+    }
+    const int64_t k = (int64_t)blockIdx.x * EDGE_BLOCK + threadIdx.x;
     R fx = R(0), fy = R(0), fz = R(0);     // this cell's obstacle force
     if (k < a.n_edge) edge_cell<S, ODD, PLAIN>(a, o, k, fx, fy, fz);
-    if (o.fpart) block_force_reduce(o, blockIdx.x, gridDim.x, (double)fx, (double)fy, (double)fz);
+    if (o.fpart) block_force_reduce(o, blockIdx.x, eblocks, (double)fx, (double)fy, (double)fz);
 }
 
 // Convective outflow, between steps (one thread per outlet column y, z).
@@ -488,11 +554,28 @@ __global__ void __launch_bounds__(256) k_batch_bulk(const BatchMember *mem, cons
     bulk_cell<S, ODD, EPI, PLAIN>(B.a, o, x, y, z);
 }
 
+// Batched edge kernel: blocks [0, eblocks) are the members' edge blocks,
+// the blocks after them the members' wall-row blocks (numbered by w_begin).
 template <class S, bool ODD, bool PLAIN>
 __global__ void __launch_bounds__(EDGE_BLOCK) k_batch_edge(const BatchMember *mem, const int64_t *begin, int nm,
-                                                           const int64_t *tdev, int epi)
+                                                           const int64_t *tdev, int epi, int64_t eblocks,
+                                                           const int64_t *w_begin)
 {
     using R = typename Store<S>::R;
+    if ((int64_t)blockIdx.x >= eblocks) {
+        const int64_t b = (int64_t)blockIdx.x - eblocks;
+        const int m = find_member(w_begin, nm, b);
+        const BatchMember &B = mem[m];
+        const int64_t local = b - w_begin[m], r = local / B.wx;
+        const int x = (int)(local - r * B.wx) * WALL_BLOCK + (int)threadIdx.x;
+        if (x >= B.a.nx) return;
+        int y, z;
+        wall_row_yz(r, B.a.ny, B.a.nz, y, z);
+        StepOut o{nullptr, nullptr, nullptr, nullptr, nullptr};
+        if (epi && samples_at(B, *tdev)) o.msum = B.msum;
+        wall_cell<S, ODD, true, PLAIN>(B.a, o, x, y, z);
+        return;
+    }
     const int m = find_member(begin, nm, blockIdx.x);
     const BatchMember &B = mem[m];
     const int64_t lb = (int64_t)blockIdx.x - begin[m], nb = begin[m + 1] - begin[m];
@@ -553,7 +636,7 @@ template <class S>
 void launch_batch_step_t(const BatchLaunch &L, bool odd, bool epi, bool plain, cudaStream_t s)
 {
     const dim3 blk(L.block_x, L.block_y);
-    const unsigned nb = (unsigned)L.bulk_blocks, ne = (unsigned)L.edge_blocks;
+    const unsigned nb = (unsigned)L.bulk_blocks, ne = (unsigned)(L.edge_blocks + L.w_blocks);
 #define LBM_BB(O, E, P) k_batch_bulk<S, O, E, P><<<nb, blk, 0, s>>>(L.mem, L.bulk_begin, L.nm, L.t)
     if (plain) {
         if (odd) { if (epi) LBM_BB(true, true, true); else LBM_BB(true, false, true); }
@@ -565,11 +648,12 @@ void launch_batch_step_t(const BatchLaunch &L, bool odd, bool epi, bool plain, c
 #undef LBM_BB
     if (ne > 0) {
         if (plain) {
-            if (odd) k_batch_edge<S, true, true><<<ne, EDGE_BLOCK, 0, s>>>(L.mem, L.edge_begin, L.nm, L.t, epi);
-            else     k_batch_edge<S, false, true><<<ne, EDGE_BLOCK, 0, s>>>(L.mem, L.edge_begin, L.nm, L.t, epi);
+#define LBM_BE(O, P) k_batch_edge<S, O, P><<<ne, EDGE_BLOCK, 0, s>>>(L.mem, L.edge_begin, L.nm, L.t, epi, \
+                                                                    L.edge_blocks, L.w_begin)
+            if (odd) LBM_BE(true, true); else LBM_BE(false, true);
         } else {
-            if (odd) k_batch_edge<S, true, false><<<ne, EDGE_BLOCK, 0, s>>>(L.mem, L.edge_begin, L.nm, L.t, epi);
-            else     k_batch_edge<S, false, false><<<ne, EDGE_BLOCK, 0, s>>>(L.mem, L.edge_begin, L.nm, L.t, epi);
+            if (odd) LBM_BE(true, false); else LBM_BE(false, false);
+#undef LBM_BE
         }
     }
     if (L.q_blocks > 0)
@@ -593,14 +677,17 @@ void launch_step_t(const StepArgs &a, bool odd, bool epi, bool plain, int block_
         else     { if (epi) launch_bulk<S, false, true, false>(a, bx, by, s, e); else launch_bulk<S, false, false, false>(a, bx, by, s, e); }
     }
     if (ev_bulk) cudaEventRecord(ev_bulk, s);
-    if (a.n_edge > 0) {
-        const dim3 eg((unsigned)((a.n_edge + EDGE_BLOCK - 1) / EDGE_BLOCK));
+    if (a.n_edge > 0 || a.n_wall > 0) {
+        const int eb = (int)((a.n_edge + EDGE_BLOCK - 1) / EDGE_BLOCK);
+        const int wx = (a.nx + WALL_BLOCK - 1) / WALL_BLOCK;
+        const int64_t wb = a.n_wall > 0 ? (int64_t)wx * wall_rows(a.ny, a.nz) : 0;
+        const dim3 eg((unsigned)(eb + wb));
         if (plain) {
-            if (odd) k_step_edge<S, true, true><<<eg, EDGE_BLOCK, 0, s>>>(a);
-            else     k_step_edge<S, false, true><<<eg, EDGE_BLOCK, 0, s>>>(a);
+            if (odd) k_step_edge<S, true, true><<<eg, EDGE_BLOCK, 0, s>>>(a, eb, wx);
+            else     k_step_edge<S, false, true><<<eg, EDGE_BLOCK, 0, s>>>(a, eb, wx);
         } else {
-            if (odd) k_step_edge<S, true, false><<<eg, EDGE_BLOCK, 0, s>>>(a);
-            else     k_step_edge<S, false, false><<<eg, EDGE_BLOCK, 0, s>>>(a);
+            if (odd) k_step_edge<S, true, false><<<eg, EDGE_BLOCK, 0, s>>>(a, eb, wx);
+            else     k_step_edge<S, false, false><<<eg, EDGE_BLOCK, 0, s>>>(a, eb, wx);
         }
     }
     launch_qbb<S>(a, !odd, s);

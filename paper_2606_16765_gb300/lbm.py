@@ -46,7 +46,7 @@ class lbm_info(C.Structure):
     _fields_ = [("cells", C.c_int64), ("fluid_cells", C.c_int64), ("edge_cells", C.c_int64),
                 ("bulk_cells", C.c_int64), ("launches", C.c_int64), ("workspace_bytes", C.c_uint64),
                 ("storage", C.c_int32), ("block_x", C.c_int32), ("omega1", C.c_double),
-                ("interior_cells", C.c_int64)]
+                ("interior_cells", C.c_int64), ("wall_cells", C.c_int64)]
 
 
 class lbm_timing_report(C.Structure):

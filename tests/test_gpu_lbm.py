@@ -234,6 +234,13 @@ def box_cases():
                                       noise=(22, 2e-3)),
         "outflow_nx2": K.case((2, 5, 4), None, omega1=1.5, faces=OUTFLOW, noise=(23, 2e-3)),
         "outflow_nx1": K.case((1, 3, 3), None, omega1=1.5, faces=OUTFLOW, noise=(24, 2e-3)),
+        # wall-row kernel: rows y = 0 and y = ny - 1 adjacent (ny = nz = 2),
+        # one periodic lateral face, rows longer than one block (nx > 128)
+        "wall_rows_2x2": K.case((20, 2, 2), None, omega1=1.6, faces=OUTFLOW, noise=(25, 2e-3)),
+        "wall_y_periodic_z": K.case(g, obs, omega1=1.7, faces=("inlet", "outflow", "wall", "periodic"),
+                                    noise=(26, 2e-3)),
+        "wall_rows_long": K.case((150, 6, 4), I.sphere((150, 6, 4), (40.0, 2.5, 1.5), 1.5), omega1=1.8,
+                                 faces=OUTFLOW, noise=(27, 2e-3)),
     }
 
 
@@ -257,6 +264,21 @@ def test_small_boxes(name, storage):
         tol = 1e-14 if storage == "f64" else 2e-7
         assert err <= tol, (name, storage, L.t, err)
     s.sync()
+
+
+def test_cell_classes_cover_the_fluid():
+    # every fluid cell is updated by exactly one of the bulk, wall-row and
+    # edge kernels; a walled channel has wall-row cells, a periodic one none
+    g = (37, 13, 11)
+    obs = I.sphere(g, (9.0, 6.0, 5.0), 3.0)
+    s = K.make_solver(K.case(g, obs, faces=OUTFLOW), "f32")
+    i = s.info()
+    assert i.fluid_cells == int((obs == 0).sum())
+    assert i.bulk_cells + i.wall_cells + i.edge_cells == i.fluid_cells
+    # rows next to the four walls, minus the x-face corners and the cells next to the sphere
+    assert 0 < i.wall_cells <= 2 * (g[0] - 2) * (g[1] + g[2] - 2)
+    p = K.make_solver(K.case(g, obs, faces=("inlet", "outflow", "periodic", "periodic")), "f32").info()
+    assert p.wall_cells == 0 and p.bulk_cells + p.edge_cells == p.fluid_cells
 
 
 def test_plain_fast_path_equals_general_path():
