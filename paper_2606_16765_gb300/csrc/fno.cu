@@ -22,6 +22,7 @@
 //   k_mse_*      masked mean square error and its gradient (deterministic)
 //   k_adam       Adam update of the flat parameter vector
 #include <cmath>
+#include <type_traits>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -782,6 +783,93 @@ __global__ void __launch_bounds__(TPB) k_dftx_fwd(const TI *x, float2 *A, const 
                 for (int r = 0; r < DFT_RT; ++r)
                     if (warp * DFT_RT + r < nr) A[(r0 + warp * DFT_RT + r) * d.Kx + j] = acc[r];
             }
+        }
+    }
+}
+
+// The same forward x stage on tensor cores, for BF16 rows of nx = 128
+// samples and Kx = 32 modes: A[R][32] = rows[R][128] T[128][64] with
+// T[x][2j] = Re twx[x][j], T[x][2j + 1] = Im twx[x][j], as mma.sync
+// m16n8k16 products (BF16 operands, FP32 accumulation); the transform is a
+// dense contraction, and as such this stage is bound by its 0.5 KB of HBM
+// traffic per row rather than by FP32 multiply-adds.  The samples are exact
+// BF16; each twiddle enters as a BF16 pair hi + lo (hi = bf16(t),
+// lo = bf16(t - hi)), two products per tile, so that the table keeps about
+// 2^-17 relative error.  A warp takes 16 rows per pass.  Lane (g, c)
+// (g = lane / 4, c = lane % 4) loads the 32 consecutive samples
+// x in [32c, 32c + 32) of rows g and g + 8 with 16-byte loads, and the
+// contraction index is permuted to match: in k-step s, fragment column
+// 2c + {0, 1} is sample 32c + 4s + {0, 1} and column 2c + 8 + {0, 1} is
+// sample 32c + 4s + {2, 3}.  The table is stored in that order, fragment by
+// fragment, so a lane reads its two B registers with one 8-byte load.
+constexpr int TCX_NX = 128, TCX_KX = 32;
+
+__device__ __forceinline__ uint32_t pack_bf16_pair(__nv_bfloat16 lo, __nv_bfloat16 hi)
+{
+    return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+}
+
+__global__ void __launch_bounds__(TPB) k_dftx_fwd_tc(const __nv_bfloat16 *x, float2 *A, const float2 *twx, int64_t R)
+{
+    __shared__ uint2 bt[2][8 * 8 * 32];     // [hi, lo][(k-step * 8 + n-tile) * 32 + lane]
+    for (int idx = threadIdx.x; idx < 8 * 8 * 32; idx += blockDim.x) {
+        const int st = idx >> 8, nt = (idx >> 5) & 7, l = idx & 31;
+        const int n = 8 * nt + (l >> 2), c = l & 3;
+        const int j = n >> 1, im = n & 1;
+        __nv_bfloat16 h[4], o[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int xs = 32 * c + 4 * st + e;
+            const float2 t = twx[xs * TCX_KX + j];
+            const float v = im ? t.y : t.x;
+            h[e] = __float2bfloat16_rn(v);
+            o[e] = __float2bfloat16_rn(v - __bfloat162float(h[e]));
+        }
+        bt[0][idx] = make_uint2(pack_bf16_pair(h[0], h[1]), pack_bf16_pair(h[2], h[3]));
+        bt[1][idx] = make_uint2(pack_bf16_pair(o[0], o[1]), pack_bf16_pair(o[2], o[3]));
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, c = lane & 3;
+    const int64_t tiles = (R + 15) / 16;
+    for (int64_t tile = (int64_t)blockIdx.x * (TPB / 32) + warp; tile < tiles; tile += (int64_t)gridDim.x * (TPB / 32)) {
+        const int64_t ra = tile * 16 + g, rb = ra + 8;
+        uint4 va[4], vb[4];
+        const uint4 *pa = reinterpret_cast<const uint4 *>(x + ra * TCX_NX + 32 * c);
+        const uint4 *pb = reinterpret_cast<const uint4 *>(x + rb * TCX_NX + 32 * c);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            va[q] = ra < R ? pa[q] : make_uint4(0u, 0u, 0u, 0u);
+            vb[q] = rb < R ? pb[q] : make_uint4(0u, 0u, 0u, 0u);
+        }
+        float acc[8][4];
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) acc[nt][e] = 0.f;
+#pragma unroll
+        for (int st = 0; st < 8; ++st) {
+            const uint4 &ua = va[st >> 1], &ub = vb[st >> 1];
+            const uint32_t a0 = (st & 1) ? ua.z : ua.x, a2 = (st & 1) ? ua.w : ua.y;
+            const uint32_t a1 = (st & 1) ? ub.z : ub.x, a3 = (st & 1) ? ub.w : ub.y;
+#pragma unroll
+            for (int nt = 0; nt < 8; ++nt) {
+#pragma unroll
+                for (int part = 0; part < 2; ++part) {
+                    const uint2 b = bt[part][(st * 8 + nt) * 32 + lane];
+                    asm volatile(
+                        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
+                        "{%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, {%0, %1, %2, %3};\n"
+                        : "+f"(acc[nt][0]), "+f"(acc[nt][1]), "+f"(acc[nt][2]), "+f"(acc[nt][3])
+                        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b.x), "r"(b.y));
+                }
+            }
+        }
+        // D: (row g, columns 2c, 2c + 1) and (row g + 8, same columns) of
+        // n-tile nt: the real and imaginary part of mode 4 nt + c
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) {
+            if (ra < R) A[ra * TCX_KX + 4 * nt + c] = make_float2(acc[nt][0], acc[nt][1]);
+            if (rb < R) A[rb * TCX_KX + 4 * nt + c] = make_float2(acc[nt][2], acc[nt][3]);
         }
     }
 }
@@ -1639,8 +1727,15 @@ void dft_fwd(fno_ctx *f, const T *x, float2 *S, const float *scale, int B)
 {
     const Dims d = dims(f, B);
     const int64_t R = d.BC * d.nz * d.ny;
-    k_dftx_fwd<T><<<(int)std::min<int64_t>((R + DFT_ROWS - 1) / DFT_ROWS, 152 * 8), TPB, smem_dftx_fwd(d), f->s>>>(
-        x, f->stA, f->twx, d, R);
+    if (std::is_same<T, __nv_bfloat16>::value && d.nx == TCX_NX && d.Kx == TCX_KX &&
+        (reinterpret_cast<uintptr_t>(x) & 15u) == 0) {
+        const int64_t warps = (R + 15) / 16;
+        k_dftx_fwd_tc<<<(int)std::min<int64_t>((warps + TPB / 32 - 1) / (TPB / 32), 152 * 8), TPB, 0, f->s>>>(
+            reinterpret_cast<const __nv_bfloat16 *>(x), f->stA, f->twx, R);
+    } else {
+        k_dftx_fwd<T><<<(int)std::min<int64_t>((R + DFT_ROWS - 1) / DFT_ROWS, 152 * 8), TPB, smem_dftx_fwd(d),
+                        f->s>>>(x, f->stA, f->twx, d, R);
+    }
     const int64_t Sl = d.BC * d.nz;
     const int SB = dfty_fwd_slabs(d);
     k_dfty_fwd<<<(int)std::min<int64_t>((Sl + SB - 1) / SB, 152 * 8), TPB, smem_dfty_fwd(d), f->s>>>(f->stA, f->stB,

@@ -171,7 +171,9 @@ def test_full_size_forward_matches_oracle():
     net.set_params(to_gpu_params(ocfg, p))
     y = net.forward(x)
     yr = F.forward(p, x.astype(np.float64), ocfg)
-    assert rel_l2(y, yr) < 2e-2
+    err = rel_l2(y, yr)
+    print(f"full-size forward (BF16 activations, tensor-core x transform and contraction): rel L2 {err:.3e}")
+    assert err < 2e-2
 
 
 def test_batches_larger_than_max_batch_are_split():
