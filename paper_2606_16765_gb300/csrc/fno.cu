@@ -787,15 +787,16 @@ __global__ void __launch_bounds__(TPB) k_dftx_fwd(const TI *x, float2 *A, const 
     }
 }
 
-// The same forward x stage on tensor cores, for BF16 rows of nx = 128
-// samples and Kx = 32 modes: A[R][32] = rows[R][128] T[128][64] with
+// The same forward x stage on tensor cores, for rows of nx = 128 samples
+// and Kx = 32 modes: A[R][32] = rows[R][128] T[128][64] with
 // T[x][2j] = Re twx[x][j], T[x][2j + 1] = Im twx[x][j], as mma.sync
 // m16n8k16 products (BF16 operands, FP32 accumulation); the transform is a
 // dense contraction, and as such this stage is bound by its 0.5 KB of HBM
-// traffic per row rather than by FP32 multiply-adds.  The samples are exact
-// BF16; each twiddle enters as a BF16 pair hi + lo (hi = bf16(t),
-// lo = bf16(t - hi)), two products per tile, so that the table keeps about
-// 2^-17 relative error.  A warp takes 16 rows per pass.  Lane (g, c)
+// traffic per row rather than by FP32 multiply-adds.  Each twiddle enters
+// as a BF16 pair hi + lo (hi = bf16(t), lo = bf16(t - hi)).  BF16 samples
+// are exact: two products per tile (hi, lo table); FP32 samples are split
+// the same way: three products (hi hi, hi lo, lo hi).  Either keeps about
+// 2^-16 relative error.  A warp takes 16 rows per pass.  Lane (g, c)
 // (g = lane / 4, c = lane % 4) loads the 32 consecutive samples
 // x in [32c, 32c + 32) of rows g and g + 8 with 16-byte loads, and the
 // contraction index is permuted to match: in k-step s, fragment column
@@ -809,7 +810,23 @@ __device__ __forceinline__ uint32_t pack_bf16_pair(__nv_bfloat16 lo, __nv_bfloat
     return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
 }
 
-__global__ void __launch_bounds__(TPB) k_dftx_fwd_tc(const __nv_bfloat16 *x, float2 *A, const float2 *twx, int64_t R)
+__device__ __forceinline__ void split_bf16(float v, __nv_bfloat16 &hi, __nv_bfloat16 &lo)
+{
+    hi = __float2bfloat16_rn(v);
+    lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+}
+
+// acc (m16n8 FP32 fragment) += A (m16k16 BF16: a0..a3) B (k16n8 BF16: b.x, b.y)
+__device__ __forceinline__ void mma_bf16(float *acc, uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, uint2 b)
+{
+    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
+                 "{%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, {%0, %1, %2, %3};\n"
+                 : "+f"(acc[0]), "+f"(acc[1]), "+f"(acc[2]), "+f"(acc[3])
+                 : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b.x), "r"(b.y));
+}
+
+template <class TI>
+__global__ void __launch_bounds__(TPB) k_dftx_fwd_tc(const TI *x, float2 *A, const float2 *twx, int64_t R)
 {
     __shared__ uint2 bt[2][8 * 8 * 32];     // [hi, lo][(k-step * 8 + n-tile) * 32 + lane]
     for (int idx = threadIdx.x; idx < 8 * 8 * 32; idx += blockDim.x) {
@@ -833,34 +850,57 @@ __global__ void __launch_bounds__(TPB) k_dftx_fwd_tc(const __nv_bfloat16 *x, flo
     const int64_t tiles = (R + 15) / 16;
     for (int64_t tile = (int64_t)blockIdx.x * (TPB / 32) + warp; tile < tiles; tile += (int64_t)gridDim.x * (TPB / 32)) {
         const int64_t ra = tile * 16 + g, rb = ra + 8;
-        uint4 va[4], vb[4];
-        const uint4 *pa = reinterpret_cast<const uint4 *>(x + ra * TCX_NX + 32 * c);
-        const uint4 *pb = reinterpret_cast<const uint4 *>(x + rb * TCX_NX + 32 * c);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            va[q] = ra < R ? pa[q] : make_uint4(0u, 0u, 0u, 0u);
-            vb[q] = rb < R ? pb[q] : make_uint4(0u, 0u, 0u, 0u);
-        }
         float acc[8][4];
 #pragma unroll
         for (int nt = 0; nt < 8; ++nt)
 #pragma unroll
             for (int e = 0; e < 4; ++e) acc[nt][e] = 0.f;
+        if (std::is_same<TI, __nv_bfloat16>::value) {
+            uint4 va[4], vb[4];
+            const uint4 *pa = reinterpret_cast<const uint4 *>(x + ra * TCX_NX + 32 * c);
+            const uint4 *pb = reinterpret_cast<const uint4 *>(x + rb * TCX_NX + 32 * c);
 #pragma unroll
-        for (int st = 0; st < 8; ++st) {
-            const uint4 &ua = va[st >> 1], &ub = vb[st >> 1];
-            const uint32_t a0 = (st & 1) ? ua.z : ua.x, a2 = (st & 1) ? ua.w : ua.y;
-            const uint32_t a1 = (st & 1) ? ub.z : ub.x, a3 = (st & 1) ? ub.w : ub.y;
+            for (int q = 0; q < 4; ++q) {
+                va[q] = ra < R ? pa[q] : make_uint4(0u, 0u, 0u, 0u);
+                vb[q] = rb < R ? pb[q] : make_uint4(0u, 0u, 0u, 0u);
+            }
 #pragma unroll
-            for (int nt = 0; nt < 8; ++nt) {
+            for (int st = 0; st < 8; ++st) {
+                const uint4 &ua = va[st >> 1], &ub = vb[st >> 1];
+                const uint32_t a0 = (st & 1) ? ua.z : ua.x, a2 = (st & 1) ? ua.w : ua.y;
+                const uint32_t a1 = (st & 1) ? ub.z : ub.x, a3 = (st & 1) ? ub.w : ub.y;
 #pragma unroll
-                for (int part = 0; part < 2; ++part) {
-                    const uint2 b = bt[part][(st * 8 + nt) * 32 + lane];
-                    asm volatile(
-                        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
-                        "{%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, {%0, %1, %2, %3};\n"
-                        : "+f"(acc[nt][0]), "+f"(acc[nt][1]), "+f"(acc[nt][2]), "+f"(acc[nt][3])
-                        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b.x), "r"(b.y));
+                for (int nt = 0; nt < 8; ++nt) {
+#pragma unroll
+                    for (int part = 0; part < 2; ++part) {
+                        const uint2 b = bt[part][(st * 8 + nt) * 32 + lane];
+                        mma_bf16(acc[nt], a0, a1, a2, a3, b);
+                    }
+                }
+            }
+        } else {
+            const float4 *pa = reinterpret_cast<const float4 *>(x + ra * TCX_NX + 32 * c);
+            const float4 *pb = reinterpret_cast<const float4 *>(x + rb * TCX_NX + 32 * c);
+#pragma unroll
+            for (int st = 0; st < 8; ++st) {
+                // samples 32c + 4st + {0..3} of rows ra and rb
+                const float4 fa = ra < R ? pa[st] : make_float4(0.f, 0.f, 0.f, 0.f);
+                const float4 fb = rb < R ? pb[st] : make_float4(0.f, 0.f, 0.f, 0.f);
+                __nv_bfloat16 ah[8], al[8];
+                split_bf16(fa.x, ah[0], al[0]); split_bf16(fa.y, ah[1], al[1]);
+                split_bf16(fa.z, ah[2], al[2]); split_bf16(fa.w, ah[3], al[3]);
+                split_bf16(fb.x, ah[4], al[4]); split_bf16(fb.y, ah[5], al[5]);
+                split_bf16(fb.z, ah[6], al[6]); split_bf16(fb.w, ah[7], al[7]);
+                const uint32_t h0 = pack_bf16_pair(ah[0], ah[1]), h2 = pack_bf16_pair(ah[2], ah[3]);
+                const uint32_t h1 = pack_bf16_pair(ah[4], ah[5]), h3 = pack_bf16_pair(ah[6], ah[7]);
+                const uint32_t l0 = pack_bf16_pair(al[0], al[1]), l2 = pack_bf16_pair(al[2], al[3]);
+                const uint32_t l1 = pack_bf16_pair(al[4], al[5]), l3 = pack_bf16_pair(al[6], al[7]);
+#pragma unroll
+                for (int nt = 0; nt < 8; ++nt) {
+                    const uint2 bh = bt[0][(st * 8 + nt) * 32 + lane], bl = bt[1][(st * 8 + nt) * 32 + lane];
+                    mma_bf16(acc[nt], h0, h1, h2, h3, bh);
+                    mma_bf16(acc[nt], h0, h1, h2, h3, bl);
+                    mma_bf16(acc[nt], l0, l1, l2, l3, bh);
                 }
             }
         }
@@ -1148,6 +1188,114 @@ __global__ void __launch_bounds__(TPB) k_dftx_inv(const float2 *It, float *out, 
                     if (pre) v *= gelu_grad(ldf(pre + off));
                     out[off] = v;
                 }
+            }
+        }
+    }
+}
+
+// The same inverse x stage on tensor cores for nx = 128 and Kx = 32:
+// out[R][128] (+)= I[R][64] T[64][128], I read as 64 reals per row (the
+// real and imaginary part of each mode in turn) and T[2j][x] = Re twx[x][j],
+// T[2j + 1][x] = Im twx[x][j] (Im twx = -sin, so the sum is the real part
+// of sum_j I_j exp(+i 2 pi k_j x / nx)).  Both operands enter as BF16
+// pairs hi + lo, and three products per tile (hi hi, hi lo, lo hi) keep
+// about 2^-16 relative error.  A warp takes 16 rows per pass.  Lane (g, c)
+// loads the 16 consecutive reals [16c, 16c + 16) of rows g and g + 8 with
+// 16-byte loads; in k-step s, fragment column 2c + {0, 1} is real
+// 16c + 4s + {0, 1} and column 2c + 8 + {0, 1} is real 16c + 4s + {2, 3},
+// and the table is stored in that order, fragment by fragment.  The
+// epilogue adds the previous output (accumulate) and multiplies by
+// gelu'(pre) when pre is given, as the plain kernel does.
+
+template <class TP>
+__global__ void __launch_bounds__(TPB) k_dftx_inv_tc(const float2 *It, float *out, const float2 *twx, int64_t R,
+                                                     int accumulate, const TP *pre)
+{
+    __shared__ uint2 bt[2][4 * 16 * 32];    // [hi, lo][(k-step * 16 + n-tile) * 32 + lane]
+    for (int idx = threadIdx.x; idx < 4 * 16 * 32; idx += blockDim.x) {
+        const int st = idx >> 9, nt = (idx >> 5) & 15, l = idx & 31;
+        const int xs = 8 * nt + (l >> 2), c = l & 3;
+        __nv_bfloat16 h[4], o[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int k = 16 * c + 4 * st + e;          // real index: mode k / 2, part k % 2
+            const float2 t = twx[xs * TCX_KX + (k >> 1)];
+            split_bf16((k & 1) ? t.y : t.x, h[e], o[e]);
+        }
+        bt[0][idx] = make_uint2(pack_bf16_pair(h[0], h[1]), pack_bf16_pair(h[2], h[3]));
+        bt[1][idx] = make_uint2(pack_bf16_pair(o[0], o[1]), pack_bf16_pair(o[2], o[3]));
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, c = lane & 3;
+    const int64_t tiles = (R + 15) / 16;
+    for (int64_t tile = (int64_t)blockIdx.x * (TPB / 32) + warp; tile < tiles; tile += (int64_t)gridDim.x * (TPB / 32)) {
+        const int64_t ra = tile * 16 + g, rb = ra + 8;
+        float4 va[4], vb[4];
+        const float4 *pa = reinterpret_cast<const float4 *>(It + ra * TCX_KX) + 4 * c;
+        const float4 *pb = reinterpret_cast<const float4 *>(It + rb * TCX_KX) + 4 * c;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            va[q] = ra < R ? pa[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+            vb[q] = rb < R ? pb[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        float acc[16][4];
+#pragma unroll
+        for (int nt = 0; nt < 16; ++nt)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) acc[nt][e] = 0.f;
+#pragma unroll
+        for (int st = 0; st < 4; ++st) {
+            // reals 16c + 4st + {0..3} of rows ra (va[st]) and rb (vb[st])
+            __nv_bfloat16 ah[8], al[8];
+            split_bf16(va[st].x, ah[0], al[0]); split_bf16(va[st].y, ah[1], al[1]);
+            split_bf16(va[st].z, ah[2], al[2]); split_bf16(va[st].w, ah[3], al[3]);
+            split_bf16(vb[st].x, ah[4], al[4]); split_bf16(vb[st].y, ah[5], al[5]);
+            split_bf16(vb[st].z, ah[6], al[6]); split_bf16(vb[st].w, ah[7], al[7]);
+            const uint32_t h0 = pack_bf16_pair(ah[0], ah[1]), h2 = pack_bf16_pair(ah[2], ah[3]);
+            const uint32_t h1 = pack_bf16_pair(ah[4], ah[5]), h3 = pack_bf16_pair(ah[6], ah[7]);
+            const uint32_t l0 = pack_bf16_pair(al[0], al[1]), l2 = pack_bf16_pair(al[2], al[3]);
+            const uint32_t l1 = pack_bf16_pair(al[4], al[5]), l3 = pack_bf16_pair(al[6], al[7]);
+#pragma unroll
+            for (int nt = 0; nt < 16; ++nt) {
+                const uint2 bh = bt[0][(st * 16 + nt) * 32 + lane];
+                const uint2 bl = bt[1][(st * 16 + nt) * 32 + lane];
+                asm volatile(
+                    "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
+                    "{%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, {%0, %1, %2, %3};\n"
+                    : "+f"(acc[nt][0]), "+f"(acc[nt][1]), "+f"(acc[nt][2]), "+f"(acc[nt][3])
+                    : "r"(h0), "r"(h1), "r"(h2), "r"(h3), "r"(bh.x), "r"(bh.y));
+                asm volatile(
+                    "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
+                    "{%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, {%0, %1, %2, %3};\n"
+                    : "+f"(acc[nt][0]), "+f"(acc[nt][1]), "+f"(acc[nt][2]), "+f"(acc[nt][3])
+                    : "r"(h0), "r"(h1), "r"(h2), "r"(h3), "r"(bl.x), "r"(bl.y));
+                asm volatile(
+                    "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
+                    "{%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, {%0, %1, %2, %3};\n"
+                    : "+f"(acc[nt][0]), "+f"(acc[nt][1]), "+f"(acc[nt][2]), "+f"(acc[nt][3])
+                    : "r"(l0), "r"(l1), "r"(l2), "r"(l3), "r"(bh.x), "r"(bh.y));
+            }
+        }
+        // D of n-tile nt: samples x = 8 nt + 2c + {0, 1} of rows g and g + 8
+#pragma unroll
+        for (int nt = 0; nt < 16; ++nt) {
+            const int xs = 8 * nt + 2 * c;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int64_t r = h ? rb : ra;
+                if (r >= R) continue;
+                float2 v = make_float2(acc[nt][2 * h], acc[nt][2 * h + 1]);
+                float2 *dst = reinterpret_cast<float2 *>(out + r * TCX_NX + xs);
+                if (accumulate) {
+                    const float2 p0 = *dst;
+                    v.x += p0.x;
+                    v.y += p0.y;
+                }
+                if (pre) {
+                    v.x *= gelu_grad(ldf(pre + r * TCX_NX + xs));
+                    v.y *= gelu_grad(ldf(pre + r * TCX_NX + xs + 1));
+                }
+                *dst = v;
             }
         }
     }
@@ -1727,11 +1875,14 @@ void dft_fwd(fno_ctx *f, const T *x, float2 *S, const float *scale, int B)
 {
     const Dims d = dims(f, B);
     const int64_t R = d.BC * d.nz * d.ny;
-    if (std::is_same<T, __nv_bfloat16>::value && d.nx == TCX_NX && d.Kx == TCX_KX &&
-        (reinterpret_cast<uintptr_t>(x) & 15u) == 0) {
+    // FP32 rows take the tensor-core stage in the BF16-activation
+    // configuration only (whose tolerance covers its 2^-16 rounding); the
+    // FP32 configuration keeps the FP32 stage
+    const bool tc_input = std::is_same<T, __nv_bfloat16>::value || f->c.act_bf16;
+    if (tc_input && d.nx == TCX_NX && d.Kx == TCX_KX && (reinterpret_cast<uintptr_t>(x) & 15u) == 0) {
         const int64_t warps = (R + 15) / 16;
-        k_dftx_fwd_tc<<<(int)std::min<int64_t>((warps + TPB / 32 - 1) / (TPB / 32), 152 * 8), TPB, 0, f->s>>>(
-            reinterpret_cast<const __nv_bfloat16 *>(x), f->stA, f->twx, R);
+        k_dftx_fwd_tc<T><<<(int)std::min<int64_t>((warps + TPB / 32 - 1) / (TPB / 32), 152 * 8), TPB, 0, f->s>>>(
+            x, f->stA, f->twx, R);
     } else {
         k_dftx_fwd<T><<<(int)std::min<int64_t>((R + DFT_ROWS - 1) / DFT_ROWS, 152 * 8), TPB, smem_dftx_fwd(d),
                         f->s>>>(x, f->stA, f->twx, d, R);
@@ -1755,8 +1906,15 @@ void dft_inv(fno_ctx *f, const float2 *S, float *out, const float *scale, int ac
     k_dfty_inv<<<(int)std::min<int64_t>((Sl + SB - 1) / SB, 152 * 8), TPB, smem_dfty_inv(d), f->s>>>(f->stB, f->stA,
                                                                                                   f->twy, d, Sl, SB);
     const int64_t R = d.BC * d.nz * d.ny;
-    k_dftx_inv<TP><<<(int)std::min<int64_t>((R + DFT_ROWS - 1) / DFT_ROWS, 152 * 8), TPB, smem_dftx_inv(d), f->s>>>(
-        f->stA, out, f->twx, d, R, accumulate, pre);
+    if (std::is_same<TP, __nv_bfloat16>::value && d.nx == TCX_NX && d.Kx == TCX_KX &&
+        (reinterpret_cast<uintptr_t>(out) & 7u) == 0) {
+        const int64_t warps = (R + 15) / 16;
+        k_dftx_inv_tc<TP><<<(int)std::min<int64_t>((warps + TPB / 32 - 1) / (TPB / 32), 152 * 8), TPB, 0, f->s>>>(
+            f->stA, out, f->twx, R, accumulate, pre);
+    } else {
+        k_dftx_inv<TP><<<(int)std::min<int64_t>((R + DFT_ROWS - 1) / DFT_ROWS, 152 * 8), TPB, smem_dftx_inv(d),
+                         f->s>>>(f->stA, out, f->twx, d, R, accumulate, pre);
+    }
 }
 
 void contract(fno_ctx *f, const float2 *Vin, int64_t oR, float2 *Gout, bool adj, int B)

@@ -172,8 +172,33 @@ def test_full_size_forward_matches_oracle():
     y = net.forward(x)
     yr = F.forward(p, x.astype(np.float64), ocfg)
     err = rel_l2(y, yr)
-    print(f"full-size forward (BF16 activations, tensor-core x transform and contraction): rel L2 {err:.3e}")
+    print(f"full-size forward (BF16 activations, tensor-core x transforms and contraction): rel L2 {err:.3e}")
     assert err < 2e-2
+
+
+def test_full_size_gradients_match_oracle():
+    """128x64x64 grid, width 32, modes 16x8x8, 4 layers, BF16 activations and
+    tensor cores (the trained configuration), batch 1: the masked loss and
+    every parameter group's gradient, whose backward runs the tensor-core
+    inverse x transform with accumulation and the GELU derivative."""
+    from paper_2606_16765_gb300 import fno as G
+    ocfg = F.FNOConfig()
+    gcfg = dict(nx=128, ny=64, nz=64, max_batch=8, act_bf16=1, tensor_cores=1)
+    GCFG_CACHE["g"] = gcfg
+    x, t, m, p = problem(ocfg, B=1, seed=31)
+    net = G.FNO(**gcfg)
+    net.set_params(to_gpu_params(ocfg, p))
+    L_gpu = net.loss_grad(x, t, m)
+    y_ref, tape = F.forward(p, x.astype(np.float64), ocfg, keep=True)
+    L_ref = F.masked_mse(y_ref, t.astype(np.float64), m.astype(np.float64))
+    g_ref = F.backward(p, tape, y_ref, t.astype(np.float64), m.astype(np.float64), ocfg)
+    g_gpu = gpu_grads_as_oracle(ocfg, gcfg, net.grads())
+    worst = max(rel_l2(g_gpu[k], g_ref[k]) for k in g_ref)
+    print(f"full-size gradients: loss rel err {abs(L_gpu - L_ref) / L_ref:.2e}, worst group rel L2 {worst:.2e}")
+    assert abs(L_gpu - L_ref) / L_ref < 2e-2
+    for k in g_ref:
+        assert cosine(g_gpu[k], g_ref[k]) > 0.999, k
+        assert rel_l2(g_gpu[k], g_ref[k]) < 3e-2, k
 
 
 def test_batches_larger_than_max_batch_are_split():
