@@ -1301,6 +1301,116 @@ __global__ void __launch_bounds__(TPB) k_dftx_inv_tc(const float2 *It, float *ou
     }
 }
 
+// Inference projection y = Q2 GELU(Q1 v + b1) + b2 on tensor cores, for
+// BF16 activations with 32 channels, 128 hidden units and co <= 8 outputs:
+// a warp takes 16 cells of one sample per pass.  First product: cells x
+// channels (BF16, exact) times Q1^T (BF16 hi + lo pairs, two products per
+// tile), 16 x 128 FP32 accumulators; bias and GELU on the accumulators,
+// which then serve directly as the A fragments of the second product (two
+// adjacent n8 tiles of the first are one k16 step of the second), split into
+// hi + lo; second product against Q2^T (hi + lo; three products per step),
+// 16 x 8 outputs.  The hidden activations never leave registers.  The
+// channels of a cell are planes N apart, so each lane gathers its sixteen
+// BF16 inputs with 2-byte loads (a warp instruction covers 8 consecutive
+// cells of 4 channels).
+constexpr int PTC_CI = 32, PTC_H = 128;
+
+__global__ void __launch_bounds__(TPB, 2) k_proj_tc(const __nv_bfloat16 *v, int co, const float *W1, const float *b1,
+                                                 const float *W2, const float *b2, float *y, int64_t N, int B)
+{
+    __shared__ uint2 q1[2][2 * 16 * 32];    // [hi, lo][(k-step * 16 + n-tile) * 32 + lane]
+    __shared__ uint2 q2[2][8 * 32];         // [hi, lo][k-step * 32 + lane]
+    __shared__ float sb1[PTC_H], sb2[8];
+    for (int idx = threadIdx.x; idx < 2 * 16 * 32; idx += blockDim.x) {
+        const int st = idx >> 9, nt = (idx >> 5) & 15, l = idx & 31;
+        const int hh = 8 * nt + (l >> 2), c = l & 3;
+        const int ks[4] = {16 * st + 2 * c, 16 * st + 2 * c + 1, 16 * st + 2 * c + 8, 16 * st + 2 * c + 9};
+        __nv_bfloat16 h[4], o[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) split_bf16(W1[hh * PTC_CI + ks[e]], h[e], o[e]);
+        q1[0][idx] = make_uint2(pack_bf16_pair(h[0], h[1]), pack_bf16_pair(h[2], h[3]));
+        q1[1][idx] = make_uint2(pack_bf16_pair(o[0], o[1]), pack_bf16_pair(o[2], o[3]));
+    }
+    for (int idx = threadIdx.x; idx < 8 * 32; idx += blockDim.x) {
+        const int st = idx >> 5, l = idx & 31;
+        const int oo = l >> 2, c = l & 3;
+        const int ks[4] = {16 * st + 2 * c, 16 * st + 2 * c + 1, 16 * st + 2 * c + 8, 16 * st + 2 * c + 9};
+        __nv_bfloat16 h[4], o[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) split_bf16(oo < co ? W2[oo * PTC_H + ks[e]] : 0.f, h[e], o[e]);
+        q2[0][idx] = make_uint2(pack_bf16_pair(h[0], h[1]), pack_bf16_pair(h[2], h[3]));
+        q2[1][idx] = make_uint2(pack_bf16_pair(o[0], o[1]), pack_bf16_pair(o[2], o[3]));
+    }
+    for (int k = threadIdx.x; k < PTC_H; k += blockDim.x) sb1[k] = b1[k];
+    if (threadIdx.x < 8) sb2[threadIdx.x] = threadIdx.x < co ? b2[threadIdx.x] : 0.f;
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, c = lane & 3;
+    const int64_t tpb = N / 16, tiles = (int64_t)B * tpb;
+    const unsigned short *vs = reinterpret_cast<const unsigned short *>(v);
+    for (int64_t tile = (int64_t)blockIdx.x * (TPB / 32) + warp; tile < tiles; tile += (int64_t)gridDim.x * (TPB / 32)) {
+        const int64_t b = tile / tpb, n0 = (tile - b * tpb) * 16;
+        const unsigned short *base = vs + b * PTC_CI * N + n0 + g;
+        // A of the first product: (cell g | g + 8, channel pairs 2c, 2c + 1 and 2c + 8, 2c + 9 of each k-step)
+        uint32_t a[2][4];
+#pragma unroll
+        for (int st = 0; st < 2; ++st) {
+            const int ch = 16 * st + 2 * c;
+            const unsigned short *p0 = base + (int64_t)ch * N, *p1 = p0 + N, *p8 = p0 + 8 * N, *p9 = p0 + 9 * N;
+            a[st][0] = (uint32_t)p0[0] | ((uint32_t)p1[0] << 16);
+            a[st][1] = (uint32_t)p0[8] | ((uint32_t)p1[8] << 16);
+            a[st][2] = (uint32_t)p8[0] | ((uint32_t)p9[0] << 16);
+            a[st][3] = (uint32_t)p8[8] | ((uint32_t)p9[8] << 16);
+        }
+        float acc[16][4];
+#pragma unroll
+        for (int nt = 0; nt < 16; ++nt)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) acc[nt][e] = 0.f;
+#pragma unroll
+        for (int st = 0; st < 2; ++st)
+#pragma unroll
+            for (int nt = 0; nt < 16; ++nt) {
+                mma_bf16(acc[nt], a[st][0], a[st][1], a[st][2], a[st][3], q1[0][(st * 16 + nt) * 32 + lane]);
+                mma_bf16(acc[nt], a[st][0], a[st][1], a[st][2], a[st][3], q1[1][(st * 16 + nt) * 32 + lane]);
+            }
+        // hidden units 8 nt + 2c + {0, 1} of cells g and g + 8
+#pragma unroll
+        for (int nt = 0; nt < 16; ++nt) {
+            const float c0 = sb1[8 * nt + 2 * c], c1 = sb1[8 * nt + 2 * c + 1];
+            acc[nt][0] = gelu(acc[nt][0] + c0);
+            acc[nt][1] = gelu(acc[nt][1] + c1);
+            acc[nt][2] = gelu(acc[nt][2] + c0);
+            acc[nt][3] = gelu(acc[nt][3] + c1);
+        }
+        float out[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int s2 = 0; s2 < 8; ++s2) {
+            const float *lo_t = acc[2 * s2], *hi_t = acc[2 * s2 + 1];
+            __nv_bfloat16 h[8], o[8];
+            split_bf16(lo_t[0], h[0], o[0]); split_bf16(lo_t[1], h[1], o[1]);
+            split_bf16(lo_t[2], h[2], o[2]); split_bf16(lo_t[3], h[3], o[3]);
+            split_bf16(hi_t[0], h[4], o[4]); split_bf16(hi_t[1], h[5], o[5]);
+            split_bf16(hi_t[2], h[6], o[6]); split_bf16(hi_t[3], h[7], o[7]);
+            // a0: (cell g, k 2c, 2c+1), a1: (cell g+8, same), a2: (cell g, k 2c+8, +9), a3: (cell g+8, same)
+            const uint32_t h0 = pack_bf16_pair(h[0], h[1]), h1 = pack_bf16_pair(h[2], h[3]);
+            const uint32_t h2 = pack_bf16_pair(h[4], h[5]), h3 = pack_bf16_pair(h[6], h[7]);
+            const uint32_t l0 = pack_bf16_pair(o[0], o[1]), l1 = pack_bf16_pair(o[2], o[3]);
+            const uint32_t l2 = pack_bf16_pair(o[4], o[5]), l3 = pack_bf16_pair(o[6], o[7]);
+            const uint2 bh = q2[0][s2 * 32 + lane], bl = q2[1][s2 * 32 + lane];
+            mma_bf16(out, h0, h1, h2, h3, bh);
+            mma_bf16(out, h0, h1, h2, h3, bl);
+            mma_bf16(out, l0, l1, l2, l3, bh);
+        }
+        // outputs 2c, 2c + 1 of cells g (out[0], out[1]) and g + 8 (out[2], out[3])
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int o = 2 * c + (e & 1);
+            const int64_t n = n0 + g + (e >> 1) * 8;
+            if (o < co) y[(b * co + o) * N + n] = out[e] + sb2[o];
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // mode contraction.  Forward: G[k][b][o] = sum_i V[k][b][i] R[k][i][o];
 // adjoint: gV[k][b][i] = sum_o gG[k][b][o] conj(R[k][i][o]).
@@ -1949,6 +2059,15 @@ lbm_status forward_impl(fno_ctx *f, const float *x, int B, bool keep = true)
     }
     const int H = c.hidden;
     const size_t smf = sizeof(float) * ((size_t)H * 32 + ((H + 3) & ~3) + (size_t)H * 8);
+    if (!keep && std::is_same<T, __nv_bfloat16>::value && W == PTC_CI && H == PTC_H && c.cout <= 8 &&
+        f->N % 16 == 0) {
+        // inference on tensor cores: projection fused, hidden activations in registers
+        const int64_t warps = (int64_t)B * f->N / 16;
+        k_proj_tc<<<(int)std::min<int64_t>((warps + TPB / 32 - 1) / (TPB / 32), 152 * 8), TPB, 0, f->s>>>(
+            reinterpret_cast<const __nv_bfloat16 *>(f->v[c.layers]), c.cout, f->params + f->oQ1_w,
+            f->params + f->oQ1_b, f->params + f->oQ2_w, f->params + f->oQ2_b, f->y, f->N, B);
+        return LBM_OK;
+    }
     if (!keep && W == 32 && f->N % 2 == 0 && smf <= 48 * 1024) {
         // inference: projection fused, hidden activations not stored
         const size_t sm = smf;
