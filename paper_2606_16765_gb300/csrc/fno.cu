@@ -1411,6 +1411,75 @@ __global__ void __launch_bounds__(TPB, 2) k_proj_tc(const __nv_bfloat16 *v, int 
     }
 }
 
+// Pointwise layer y = act(W x + b + extra) on tensor cores for BF16
+// activations with 32 inputs and CO outputs (used for CO = 128): a warp takes 16
+// cells of one sample per pass; cells x inputs (BF16, exact, gathered as in
+// k_proj_tc) times W^T (BF16 hi + lo pairs, two products per tile), FP32
+// accumulators, then bias, the extra (spectral) term, the stored
+// pre-activation and the activation per element.
+template <int CO>
+__global__ void __launch_bounds__(TPB) k_pw_tc(const __nv_bfloat16 *x, const float *W, const float *bias,
+                                               const float *extra, __nv_bfloat16 *pre, __nv_bfloat16 *y, int act,
+                                               int64_t N, int B)
+{
+    constexpr int NT = CO / 8;
+    __shared__ uint2 q[2][2 * NT * 32];     // [hi, lo][(k-step * NT + n-tile) * 32 + lane]
+    __shared__ float sb[CO];
+    for (int idx = threadIdx.x; idx < 2 * NT * 32; idx += blockDim.x) {
+        const int st = idx / (NT * 32), nt = (idx / 32) % NT, l = idx & 31;
+        const int o = 8 * nt + (l >> 2), c = l & 3;
+        const int ks[4] = {16 * st + 2 * c, 16 * st + 2 * c + 1, 16 * st + 2 * c + 8, 16 * st + 2 * c + 9};
+        __nv_bfloat16 h[4], lo[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) split_bf16(W[o * PTC_CI + ks[e]], h[e], lo[e]);
+        q[0][idx] = make_uint2(pack_bf16_pair(h[0], h[1]), pack_bf16_pair(h[2], h[3]));
+        q[1][idx] = make_uint2(pack_bf16_pair(lo[0], lo[1]), pack_bf16_pair(lo[2], lo[3]));
+    }
+    for (int k = threadIdx.x; k < CO; k += blockDim.x) sb[k] = bias[k];
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, c = lane & 3;
+    const int64_t tpb = N / 16, tiles = (int64_t)B * tpb;
+    const unsigned short *xs = reinterpret_cast<const unsigned short *>(x);
+    for (int64_t tile = (int64_t)blockIdx.x * (TPB / 32) + warp; tile < tiles; tile += (int64_t)gridDim.x * (TPB / 32)) {
+        const int64_t b = tile / tpb, n0 = (tile - b * tpb) * 16;
+        const unsigned short *base = xs + b * PTC_CI * N + n0 + g;
+        uint32_t a[2][4];
+#pragma unroll
+        for (int st = 0; st < 2; ++st) {
+            const unsigned short *p0 = base + (int64_t)(16 * st + 2 * c) * N, *p1 = p0 + N, *p8 = p0 + 8 * N,
+                                 *p9 = p0 + 9 * N;
+            a[st][0] = (uint32_t)p0[0] | ((uint32_t)p1[0] << 16);
+            a[st][1] = (uint32_t)p0[8] | ((uint32_t)p1[8] << 16);
+            a[st][2] = (uint32_t)p8[0] | ((uint32_t)p9[0] << 16);
+            a[st][3] = (uint32_t)p8[8] | ((uint32_t)p9[8] << 16);
+        }
+        float acc[NT][4];
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) acc[nt][e] = 0.f;
+#pragma unroll
+        for (int st = 0; st < 2; ++st)
+#pragma unroll
+            for (int nt = 0; nt < NT; ++nt) {
+                mma_bf16(acc[nt], a[st][0], a[st][1], a[st][2], a[st][3], q[0][(st * NT + nt) * 32 + lane]);
+                mma_bf16(acc[nt], a[st][0], a[st][1], a[st][2], a[st][3], q[1][(st * NT + nt) * 32 + lane]);
+            }
+        // element e of n-tile nt: output 8 nt + 2c + (e & 1) of cell g + 8 (e >> 1)
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int o = 8 * nt + 2 * c + (e & 1);
+                const int64_t off = (b * CO + o) * N + n0 + g + 8 * (e >> 1);
+                float v = acc[nt][e] + sb[o];
+                if (extra) v += extra[off];
+                if (pre) pre[off] = __float2bfloat16_rn(v);
+                y[off] = __float2bfloat16_rn(act ? gelu(v) : v);
+            }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // mode contraction.  Forward: G[k][b][o] = sum_i V[k][b][i] R[k][i][o];
 // adjoint: gV[k][b][i] = sum_o gG[k][b][o] conj(R[k][i][o]).
@@ -1922,7 +1991,18 @@ void pw_fwd(fno_ctx *f, const T *x, int ci, int co, int64_t oW, int64_t ob, cons
     if (ci <= 32 && !y_is_float) {
         const size_t sm = sizeof(float) * (co * ci + co);
         T *yt = static_cast<T *>(y);
-        if (pairs && ci == 32 && co % 8 == 0)
+        // 32 -> 128 (the training path of the projection's hidden layer): tensor
+        // cores pay off.  32 -> 32 stays on the paired SIMT kernel: there the
+        // per-element stores of the fragment layout (2 bytes into 4 channel
+        // planes per warp instruction) cost more than the multiply-adds saved
+        // (0.50 against 0.39 ms per layer at batch 8).
+        if (std::is_same<T, __nv_bfloat16>::value && ci == PTC_CI && co == 128 && f->N % 16 == 0) {
+            const int64_t warps = (int64_t)B * f->N / 16;
+            const int blocks = (int)std::min<int64_t>((warps + TPB / 32 - 1) / (TPB / 32), 152 * 8);
+            k_pw_tc<128><<<blocks, TPB, 0, f->s>>>(reinterpret_cast<const __nv_bfloat16 *>(x), W, bias, extra,
+                                                   reinterpret_cast<__nv_bfloat16 *>(pre),
+                                                   reinterpret_cast<__nv_bfloat16 *>(yt), act, f->N, B);
+        } else if (pairs && ci == 32 && co % 8 == 0)
             k_pw_fwd_in2<T, T, 32><<<grid_for(units), TPB, sm, f->s>>>(x, co, W, bias, extra, pre, yt, act, f->N, B);
         else if (pairs && ci == 4 && co % 8 == 0)
             k_pw_fwd_in2<T, T, 4><<<grid_for(units), TPB, sm, f->s>>>(x, co, W, bias, extra, pre, yt, act, f->N, B);
