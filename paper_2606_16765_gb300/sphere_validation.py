@@ -49,6 +49,24 @@ def sphere_channel(L):
     return grid, D, c, prims, mask, I.link_wall_distances(grid, prims, mask)
 
 
+def centreline(field, c):
+    """Profile along x of a [nz, ny, nx] field on the axis through c = (x, y, z)
+    (cell centres): the mean of the four rows around (c[1], c[2])."""
+    y0, y1 = int(math.floor(c[1])), int(math.ceil(c[1]))
+    z0, z1 = int(math.floor(c[2])), int(math.ceil(c[2]))
+    return 0.25 * (field[z0, y0] + field[z0, y1] + field[z1, y0] + field[z1, y1])
+
+
+def profile_peaks(values, xs, lo, hi, count=2):
+    """Positions xs of the `count` largest local maxima of a profile with
+    lo < xs < hi, in increasing order of position."""
+    idx = np.nonzero((xs > lo) & (xs < hi))[0]
+    v = values[idx]
+    peaks = [i for i in range(1, len(v) - 1) if v[i] >= v[i - 1] and v[i] >= v[i + 1]]
+    top = sorted(peaks, key=lambda i: -v[i])[:count]
+    return sorted(float(xs[idx[i]]) for i in top)
+
+
 def drag_coefficient(fx, D):
     """C_d of the sphere from a streamwise force record."""
     return float(np.mean(fx)) / (0.5 * U * U * math.pi * D * D / 4.0)
@@ -118,20 +136,14 @@ def wake_run(L, re=1000.0, n_ft=12.0, mean_from_ft=4.0, storage="f32", probe_eve
     k0 = t0s // probe_every
     cd = drag_coefficient(F[k0:, 0], D)
     sts = [float(wake.strouhal(P[k0:, j, 1], D, U, every=probe_every, st_band=(0.05, 0.5))) for j in range(len(px))]
-    y0, y1 = int(math.floor(c[1])), int(math.ceil(c[1]))
-    z0, z1 = int(math.floor(c[2])), int(math.ceil(c[2]))
-    u_c = 0.25 * (m[z0, y0, :, 0] + m[z0, y1, :, 0] + m[z1, y0, :, 0] + m[z1, y1, :, 0])
+    u_c = centreline(m[..., 0], c)
     lr = wake.recirculation_length(u_c, c[0] + 0.5 * D) / D
-    uu = 0.25 * (st[z0, y0, :, 0] + st[z0, y1, :, 0] + st[z1, y0, :, 0] + st[z1, y1, :, 0])
-    urms = np.sqrt(np.maximum(uu, 0.0)) / U
+    urms = np.sqrt(np.maximum(centreline(st[..., 0], c), 0.0)) / U
     xs = (np.arange(nx) - c[0]) / D
     behind = (xs > 0.5) & (xs < 5.0)
-    idx = np.nonzero(behind)[0]
-    ur = urms[idx]
-    peaks = [float(xs[idx[i]]) for i in range(1, len(ur) - 1) if ur[i] >= ur[i - 1] and ur[i] >= ur[i + 1]]
-    top = sorted(peaks, key=lambda x: -urms[int(round(c[0] + x * D))])[:2]
     return dict(L=L, re_s=re, cd=cd, st_probes=sts, probe_x_over_d=[(x - c[0]) / D for x in px], lr_over_d=lr,
-                urms_peaks_x_over_d=sorted(top), urms_max=float(ur.max()), mean_samples=int(ns), steps=steps,
+                urms_peaks_x_over_d=profile_peaks(urms, xs, 0.5, 5.0), urms_max=float(urms[behind].max()),
+                mean_samples=int(ns), steps=steps,
                 seconds=sec, centreline_u=[float(v) for v in u_c / U],
                 centreline_urms=[float(v) for v in urms])
 

@@ -51,3 +51,19 @@ def test_drag_normalisation():
     D = 128 / 6
     fx = np.full(50, 0.5 * V.U ** 2 * math.pi * D * D / 4 * 1.1)
     assert V.drag_coefficient(fx, D) == pytest.approx(1.1)
+
+
+def test_centreline_is_the_mean_of_the_four_rows_around_the_axis():
+    f = np.zeros((4, 6, 5))
+    f[1, 2], f[1, 3], f[2, 2], f[2, 3] = 1.0, 2.0, 3.0, 6.0
+    assert np.allclose(V.centreline(f, (0.0, 2.5, 1.5)), 3.0)
+    g = np.arange(4 * 6 * 5, dtype=float).reshape(4, 6, 5)
+    assert np.allclose(V.centreline(g, (0.0, 3.0, 2.0)), g[2, 3])      # on a cell centre: that row
+
+
+def test_profile_peaks_of_a_two_bump_profile():
+    xs = np.linspace(0.0, 6.0, 601)
+    v = np.exp(-((xs - 1.5) / 0.2) ** 2) + 1.2 * np.exp(-((xs - 2.4) / 0.3) ** 2) + 0.3 * np.exp(-((xs - 4.0) / 0.2) ** 2)
+    assert V.profile_peaks(v, xs, 0.5, 5.0) == pytest.approx([1.5, 2.4], abs=0.02)
+    assert V.profile_peaks(v, xs, 0.5, 5.0, count=3)[-1] == pytest.approx(4.0, abs=0.02)
+    assert V.profile_peaks(v, xs, 2.0, 5.0, count=1) == pytest.approx([2.4], abs=0.02)
