@@ -88,18 +88,24 @@ def recorded_instructions(kernel):
     return None
 
 
-def alu_roofline(kernel, cells, ms, clocks):
+def sm_count():
+    """Multiprocessor count of the current device (cudaDevAttrMultiProcessorCount)."""
+    import torch
+    return int(torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count)
+
+
+def alu_roofline(kernel, cells, ms, clocks, sms):
     """Issue-rate roofline of a bulk kernel: achieved warp instructions per
-    second against 152 SMs x 4 schedulers x 1 warp instruction per clock at
-    the SM clock sampled during the run (the unit counts of GB300)."""
+    second against `sms` SMs (read from the device) x 4 schedulers x 1 warp
+    instruction per clock at the SM clock sampled during the run."""
     ipc = recorded_instructions(kernel)
     if ipc is None or not clocks:
         return None
     achieved = ipc * cells / (ms / 1e3)
-    peak = 152 * 4 * clocks["sm_mhz"] * 1e6
+    peak = sms * 4 * clocks["sm_mhz"] * 1e6
     return {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "T warp-instructions/s",
             "frac": achieved / peak, "warp_instructions_per_cell": ipc, "kernel": kernel,
-            "peak_source": "152 SMs x 4 issue slots x sampled SM clock"}
+            "peak_source": f"{sms} SMs (device attribute) x 4 issue slots x sampled SM clock"}
 
 
 # ---------------------------------------------------------------------------
@@ -196,9 +202,21 @@ def workload(grid):
 def schedule(steps, warmup):
     """Epilogue schedule over the timed window [warmup, warmup + steps)."""
     nsnap = min(20, max(1, steps // 25))
+    # the last snapshot at the last timed step, the others 25 steps apart before it
     return dict(mean_start=warmup, mean_end=warmup + steps, mean_every=10,
-                snap_first=warmup + steps - 25 * nsnap, snap_every=25, snap_count=nsnap,
+                snap_first=warmup + steps - 1 - 25 * (nsnap - 1), snap_every=25, snap_count=nsnap,
                 snap_halfres=1, force_every=1)
+
+
+def epilogue_counts(sch, warmup, steps):
+    """Snapshots, mean samples and force rows that fall inside the timed
+    window [warmup, warmup + steps) under the schedule `sch`."""
+    lo, hi = warmup, warmup + steps
+    snaps = [sch["snap_first"] + k * sch["snap_every"] for k in range(sch["snap_count"])]
+    means = range(sch["mean_start"], sch["mean_end"], sch["mean_every"])
+    return {"snapshots": sum(1 for t in snaps if lo <= t < hi),
+            "mean_samples": sum(1 for t in means if lo <= t < hi),
+            "force_rows": len(range(lo, hi, sch["force_every"]))}
 
 
 def run_ours(args, storage, d, ws, device_index):
@@ -257,14 +275,19 @@ def run_e2e(args, storage, d):
     t0 = time.perf_counter()
     h = B.lbm_create(grid, mask, p, torch.cuda.current_stream().cuda_stream)
     B.lbm_set_wall_distances(h, *d["links"])
-    B.lbm_step(h, K)
-    B.lbm_read_mean(h, mean, 1, 1)
+    B.lbm_sync(h)
     t1 = time.perf_counter()
+    B.lbm_step(h, K)
+    B.lbm_sync(h)
+    t2 = time.perf_counter()
+    B.lbm_read_mean(h, mean, 1, 1)
+    t3 = time.perf_counter()
     info = B.lbm_get_info(h)
     B.lbm_destroy(h)
     torch.cuda.empty_cache()
     link_bytes = sum(a.nbytes for a in d["links"])
-    return dict(seconds=t1 - t0, fluid=info.fluid_cells, h2d=mask.nbytes + link_bytes, d2h=mean.nbytes)
+    return dict(seconds=t3 - t0, fluid=info.fluid_cells, h2d=mask.nbytes + link_bytes, d2h=mean.nbytes,
+                split={"create_upload_s": t1 - t0, "step_s": t2 - t1, "readback_s": t3 - t2})
 
 
 def run_batch(steps, warmup, storage="f16s", n=32):
@@ -332,6 +355,29 @@ def run_fno(batch=8, reps=10):
             "speedup_vs_lbm": t_lbm / (fwd / batch / 1e3), "dtype": "bf16 activations, fp32 accumulation"}
 
 
+def oracle_sub_box(O, d, bx, by, bz):
+    """FP64 oracle lattice on a bx x by x bz sub-box of the channel around the
+    obstacle, with the GPU arm's boundary set: moving-wall inlet, convective
+    outflow, no-slip lateral walls and the interpolated bounce-back on the
+    sub-box's obstacle links (wall distances of the shifted primitives)."""
+    import dataclasses
+    import numpy as np
+    from paper_2606_16765_gb300 import inputs as I
+    nx, ny, nz = d["grid"]
+    bx, by, bz = min(bx, nx), min(by, ny), min(bz, nz)
+    x0 = max(0, min(nx - bx, int(0.3 * nx) - bx // 3))
+    y0, z0 = (ny - by) // 2, (nz - bz) // 2
+    sub = np.ascontiguousarray(d["mask"][z0:z0 + bz, y0:y0 + by, x0:x0 + bx])
+    prims = [dataclasses.replace(pr, center=(pr.center[0] - x0, pr.center[1] - y0, pr.center[2] - z0))
+             for pr in d["obstacle"].prims]
+    w1 = O.omega_from_re(d["re"], d["u_in"], d["l_ref"])
+    L = O.Lattice(O.params(bx, by, bz, w1, u_in=d["u_in"], faces=("inlet", "outflow", "wall", "wall")), sub)
+    links = I.link_wall_distances((bx, by, bz), prims, sub)
+    if len(links[0]):
+        L.set_q(I.dense_wall_distances((bx, by, bz), links))
+    return L, sub, (bx, by, bz), len(links[0])
+
+
 def cpu_baseline(d, seconds=12.0, box=(128, 96, 96)):
     """FP64 oracle on the host cores, on a sub-box of the same channel around
     the obstacle, stepped until ~`seconds` of CPU work."""
@@ -339,13 +385,7 @@ def cpu_baseline(d, seconds=12.0, box=(128, 96, 96)):
     cores = os.cpu_count() or 1
     os.environ.setdefault("OMP_NUM_THREADS", str(cores))
     import oracle.lbm as O
-    nx, ny, nz = d["grid"]
-    bx, by, bz = (min(box[0], nx), min(box[1], ny), min(box[2], nz))
-    x0 = max(0, min(nx - bx, int(0.3 * nx) - bx // 3))
-    y0, z0 = (ny - by) // 2, (nz - bz) // 2
-    sub = np.ascontiguousarray(d["mask"][z0:z0 + bz, y0:y0 + by, x0:x0 + bx])
-    w1 = O.omega_from_re(d["re"], d["u_in"], d["l_ref"])
-    L = O.Lattice(O.params(bx, by, bz, w1, u_in=d["u_in"]), sub)
+    L, sub, (bx, by, bz), nq = oracle_sub_box(O, d, *box)
     fluid = int((sub == 0).sum())
     steps, t0 = 0, time.perf_counter()
     while True:
@@ -356,7 +396,8 @@ def cpu_baseline(d, seconds=12.0, box=(128, 96, 96)):
             break
     return {"value": fluid * steps / el / 1e6, "unit": "MLUPS", "cores": int(os.environ["OMP_NUM_THREADS"]),
             "kind": "oracle",
-            "sample": f"{bx}x{by}x{bz} sub-box of the channel around the obstacle, {steps} FP64 steps, {el:.1f} s"}
+            "sample": f"{bx}x{by}x{bz} sub-box of the channel around the obstacle, {steps} FP64 steps, {el:.1f} s; "
+                      f"inlet, convective outflow, walls, interpolated bounce-back on {nq} links"}
 
 
 def reference_arm(args):
@@ -381,18 +422,15 @@ def reference_arm(args):
     budget = 100.0 / max(1, args.steps + args.warmup)
     cells = max(16 * 8 * 8, min(nx * ny * nz, int(budget / per_cell)))
     a = max(8, int(round((cells / 2) ** (1 / 3))))
-    bx, by, bz = min(2 * a, nx), min(a, ny), min(a, nz)
-    x0 = max(0, min(nx - bx, int(0.3 * nx) - bx // 3))
-    y0, z0 = (ny - by) // 2, (nz - bz) // 2
-    sub = np.ascontiguousarray(d["mask"][z0:z0 + bz, y0:y0 + by, x0:x0 + bx])
-    L = O.Lattice(O.params(bx, by, bz, w1, u_in=d["u_in"]), sub)
+    L, sub, (bx, by, bz), nq = oracle_sub_box(O, d, 2 * a, a, a)
     fluid = int((sub == 0).sum())
     L.step(args.warmup)
     t0 = time.perf_counter()
     L.step(args.steps)
     el = time.perf_counter() - t0
     v = fluid * args.steps / el / 1e6
-    sample = f"{bx}x{by}x{bz} sub-box of the channel around the obstacle per step"
+    sample = (f"{bx}x{by}x{bz} sub-box of the channel around the obstacle per step; inlet, convective outflow, "
+              f"walls, interpolated bounce-back on {nq} links")
     line = {
         "metric": METRIC, "value": v, "unit": "MLUPS", "impl": "reference", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
@@ -405,11 +443,17 @@ def reference_arm(args):
     print(json.dumps(line), flush=True)
 
 
-def config_block(grid, storage, info):
+def config_block(grid, storage, info, counts=None):
     nx, ny, nz = grid
+    if counts is None:
+        epi = "obstacle force every step, FP64 mean every 10 steps, half-res snapshots 25 steps apart"
+    else:
+        epi = (f"obstacle force every step ({counts['force_rows']} rows), FP64 mean every 10 steps "
+               f"({counts['mean_samples']} samples), {counts['snapshots']} half-res snapshots 25 steps apart "
+               f"in the timed window")
     c = {"workload": f"composite-obstacle channel {nx}x{ny}x{nz}, Re=1e4 on the channel height, u_in=0.05, seed 0",
          "grid": [nx, ny, nz], "storage": storage,
-         "epilogues": "obstacle force every step, FP64 mean every 10 steps, 20 half-res snapshots 25 steps apart",
+         "epilogues": epi,
          "boundaries": "moving-wall velocity inlet, convective extrapolation outflow, no-slip walls, "
                        "interpolated (quadratic) bounce-back on the obstacle links",
          "l2": "inputs larger than L2 (pdf array >> 129 MB), no flush"}
@@ -459,12 +503,14 @@ def main():
     grid = tuple(int(v) for v in args.grid.split(","))
     d = workload(grid)
     res = run_ours(args, args.storage, d, ws, local)
+    counts = epilogue_counts(schedule(args.steps, args.warmup), args.warmup, args.steps)
     info, rep = res["info"], res["rep"]
     K = args.steps
     ms, units = aggregate(res["ms"], float(info.fluid_cells) * K, ws, backend)
     mlups = units / (ms / 1e3) / 1e6
 
     peak, peak_kind = measured_peaks()
+    sms = sm_count()
     s_b = BYTES_PER_POP[args.storage]
     # dominant kernel: the bulk kernel of odd steps without epilogue
     kind = 1 if rep.bulk_n[1] > 0 else 0
@@ -485,12 +531,18 @@ def main():
         "metric": METRIC, "value": mlups, "unit": "MLUPS", "n_gpus": ws, "steps": K, "warmup": args.warmup,
         "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if args.storage == "f64" else "f32", "data": "synthetic",
-        "config": config_block(grid, args.storage, info),
+        "config": config_block(grid, args.storage, info, counts),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_source": peak_kind,
-                     "kernel": kname, "bytes_per_launch": bytes_launch,
+                     "kernel": kname, "scope": "bulk kernel only (odd step, no epilogue)",
+                     "bytes_per_launch": bytes_launch,
                      "frac_of_nominal_8000": achieved / NOMINAL_HBM_GBS},
-        "alu_roofline": alu_roofline(kname, info.interior_cells, bulk_ms, res["clocks"]),
+        "step_roofline": {"scope": "whole step (bulk + edge + between-step kernels + epilogues): "
+                                   "fluid MLUPS x pdf bytes per update",
+                          "achieved": mlups * 1e6 * 54 * s_b / 1e9, "peak": peak, "unit": "GB/s",
+                          "frac": mlups * 1e6 * 54 * s_b / 1e9 / peak / max(1, ws)},
+        "sm_count": sms,
+        "alu_roofline": alu_roofline(kname, info.interior_cells, bulk_ms, res["clocks"], sms),
         "kernels": {"bulk": per_kind, "edge_ms_per_launch": edge_ms},
         "gpu_launches": int(res["launches"]),
         "clocks": res["clocks"],
@@ -507,7 +559,7 @@ def main():
                 "interior_kernel_gbs": b2 * r2["info"].interior_cells / (t2 / 1e3) / 1e9,
                 "interior_kernel_frac": b2 * r2["info"].interior_cells / (t2 / 1e3) / 1e9 / peak,
                 "alu_roofline": alu_roofline(f"k_step_bulk<{extra},odd={bool(k2 & 1)},epi=False>",
-                                             r2["info"].interior_cells, t2, r2["clocks"]),
+                                             r2["info"].interior_cells, t2, r2["clocks"], sms),
                 "clocks": r2["clocks"]}
         if not args.no_batch:
             line["batch"] = run_batch(args.steps, 20)
@@ -517,7 +569,9 @@ def main():
             e = run_e2e(args, args.storage, d)
             line["e2e"] = {"value": e["fluid"] * K / e["seconds"] / 1e6, "unit": "MLUPS",
                            "h2d_bytes_per_step": e["h2d"] / K, "d2h_bytes_per_step": e["d2h"] / K,
-                           "seconds": e["seconds"]}
+                           "seconds": e["seconds"], "split_seconds": e["split"],
+                           "note": "create+upload covers the device allocation of the 29 GB pdf array, "
+                                   "the mask and link upload and the cell classification"}
         if ws == 1 and not args.no_cpu:
             line["cpu_baseline"] = cpu_baseline(d)
         print(json.dumps(line), flush=True)

@@ -197,8 +197,12 @@ lbm_status lbm_read_snapshot(lbm_ctx *ctx, int32_t k, float *dst);
 /* Density and velocity of the current state: rho [N], u [N][3] (doubles). */
 lbm_status lbm_read_macros(lbm_ctx *ctx, double *rho, double *u);
 
-/* Obstacle force F(t) = sum over obstacle links of 2 c_i f*_i (momentum
- * exchange), one row (Fx, Fy, Fz) per recorded step, oldest first.  Writes at
+/* Obstacle force by momentum exchange (Sec. 2: forces on the object),
+ * F(t) = sum over obstacle links (x, i) of c_i (f*_i(x) + f_back), where f_back
+ * is the population returned into the opposite direction: f*_i itself on
+ * halfway bounce-back links (2 c_i f*_i), the interpolated value on links
+ * with wall distances (lbm_set_wall_distances).  Walls are not part of the
+ * body.  One row (Fx, Fy, Fz) per recorded step, oldest first.  Writes at
  * most max_rows rows; *n_rows receives the number recorded. */
 lbm_status lbm_read_forces(lbm_ctx *ctx, double *dst, int64_t max_rows, int64_t *n_rows);
 
@@ -357,13 +361,18 @@ lbm_status lbm_reset(lbm_ctx *ctx);
  * quantities as lbm_totals: out[0] = sum of f_i - w_i over fluid cells,
  * out[1..3] = momentum, by a deterministic two-pass FP64 reduction.
  *
- *   pdf          device array of 27 slots x slot_stride values of `storage`
- *                type holding f_i - w_i in natural order (the layout a context
+ *   pdf          device (or managed) array of 27 slots x slot_stride values
+ *                of `storage` type (any lbm_storage, LBM_F16C included)
+ *                holding f_i - w_i in natural order (the layout a context
  *                holds at even time steps), cell c of direction i at
  *                i * slot_stride + c; slot_stride >= nx*ny*nz.
- *   mask         device array of nx*ny*nz bytes, 1 = solid (skipped), or NULL.
+ *   mask         device (or managed) array of nx*ny*nz bytes, 1 = solid
+ *                (skipped), or NULL.  A host pdf or mask returns LBM_ERR_ARG
+ *                before anything is launched.
  *   out          4 doubles, host or device; for a host buffer the call waits
- *                for the stream, for a device buffer it does not.
+ *                for the stream (cudaStreamSynchronize), for a device buffer
+ *                it does not.  Only a device `out` can be used while the
+ *                stream is being captured into a graph.
  *
  * Its only scratch is a fixed array compiled into the library (512 KiB, held
  * by every GPU that loads the library until the process exits), which limits

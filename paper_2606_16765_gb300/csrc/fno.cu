@@ -32,6 +32,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/fno.h"
+#include "sm_count.h"
 
 namespace {
 
@@ -54,7 +55,7 @@ __device__ __forceinline__ float gelu_grad(float x)
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) { return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
 __device__ __forceinline__ float2 cmulc(float2 a, float2 b) { return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y); }  // a conj(b)
 
-int grid_for(int64_t n, int block = TPB) { return (int)std::min<int64_t>((n + block - 1) / block, 152 * 16); }
+int grid_for(int64_t n, int block = TPB) { return (int)std::min<int64_t>((n + block - 1) / block, gb300::sm_count() * 16); }
 
 // ---------------------------------------------------------------------------
 // pointwise layers
@@ -1891,7 +1892,7 @@ extern "C" lbm_status fno_create(const fno_config *cfg, void *stream, fno_ctx **
     chk(f->twz = f->alloc<float2>((int64_t)c.nz * f->Kz));
     chk(f->scale_one = f->alloc<float>(16));
     chk(f->scale_inv = f->alloc<float>(16));
-    f->nparts = 152 * 4;
+    f->nparts = gb300::sm_count() * 4;
     chk(f->part = f->alloc<double>(2 * f->nparts));
     chk(f->res = f->alloc<double>(2));
     if (!ok) {
@@ -1998,7 +1999,7 @@ void pw_fwd(fno_ctx *f, const T *x, int ci, int co, int64_t oW, int64_t ob, cons
         // (0.50 against 0.39 ms per layer at batch 8).
         if (std::is_same<T, __nv_bfloat16>::value && ci == PTC_CI && co == 128 && f->N % 16 == 0) {
             const int64_t warps = (int64_t)B * f->N / 16;
-            const int blocks = (int)std::min<int64_t>((warps + TPB / 32 - 1) / (TPB / 32), 152 * 8);
+            const int blocks = (int)std::min<int64_t>((warps + TPB / 32 - 1) / (TPB / 32), gb300::sm_count() * 8);
             k_pw_tc<128><<<blocks, TPB, 0, f->s>>>(reinterpret_cast<const __nv_bfloat16 *>(x), W, bias, extra,
                                                    reinterpret_cast<__nv_bfloat16 *>(pre),
                                                    reinterpret_cast<__nv_bfloat16 *>(yt), act, f->N, B);
@@ -2071,15 +2072,15 @@ void dft_fwd(fno_ctx *f, const T *x, float2 *S, const float *scale, int B)
     const bool tc_input = std::is_same<T, __nv_bfloat16>::value || f->c.act_bf16;
     if (tc_input && d.nx == TCX_NX && d.Kx == TCX_KX && (reinterpret_cast<uintptr_t>(x) & 15u) == 0) {
         const int64_t warps = (R + 15) / 16;
-        k_dftx_fwd_tc<T><<<(int)std::min<int64_t>((warps + TPB / 32 - 1) / (TPB / 32), 152 * 8), TPB, 0, f->s>>>(
+        k_dftx_fwd_tc<T><<<(int)std::min<int64_t>((warps + TPB / 32 - 1) / (TPB / 32), gb300::sm_count() * 8), TPB, 0, f->s>>>(
             x, f->stA, f->twx, R);
     } else {
-        k_dftx_fwd<T><<<(int)std::min<int64_t>((R + DFT_ROWS - 1) / DFT_ROWS, 152 * 8), TPB, smem_dftx_fwd(d),
+        k_dftx_fwd<T><<<(int)std::min<int64_t>((R + DFT_ROWS - 1) / DFT_ROWS, gb300::sm_count() * 8), TPB, smem_dftx_fwd(d),
                         f->s>>>(x, f->stA, f->twx, d, R);
     }
     const int64_t Sl = d.BC * d.nz;
     const int SB = dfty_fwd_slabs(d);
-    k_dfty_fwd<<<(int)std::min<int64_t>((Sl + SB - 1) / SB, 152 * 8), TPB, smem_dfty_fwd(d), f->s>>>(f->stA, f->stB,
+    k_dfty_fwd<<<(int)std::min<int64_t>((Sl + SB - 1) / SB, gb300::sm_count() * 8), TPB, smem_dfty_fwd(d), f->s>>>(f->stA, f->stB,
                                                                                                   f->twy, d, Sl, SB);
     k_dftz_fwd<<<grid_for(d.BC * d.Ky * d.Kx), TPB, 0, f->s>>>(f->stB, S, f->twz, scale, d);
 }
@@ -2093,16 +2094,16 @@ void dft_inv(fno_ctx *f, const float2 *S, float *out, const float *scale, int ac
     k_dftz_inv<<<grid_for(d.BC * d.Ky * d.Kx), TPB, 0, f->s>>>(S, f->stB, f->twz, scale, d);
     const int64_t Sl = d.BC * d.nz;
     const int SB = dfty_inv_slabs(d);
-    k_dfty_inv<<<(int)std::min<int64_t>((Sl + SB - 1) / SB, 152 * 8), TPB, smem_dfty_inv(d), f->s>>>(f->stB, f->stA,
+    k_dfty_inv<<<(int)std::min<int64_t>((Sl + SB - 1) / SB, gb300::sm_count() * 8), TPB, smem_dfty_inv(d), f->s>>>(f->stB, f->stA,
                                                                                                   f->twy, d, Sl, SB);
     const int64_t R = d.BC * d.nz * d.ny;
     if (std::is_same<TP, __nv_bfloat16>::value && d.nx == TCX_NX && d.Kx == TCX_KX &&
         (reinterpret_cast<uintptr_t>(out) & 7u) == 0) {
         const int64_t warps = (R + 15) / 16;
-        k_dftx_inv_tc<TP><<<(int)std::min<int64_t>((warps + TPB / 32 - 1) / (TPB / 32), 152 * 8), TPB, 0, f->s>>>(
+        k_dftx_inv_tc<TP><<<(int)std::min<int64_t>((warps + TPB / 32 - 1) / (TPB / 32), gb300::sm_count() * 8), TPB, 0, f->s>>>(
             f->stA, out, f->twx, R, accumulate, pre);
     } else {
-        k_dftx_inv<TP><<<(int)std::min<int64_t>((R + DFT_ROWS - 1) / DFT_ROWS, 152 * 8), TPB, smem_dftx_inv(d),
+        k_dftx_inv<TP><<<(int)std::min<int64_t>((R + DFT_ROWS - 1) / DFT_ROWS, gb300::sm_count() * 8), TPB, smem_dftx_inv(d),
                          f->s>>>(f->stA, out, f->twx, d, R, accumulate, pre);
     }
 }
@@ -2112,7 +2113,7 @@ void contract(fno_ctx *f, const float2 *Vin, int64_t oR, float2 *Gout, bool adj,
     const float2 *R = reinterpret_cast<const float2 *>(f->params + oR);
     const int C = f->c.width;
     if (f->c.tensor_cores) {
-        const int blocks = (int)std::min<int64_t>((f->K * 32 + TPB - 1) / TPB, 152 * 8);
+        const int blocks = (int)std::min<int64_t>((f->K * 32 + TPB - 1) / TPB, gb300::sm_count() * 8);
         if (adj) k_contract_tc<true><<<blocks, TPB, 0, f->s>>>(Vin, R, Gout, C, B, f->K);
         else k_contract_tc<false><<<blocks, TPB, 0, f->s>>>(Vin, R, Gout, C, B, f->K);
     } else {
@@ -2143,7 +2144,7 @@ lbm_status forward_impl(fno_ctx *f, const float *x, int B, bool keep = true)
         f->N % 16 == 0) {
         // inference on tensor cores: projection fused, hidden activations in registers
         const int64_t warps = (int64_t)B * f->N / 16;
-        k_proj_tc<<<(int)std::min<int64_t>((warps + TPB / 32 - 1) / (TPB / 32), 152 * 8), TPB, 0, f->s>>>(
+        k_proj_tc<<<(int)std::min<int64_t>((warps + TPB / 32 - 1) / (TPB / 32), gb300::sm_count() * 8), TPB, 0, f->s>>>(
             reinterpret_cast<const __nv_bfloat16 *>(f->v[c.layers]), c.cout, f->params + f->oQ1_w,
             f->params + f->oQ1_b, f->params + f->oQ2_w, f->params + f->oQ2_b, f->y, f->N, B);
         return LBM_OK;

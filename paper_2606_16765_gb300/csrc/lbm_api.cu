@@ -71,7 +71,7 @@ Layout make_layout(const lbm_grid &g, const lbm_params &p, int64_t n_solid)
     L.force = take(p.force_every > 0 ? (size_t)cap * 3 * 8 : 0);
     L.fpart = take((size_t)3 * 8 * ((L.n + EDGE_BLOCK - 1) / EDGE_BLOCK + 1));
     L.fcount = take(sizeof(unsigned));
-    L.tot_blocks = (int)std::max<int64_t>(1, std::min<int64_t>((L.n + 255) / 256, 152 * 8));
+    L.tot_blocks = (int)std::max<int64_t>(1, std::min<int64_t>((L.n + 255) / 256, gb300::sm_count() * 8));
     L.tpart = take((size_t)4 * 8 * L.tot_blocks);
     L.tout = take(4 * 8);
     L.status = take(sizeof(int));

@@ -330,7 +330,7 @@ __global__ void k_probe(StepArgs a, bool odd, const int64_t *cells, int64_t coun
 // ---------------------------------------------------------------------------
 // host launchers
 // ---------------------------------------------------------------------------
-static int grid_for(int64_t n, int block) { return (int)std::min<int64_t>((n + block - 1) / block, 152 * 32); }
+static int grid_for(int64_t n, int block) { return (int)std::min<int64_t>((n + block - 1) / block, gb300::sm_count() * 32); }
 
 template <class S>
 static void launch_aux_t(AuxOp op, const StepArgs &a, bool odd, const AuxArgs &x, cudaStream_t s)

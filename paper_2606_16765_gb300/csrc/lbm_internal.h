@@ -6,6 +6,7 @@
 #include <cstdint>
 
 #include "lbm_device.cuh"
+#include "sm_count.h"
 
 namespace lbm {
 

@@ -137,8 +137,14 @@ extern "C" lbm_status lbm_totals_noalloc(const void *pdf, int32_t storage, int64
                                          const uint8_t *mask, int32_t nx, int32_t ny, int32_t nz,
                                          void *cuda_stream, double *out)
 {
-    if (!pdf || !out || storage < LBM_F64 || storage > LBM_BF16S || nx < 1 || ny < 1 || nz < 1) {
+    if (!pdf || !out || storage < LBM_F64 || storage > LBM_F16C || nx < 1 || ny < 1 || nz < 1) {
         set_global_error("lbm_totals_noalloc: null pointer, unknown storage or empty grid");
+        return LBM_ERR_ARG;
+    }
+    // a host pdf or mask would reach the kernel as an address the GPU may not
+    // translate: refuse it here, before anything is launched
+    if (!on_device(pdf) || (mask && !on_device(mask))) {
+        set_global_error("lbm_totals_noalloc: pdf and mask must be device (or managed) memory");
         return LBM_ERR_ARG;
     }
     const int64_t n = (int64_t)nx * ny * nz;
@@ -160,7 +166,8 @@ extern "C" lbm_status lbm_totals_noalloc(const void *pdf, int32_t storage, int64
     case LBM_F64: k_na_partial<double><<<nblocks, NA_THREADS, 0, s>>>((const double *)pdf, slot_stride, mask, n, scratch); break;
     case LBM_F32: k_na_partial<float><<<nblocks, NA_THREADS, 0, s>>>((const float *)pdf, slot_stride, mask, n, scratch); break;
     case LBM_F16S: k_na_partial<__half><<<nblocks, NA_THREADS, 0, s>>>((const __half *)pdf, slot_stride, mask, n, scratch); break;
-    default: k_na_partial<__nv_bfloat16><<<nblocks, NA_THREADS, 0, s>>>((const __nv_bfloat16 *)pdf, slot_stride, mask, n, scratch); break;
+    case LBM_BF16S: k_na_partial<__nv_bfloat16><<<nblocks, NA_THREADS, 0, s>>>((const __nv_bfloat16 *)pdf, slot_stride, mask, n, scratch); break;
+    default: k_na_partial<F16C><<<nblocks, NA_THREADS, 0, s>>>((const F16C *)pdf, slot_stride, mask, n, scratch); break;
     }
     k_na_final<<<1, NA_THREADS, 0, s>>>(scratch, nblocks);
     cudaError_t e = cudaGetLastError();

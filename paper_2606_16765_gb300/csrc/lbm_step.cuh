@@ -19,6 +19,7 @@
 #pragma once
 
 #include "lbm_device.cuh"
+#include "sm_count.h"
 
 namespace lbm {
 
@@ -430,7 +431,7 @@ static void launch_outflow(const StepArgs &a, bool fix, bool next_odd, cudaStrea
 {
     if (a.face_x_hi != FACE_OUTFLOW) return;
     const int64_t P = (int64_t)a.ny * a.nz;
-    k_outflow<S><<<(unsigned)std::min<int64_t>((9 * P + 255) / 256, 152 * 16), 256, 0, s>>>(a, fix ? 1 : 0,
+    k_outflow<S><<<(unsigned)std::min<int64_t>((9 * P + 255) / 256, gb300::sm_count() * 16), 256, 0, s>>>(a, fix ? 1 : 0,
                                                                                           next_odd ? 1 : 0);
 }
 

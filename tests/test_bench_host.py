@@ -51,14 +51,28 @@ def test_no_samples_give_no_record():
 
 def test_issue_rate_roofline_arithmetic(monkeypatch):
     monkeypatch.setattr(bench, "recorded_instructions", lambda kernel: 24.0)
-    r = bench.alu_roofline("k", cells=1_000_000, ms=1.0, clocks={"sm_mhz": 2000.0})
+    r = bench.alu_roofline("k", cells=1_000_000, ms=1.0, clocks={"sm_mhz": 2000.0}, sms=152)
     # 24 warp instructions per cell x 1e6 cells in 1 ms, against 152 SMs x 4 schedulers x 2 GHz
     assert r["achieved"] == pytest.approx(24e6 / 1e-3 / 1e12)
     assert r["peak"] == pytest.approx(152 * 4 * 2000e6 / 1e12)
     assert r["frac"] == pytest.approx((24e6 / 1e-3) / (152 * 4 * 2000e6))
-    assert bench.alu_roofline("k", 1, 1.0, None) is None
+    # the SM count is the device's, not a constant
+    r2 = bench.alu_roofline("k", cells=1_000_000, ms=1.0, clocks={"sm_mhz": 2000.0}, sms=76)
+    assert r2["frac"] == pytest.approx(2 * r["frac"])
+    assert bench.alu_roofline("k", 1, 1.0, None, 152) is None
     monkeypatch.setattr(bench, "recorded_instructions", lambda kernel: None)
-    assert bench.alu_roofline("k", 1, 1.0, {"sm_mhz": 2000.0}) is None
+    assert bench.alu_roofline("k", 1, 1.0, {"sm_mhz": 2000.0}, 152) is None
+
+
+def test_epilogue_schedule_counts():
+    """The label names the snapshots and mean samples the timed window takes."""
+    sch = bench.schedule(20, 3)
+    assert sch["snap_count"] == 1 and sch["snap_first"] == 3 + 20 - 1
+    c = bench.epilogue_counts(sch, 3, 20)
+    assert c == {"snapshots": 1, "mean_samples": 2, "force_rows": 20}
+    sch = bench.schedule(500, 10)
+    c = bench.epilogue_counts(sch, 10, 500)
+    assert c == {"snapshots": 20, "mean_samples": 50, "force_rows": 500}
 
 
 def _fake_tree(root, source):

@@ -626,3 +626,48 @@ def test_interpolated_bounce_back_puts_the_wall_at_q(q, w1):
     (about 5 %)."""
     assert abs(shear_wave_rate_error(q, w1, True)) < 5e-3
     assert abs(shear_wave_rate_error(q, w1, False)) > 4e-2
+
+
+# --------------------------------------------------------------------------
+# momentum-exchange force: exact momentum balance of the fluid
+# --------------------------------------------------------------------------
+def fluid_momentum(L, solid):
+    """Sum over fluid cells of c_i f_i, each component summed exactly
+    (math.fsum: c_i is -1, 0 or 1, so the products are exact)."""
+    f = L.get_f()[:, solid == 0]
+    return np.array([math.fsum((CV[:, a, None] * f).ravel()) for a in range(3)])
+
+
+@pytest.mark.parametrize("wall_distances", [False, True])
+def test_force_is_the_momentum_the_fluid_loses(wall_distances):
+    """In a box periodic on every face the only momentum sink is the
+    obstacle: every population that heads into it leaves the fluid with
+    c_i f*_i and the population returned in its place brings -c_i f_back.
+    So the fluid's total momentum after step t minus that before it is -F(t)
+    exactly, for halfway (f_back = f*_i) and interpolated bounce-back alike.
+    A factor 2, a dropped returned term or a wrong sign in the force fails."""
+    nx, ny, nz = 20, 14, 12
+    prims = [I.Primitive("sphere", (8.3, 6.7, 5.4), (6.2,)),
+             I.Primitive("rectangle", (11.0, 7.2, 6.1), (3.0, 5.0, 4.0))]
+    solid = I.voxelize((nx, ny, nz), prims)
+    p = O.params(nx, ny, nz, 1.7, u_in=0.0, faces=("periodic",) * 4)
+    L = O.Lattice(p, solid)
+    r = rng(31)
+    f = np.zeros((Q, nz, ny, nx))
+    u0 = (0.06, -0.02, 0.015)
+    feq = np.asarray(O.equilibrium(1.0, *u0))
+    f[:] = feq[:, None, None, None] * (1 + 0.02 * r.uniform(-1, 1, (Q, nz, ny, nx)))
+    L.set_f(f)
+    if wall_distances:
+        q = I.dense_wall_distances((nx, ny, nz), I.link_wall_distances((nx, ny, nz), prims, solid))
+        assert np.abs(q - 0.5).max() > 0.3          # genuinely off-centre walls
+        L.set_q(q)
+    P = [fluid_momentum(L, solid)]
+    for _ in range(8):
+        L.step(1)
+        P.append(fluid_momentum(L, solid))
+    F = L.forces()
+    dP = np.diff(np.array(P), axis=0)
+    scale = np.abs(F).max()
+    assert scale > 1e-3                              # a real force, not rounding
+    assert np.abs(dP + F).max() < 1e-13 * scale, np.abs(dP + F).max() / scale
