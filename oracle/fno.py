@@ -1,16 +1,18 @@
 """Plain FP64 reference of the Fourier Neural Operator surrogate (test
 infrastructure only; the product path never imports it).
 
-The paper (Sec. 4 and the appendix on the baseline models) trains an FNO
-(Li et al. 2021) that maps the obstacle mask and Re to the mean flow field:
-a pointwise lifting layer to the 32-channel co-domain, Fourier layers that
-keep a box of low Fourier modes, and a pointwise projection.  This module
+The paper (Sec. 4 and App. B) trains an FNO (Li et al. 2021) that maps the
+obstacle mask and Re to the mean flow field.  App. B fixes three parts of it:
+the lifting layer is a simple feed-forward network that expands the inputs to
+the 32-channel co-domain, the Fourier layers keep a box of low modes, and the
+projection is a SIREN (Sitzmann et al. 2020: layers with sine activations
+sin(omega0 (W x + b)), omega0 = 30, and their initialisation).  This module
 restates that network for fields laid out [batch, channel, z, y, x]:
 
-  lift      v0 = P x + bP                             (pointwise, cin -> width)
-  layer l   v_{l+1} = act( K_l v_l + W_l v_l + b_l )   (act = GELU except the last)
-            K_l v = IDFT_r( R_l . DFT_r(v) )           (retained modes only)
-  project   h = GELU(Q1 v_L + bQ1);  y = Q2 h + bQ2    (width -> hidden -> cout)
+  lift      a = GELU(P1 x + bP1);  v0 = P2 a + bP2         (cin -> lift_hidden -> width)
+  layer l   v_{l+1} = act( K_l v_l + W_l v_l + b_l )       (act = GELU except the last)
+            K_l v = IDFT_r( R_l . DFT_r(v) )               (retained modes only)
+  project   h = sin(omega0 (Q1 v_L + bQ1));  y = Q2 h + bQ2 (width -> hidden -> cout)
 
 DFT_r is the discrete Fourier transform restricted to the retained modes
 kx in [0, mx) U [-mx, 0), ky in [0, my) U [-my, 0), kz in [0, mz) (z is the
@@ -24,7 +26,8 @@ GELU is the exact form x Phi(x).  The loss is the masked mean square error
 sum_{b,c,x} M(b,x) (y - t)^2 / (C * sum M).
 
 Gradients are written by hand; complex gradients use g = dL/dRe + i dL/dIm,
-for which a product z = a w gives g_a = g_z conj(w), g_w = g_z conj(a).
+for which a product z = a w gives g_a = g_z conj(w), g_w = g_z conj(a).  The
+sine layer's derivative is d sin(omega0 z)/dz = omega0 cos(omega0 z).
 """
 from __future__ import annotations
 
@@ -47,7 +50,9 @@ class FNOConfig:
     cout: int = 4
     modes: tuple = (8, 8, 16)          # (mz, my, mx)
     layers: int = 4
-    hidden: int = 128
+    hidden: int = 128                  # SIREN projection width
+    lift_hidden: int = 32              # hidden width of the feed-forward lift
+    omega0: float = 30.0               # SIREN frequency factor
 
     @property
     def nmodes(self):
@@ -129,34 +134,47 @@ def channel_outer(a, b):
     return np.einsum('bon,bin->oi', a.reshape(a.shape[0], a.shape[1], -1), b.reshape(b.shape[0], b.shape[1], -1))
 
 
+def siren(w, b, v, omega0):
+    """SIREN layer: sin(omega0 (W v + b)) and its pre-activation W v + b."""
+    z = pointwise(w, b, v)
+    return np.sin(omega0 * z), z
+
+
 def init_params(cfg, seed=0):
-    """Deterministic FP64 parameters: uniform(-s, s) with s = 1/sqrt(fan_in);
-    spectral weights uniform with scale 1/(width^2) on real and imaginary parts."""
+    """Deterministic FP64 parameters.  Lift, Fourier-layer pointwise weights
+    and biases: uniform(-s, s) with s = 1/sqrt(fan_in); spectral weights
+    uniform with scale 1/(width^2) on real and imaginary parts; SIREN
+    projection (Sitzmann et al. 2020): first (sine) layer weights uniform
+    within 1/fan_in, the last (linear) layer's within sqrt(6/fan_in)/omega0,
+    biases within 1/sqrt(fan_in)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     W = cfg.width
+    LH = cfg.lift_hidden
     mz, my, mx = cfg.modes
 
-    def u(shape, fan):
-        s = 1.0 / math.sqrt(fan)
+    def u(shape, s):
         return rng.uniform(-s, s, shape)
 
-    p = {"P_w": u((W, cfg.cin), cfg.cin), "P_b": u((W,), cfg.cin)}
+    p = {"P1_w": u((LH, cfg.cin), 1 / math.sqrt(cfg.cin)), "P1_b": u((LH,), 1 / math.sqrt(cfg.cin)),
+         "P2_w": u((W, LH), 1 / math.sqrt(LH)), "P2_b": u((W,), 1 / math.sqrt(LH))}
     for l in range(cfg.layers):
         scale = 1.0 / (W * W)
         p[f"R{l}"] = (rng.uniform(-scale, scale, (W, W, mz, 2 * my, 2 * mx))
                       + 1j * rng.uniform(-scale, scale, (W, W, mz, 2 * my, 2 * mx)))
-        p[f"W{l}_w"] = u((W, W), W)
-        p[f"W{l}_b"] = u((W,), W)
-    p["Q1_w"] = u((cfg.hidden, W), W)
-    p["Q1_b"] = u((cfg.hidden,), W)
-    p["Q2_w"] = u((cfg.cout, cfg.hidden), cfg.hidden)
-    p["Q2_b"] = u((cfg.cout,), cfg.hidden)
+        p[f"W{l}_w"] = u((W, W), 1 / math.sqrt(W))
+        p[f"W{l}_b"] = u((W,), 1 / math.sqrt(W))
+    p["Q1_w"] = u((cfg.hidden, W), 1.0 / W)
+    p["Q1_b"] = u((cfg.hidden,), 1 / math.sqrt(W))
+    p["Q2_w"] = u((cfg.cout, cfg.hidden), math.sqrt(6.0 / cfg.hidden) / cfg.omega0)
+    p["Q2_b"] = u((cfg.cout,), 1 / math.sqrt(cfg.hidden))
     return p
 
 
 def forward(p, x, cfg, keep=False):
-    v = pointwise(p["P_w"], p["P_b"], x)
-    tape = {"x": x, "v": [v], "pre": [], "Vhat": []}
+    apre = pointwise(p["P1_w"], p["P1_b"], x)                  # feed-forward lift
+    a = gelu(apre)
+    v = pointwise(p["P2_w"], p["P2_b"], a)
+    tape = {"x": x, "apre": apre, "a": a, "v": [v], "pre": [], "Vhat": []}
     for l in range(cfg.layers):
         Vh = dft_r(v, cfg)                                        # [B, i, K]
         G = np.einsum('bi...,io...->bo...', Vh, p[f"R{l}"])
@@ -165,8 +183,7 @@ def forward(p, x, cfg, keep=False):
         tape["Vhat"].append(Vh)
         tape["pre"].append(pre)
         tape["v"].append(v)
-    hpre = pointwise(p["Q1_w"], p["Q1_b"], v)
-    h = gelu(hpre)
+    h, hpre = siren(p["Q1_w"], p["Q1_b"], v, cfg.omega0)         # SIREN projection
     y = pointwise(p["Q2_w"], p["Q2_b"], h)
     tape.update(hpre=hpre, h=h)
     return (y, tape) if keep else y
@@ -186,7 +203,7 @@ def backward(p, tape, y, t, m, cfg):
     h, hpre = tape["h"], tape["hpre"]
     g["Q2_w"] = channel_outer(gy, h)
     g["Q2_b"] = gy.sum(axis=tuple(i for i in range(gy.ndim) if i != 1))
-    gh = np.einsum('oi,bo...->bi...', p["Q2_w"], gy) * gelu_grad(hpre)
+    gh = np.einsum('oi,bo...->bi...', p["Q2_w"], gy) * (cfg.omega0 * np.cos(cfg.omega0 * hpre))
     v = tape["v"][-1]
     g["Q1_w"] = channel_outer(gh, v)
     g["Q1_b"] = gh.sum(axis=tuple(i for i in range(gh.ndim) if i != 1))
@@ -203,9 +220,12 @@ def backward(p, tape, y, t, m, cfg):
         g[f"R{l}"] = np.einsum('boklm,biklm->ioklm', gG, np.conj(Vh))
         gVh = np.einsum('bo...,io...->bi...', gG, np.conj(p[f"R{l}"]))
         gv = gv_point + dft_r_adjoint(gVh, cfg)
-    x = tape["x"]
-    g["P_w"] = channel_outer(gv, x)
-    g["P_b"] = gv.sum(axis=tuple(i for i in range(gv.ndim) if i != 1))
+    a, apre, x = tape["a"], tape["apre"], tape["x"]
+    g["P2_w"] = channel_outer(gv, a)
+    g["P2_b"] = gv.sum(axis=tuple(i for i in range(gv.ndim) if i != 1))
+    ga = np.einsum('oi,bo...->bi...', p["P2_w"], gv) * gelu_grad(apre)
+    g["P1_w"] = channel_outer(ga, x)
+    g["P1_b"] = ga.sum(axis=tuple(i for i in range(ga.ndim) if i != 1))
     return g
 
 

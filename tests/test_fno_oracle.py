@@ -8,8 +8,9 @@ import pytest
 import oracle.fno as F
 
 
-def tiny(grid=(8, 6, 10), modes=(3, 2, 3), width=3, layers=2, hidden=5):
-    return F.FNOConfig(grid=grid, cin=2, width=width, cout=2, modes=modes, layers=layers, hidden=hidden)
+def tiny(grid=(8, 6, 10), modes=(3, 2, 3), width=3, layers=2, hidden=5, lift_hidden=4, omega0=30.0):
+    return F.FNOConfig(grid=grid, cin=2, width=width, cout=2, modes=modes, layers=layers, hidden=hidden,
+                       lift_hidden=lift_hidden, omega0=omega0)
 
 
 def rng(s=0):
@@ -132,3 +133,71 @@ def test_region_mask_box():
     z, y, x = np.nonzero(m)
     assert (x.min(), x.max() + 1) == (12, 115) and (y.min(), y.max() + 1) == (16, 48)
     assert (z.min(), z.max() + 1) == (16, 48)
+
+
+# --------------------------------------------------------------------------
+# App. B's lift (feed-forward network) and projection (SIREN)
+# --------------------------------------------------------------------------
+def test_siren_projection_is_periodic_in_its_bias():
+    """sin(omega0 (Q1 v + b)) is unchanged when b moves by 2 pi / omega0: the
+    frequency factor multiplies the bias as well as Q1 v."""
+    cfg = tiny()
+    p = F.init_params(cfg, seed=11)
+    x = rng(12).normal(size=(2, cfg.cin) + cfg.grid)
+    y0 = F.forward(p, x, cfg)
+    q = dict(p)
+    q["Q1_b"] = p["Q1_b"] + 2 * np.pi / cfg.omega0 * rng(13).integers(-3, 4, size=p["Q1_b"].shape)
+    assert np.abs(F.forward(q, x, cfg) - y0).max() < 1e-12 * np.abs(y0).max()
+    q["Q1_b"] = p["Q1_b"] + np.pi / cfg.omega0         # half a period flips every hidden unit
+    assert np.abs(F.forward(q, x, cfg) - (2 * p["Q2_b"][None, :, None, None, None] - y0)).max() < 1e-12
+
+
+def test_siren_projection_tends_to_the_linear_map_at_small_frequency():
+    """With the output weights scaled by 1/omega0, Q2 sin(omega0 z)/omega0 ->
+    Q2 z as omega0 -> 0, with an error that falls as omega0^2 (the cubic term
+    of the sine)."""
+    base = tiny()
+    p = F.init_params(base, seed=14)
+    x = rng(15).normal(size=(1, base.cin) + base.grid)
+    _, tape = F.forward(p, x, base, keep=True)
+    vL = tape["v"][-1]
+    lin = F.pointwise(p["Q2_w"], p["Q2_b"], F.pointwise(p["Q1_w"], p["Q1_b"], vL))
+    errs = []
+    for w0 in (1e-2, 5e-3):
+        cfg = tiny(omega0=w0)
+        q = dict(p)
+        q["Q2_w"] = p["Q2_w"] / w0
+        errs.append(np.abs(F.forward(q, x, cfg) - lin).max())
+    assert errs[0] < 1e-3 * np.abs(lin).max()
+    assert 3.9 < errs[0] / errs[1] < 4.1
+
+
+def test_lift_is_two_layers_with_gelu_between():
+    """Where every hidden pre-activation is large and positive, GELU is the
+    identity to rounding (x Phi(x), Phi(9) = 1 - 1e-19), so the lift collapses
+    to the affine map P2 (P1 x + b1) + b2; where they are large and negative
+    GELU is 0 and the lift is the constant b2."""
+    cfg = tiny(layers=1)
+    p = F.init_params(cfg, seed=16)
+    x = np.abs(rng(17).normal(size=(1, cfg.cin) + cfg.grid))
+    for sign in (1.0, -1.0):
+        q = dict(p)
+        q["P1_w"] = sign * np.abs(p["P1_w"])
+        q["P1_b"] = np.full_like(p["P1_b"], sign * 9.0)
+        _, tape = F.forward(q, x, cfg, keep=True)
+        v0 = tape["v"][0]
+        if sign > 0:
+            ref = F.pointwise(q["P2_w"], q["P2_b"], F.pointwise(q["P1_w"], q["P1_b"], x))
+        else:
+            ref = np.broadcast_to(q["P2_b"][None, :, None, None, None], v0.shape)
+        assert np.abs(v0 - ref).max() < 1e-12 * max(1.0, np.abs(ref).max())
+
+
+def test_siren_initialisation_ranges():
+    """Sitzmann et al.'s initialisation of the projection: first-layer weights
+    within 1/fan_in, output weights within sqrt(6/fan_in)/omega0."""
+    cfg = F.FNOConfig(grid=(4, 4, 4), width=32, hidden=128)
+    p = F.init_params(cfg, seed=18)
+    assert np.abs(p["Q1_w"]).max() <= 1 / 32 and np.abs(p["Q1_w"]).max() > 0.9 / 32
+    lim = math.sqrt(6 / 128) / 30
+    assert np.abs(p["Q2_w"]).max() <= lim and np.abs(p["Q2_w"]).max() > 0.9 * lim
