@@ -24,6 +24,7 @@ class OracleParams(C.Structure):
         ("galilean", C.c_int32), ("pad0", C.c_int32),
         ("u_in", C.c_double), ("rho_in", C.c_double), ("rho_out", C.c_double),
         ("mean_start", C.c_int64), ("mean_end", C.c_int64), ("mean_every", C.c_int64),
+        ("param4", C.c_int32), ("pad1", C.c_int32), ("limiter", C.c_double),
     ]
 
 
@@ -40,6 +41,7 @@ def lib():
         L.oracle_weights.argtypes = [dp]
         L.oracle_omega_from_re.argtypes = [C.c_double] * 3
         L.oracle_omega_from_re.restype = C.c_double
+        L.oracle_param4_rates.argtypes = [C.c_double, C.c_double, dp]
         L.oracle_equilibrium.argtypes = [C.c_double] * 4 + [dp]
         L.oracle_macros.argtypes = [dp, dp, dp]
         L.oracle_central_moments.argtypes = [dp, dp, dp, dp]
@@ -92,7 +94,7 @@ def omega_from_re(re, u, l_ref):
 
 def params(nx, ny, nz, omega1, omega2=1.0, omega3=1.0, galilean=1, u_in=0.0,
            rho_in=1.0, rho_out=1.0, faces=("inlet", "outlet", "wall", "wall"),
-           mean=(0, 0, 0)):
+           mean=(0, 0, 0), param4=0, limiter=0.01):
     kinds = {"wall": FACE_WALL, "periodic": FACE_PERIODIC,
              "inlet": FACE_INLET, "outlet": FACE_OUTLET, "outflow": FACE_OUTFLOW}
     p = OracleParams()
@@ -102,7 +104,15 @@ def params(nx, ny, nz, omega1, omega2=1.0, omega3=1.0, galilean=1, u_in=0.0,
     p.galilean = int(galilean)
     p.u_in, p.rho_in, p.rho_out = u_in, rho_in, rho_out
     p.mean_start, p.mean_end, p.mean_every = mean
+    p.param4, p.limiter = int(param4), float(limiter)
     return p
+
+
+def param4_rates(w1, w2=1.0):
+    """(omega3, omega4, omega5, A, B) of the fourth-order parametrisation."""
+    out = np.zeros(5)
+    lib().oracle_param4_rates(float(w1), float(w2), _dp(out))
+    return out
 
 
 def equilibrium(rho, ux, uy, uz):

@@ -78,6 +78,10 @@ typedef struct {
     double rho_in;                /* wall density in the moving-wall term */
     double rho_out;               /* outlet density                     */
     int64_t mean_start, mean_end, mean_every; /* averaging window (steps) */
+    int32_t param4;               /* 1: fourth-order parametrisation with limiter
+                                   * (Geier et al. 2017) instead of omega3      */
+    int32_t pad1;
+    double limiter;               /* lambda of that limiter                    */
 } oracle_params;
 
 /* Shear rate from the Reynolds number at fixed inlet velocity (Sec. 3.1:
@@ -257,13 +261,84 @@ void oracle_moments_from_cumulants(const double *C, double *k)
 #undef K
 
 /* ---- relaxation --------------------------------------------------------- */
+/* Rates of the fourth-order parametrisation (Geier, Pasquali & Schoenherr
+ * 2017), functions of the shear rate w1 and the bulk rate w2 chosen so that
+ * the leading error of the diffusion term cancels: omega3 (sums of third-
+ * order cumulant pairs), omega4 (their differences), omega5 (C_111), and the
+ * coefficients A, B of the fourth-order cumulants' equilibria.  Undefined at
+ * w1 = w2 (A and B have the factor w1 - w2 in their denominators). */
+void oracle_param4_rates(double w1, double w2, double *out5)
+{
+    out5[0] = 8.0 * (w1 - 2.0) * (w2 * (3.0 * w1 - 1.0) - 5.0 * w1)
+            / (8.0 * (5.0 - 2.0 * w1) * w1 + w2 * (8.0 + w1 * (9.0 * w1 - 26.0)));
+    out5[1] = 8.0 * (w1 - 2.0) * (w1 + w2 * (3.0 * w1 - 7.0))
+            / (w2 * (56.0 - 42.0 * w1 + 9.0 * w1 * w1) - 8.0 * w1);
+    out5[2] = 24.0 * (w1 - 2.0) * (4.0 * w1 * w1 + w1 * w2 * (18.0 - 13.0 * w1) + w2 * w2 * (2.0 + w1 * (6.0 * w1 - 11.0)))
+            / (16.0 * w1 * w1 * (w1 - 6.0) - 2.0 * w1 * w2 * (216.0 + 5.0 * w1 * (9.0 * w1 - 46.0))
+               + w2 * w2 * (w1 * (3.0 * w1 - 10.0) * (15.0 * w1 - 28.0) - 48.0));
+    const double den = (w1 - w2) * (w2 * (2.0 + 3.0 * w1) - 8.0 * w1);
+    out5[3] = (4.0 * w1 * w1 + 2.0 * w1 * w2 * (w1 - 6.0) + w2 * w2 * (w1 * (10.0 - 3.0 * w1) - 4.0)) / den;
+    out5[4] = (4.0 * w1 * w2 * (9.0 * w1 - 16.0) - 4.0 * w1 * w1 - 2.0 * w2 * w2 * (2.0 + 9.0 * w1 * (w1 - 2.0)))
+            / (3.0 * den);
+}
+
+/* Relaxation rate w raised towards 1 where the cumulant X is large against
+ * the limiter lambda: w + (1 - w) |X| / (|X| + lambda). */
+static double limited(double w, double X, double lambda)
+{
+    return w + (1.0 - w) * fabs(X) / (fabs(X) + lambda);
+}
+
+/* Orders 3..6 of the parametrised operator (normalised cumulants):
+ *   third order in the combinations C_210 +- C_012, C_201 +- C_021,
+ *   C_120 +- C_102 (sums with omega3, differences with omega4) and C_111
+ *   (omega5), each rate limited by the size of its own combination;
+ *   fourth order set to the equilibria that carry the velocity gradients
+ *   (rates 1): C*_220 = -(2/3) A (1/w1 - 1/2)(dxu + dyv) and its two
+ *   permutations, C*_211 = -(1/3) B (1/w1 - 1/2) D_yz with D_yz = -3 w1 C_011
+ *   the shear-rate estimate, and its two permutations;
+ *   fifth and sixth orders to 0. */
+static void parametrised_higher_orders(const oracle_params *p, const double *C, double dxu, double dyv, double dzw,
+                                       double *Cs)
+{
+    const double w1 = p->omega1, lam = p->limiter;
+    double r[5];
+    oracle_param4_rates(w1, p->omega2, r);
+    const double w3 = r[0], w4 = r[1], w5 = r[2], A = r[3], B = r[4];
+    /* third order: (first, second) of each pair, sum and difference */
+    static const int pairs[3][2][3] = {{{2, 1, 0}, {0, 1, 2}}, {{2, 0, 1}, {0, 2, 1}}, {{1, 2, 0}, {1, 0, 2}}};
+    for (int k = 0; k < 3; ++k) {
+        const int a = MI(pairs[k][0][0], pairs[k][0][1], pairs[k][0][2]);
+        const int b = MI(pairs[k][1][0], pairs[k][1][1], pairs[k][1][2]);
+        const double sp = C[a] + C[b], sm = C[a] - C[b];
+        const double sps = (1.0 - limited(w3, sp, lam)) * sp;
+        const double sms = (1.0 - limited(w4, sm, lam)) * sm;
+        Cs[a] = 0.5 * (sps + sms);
+        Cs[b] = 0.5 * (sps - sms);
+    }
+    Cs[MI(1,1,1)] = (1.0 - limited(w5, C[MI(1,1,1)], lam)) * C[MI(1,1,1)];
+    /* fourth order */
+    const double visc = 1.0 / w1 - 0.5;
+    Cs[MI(2,2,0)] = -(2.0 / 3.0) * A * visc * (dxu + dyv);
+    Cs[MI(2,0,2)] = -(2.0 / 3.0) * A * visc * (dxu + dzw);
+    Cs[MI(0,2,2)] = -(2.0 / 3.0) * A * visc * (dyv + dzw);
+    Cs[MI(2,1,1)] = -(1.0 / 3.0) * B * visc * (-3.0 * w1 * C[MI(0,1,1)]);
+    Cs[MI(1,2,1)] = -(1.0 / 3.0) * B * visc * (-3.0 * w1 * C[MI(1,0,1)]);
+    Cs[MI(1,1,2)] = -(1.0 / 3.0) * B * visc * (-3.0 * w1 * C[MI(1,1,0)]);
+    /* fifth and sixth */
+    Cs[MI(1,2,2)] = Cs[MI(2,1,2)] = Cs[MI(2,2,1)] = 0.0;
+    Cs[MI(2,2,2)] = 0.0;
+}
+
 /* Cumulant relaxation (Geier et al. 2015, the operator of Sec. 3.2):
  *   - off-diagonal second order relaxes with the shear rate omega1,
  *   - the two deviatoric differences of the diagonal with omega1 and the trace
  *     with the bulk rate omega2, towards 0 and 1 (normalised), each carrying the
  *     Galilean correction built from the velocity-derivative estimates
  *     dxu, dyv, dzw that the non-equilibrium diagonal moments imply,
- *   - every cumulant of order 3..6 relaxes with omega3 towards 0. */
+ *   - every cumulant of order 3..6 relaxes with omega3 towards 0, or, with
+ *     param4, as the fourth-order parametrisation prescribes (see
+ *     parametrised_higher_orders). */
 void oracle_relax(const oracle_params *p, const double *u, const double *C, double *Cs)
 {
     const double w1 = p->omega1, w2 = p->omega2, w3 = p->omega3;
@@ -291,6 +366,8 @@ void oracle_relax(const oracle_params *p, const double *u, const double *C, doub
     Cs[MI(2,0,0)] = (dxy_s + dxz_s + tr_s) / 3.0;
     Cs[MI(0,2,0)] = Cs[MI(2,0,0)] - dxy_s;
     Cs[MI(0,0,2)] = Cs[MI(2,0,0)] - dxz_s;
+
+    if (p->param4) parametrised_higher_orders(p, C, dxu, dyv, dzw, Cs);
 }
 
 /* ---- back to populations -------------------------------------------- */
