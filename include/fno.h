@@ -5,11 +5,13 @@
  * trained with a masked mean square error on the inner region of the
  * channel, Adam, cosine learning-rate schedule).
  *
- * Network, for fields laid out [batch][channel][z][y][x] (x fastest):
- *   lift      v0 = P x + bP                           (pointwise cin -> width)
- *   layer l   v_{l+1} = act(K_l v_l + W_l v_l + b_l)  (GELU except after the last)
- *             K_l v = IDFT_r(R_l . DFT_r(v))          (retained modes only)
- *   project   y = Q2 GELU(Q1 v_L + bQ1) + bQ2         (width -> hidden -> cout)
+ * Network (App. B: feed-forward lifting network, Fourier layers, SIREN
+ * projection of Sitzmann et al. 2020), for fields laid out
+ * [batch][channel][z][y][x] (x fastest):
+ *   lift      v0 = P2 GELU(P1 x + bP1) + bP2           (cin -> lift_hidden -> width)
+ *   layer l   v_{l+1} = act(K_l v_l + W_l v_l + b_l)   (GELU except after the last)
+ *             K_l v = IDFT_r(R_l . DFT_r(v))           (retained modes only)
+ *   project   y = Q2 sin(omega0 (Q1 v_L + bQ1)) + bQ2  (width -> hidden -> cout)
  * DFT_r keeps kx in [0,mx) U [-mx,0), ky in [0,my) U [-my,0), kz in [0,mz)
  * (z is the real-to-half-complex axis); the inverse is
  * y(x) = (1/N) Re[sum_k c_kz G(k) exp(+i theta_k . x)], c_0 = 1, c_kz = 2.
@@ -18,7 +20,8 @@
  * Parameters are one flat FP32 vector, in this order:
  *   R_0 .. R_{layers-1}, each [K][width_in][width_out][re, im] (K = mz*2my*2mx
  *   modes, k = (kz*2my + jy)*2mx + jx; first, so that every complex entry is
- *   8-byte aligned), P_w [width][cin], P_b [width],
+ *   8-byte aligned), P1_w [lift_hidden][cin], P1_b [lift_hidden],
+ *   P2_w [width][lift_hidden], P2_b [width],
  *   per layer l: W_l_w [width][width], W_l_b [width],
  *   Q1_w [hidden][width], Q1_b [hidden], Q2_w [cout][hidden], Q2_b [cout].
  *
@@ -48,12 +51,18 @@ typedef struct {
     int32_t act_bf16;            /* 1: activations stored in BF16 (else FP32)      */
     int32_t tensor_cores;        /* 1: mode contraction on tensor cores in BF16
                                     with FP32 accumulation (needs width % 8 == 0) */
+    int32_t lift_hidden;         /* hidden width of the lifting network (<= 32)    */
+    float omega0;                /* SIREN frequency factor (> 0; default 30)       */
     uint64_t seed;               /* initial parameters                             */
 } fno_config;
 
 /* Defaults of the channel surrogate: 128x64x64 grid, 4 inputs (mask, log10
- * Re, cos and sin of the angle of attack), width 32, modes 16x8x8, 4 layers,
- * hidden 128, 4 outputs (u, v, w, p), batch 8, BF16 activations, tensor cores. */
+ * Re, cos and sin of the angle of attack), lift 4 -> 32 -> 32, width 32, modes
+ * 16x8x8, 4 layers, SIREN projection 32 -> 128 -> 4 with omega0 = 30, 4
+ * outputs (u, v, w, p), batch 8, BF16 activations, tensor cores.  Initial
+ * parameters: uniform within 1/sqrt(fan_in), spectral weights within
+ * 1/width^2, SIREN first layer within 1/fan_in and output layer within
+ * sqrt(6/fan_in)/omega0 (Sitzmann et al. 2020). */
 void fno_config_default(fno_config *c);
 
 lbm_status fno_create(const fno_config *c, void *cuda_stream, fno_ctx **out);

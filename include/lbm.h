@@ -102,7 +102,22 @@ typedef struct {
     int32_t block_y;        /* rows per block (0: 1); block_x * block_y <= 256   */
     int32_t stats;          /* 1: also accumulate the velocity products of the
                                averaged samples (lbm_read_stats)                */
-    int32_t reserved[5];
+    /* Sec. 3.2: the fourth-order parametrisation with limiter (Geier,
+     * Pasquali & Schoenherr 2017) in place of omega_higher: third-order
+     * cumulants relax in the combinations C_210 +- C_012, C_201 +- C_021,
+     * C_120 +- C_102 (sums with omega3, differences with omega4) and C_111
+     * (omega5), each rate limited as w + (1 - w)|X| / (|X| + limiter); the
+     * fourth-order cumulants are set to C_220 = -(2/3) A (1/w1 - 1/2)(dxu + dyv)
+     * (and permutations) and C_211 = B (1 - w1/2) C_011 (and permutations),
+     * with dxu, dyv, dzw the velocity-derivative estimates of the Galilean
+     * correction; fifth and sixth orders to 0.  omega3..5, A and B are the
+     * published functions of omega1 and omega_bulk; they are undefined at
+     * omega1 = omega_bulk (LBM_ERR_ARG).  The paper switches it on for
+     * Re_c >= 3000 only: at elevated viscosity (omega1 below about 1.8 with
+     * omega_bulk = 1) some of these rates leave (0, 2). */
+    int32_t param4;         /* 1: the parametrisation above (default 0)          */
+    double limiter;         /* its limiter lambda (default 0.01)                 */
+    int32_t reserved[2];
 } lbm_params;
 
 /* Fill *p with the defaults listed above (re = 1000, u_in = 0.05, l_ref = 1,
@@ -181,6 +196,21 @@ lbm_status lbm_set_probes(lbm_ctx *ctx, int64_t n, const int64_t *cells, int64_t
 /* The probe record so far, rows of n x 4 floats (host or device dst, at most
  * max_rows rows); n_rows (may be NULL) receives the rows recorded. */
 lbm_status lbm_read_probes(lbm_ctx *ctx, float *dst, int64_t max_rows, int64_t *n_rows);
+
+/* Monitor plane (Sec. 2: "2D snapshots of the center x-y plane for
+ * monitoring the development of the entire simulation"): before every step t
+ * with t % every == 0, the (ux, uy, uz, p) of the plane z (z < 0: nz / 2) of
+ * the state at t are recorded as FP32 [ny][nx][4] (solid cells 0) into a
+ * device ring of `capacity` planes that is flushed to host memory when full.
+ * every = 0 switches it off.  Not on batch members (LBM_ERR_STATE).  Setting
+ * it discards the planes recorded so far. */
+lbm_status lbm_set_plane_monitor(lbm_ctx *ctx, int32_t z, int64_t every, int64_t capacity);
+
+/* The planes recorded so far, oldest first: dst [k][ny][nx][4] floats (host or
+ * device), at most max_planes; *n_planes (may be NULL) receives the number
+ * recorded and steps[k] (host, may be NULL) the step of plane k. */
+lbm_status lbm_read_plane_monitor(lbm_ctx *ctx, float *dst, int64_t max_planes, int64_t *n_planes,
+                                  int64_t *steps);
 
 /* Turbulence statistics (Sec. 3.3 validates turbulent fluctuations): the
  * velocity covariances over the same samples as the time average, per cell
@@ -388,6 +418,21 @@ lbm_status lbm_totals_noalloc(const void *pdf, int32_t storage, int64_t slot_str
                               void *cuda_stream, double *out);
 
 /* Last error message of this context (never NULL). */
+/* Resampling of mean fields onto another grid (App. B: the simulated fields
+ * are scaled down to the surrogate's 128x64x64 grid): cell-centred trilinear
+ * interpolation.  Target cell o of an axis with n source and m target cells
+ * samples the source at s = (o + 1/2) n/m - 1/2 clamped to [0, n - 1],
+ * linearly between floor(s) and floor(s) + 1 (a factor 2 is the 2-cell mean,
+ * a factor 1 the identity); the 3D map is the product of the three axes.
+ *   src    device array of `channels` fields on the nx x ny x nz grid:
+ *          src_layout 0 = [z][y][x][channels] (the layout of lbm_read_mean),
+ *          1 = [channels][z][y][x].
+ *   dst    device array [channels][mz][my][mx] (the FNO's input layout).
+ * FP32 arithmetic; asynchronous on cuda_stream.  Host pointers, empty grids
+ * or an unknown layout return LBM_ERR_ARG (message in lbm_last_error(NULL)). */
+lbm_status lbm_resample(const float *src, int32_t nx, int32_t ny, int32_t nz, int32_t channels, int32_t src_layout,
+                        float *dst, int32_t mx, int32_t my, int32_t mz, void *cuda_stream);
+
 const char *lbm_last_error(const lbm_ctx *ctx);
 const char *lbm_status_string(lbm_status s);
 

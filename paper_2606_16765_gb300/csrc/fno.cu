@@ -3,12 +3,17 @@
 // baseline models: FNO of Li et al. 2021 mapping mask and Re to the mean
 // field).
 //
+// Network (App. B): feed-forward lift P2 GELU(P1 x), Fourier layers, SIREN
+// projection Q2 sin(omega0 (Q1 v + b)) (Sitzmann et al. 2020).
+//
 // Kernels:
 //   k_pw_fwd_*   pointwise layers (lift, W path, projection) with fused bias,
-//                spectral-branch add and GELU; pre-activations kept for backward
-//   k_proj_fused inference projection Q2 GELU(Q1 v) without storing the
-//                hidden activations
-//   k_pw_bwd_*   input gradients of pointwise layers with fused GELU'
+//                spectral-branch add and activation (GELU, or the SIREN sine,
+//                whose kept value is cos(omega0 z) for the backward)
+//   k_proj_fused inference projection Q2 sin(omega0 (Q1 v + b1)) without
+//                storing the hidden activations
+//   k_pw_bwd_*   input gradients of pointwise layers with the fused
+//                activation derivative
 //   k_outer      weight/bias gradients sum_{b,cell} gout x (k_outer_async:
 //                cp.async double-buffered tiles)
 //   k_dft*       truncated DFT in three separable stages (x, y, z) and the
@@ -52,6 +57,36 @@ __device__ __forceinline__ float gelu_grad(float x)
     return 0.5f * (1.f + erff(x * 0.70710678118654752f)) + x * expf(-0.5f * x * x) * 0.39894228040143268f;
 }
 
+// Activations of the pointwise layers.  The forward keeps, per element, what
+// the backward needs: the pre-activation z for GELU, cos(omega0 z) for the
+// SIREN sine (so that the backward needs no transcendental and does not
+// amplify the storage rounding of z by omega0).  FP32 activations take the
+// accurate sincosf, BF16 activations the hardware __sincosf, whose phase
+// error (about |omega0 z| x 2^-23) is far below BF16's rounding.
+enum { ACT_NONE = 0, ACT_GELU = 1, ACT_SIREN = 2 };
+
+template <bool FAST>
+__device__ __forceinline__ float act_fwd(int act, float w0, float z, float &keep)
+{
+    if (act == ACT_SIREN) {
+        float sn, cs;
+        if (FAST) __sincosf(w0 * z, &sn, &cs);
+        else sincosf(w0 * z, &sn, &cs);
+        keep = cs;
+        return sn;
+    }
+    keep = z;
+    return act == ACT_GELU ? gelu(z) : z;
+}
+
+__device__ __forceinline__ float act_grad(int act, float w0, float kept)
+{
+    return act == ACT_SIREN ? w0 * kept : gelu_grad(kept);
+}
+
+template <class T> struct IsBF16 { static constexpr bool value = false; };
+template <> struct IsBF16<__nv_bfloat16> { static constexpr bool value = true; };
+
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) { return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
 __device__ __forceinline__ float2 cmulc(float2 a, float2 b) { return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y); }  // a conj(b)
 
@@ -63,7 +98,8 @@ int grid_for(int64_t n, int block = TPB) { return (int)std::min<int64_t>((n + bl
 // y = act(W x + b + extra) for ci <= 32 (inputs cached in registers).
 template <class TI, class TO>
 __global__ void __launch_bounds__(TPB) k_pw_fwd_in(const TI *x, int ci, int co, const float *W, const float *bias,
-                                                   const float *extra, TO *pre, TO *y, int act, int64_t N, int B)
+                                                   const float *extra, TO *pre, TO *y, int act, float w0, int64_t N,
+                                                   int B)
 {
     extern __shared__ float sm[];
     float *sw = sm, *sb = sm + co * ci;
@@ -83,8 +119,10 @@ __global__ void __launch_bounds__(TPB) k_pw_fwd_in(const TI *x, int ci, int co, 
                 if (i < ci) acc += sw[o * ci + i] * xv[i];
             const int64_t off = (b * co + o) * N + n;
             if (extra) acc += extra[off];
-            if (pre) stf(pre + off, acc);
-            stf(y + off, act ? gelu(acc) : acc);
+            float keep;
+            const float out = act_fwd<IsBF16<TO>::value>(act, w0, acc, keep);
+            if (pre) stf(pre + off, keep);
+            stf(y + off, out);
         }
     }
 }
@@ -164,7 +202,8 @@ __device__ __forceinline__ void st2(__nv_bfloat16 *p, float a, float b)
 // y = act(W x + b + extra) for CI inputs (a multiple of 4) held in registers.
 template <class TI, class TO, int CI>
 __global__ void __launch_bounds__(TPB) k_pw_fwd_in2(const TI *x, int co, const float *W, const float *bias,
-                                                    const float *extra, TO *pre, TO *y, int act, int64_t N, int B)
+                                                    const float *extra, TO *pre, TO *y, int act, float w0, int64_t N,
+                                                    int B)
 {
     extern __shared__ float4 smv[];
     float *sw = reinterpret_cast<float *>(smv), *sb = sw + co * CI;
@@ -194,20 +233,24 @@ __global__ void __launch_bounds__(TPB) k_pw_fwd_in2(const TI *x, int co, const f
                     a1 += w.x * xv[4 * q].y + w.y * xv[4 * q + 1].y + w.z * xv[4 * q + 2].y + w.w * xv[4 * q + 3].y;
                 }
                 const int64_t off = (b * co + o) * N + n;
-                if (pre) st2(pre + off, a0, a1);
-                st2(y + off, act ? gelu(a0) : a0, act ? gelu(a1) : a1);
+                float k0, k1;
+                const float y0 = act_fwd<IsBF16<TO>::value>(act, w0, a0, k0);
+                const float y1 = act_fwd<IsBF16<TO>::value>(act, w0, a1, k1);
+                if (pre) st2(pre + off, k0, k1);
+                st2(y + off, y0, y1);
             }
         }
     }
 }
 
-// Inference projection y = Q2 GELU(Q1 v + b1) + b2 in one pass (the hidden
+// Inference projection y = Q2 sin(omega0 (Q1 v + b1)) + b2 in one pass (the hidden
 // activations are never stored): CI inputs and co <= 8 outputs in registers,
 // the H hidden units streamed, two adjacent cells per thread.  Shared
 // memory: Q1 [H][CI], b1 [H], Q2 transposed to [H][8] (zero padded).
 template <class TI, int CI>
 __global__ void __launch_bounds__(TPB) k_proj_fused(const TI *v, int H, int co, const float *W1, const float *b1,
-                                                    const float *W2, const float *b2, float *y, int64_t N, int B)
+                                                    const float *W2, const float *b2, float w0, float *y, int64_t N,
+                                                    int B)
 {
     extern __shared__ float4 smv[];
     float *s1 = reinterpret_cast<float *>(smv);
@@ -239,7 +282,9 @@ __global__ void __launch_bounds__(TPB) k_proj_fused(const TI *v, int H, int co, 
                 a0 += w.x * xv[4 * q].x + w.y * xv[4 * q + 1].x + w.z * xv[4 * q + 2].x + w.w * xv[4 * q + 3].x;
                 a1 += w.x * xv[4 * q].y + w.y * xv[4 * q + 1].y + w.z * xv[4 * q + 2].y + w.w * xv[4 * q + 3].y;
             }
-            const float g0 = gelu(a0), g1 = gelu(a1);
+            float k0, k1;
+            const float g0 = act_fwd<IsBF16<TI>::value>(ACT_SIREN, w0, a0, k0);
+            const float g1 = act_fwd<IsBF16<TI>::value>(ACT_SIREN, w0, a1, k1);
             const float4 wa = reinterpret_cast<const float4 *>(s2)[2 * hh];
             const float4 wb = reinterpret_cast<const float4 *>(s2)[2 * hh + 1];
             const float w2[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
@@ -297,10 +342,11 @@ __global__ void __launch_bounds__(TPB) k_pw_fwd_out2(const TI *x, int ci, int co
     }
 }
 
-// gx = (W^T g) * (pre_in ? gelu'(pre_in) : 1) for CI inputs (a multiple of 4).
+// gx = (W^T g) * (pre_in ? act'(pre_in) : 1) for CI inputs (a multiple of 4);
+// pre_in holds what the forward kept (see act_fwd).
 template <class TP, int CI>
 __global__ void __launch_bounds__(TPB) k_pw_bwd_in2(const float *g, int co, const float *W, const TP *pre_in,
-                                                    float *gx, int64_t N, int B)
+                                                    int act, float w0, float *gx, int64_t N, int B)
 {
     extern __shared__ float4 smv[];
     float *sw = reinterpret_cast<float *>(smv);
@@ -335,8 +381,8 @@ __global__ void __launch_bounds__(TPB) k_pw_bwd_in2(const float *g, int co, cons
 #pragma unroll
             for (int i = 0; i < CI; ++i) {
                 const float2 p = ld2(pre_in + (b * CI + i) * N + n);
-                acc[i].x *= gelu_grad(p.x);
-                acc[i].y *= gelu_grad(p.y);
+                acc[i].x *= act_grad(act, w0, p.x);
+                acc[i].y *= act_grad(act, w0, p.y);
             }
         }
 #pragma unroll
@@ -347,7 +393,7 @@ __global__ void __launch_bounds__(TPB) k_pw_bwd_in2(const float *g, int co, cons
 // Same for co <= 8 gradient rows and any number of inputs ([ci][8] weights).
 template <class TP>
 __global__ void __launch_bounds__(TPB) k_pw_bwd_out2(const float *g, int co, int ci, const float *W, const TP *pre_in,
-                                                     float *gx, int64_t N, int B)
+                                                     int act, float w0, float *gx, int64_t N, int B)
 {
     extern __shared__ float4 smv[];
     float *swt = reinterpret_cast<float *>(smv);
@@ -380,8 +426,8 @@ __global__ void __launch_bounds__(TPB) k_pw_bwd_out2(const float *g, int co, int
                     a.y += w[o] * gv[o].y;
                 }
                 if (pre_in) {
-                    a.x *= gelu_grad(p[u].x);
-                    a.y *= gelu_grad(p[u].y);
+                    a.x *= act_grad(act, w0, p[u].x);
+                    a.y *= act_grad(act, w0, p[u].y);
                 }
                 st2(gx + (b * ci + i) * N + n, a.x, a.y);
             }
@@ -389,10 +435,10 @@ __global__ void __launch_bounds__(TPB) k_pw_bwd_out2(const float *g, int co, int
     }
 }
 
-// gx = (W^T g) * (act ? gelu'(pre_in) : 1), ci <= 32 (gx accumulated in registers).
+// gx = (W^T g) * (pre_in ? act'(pre_in) : 1), ci <= 32 (gx accumulated in registers).
 template <class TP>
 __global__ void __launch_bounds__(TPB) k_pw_bwd_in(const float *g, int co, int ci, const float *W, const TP *pre_in,
-                                                   float *gx, int64_t N, int B)
+                                                   int act, float w0, float *gx, int64_t N, int B)
 {
     extern __shared__ float sm[];
     for (int k = threadIdx.x; k < co * ci; k += blockDim.x) sm[k] = W[k];
@@ -413,7 +459,7 @@ __global__ void __launch_bounds__(TPB) k_pw_bwd_in(const float *g, int co, int c
         for (int i = 0; i < 32; ++i)
             if (i < ci) {
                 const int64_t off = (b * ci + i) * N + n;
-                gx[off] = pre_in ? acc[i] * gelu_grad(ldf(pre_in + off)) : acc[i];
+                gx[off] = pre_in ? acc[i] * act_grad(act, w0, ldf(pre_in + off)) : acc[i];
             }
     }
 }
@@ -421,7 +467,7 @@ __global__ void __launch_bounds__(TPB) k_pw_bwd_in(const float *g, int co, int c
 // Same for co <= 8 and any ci (g cached in registers, inputs streamed).
 template <class TP>
 __global__ void __launch_bounds__(TPB) k_pw_bwd_out(const float *g, int co, int ci, const float *W, const TP *pre_in,
-                                                    float *gx, int64_t N, int B)
+                                                    int act, float w0, float *gx, int64_t N, int B)
 {
     extern __shared__ float sm[];
     for (int k = threadIdx.x; k < co * ci; k += blockDim.x) sm[k] = W[k];
@@ -438,7 +484,7 @@ __global__ void __launch_bounds__(TPB) k_pw_bwd_out(const float *g, int co, int 
             for (int o = 0; o < 8; ++o)
                 if (o < co) acc += sm[o * ci + i] * gv[o];
             const int64_t off = (b * ci + i) * N + n;
-            gx[off] = pre_in ? acc * gelu_grad(ldf(pre_in + off)) : acc;
+            gx[off] = pre_in ? acc * act_grad(act, w0, ldf(pre_in + off)) : acc;
         }
     }
 }
@@ -1302,11 +1348,11 @@ __global__ void __launch_bounds__(TPB) k_dftx_inv_tc(const float2 *It, float *ou
     }
 }
 
-// Inference projection y = Q2 GELU(Q1 v + b1) + b2 on tensor cores, for
+// Inference projection y = Q2 sin(omega0 (Q1 v + b1)) + b2 on tensor cores, for
 // BF16 activations with 32 channels, 128 hidden units and co <= 8 outputs:
 // a warp takes 16 cells of one sample per pass.  First product: cells x
 // channels (BF16, exact) times Q1^T (BF16 hi + lo pairs, two products per
-// tile), 16 x 128 FP32 accumulators; bias and GELU on the accumulators,
+// tile), 16 x 128 FP32 accumulators; bias and the sine on the accumulators,
 // which then serve directly as the A fragments of the second product (two
 // adjacent n8 tiles of the first are one k16 step of the second), split into
 // hi + lo; second product against Q2^T (hi + lo; three products per step),
@@ -1317,7 +1363,8 @@ __global__ void __launch_bounds__(TPB) k_dftx_inv_tc(const float2 *It, float *ou
 constexpr int PTC_CI = 32, PTC_H = 128;
 
 __global__ void __launch_bounds__(TPB, 2) k_proj_tc(const __nv_bfloat16 *v, int co, const float *W1, const float *b1,
-                                                 const float *W2, const float *b2, float *y, int64_t N, int B)
+                                                 const float *W2, const float *b2, float w0, float *y, int64_t N,
+                                                 int B)
 {
     __shared__ uint2 q1[2][2 * 16 * 32];    // [hi, lo][(k-step * 16 + n-tile) * 32 + lane]
     __shared__ uint2 q2[2][8 * 32];         // [hi, lo][k-step * 32 + lane]
@@ -1378,10 +1425,10 @@ __global__ void __launch_bounds__(TPB, 2) k_proj_tc(const __nv_bfloat16 *v, int 
 #pragma unroll
         for (int nt = 0; nt < 16; ++nt) {
             const float c0 = sb1[8 * nt + 2 * c], c1 = sb1[8 * nt + 2 * c + 1];
-            acc[nt][0] = gelu(acc[nt][0] + c0);
-            acc[nt][1] = gelu(acc[nt][1] + c1);
-            acc[nt][2] = gelu(acc[nt][2] + c0);
-            acc[nt][3] = gelu(acc[nt][3] + c1);
+            acc[nt][0] = __sinf(w0 * (acc[nt][0] + c0));
+            acc[nt][1] = __sinf(w0 * (acc[nt][1] + c1));
+            acc[nt][2] = __sinf(w0 * (acc[nt][2] + c0));
+            acc[nt][3] = __sinf(w0 * (acc[nt][3] + c1));
         }
         float out[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
@@ -1421,7 +1468,7 @@ __global__ void __launch_bounds__(TPB, 2) k_proj_tc(const __nv_bfloat16 *v, int 
 template <int CO>
 __global__ void __launch_bounds__(TPB) k_pw_tc(const __nv_bfloat16 *x, const float *W, const float *bias,
                                                const float *extra, __nv_bfloat16 *pre, __nv_bfloat16 *y, int act,
-                                               int64_t N, int B)
+                                               float w0, int64_t N, int B)
 {
     constexpr int NT = CO / 8;
     __shared__ uint2 q[2][2 * NT * 32];     // [hi, lo][(k-step * NT + n-tile) * 32 + lane]
@@ -1475,8 +1522,10 @@ __global__ void __launch_bounds__(TPB) k_pw_tc(const __nv_bfloat16 *x, const flo
                 const int64_t off = (b * CO + o) * N + n0 + g + 8 * (e >> 1);
                 float v = acc[nt][e] + sb[o];
                 if (extra) v += extra[off];
-                if (pre) pre[off] = __float2bfloat16_rn(v);
-                y[off] = __float2bfloat16_rn(act ? gelu(v) : v);
+                float keep;
+                const float out = act_fwd<true>(act, w0, v, keep);
+                if (pre) pre[off] = __float2bfloat16_rn(keep);
+                y[off] = __float2bfloat16_rn(out);
             }
     }
 }
@@ -1739,7 +1788,7 @@ struct fno_ctx {
     int64_t N = 0, K = 0, np = 0;
     int Kx = 0, Ky = 0, Kz = 0;
     // parameter offsets in the flat vector
-    int64_t oP_w = 0, oP_b = 0, oQ1_w = 0, oQ1_b = 0, oQ2_w = 0, oQ2_b = 0;
+    int64_t oP1_w = 0, oP1_b = 0, oP2_w = 0, oP2_b = 0, oQ1_w = 0, oQ1_b = 0, oQ2_w = 0, oQ2_b = 0;
     std::vector<int64_t> oR, oW_w, oW_b;
     float *params = nullptr, *grads = nullptr, *m1 = nullptr, *m2 = nullptr;
     int64_t adam_t = 0;
@@ -1747,7 +1796,8 @@ struct fno_ctx {
     std::vector<void *> allocs;
     void *xa = nullptr;                       // converted input (act type)
     std::vector<void *> v, pre;               // activations
-    void *hpre = nullptr, *h = nullptr;
+    void *apre = nullptr, *a = nullptr;       // lift hidden layer: pre-activation, GELU output
+    void *hcos = nullptr, *h = nullptr;       // SIREN hidden layer: cos(omega0 z), sin(omega0 z)
     float *y = nullptr, *spec = nullptr, *gy = nullptr, *ghpre = nullptr, *gA = nullptr, *gB = nullptr;
     float *xin = nullptr, *tin = nullptr, *min = nullptr;
     float2 *stA = nullptr, *stB = nullptr;    // DFT stage temporaries
@@ -1789,6 +1839,8 @@ extern "C" void fno_config_default(fno_config *c)
     c->max_batch = 8;
     c->act_bf16 = 1;
     c->tensor_cores = 1;
+    c->lift_hidden = 32;
+    c->omega0 = 30.f;
     c->seed = 0;
 }
 
@@ -1822,6 +1874,8 @@ extern "C" lbm_status fno_create(const fno_config *cfg, void *stream, fno_ctx **
         c.max_batch < 1)
         return bad("non-positive size");
     if (c.cin > 32 || c.width > 32 || c.cout > 8) return bad("cin and width must be <= 32, cout <= 8");
+    if (c.lift_hidden < 1 || c.lift_hidden > 32) return bad("lift_hidden must be in [1, 32]");
+    if (!(c.omega0 > 0.f) || !std::isfinite(c.omega0)) return bad("omega0 must be a positive finite number");
     if (c.mx < 1 || c.my < 1 || c.mz < 1 || 2 * c.mx > c.nx || 2 * c.my > c.ny || c.mz >= c.nz / 2 + 1 || c.mz > 16)
         return bad("modes must satisfy 2mx <= nx, 2my <= ny, mz <= nz/2, mz <= 16");
     if (c.tensor_cores && c.width % 8 != 0) return bad("tensor-core contraction needs width % 8 == 0");
@@ -1832,7 +1886,8 @@ extern "C" lbm_status fno_create(const fno_config *cfg, void *stream, fno_ctx **
         smem_dfty_inv(d0) > sm_max)
         return bad("grid x modes too large for the shared-memory twiddle tables");
     if (outer_units(c.hidden, c.width) > 2 * TPB || outer_units(c.cout, c.hidden) > 2 * TPB ||
-        outer_units(c.width, c.width) > 2 * TPB || outer_units(c.width, c.cin) > 2 * TPB)
+        outer_units(c.width, c.width) > 2 * TPB || outer_units(c.width, c.lift_hidden) > 2 * TPB ||
+        outer_units(c.lift_hidden, c.cin) > 2 * TPB)
         return bad("layer too wide for the gradient reduction");
     if (smem_outer(c.hidden, c.width) > sm_max || smem_outer(c.cout, c.hidden) > sm_max)
         return bad("layer too wide for the gradient reduction tiles");
@@ -1843,13 +1898,15 @@ extern "C" lbm_status fno_create(const fno_config *cfg, void *stream, fno_ctx **
     f->N = (int64_t)c.nx * c.ny * c.nz;
     f->Kx = 2 * c.mx; f->Ky = 2 * c.my; f->Kz = c.mz;
     f->K = (int64_t)f->Kx * f->Ky * f->Kz;
-    const int W = c.width, H = c.hidden;
+    const int W = c.width, H = c.hidden, LH = c.lift_hidden;
     // spectral weights first: every R_l starts at an even float index, so
     // its complex entries are 8-byte aligned
     int64_t o = 0;
     for (int l = 0; l < c.layers; ++l) { f->oR.push_back(o); o += 2 * f->K * W * W; }
-    f->oP_w = o; o += (int64_t)W * c.cin;
-    f->oP_b = o; o += W;
+    f->oP1_w = o; o += (int64_t)LH * c.cin;
+    f->oP1_b = o; o += LH;
+    f->oP2_w = o; o += (int64_t)W * LH;
+    f->oP2_b = o; o += W;
     for (int l = 0; l < c.layers; ++l) {
         f->oW_w.push_back(o); o += (int64_t)W * W;
         f->oW_b.push_back(o); o += W;
@@ -1869,14 +1926,16 @@ extern "C" lbm_status fno_create(const fno_config *cfg, void *stream, fno_ctx **
     chk(f->xa = f->alloc<char>(B * c.cin * N * es));
     for (int l = 0; l <= c.layers; ++l) { void *p = f->alloc<char>(B * W * N * es); chk(p); f->v.push_back(p); }
     for (int l = 0; l < c.layers; ++l) { void *p = f->alloc<char>(B * W * N * es); chk(p); f->pre.push_back(p); }
-    chk(f->hpre = f->alloc<char>(B * H * N * es));
+    chk(f->apre = f->alloc<char>(B * LH * N * es));
+    chk(f->a = f->alloc<char>(B * LH * N * es));
+    chk(f->hcos = f->alloc<char>(B * H * N * es));
     chk(f->h = f->alloc<char>(B * H * N * es));
     chk(f->y = f->alloc<float>(B * c.cout * N));
     chk(f->spec = f->alloc<float>(B * W * N));
     chk(f->gy = f->alloc<float>(B * c.cout * N));
     chk(f->ghpre = f->alloc<float>(B * H * N));
-    chk(f->gA = f->alloc<float>(B * W * N));
-    chk(f->gB = f->alloc<float>(B * W * N));
+    chk(f->gA = f->alloc<float>(B * std::max(W, LH) * N));
+    chk(f->gB = f->alloc<float>(B * std::max(W, LH) * N));
     chk(f->xin = f->alloc<float>(B * c.cin * N));
     chk(f->tin = f->alloc<float>(B * c.cout * N));
     chk(f->min = f->alloc<float>(B * N));
@@ -1923,20 +1982,24 @@ extern "C" lbm_status fno_create(const fno_config *cfg, void *stream, fno_ctx **
     }
     ok = ok && cudaMemcpy(f->scale_one, one, sizeof one, cudaMemcpyHostToDevice) == cudaSuccess &&
          cudaMemcpy(f->scale_inv, inv, sizeof inv, cudaMemcpyHostToDevice) == cudaSuccess;
-    // initial parameters (same scales as a 1/sqrt(fan-in) uniform init)
+    // initial parameters: uniform within 1/sqrt(fan-in); the SIREN projection
+    // as Sitzmann et al. (first layer within 1/fan-in, output layer within
+    // sqrt(6/fan-in)/omega0)
     std::vector<float> p0(o);
     uint64_t st = c.seed * 0x9E3779B97F4A7C15ull + 12345;
     auto fill = [&](int64_t off, int64_t cnt, double s) { for (int64_t k = 0; k < cnt; ++k) p0[off + k] = (float)(s * unif(st)); };
-    fill(f->oP_w, (int64_t)W * c.cin, 1.0 / std::sqrt((double)c.cin));
-    fill(f->oP_b, W, 1.0 / std::sqrt((double)c.cin));
+    fill(f->oP1_w, (int64_t)LH * c.cin, 1.0 / std::sqrt((double)c.cin));
+    fill(f->oP1_b, LH, 1.0 / std::sqrt((double)c.cin));
+    fill(f->oP2_w, (int64_t)W * LH, 1.0 / std::sqrt((double)LH));
+    fill(f->oP2_b, W, 1.0 / std::sqrt((double)LH));
     for (int l = 0; l < c.layers; ++l) {
         fill(f->oR[l], 2 * f->K * W * W, 1.0 / ((double)W * W));
         fill(f->oW_w[l], (int64_t)W * W, 1.0 / std::sqrt((double)W));
         fill(f->oW_b[l], W, 1.0 / std::sqrt((double)W));
     }
-    fill(f->oQ1_w, (int64_t)H * W, 1.0 / std::sqrt((double)W));
+    fill(f->oQ1_w, (int64_t)H * W, 1.0 / (double)W);
     fill(f->oQ1_b, H, 1.0 / std::sqrt((double)W));
-    fill(f->oQ2_w, (int64_t)c.cout * H, 1.0 / std::sqrt((double)H));
+    fill(f->oQ2_w, (int64_t)c.cout * H, std::sqrt(6.0 / (double)H) / (double)c.omega0);
     fill(f->oQ2_b, c.cout, 1.0 / std::sqrt((double)H));
     ok = ok && cudaMemcpy(f->params, p0.data(), o * sizeof(float), cudaMemcpyHostToDevice) == cudaSuccess &&
          cudaMemset(f->m1, 0, o * sizeof(float)) == cudaSuccess && cudaMemset(f->m2, 0, o * sizeof(float)) == cudaSuccess &&
@@ -1986,6 +2049,7 @@ template <class T>
 void pw_fwd(fno_ctx *f, const T *x, int ci, int co, int64_t oW, int64_t ob, const float *extra, T *pre, void *y,
             bool y_is_float, int act, int B)
 {
+    const float w0 = f->c.omega0;
     const bool pairs = f->N % 2 == 0;
     const int64_t units = pairs ? (int64_t)B * f->N / 2 : (int64_t)B * f->N;
     const float *W = f->params + oW, *bias = f->params + ob;
@@ -2002,13 +2066,14 @@ void pw_fwd(fno_ctx *f, const T *x, int ci, int co, int64_t oW, int64_t ob, cons
             const int blocks = (int)std::min<int64_t>((warps + TPB / 32 - 1) / (TPB / 32), gb300::sm_count() * 8);
             k_pw_tc<128><<<blocks, TPB, 0, f->s>>>(reinterpret_cast<const __nv_bfloat16 *>(x), W, bias, extra,
                                                    reinterpret_cast<__nv_bfloat16 *>(pre),
-                                                   reinterpret_cast<__nv_bfloat16 *>(yt), act, f->N, B);
+                                                   reinterpret_cast<__nv_bfloat16 *>(yt), act, w0, f->N, B);
         } else if (pairs && ci == 32 && co % 8 == 0)
-            k_pw_fwd_in2<T, T, 32><<<grid_for(units), TPB, sm, f->s>>>(x, co, W, bias, extra, pre, yt, act, f->N, B);
+            k_pw_fwd_in2<T, T, 32><<<grid_for(units), TPB, sm, f->s>>>(x, co, W, bias, extra, pre, yt, act, w0, f->N,
+                                                                      B);
         else if (pairs && ci == 4 && co % 8 == 0)
-            k_pw_fwd_in2<T, T, 4><<<grid_for(units), TPB, sm, f->s>>>(x, co, W, bias, extra, pre, yt, act, f->N, B);
+            k_pw_fwd_in2<T, T, 4><<<grid_for(units), TPB, sm, f->s>>>(x, co, W, bias, extra, pre, yt, act, w0, f->N, B);
         else
-            k_pw_fwd_in<T, T><<<grid_for(units), TPB, sm, f->s>>>(x, ci, co, W, bias, extra, pre, yt, act, f->N, B);
+            k_pw_fwd_in<T, T><<<grid_for(units), TPB, sm, f->s>>>(x, ci, co, W, bias, extra, pre, yt, act, w0, f->N, B);
     } else if (pairs && ci % 8 == 0) {
         k_pw_fwd_out2<T><<<grid_for(units), TPB, sizeof(float) * ci * 8, f->s>>>(x, ci, co, W, bias,
                                                                                 static_cast<float *>(y), f->N, B);
@@ -2019,19 +2084,24 @@ void pw_fwd(fno_ctx *f, const T *x, int ci, int co, int64_t oW, int64_t ob, cons
 }
 
 template <class T>
-void pw_bwd_input(fno_ctx *f, const float *g, int co, int ci, int64_t oW, const T *pre_in, float *gx, int B)
+void pw_bwd_input(fno_ctx *f, const float *g, int co, int ci, int64_t oW, const T *pre_in, int act, float *gx, int B)
 {
     const bool pairs = f->N % 2 == 0;
     const int64_t units = pairs ? (int64_t)B * f->N / 2 : (int64_t)B * f->N;
     const float *W = f->params + oW;
+    const float w0 = f->c.omega0;
     if (pairs && ci == 32 && co % 8 == 0)
-        k_pw_bwd_in2<T, 32><<<grid_for(units), TPB, sizeof(float) * co * ci, f->s>>>(g, co, W, pre_in, gx, f->N, B);
+        k_pw_bwd_in2<T, 32><<<grid_for(units), TPB, sizeof(float) * co * ci, f->s>>>(g, co, W, pre_in, act, w0, gx,
+                                                                                    f->N, B);
     else if (ci <= 32)
-        k_pw_bwd_in<T><<<grid_for(units), TPB, sizeof(float) * co * ci, f->s>>>(g, co, ci, W, pre_in, gx, f->N, B);
+        k_pw_bwd_in<T><<<grid_for(units), TPB, sizeof(float) * co * ci, f->s>>>(g, co, ci, W, pre_in, act, w0, gx,
+                                                                               f->N, B);
     else if (pairs && ci % 8 == 0)
-        k_pw_bwd_out2<T><<<grid_for(units), TPB, sizeof(float) * ci * 8, f->s>>>(g, co, ci, W, pre_in, gx, f->N, B);
+        k_pw_bwd_out2<T><<<grid_for(units), TPB, sizeof(float) * ci * 8, f->s>>>(g, co, ci, W, pre_in, act, w0, gx,
+                                                                                f->N, B);
     else
-        k_pw_bwd_out<T><<<grid_for(units), TPB, sizeof(float) * co * ci, f->s>>>(g, co, ci, W, pre_in, gx, f->N, B);
+        k_pw_bwd_out<T><<<grid_for(units), TPB, sizeof(float) * co * ci, f->s>>>(g, co, ci, W, pre_in, act, w0, gx,
+                                                                                f->N, B);
 }
 
 template <class T>
@@ -2129,14 +2199,19 @@ lbm_status forward_impl(fno_ctx *f, const float *x, int B, bool keep = true)
     const int W = c.width;
     T *xa = static_cast<T *>(f->xa);
     k_convert<T><<<grid_for((int64_t)B * c.cin * f->N), TPB, 0, f->s>>>(x, xa, (int64_t)B * c.cin * f->N);
-    pw_fwd<T>(f, xa, c.cin, W, f->oP_w, f->oP_b, nullptr, nullptr, f->v[0], false, 0, B);
+    // feed-forward lift: v0 = P2 GELU(P1 x + b1) + b2
+    pw_fwd<T>(f, xa, c.cin, c.lift_hidden, f->oP1_w, f->oP1_b, nullptr, keep ? static_cast<T *>(f->apre) : nullptr,
+              f->a, false, ACT_GELU, B);
+    pw_fwd<T>(f, static_cast<T *>(f->a), c.lift_hidden, W, f->oP2_w, f->oP2_b, nullptr, nullptr, f->v[0], false,
+              ACT_NONE, B);
     for (int l = 0; l < c.layers; ++l) {
         T *vin = static_cast<T *>(f->v[l]);
         dft_fwd<T>(f, vin, f->Vh[l], f->scale_one, B);
         contract(f, f->Vh[l], f->oR[l], f->G, false, B);
         dft_inv<T>(f, f->G, f->spec, f->scale_inv, 0, nullptr, B);
-        pw_fwd<T>(f, vin, W, W, f->oW_w[l], f->oW_b[l], f->spec, static_cast<T *>(f->pre[l]), f->v[l + 1], false,
-                  l < c.layers - 1 ? 1 : 0, B);
+        pw_fwd<T>(f, vin, W, W, f->oW_w[l], f->oW_b[l], f->spec, keep ? static_cast<T *>(f->pre[l]) : nullptr,
+                  f->v[l + 1], false,
+                  l < c.layers - 1 ? ACT_GELU : ACT_NONE, B);
     }
     const int H = c.hidden;
     const size_t smf = sizeof(float) * ((size_t)H * 32 + ((H + 3) & ~3) + (size_t)H * 8);
@@ -2146,7 +2221,7 @@ lbm_status forward_impl(fno_ctx *f, const float *x, int B, bool keep = true)
         const int64_t warps = (int64_t)B * f->N / 16;
         k_proj_tc<<<(int)std::min<int64_t>((warps + TPB / 32 - 1) / (TPB / 32), gb300::sm_count() * 8), TPB, 0, f->s>>>(
             reinterpret_cast<const __nv_bfloat16 *>(f->v[c.layers]), c.cout, f->params + f->oQ1_w,
-            f->params + f->oQ1_b, f->params + f->oQ2_w, f->params + f->oQ2_b, f->y, f->N, B);
+            f->params + f->oQ1_b, f->params + f->oQ2_w, f->params + f->oQ2_b, c.omega0, f->y, f->N, B);
         return LBM_OK;
     }
     if (!keep && W == 32 && f->N % 2 == 0 && smf <= 48 * 1024) {
@@ -2154,12 +2229,14 @@ lbm_status forward_impl(fno_ctx *f, const float *x, int B, bool keep = true)
         const size_t sm = smf;
         k_proj_fused<T, 32><<<grid_for((int64_t)B * f->N / 2), TPB, sm, f->s>>>(
             static_cast<T *>(f->v[c.layers]), H, c.cout, f->params + f->oQ1_w, f->params + f->oQ1_b,
-            f->params + f->oQ2_w, f->params + f->oQ2_b, f->y, f->N, B);
+            f->params + f->oQ2_w, f->params + f->oQ2_b, c.omega0, f->y, f->N, B);
         return LBM_OK;
     }
-    pw_fwd<T>(f, static_cast<T *>(f->v[c.layers]), W, c.hidden, f->oQ1_w, f->oQ1_b, nullptr, static_cast<T *>(f->hpre),
-              f->h, false, 1, B);
-    pw_fwd<T>(f, static_cast<T *>(f->h), c.hidden, c.cout, f->oQ2_w, f->oQ2_b, nullptr, nullptr, f->y, true, 0, B);
+    // SIREN projection: h = sin(omega0 (Q1 v + b1)) (cos kept for the backward), y = Q2 h + b2
+    pw_fwd<T>(f, static_cast<T *>(f->v[c.layers]), W, c.hidden, f->oQ1_w, f->oQ1_b, nullptr, static_cast<T *>(f->hcos),
+              f->h, false, ACT_SIREN, B);
+    pw_fwd<T>(f, static_cast<T *>(f->h), c.hidden, c.cout, f->oQ2_w, f->oQ2_b, nullptr, nullptr, f->y, true, ACT_NONE,
+              B);
     return LBM_OK;
 }
 
@@ -2169,13 +2246,13 @@ lbm_status backward_impl(fno_ctx *f, int B)
     const fno_config &c = f->c;
     const int W = c.width, H = c.hidden;
     cudaMemsetAsync(f->grads, 0, f->np * sizeof(float), f->s);
-    // projection: y = Q2 h + b2, h = GELU(hpre), hpre = Q1 v_L + b1
+    // projection: y = Q2 h + b2, h = sin(omega0 z), z = Q1 v_L + b1; dh/dz = omega0 cos(omega0 z)
     outer<T>(f, f->gy, c.cout, static_cast<T *>(f->h), H, f->oQ2_w, f->oQ2_b, B);
-    pw_bwd_input<T>(f, f->gy, c.cout, H, f->oQ2_w, static_cast<T *>(f->hpre), f->ghpre, B);
+    pw_bwd_input<T>(f, f->gy, c.cout, H, f->oQ2_w, static_cast<T *>(f->hcos), ACT_SIREN, f->ghpre, B);
     outer<T>(f, f->ghpre, H, static_cast<T *>(f->v[c.layers]), W, f->oQ1_w, f->oQ1_b, B);
     float *gpre = f->gA, *gnext = f->gB;
     // gradient of v_L = pre_{L-1} (no activation after the last layer)
-    pw_bwd_input<T>(f, f->ghpre, H, W, f->oQ1_w, static_cast<const T *>(nullptr), gpre, B);
+    pw_bwd_input<T>(f, f->ghpre, H, W, f->oQ1_w, static_cast<const T *>(nullptr), ACT_NONE, gpre, B);
     for (int l = c.layers - 1; l >= 0; --l) {
         T *vin = static_cast<T *>(f->v[l]);
         outer<T>(f, gpre, W, vin, W, f->oW_w[l], f->oW_b[l], B);
@@ -2185,12 +2262,15 @@ lbm_status backward_impl(fno_ctx *f, int B)
                                                            reinterpret_cast<float2 *>(f->grads + f->oR[l]), W, B, f->K);
         contract(f, f->gG, f->oR[l], f->gVh, true, B);
         // gv_l = W_l^T gpre + adjoint DFT(gV), times gelu'(pre_{l-1}) for l > 0
-        pw_bwd_input<T>(f, gpre, W, W, f->oW_w[l], static_cast<const T *>(nullptr), gnext, B);
+        pw_bwd_input<T>(f, gpre, W, W, f->oW_w[l], static_cast<const T *>(nullptr), ACT_NONE, gnext, B);
         const T *pre_prev = l > 0 ? static_cast<T *>(f->pre[l - 1]) : nullptr;
         dft_inv<T>(f, f->gVh, gnext, f->scale_one, 1, pre_prev, B);
         std::swap(gpre, gnext);
     }
-    outer<T>(f, gpre, W, static_cast<T *>(f->xa), c.cin, f->oP_w, f->oP_b, B);
+    // lift: v0 = P2 a + b2, a = GELU(P1 x + b1)
+    outer<T>(f, gpre, W, static_cast<T *>(f->a), c.lift_hidden, f->oP2_w, f->oP2_b, B);
+    pw_bwd_input<T>(f, gpre, W, c.lift_hidden, f->oP2_w, static_cast<T *>(f->apre), ACT_GELU, gnext, B);
+    outer<T>(f, gnext, c.lift_hidden, static_cast<T *>(f->xa), c.cin, f->oP1_w, f->oP1_b, B);
     return LBM_OK;
 }
 

@@ -96,6 +96,28 @@ namespace lbm {
 void set_global_error(const std::string &m) { g_err = m; }
 }  // namespace lbm
 
+// Fourth-order parametrisation (Sec. 3.2; Geier, Pasquali & Schoenherr 2017):
+// the published rates omega3 (sums of third-order pairs), omega4 (their
+// differences), omega5 (C_111) and the factors of the fourth-order equilibria,
+// as functions of the shear rate w1 and the bulk rate w2; out = {omega3,
+// omega4, omega5, -(2/3) A (1/w1 - 1/2), B (1 - w1/2), lambda}.
+static void param4_factors(double w1, double w2, double lambda, double out[6])
+{
+    const double w1s = w1 * w1, w2s = w2 * w2;
+    out[0] = 8.0 * (w1 - 2.0) * (w2 * (3.0 * w1 - 1.0) - 5.0 * w1) /
+             (8.0 * (5.0 - 2.0 * w1) * w1 + w2 * (8.0 + w1 * (9.0 * w1 - 26.0)));
+    out[1] = 8.0 * (w1 - 2.0) * (w1 + w2 * (3.0 * w1 - 7.0)) / (w2 * (56.0 - 42.0 * w1 + 9.0 * w1s) - 8.0 * w1);
+    out[2] = 24.0 * (w1 - 2.0) * (4.0 * w1s + w1 * w2 * (18.0 - 13.0 * w1) + w2s * (2.0 + w1 * (6.0 * w1 - 11.0))) /
+             (16.0 * w1s * (w1 - 6.0) - 2.0 * w1 * w2 * (216.0 + 5.0 * w1 * (9.0 * w1 - 46.0)) +
+              w2s * (w1 * (3.0 * w1 - 10.0) * (15.0 * w1 - 28.0) - 48.0));
+    const double den = (w1 - w2) * (w2 * (2.0 + 3.0 * w1) - 8.0 * w1);
+    const double A = (4.0 * w1s + 2.0 * w1 * w2 * (w1 - 6.0) + w2s * (w1 * (10.0 - 3.0 * w1) - 4.0)) / den;
+    const double B = (4.0 * w1 * w2 * (9.0 * w1 - 16.0) - 4.0 * w1s - 2.0 * w2s * (2.0 + 9.0 * w1 * (w1 - 2.0))) / (3.0 * den);
+    out[3] = -(2.0 / 3.0) * A * (1.0 / w1 - 0.5);
+    out[4] = B * (1.0 - 0.5 * w1);
+    out[5] = lambda;
+}
+
 struct lbm_ctx {
     lbm_grid g;
     lbm_params p;
@@ -125,6 +147,13 @@ struct lbm_ctx {
     float *probe_ring = nullptr;
     int64_t n_probes = 0, probe_every = 1, probe_cap = 0, probe_rows_dev = 0;
     std::vector<float> probe_host;
+    // monitor plane (Sec. 2): (u, v, w, p) of the plane z = plane_z every
+    // plane_every steps, a device ring of plane_cap planes flushed to the host
+    int plane_z = -1;
+    float *plane_ring = nullptr;
+    int64_t plane_every = 1, plane_cap = 0, plane_rows_dev = 0;
+    std::vector<float> plane_host;
+    std::vector<int64_t> plane_steps;
     std::string err;
     int64_t n_fluid = 0, n_bulk = 0, n_wall = 0, launches = 0;
     // kernel timing: events recorded per step (start, mid, end) and the step kind
@@ -152,6 +181,9 @@ struct lbm_ctx {
         a.face_x_lo = p.face_x_lo; a.face_x_hi = p.face_x_hi; a.face_y = p.face_y; a.face_z = p.face_z;
         a.u_in = p.u_in; a.rho_in = p.rho_in; a.rho_out = p.rho_out;
         a.w1f = (float)a.w1; a.w2f = (float)a.w2; a.w3f = (float)a.w3;
+        a.param4 = p.param4 ? 1 : 0;
+        if (a.param4) param4_factors(a.w1, a.w2, p.limiter, a.p4);
+        for (int k = 0; k < 6; ++k) a.p4f[k] = (float)a.p4[k];
         const int64_t es = (int64_t)storage_bytes(p.storage);
         for (int i = 0; i < Q; ++i) {
             const int64_t off = cx_of(i) + (int64_t)cy_of(i) * g.nx + (int64_t)cz_of(i) * a.nxy;
@@ -201,6 +233,7 @@ extern "C" void lbm_params_default(lbm_params *p)
     p->face_x_lo = LBM_FACE_INLET; p->face_x_hi = LBM_FACE_OUTFLOW;
     p->face_y = LBM_FACE_WALL; p->face_z = LBM_FACE_WALL;
     p->force_capacity = 65536;
+    p->param4 = 0; p->limiter = 0.01;
 }
 
 static std::string validate(const lbm_grid *g, const lbm_params *p)
@@ -226,6 +259,13 @@ static std::string validate(const lbm_grid *g, const lbm_params *p)
     if (p->block_x != 0 && (p->block_x % 32 != 0 || p->block_x > 256)) return "block_x must be a multiple of 32, <= 256";
     if (p->block_y < 0 || (p->block_x ? p->block_x : 128) * (p->block_y ? p->block_y : 1) > 256)
         return "block_x * block_y must be <= 256";
+    if (p->param4 != 0 && p->param4 != 1) return "param4 must be 0 or 1";
+    if (p->param4) {
+        if (!(p->limiter > 0.0)) return "param4 needs limiter > 0";
+        const double w1 = p->omega1 > 0 ? p->omega1 : 1.0 / (3.0 * p->u_in * p->l_ref / p->re + 0.5);
+        if (std::fabs(w1 - p->omega_bulk) < 1e-9)
+            return "param4 is undefined at omega1 = omega_bulk (choose another bulk rate)";
+    }
     return "";
 }
 
@@ -275,7 +315,7 @@ static lbm_status create_impl(const lbm_grid *g, const uint8_t *mask, const lbm_
     ctx->L = make_layout(*g, ctx->p, n_solid);
     ctx->stream = static_cast<cudaStream_t>(stream);
     ctx->w1 = p->omega1 > 0 ? p->omega1 : 1.0 / (3.0 * p->u_in * p->l_ref / p->re + 0.5);
-    ctx->plain = (p->omega_higher == 1.0);
+    ctx->plain = (p->omega_higher == 1.0) && !p->param4;
     ctx->block_x = p->block_x ? p->block_x : 128;
     ctx->block_y = p->block_y ? p->block_y : 1;
     ctx->force_cap = ctx->p.force_capacity;
@@ -420,6 +460,7 @@ extern "C" lbm_status lbm_destroy(lbm_ctx *ctx)
     for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
     cudaFree(ctx->probe_cells);
     cudaFree(ctx->probe_ring);
+    cudaFree(ctx->plane_ring);
     cudaFree(ctx->qlinks);
     cudaFree(ctx->qval);
     cudaFree(ctx->qpart);
@@ -440,6 +481,19 @@ static lbm_status flush_forces(lbm_ctx *ctx)
                        sizeof(double) * 3 * ctx->force_rows_dev, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     ctx->force_rows_dev = 0;
+    return LBM_OK;
+}
+
+static lbm_status flush_planes(lbm_ctx *ctx)
+{
+    if (ctx->plane_rows_dev == 0) return LBM_OK;
+    const size_t per = (size_t)4 * ctx->g.nx * ctx->g.ny;
+    const size_t old = ctx->plane_host.size(), cnt = per * ctx->plane_rows_dev;
+    ctx->plane_host.resize(old + cnt);
+    CK(cudaMemcpyAsync(ctx->plane_host.data() + old, ctx->plane_ring, sizeof(float) * cnt, cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->plane_rows_dev = 0;
     return LBM_OK;
 }
 
@@ -559,6 +613,19 @@ extern "C" lbm_status lbm_step(lbm_ctx *ctx, int64_t nsteps)
             x.fout = ctx->probe_ring + 4 * ctx->n_probes * ctx->probe_rows_dev;
             launch_aux(p.storage, AUX_PROBE, base, (t & 1) != 0, x, ctx->stream);
             ctx->probe_rows_dev++;
+            ctx->launches++;
+        }
+        if (ctx->plane_ring && t % ctx->plane_every == 0) {     // the state at t, before the step
+            if (ctx->plane_rows_dev == ctx->plane_cap) {
+                lbm_status st = flush_planes(ctx);
+                if (st != LBM_OK) return st;
+            }
+            AuxArgs x;
+            x.count = ctx->plane_z;
+            x.fout = ctx->plane_ring + (size_t)4 * ctx->g.nx * ctx->g.ny * ctx->plane_rows_dev;
+            launch_aux(p.storage, AUX_PLANE, base, (t & 1) != 0, x, ctx->stream);
+            ctx->plane_rows_dev++;
+            ctx->plane_steps.push_back(t);
             ctx->launches++;
         }
         step_launch(ctx, a, (t & 1) != 0, a.msum != nullptr || a.snap != nullptr);
@@ -740,6 +807,49 @@ extern "C" lbm_status lbm_set_probes(lbm_ctx *ctx, int64_t n, const int64_t *cel
     ctx->n_probes = n;
     ctx->probe_every = every;
     ctx->probe_cap = capacity;
+    return LBM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// monitor plane (Sec. 2: 2D snapshots of the centre x-y plane)
+// ---------------------------------------------------------------------------
+extern "C" lbm_status lbm_set_plane_monitor(lbm_ctx *ctx, int32_t z, int64_t every, int64_t capacity)
+{
+    if (!ctx) return LBM_ERR_ARG;
+    if (ctx->in_batch) return fail(ctx, LBM_ERR_STATE, "the monitor plane is not supported on batch members");
+    if (every < 0 || (every > 0 && capacity < 1)) return fail(ctx, LBM_ERR_ARG, "bad monitor-plane arguments");
+    const int zz = z < 0 ? ctx->g.nz / 2 : z;
+    if (zz >= ctx->g.nz) return fail(ctx, LBM_ERR_ARG, "monitor plane z out of range");
+    CK(cudaStreamSynchronize(ctx->stream));
+    cudaFree(ctx->plane_ring);
+    ctx->plane_ring = nullptr;
+    ctx->plane_rows_dev = 0;
+    ctx->plane_host.clear();
+    ctx->plane_steps.clear();
+    if (every == 0) return LBM_OK;
+    CK(cudaMalloc(&ctx->plane_ring, sizeof(float) * 4 * (size_t)ctx->g.nx * ctx->g.ny * capacity));
+    ctx->plane_z = zz;
+    ctx->plane_every = every;
+    ctx->plane_cap = capacity;
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_read_plane_monitor(lbm_ctx *ctx, float *dst, int64_t max_planes, int64_t *n_planes,
+                                             int64_t *steps)
+{
+    if (!ctx || max_planes < 0 || (max_planes > 0 && !dst))
+        return ctx ? fail(ctx, LBM_ERR_ARG, "bad monitor-plane read arguments") : LBM_ERR_ARG;
+    lbm_status st = flush_planes(ctx);
+    if (st != LBM_OK) return st;
+    const int64_t per = 4 * (int64_t)ctx->g.nx * ctx->g.ny;
+    const int64_t rows = (int64_t)ctx->plane_steps.size();
+    if (n_planes) *n_planes = rows;
+    const int64_t m = std::min(rows, max_planes);
+    if (m > 0) {
+        if (is_device_ptr(dst)) CK(cudaMemcpy(dst, ctx->plane_host.data(), sizeof(float) * per * m, cudaMemcpyHostToDevice));
+        else std::memcpy(dst, ctx->plane_host.data(), sizeof(float) * per * m);
+        if (steps) std::memcpy(steps, ctx->plane_steps.data(), sizeof(int64_t) * m);
+    }
     return LBM_OK;
 }
 
@@ -1076,6 +1186,9 @@ extern "C" lbm_status lbm_reset(lbm_ctx *ctx)
     ctx->force_rows_dev = 0;
     ctx->probe_host.clear();
     ctx->probe_rows_dev = 0;
+    ctx->plane_host.clear();
+    ctx->plane_steps.clear();
+    ctx->plane_rows_dev = 0;
     std::fill(ctx->snap_taken.begin(), ctx->snap_taken.end(), 0);
     ctx->unstable = false;
     ctx->ev_kind.clear();
@@ -1268,8 +1381,9 @@ extern "C" lbm_status lbm_batch_create(int32_t n, const lbm_grid *grids, const u
     for (int g = 0; g < n; ++g) {
         const lbm_params &p = params[g];
         if (p.storage != p0.storage) return batch_fail(nullptr, LBM_ERR_ARG, "batch members need one storage");
-        if ((p.omega_higher == 1.0) != (p0.omega_higher == 1.0))
-            return batch_fail(nullptr, LBM_ERR_ARG, "batch members need the same omega_higher == 1 choice");
+        if ((p.omega_higher == 1.0 && !p.param4) != (p0.omega_higher == 1.0 && !p0.param4))
+            return batch_fail(nullptr, LBM_ERR_ARG,
+                              "batch members need the same collision kind (plain: omega_higher == 1, no param4)");
         if (p.snap_count > 0) return batch_fail(nullptr, LBM_ERR_ARG, "batch members take no snapshots");
         if (p.mean_every > 0) {
             if (me && p.mean_every != me) return batch_fail(nullptr, LBM_ERR_ARG, "batch members need one mean_every");
@@ -1285,7 +1399,7 @@ extern "C" lbm_status lbm_batch_create(int32_t n, const lbm_grid *grids, const u
     b->mean_every = me;
     b->chunk = me > 0 ? me : 2;
     b->storage = p0.storage;
-    b->plain = p0.omega_higher == 1.0;
+    b->plain = p0.omega_higher == 1.0 && !p0.param4;
     b->block_x = p0.block_x ? p0.block_x : 128;
     b->block_y = p0.block_y ? p0.block_y : 1;
     for (int g = 0; g < n; ++g) {

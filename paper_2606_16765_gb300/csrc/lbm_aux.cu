@@ -302,29 +302,45 @@ __global__ void k_halfres(const T *in, int nx, int ny, int nz, T *out)
     }
 }
 
-// Probe row: (ux, uy, uz, p) of the current state at the listed cells
-// (p = (rho - 1)/3; solid or out-of-range cells give 0).
+// (ux, uy, uz, p) of the current state at cell c (p = (rho - 1)/3; solid or
+// out-of-range cells give 0).
+template <class S>
+__device__ __forceinline__ float4 cell_macros(const StepArgs &a, bool odd, int64_t c)
+{
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (c >= 0 && c < a.n && !(a.flags[c] & CELL_SOLID)) {
+        double f[Q];
+        gather_natural<S>(a, odd, c, f);
+        double d = 0, jx = 0, jy = 0, jz = 0;
+        for (int i = 0; i < Q; ++i) {
+            d += f[i];
+            jx += cx_of(i) * f[i];
+            jy += cy_of(i) * f[i];
+            jz += cz_of(i) * f[i];
+        }
+        const double r = 1.0 + d;
+        v = make_float4((float)(jx / r), (float)(jy / r), (float)(jz / r), (float)(d / 3.0));
+    }
+    return v;
+}
+
+// Probe row: (ux, uy, uz, p) of the current state at the listed cells.
 template <class S>
 __global__ void k_probe(StepArgs a, bool odd, const int64_t *cells, int64_t count, float *out)
 {
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < count; k += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t c = cells[k];
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (c >= 0 && c < a.n && !(a.flags[c] & CELL_SOLID)) {
-            double f[Q];
-            gather_natural<S>(a, odd, c, f);
-            double d = 0, jx = 0, jy = 0, jz = 0;
-            for (int i = 0; i < Q; ++i) {
-                d += f[i];
-                jx += cx_of(i) * f[i];
-                jy += cy_of(i) * f[i];
-                jz += cz_of(i) * f[i];
-            }
-            const double r = 1.0 + d;
-            v = make_float4((float)(jx / r), (float)(jy / r), (float)(jz / r), (float)(d / 3.0));
-        }
-        reinterpret_cast<float4 *>(out)[k] = v;
-    }
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < count; k += (int64_t)gridDim.x * blockDim.x)
+        reinterpret_cast<float4 *>(out)[k] = cell_macros<S>(a, odd, cells[k]);
+}
+
+// Monitor plane (Sec. 2: 2D snapshots of the centre x-y plane): (ux, uy, uz,
+// p) of every cell of the plane z = z0 of the current state, [y][x] float4;
+// consecutive threads take consecutive x.
+template <class S>
+__global__ void k_plane(StepArgs a, bool odd, int z0, float *out)
+{
+    const int64_t m = a.nxy, base = a.nxy * z0;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < m; k += (int64_t)gridDim.x * blockDim.x)
+        reinterpret_cast<float4 *>(out)[k] = cell_macros<S>(a, odd, base + k);
 }
 
 // ---------------------------------------------------------------------------
@@ -354,6 +370,9 @@ static void launch_aux_t(AuxOp op, const StepArgs &a, bool odd, const AuxArgs &x
         break;
     case AUX_PROBE:
         k_probe<S><<<grid_for(x.count, 128), 128, 0, s>>>(a, odd, x.cells, x.count, x.fout);
+        break;
+    case AUX_PLANE:
+        k_plane<S><<<grid_for(a.nxy, 128), 128, 0, s>>>(a, odd, (int)x.count, x.fout);
         break;
     case AUX_EQUILIBRIUM:
         k_equilibrium<S><<<grid_for(a.n, 256), 256, 0, s>>>((S *)a.pdf, a.slot, a.flags, a.n, x.fsrc);

@@ -128,6 +128,12 @@ struct StepArgs {
     int64_t nxy, n;
     double w1, w2, w3;      // shear, bulk, higher-order rates
     int galilean;
+    // fourth-order parametrisation (param4 != 0): omega3, omega4, omega5,
+    // the fourth-order factors -(2/3) A (1/w1 - 1/2) and B (1 - w1/2), and
+    // the limiter lambda (p4) with their FP32 copies (p4f)
+    int param4;
+    double p4[6];
+    float p4f[6];
     int face_x_lo, face_x_hi, face_y, face_z;
     double u_in, rho_in, rho_out;
     // FP32 copies of the rates and boundary constants, so that FP32 kernels
@@ -325,12 +331,26 @@ template <class R>
 struct Rates {
     R w1, w2, w3;
     int galilean;
+    int param4;
+    R p4[6];
 };
 
 template <class R>
 __device__ __forceinline__ Rates<R> rates_of(const StepArgs &a)
 {
-    return Rates<R>{pick<R>(a.w1, a.w1f), pick<R>(a.w2, a.w2f), pick<R>(a.w3, a.w3f), a.galilean};
+    Rates<R> r{pick<R>(a.w1, a.w1f), pick<R>(a.w2, a.w2f), pick<R>(a.w3, a.w3f), a.galilean, a.param4, {}};
+#pragma unroll
+    for (int k = 0; k < 6; ++k) r.p4[k] = pick<R>(a.p4[k], a.p4f[k]);
+    return r;
+}
+
+// Rate w raised towards 1 where the cumulant combination X is large against
+// the limiter lambda (fourth-order parametrisation): w + (1 - w)|X|/(|X| + lambda).
+template <class R>
+__device__ __forceinline__ R limited_rate(R w, R X, R lambda)
+{
+    const R ax = X < R(0) ? -X : X;
+    return w + (R(1) - w) * ax / (ax + lambda);
 }
 
 // Cumulant collision of one cell, in place on the shifted populations f[27].
@@ -491,24 +511,61 @@ __device__ __forceinline__ void collide(R *f, const Rates<R> &rt, R &drho_out, R
                      + d200 * d020 * d002;
         const R C222 = e222 - S42 - S33 + R(2) * S222;
 
-        // relax every cumulant of order 3..6 with omega_higher, then rebuild
-        // central moments order by order from the post-collision lower orders
-        s111 = r3 * k111;
-        s210 = r3 * k210; s201 = r3 * k201; s120 = r3 * k120;
-        s021 = r3 * k021; s102 = r3 * k102; s012 = r3 * k012;
-        s211 = r3 * C211 + (third + s200) * s011 + R(2) * s110 * s101;
-        s121 = r3 * C121 + (third + s020) * s101 + R(2) * s110 * s011;
-        s112 = r3 * C112 + (third + s002) * s110 + R(2) * s101 * s011;
-        e220s = r3 * C220 + (s200 + s020) * third + s200 * s020 + R(2) * s110 * s110;
-        e202s = r3 * C202 + (s200 + s002) * third + s200 * s002 + R(2) * s101 * s101;
-        e022s = r3 * C022 + (s020 + s002) * third + s020 * s002 + R(2) * s011 * s011;
-        s122 = r3 * C122 + (third + s002) * s120 + (third + s020) * s102 + R(4) * s011 * s111
+        // post-collision cumulants of orders 3..6: one rate omega_higher for
+        // all of them, or the fourth-order parametrisation
+        R c111, c210, c201, c120, c021, c102, c012, c211, c121, c112, c220, c202, c022, c122, c212, c221, c222;
+        if (rt.param4) {
+            // third order in the combinations of Geier et al. 2017: sums with
+            // omega3, differences with omega4, C_111 with omega5, each limited
+            const R lam = rt.p4[5];
+            const R p1 = k210 + k012, m1 = k210 - k012;
+            const R p2 = k201 + k021, m2 = k201 - k021;
+            const R p3 = k120 + k102, m3 = k120 - k102;
+            const R p1s = (R(1) - limited_rate<R>(rt.p4[0], p1, lam)) * p1;
+            const R m1s = (R(1) - limited_rate<R>(rt.p4[1], m1, lam)) * m1;
+            const R p2s = (R(1) - limited_rate<R>(rt.p4[0], p2, lam)) * p2;
+            const R m2s = (R(1) - limited_rate<R>(rt.p4[1], m2, lam)) * m2;
+            const R p3s = (R(1) - limited_rate<R>(rt.p4[0], p3, lam)) * p3;
+            const R m3s = (R(1) - limited_rate<R>(rt.p4[1], m3, lam)) * m3;
+            c210 = R(0.5) * (p1s + m1s); c012 = R(0.5) * (p1s - m1s);
+            c201 = R(0.5) * (p2s + m2s); c021 = R(0.5) * (p2s - m2s);
+            c120 = R(0.5) * (p3s + m3s); c102 = R(0.5) * (p3s - m3s);
+            c111 = (R(1) - limited_rate<R>(rt.p4[2], k111, lam)) * k111;
+            // fourth order: the equilibria carrying the velocity gradients
+            c220 = rt.p4[3] * (dxu + dyv);
+            c202 = rt.p4[3] * (dxu + dzw);
+            c022 = rt.p4[3] * (dyv + dzw);
+            c211 = rt.p4[4] * k011;
+            c121 = rt.p4[4] * k101;
+            c112 = rt.p4[4] * k110;
+            c122 = c212 = c221 = c222 = R(0);
+        } else {
+            c111 = r3 * k111;
+            c210 = r3 * k210; c201 = r3 * k201; c120 = r3 * k120;
+            c021 = r3 * k021; c102 = r3 * k102; c012 = r3 * k012;
+            c211 = r3 * C211; c121 = r3 * C121; c112 = r3 * C112;
+            c220 = r3 * C220; c202 = r3 * C202; c022 = r3 * C022;
+            c122 = r3 * C122; c212 = r3 * C212; c221 = r3 * C221;
+            c222 = r3 * C222;
+        }
+        // rebuild central moments order by order from the post-collision
+        // lower orders
+        s111 = c111;
+        s210 = c210; s201 = c201; s120 = c120;
+        s021 = c021; s102 = c102; s012 = c012;
+        s211 = c211 + (third + s200) * s011 + R(2) * s110 * s101;
+        s121 = c121 + (third + s020) * s101 + R(2) * s110 * s011;
+        s112 = c112 + (third + s002) * s110 + R(2) * s101 * s011;
+        e220s = c220 + (s200 + s020) * third + s200 * s020 + R(2) * s110 * s110;
+        e202s = c202 + (s200 + s002) * third + s200 * s002 + R(2) * s101 * s101;
+        e022s = c022 + (s020 + s002) * third + s020 * s002 + R(2) * s011 * s011;
+        s122 = c122 + (third + s002) * s120 + (third + s020) * s102 + R(4) * s011 * s111
              + R(2) * (s101 * s021 + s110 * s012);
-        s212 = r3 * C212 + (third + s200) * s012 + (third + s002) * s210 + R(4) * s101 * s111
+        s212 = c212 + (third + s200) * s012 + (third + s002) * s210 + R(4) * s101 * s111
              + R(2) * (s110 * s102 + s011 * s201);
-        s221 = r3 * C221 + (third + s200) * s021 + (third + s020) * s201 + R(4) * s110 * s111
+        s221 = c221 + (third + s200) * s021 + (third + s020) * s201 + R(4) * s110 * s111
              + R(2) * (s101 * s120 + s011 * s210);
-        e222s = r3 * C222;   // plus the product terms added below
+        e222s = c222;   // plus the product terms added below
     }
     {
         // sixth order: add sum(4,2) + sum(3,3) - 2 sum(2,2,2) of post-collision moments

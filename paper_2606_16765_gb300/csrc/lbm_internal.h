@@ -32,7 +32,7 @@ void launch_step_f16c(const StepArgs &a, bool odd, bool epi, bool plain, int blo
 void launch_batch_step_f16c(const BatchLaunch &L, bool odd, bool epi, bool plain, cudaStream_t s);
 void launch_outflow_record_f16c(const StepArgs &a, bool odd, cudaStream_t s);
 
-enum AuxOp { AUX_NOISE, AUX_GATHER, AUX_SET, AUX_MACROS, AUX_TOTALS, AUX_PROBE, AUX_EQUILIBRIUM };
+enum AuxOp { AUX_NOISE, AUX_GATHER, AUX_SET, AUX_MACROS, AUX_TOTALS, AUX_PROBE, AUX_EQUILIBRIUM, AUX_PLANE };
 
 struct AuxArgs {
     uint64_t seed = 0;

@@ -18,7 +18,8 @@ class fno_config(C.Structure):
                 ("cin", C.c_int32), ("width", C.c_int32), ("cout", C.c_int32),
                 ("mx", C.c_int32), ("my", C.c_int32), ("mz", C.c_int32),
                 ("layers", C.c_int32), ("hidden", C.c_int32), ("max_batch", C.c_int32),
-                ("act_bf16", C.c_int32), ("tensor_cores", C.c_int32), ("seed", C.c_uint64)]
+                ("act_bf16", C.c_int32), ("tensor_cores", C.c_int32),
+                ("lift_hidden", C.c_int32), ("omega0", C.c_float), ("seed", C.c_uint64)]
 
 
 class FNOError(RuntimeError):
@@ -192,9 +193,10 @@ class FNO:
 def layout(cfg):
     """[(name, shape, complex)] in the order of the flat vector."""
     K = cfg.mz * 2 * cfg.my * 2 * cfg.mx
-    W, H = cfg.width, cfg.hidden
+    W, H, LH = cfg.width, cfg.hidden, cfg.lift_hidden
     out = [(f"R{l}", (K, W, W), True) for l in range(cfg.layers)]
-    out += [("P_w", (W, cfg.cin), False), ("P_b", (W,), False)]
+    out += [("P1_w", (LH, cfg.cin), False), ("P1_b", (LH,), False),
+            ("P2_w", (W, LH), False), ("P2_b", (W,), False)]
     for l in range(cfg.layers):
         out += [(f"W{l}_w", (W, W), False), (f"W{l}_b", (W,), False)]
     out += [("Q1_w", (H, W), False), ("Q1_b", (H,), False), ("Q2_w", (cfg.cout, H), False),

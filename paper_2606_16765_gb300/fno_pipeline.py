@@ -2,23 +2,31 @@
 
 The pipeline of the paper's Sec. 2 (geometry generation -> LBM simulation,
 mean velocity and pressure after the flow-through times -> scaling -> NN
-training) and the FNO baseline of its appendix (masked MSE on the inner region
+training) and the FNO baseline of its App. B (feed-forward lift, Fourier
+layers, SIREN projection; masked MSE on the inner region
 [(0.2,0.25,0.25),(1.8,0.75,0.75)] of the (2,1,1) channel, Adam, cosine
-learning-rate schedule, 50 epochs), run on the 128x64x64 grid the surrogate
-works on:
+learning-rate schedule, 50 epochs):
 
-  1. seeded composite obstacles (5 primitive kinds, angle of attack in
-     [-30, 30] deg), Re log-uniform in a range on the 64-cell channel height:
-     by default [125, 1250], the lattice viscosities of the paper's Re 1e3 -
-     1e4 runs on a 512-cell height (whose fields the paper downsamples to
-     this grid); --re-range 1000,10000 puts the paper's Re on the coarse grid
-     itself (lattice viscosity down to 3.2e-4);
+  1. seeded geometries as the batched configuration draws them (default,
+     --grids config4): a grid from {128,192,256} x {64,96,128}^2, Re
+     log-uniform in [1e3, 1e4] on the channel height, a composite of 2-4
+     primitives (5 kinds) 20-60 cells across scaled by ny/512 (at least 6
+     cells), one angle of attack in [-30, 30] deg.  Variants: --grids direct
+     draws every geometry on the surrogate's 128x64x64 grid itself with
+     6-12-cell primitives; --re-range 125,1250 puts the lattice viscosities
+     of Re 1e3-1e4 on a 512-cell height onto the 64-cell one;
   2. all geometries stepped together by the batched LBM driver to 15
-     flow-through times, the time average taken over flow-through times 5-15;
-  3. inputs (mask, log10 Re - 2, cos and sin of the angle), targets (u, v, w,
-     p) min-max scaled per field on the training set;
-  4. training, evaluation on held-out seeds against the LBM, and the time of an
-     FNO prediction against the LBM run it replaces.
+     flow-through times, the time average taken over flow-through times 5-15,
+     then resampled on the GPU onto 128x64x64 (lbm_resample: cell-centred
+     trilinear, App. B's scaling down);
+  3. inputs: the obstacle as a binary field on 128x64x64 (each target cell
+     solid iff its centre, mapped to the native grid, is inside), log10 Re
+     minus the centre of the log range (3.5 for 1e3-1e4), cos and sin of the
+     angle; targets (u, v, w, p) min-max scaled per field on the training set;
+  4. training, evaluation on held-out seeds against the LBM (rel-L2 over the
+     fluid cells of the loss region and over all fluid cells), the
+     train-set mean field as the method without the network, and the time of
+     an FNO prediction against the LBM run it replaces.
 
 Usage: python -m paper_2606_16765_gb300.fno_pipeline --out report.json [--quick]
 """
@@ -33,52 +41,110 @@ import numpy as np
 
 from . import inputs as I
 
-GRID = (128, 64, 64)          # (nx, ny, nz)
+GRID = (128, 64, 64)          # (nx, ny, nz) of the surrogate
 U_IN = 0.05
 
+# Re log-uniform on the channel height, as the batched configuration draws it
+RE_RANGE = (1000.0, 10000.0)
+# variant: the lattice viscosities nu = U 512 / Re of Re 1e3 - 1e4 on a
+# 512-cell height, put onto a 64-cell height
+RE_RANGE_COARSE = (125.0, 1250.0)
+GRID_SETS = ((128, 192, 256), (64, 96, 128), (64, 96, 128))
 
-# Default Re range on the 64-cell channel height: the lattice viscosities
-# nu = U 512 / Re of the paper's Re 1e3 - 1e4 runs on a 512-cell height.
-RE_RANGE = (125.0, 1250.0)
 
-
-def sample(seed, grid=GRID, re_range=RE_RANGE):
-    """Geometry and Re of one sample (deterministic in seed)."""
+def sample(seed, re_range=RE_RANGE, grids="config4"):
+    """Geometry, grid and Re of one sample (deterministic in seed)."""
     rng = np.random.Generator(np.random.PCG64(70_000 + seed))
     re = float(math.exp(rng.uniform(math.log(re_range[0]), math.log(re_range[1]))))
-    obs = I.composite(seed, grid, size_range=(6.0, 12.0), jitter=2.0)
+    if grids == "config4":
+        grid = tuple(int(rng.choice(c)) for c in GRID_SETS)
+        sc = grid[1] / 512.0
+        size, jitter = (max(6.0, 20.0 * sc), max(6.0, 60.0 * sc)), 10.0 * sc
+    elif grids == "direct":
+        grid, size, jitter = GRID, (6.0, 12.0), 2.0
+    else:
+        raise ValueError(grids)
+    obs = I.composite(seed, grid, size_range=size, jitter=jitter)
     return dict(seed=seed, grid=tuple(grid), mask=obs.mask(), re=re, angle=obs.angle_deg, prims=obs.prims)
 
 
+def target_mask(s, grid=GRID):
+    """Obstacle as a binary field on the surrogate grid: a target cell is
+    solid iff its centre, mapped to the sample's own grid by the resampler's
+    map (o + 1/2) n/m - 1/2, is inside the union of primitives."""
+    (nx, ny, nz), (mx, my, mz) = s["grid"], grid
+    x = (np.arange(mx) + 0.5) * nx / mx - 0.5
+    y = (np.arange(my) + 0.5) * ny / my - 0.5
+    z = (np.arange(mz) + 0.5) * nz / mz - 0.5
+    Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
+    ins = np.zeros(Z.shape, bool)
+    for p in s["prims"]:
+        ins |= p.inside(X, Y, Z)
+    return ins.astype(np.uint8)
+
+
 def features(s, re_range=RE_RANGE):
-    """FNO input channels [4, nz, ny, nx]: mask, log10 Re centred on the
-    range (log10 of Re over the geometric mean of its ends), cos a, sin a."""
-    m = s["mask"].astype(np.float32)
+    """FNO input channels [4, nz, ny, nx] on the surrogate grid: obstacle
+    mask, log10 Re centred on the range (log10 of Re over the geometric mean
+    of its ends: log10 Re - 3.5 for [1e3, 1e4]), cos a, sin a."""
+    m = target_mask(s).astype(np.float32)
     a = math.radians(s["angle"])
     re_c = 0.5 * (math.log10(re_range[0]) + math.log10(re_range[1]))
     return np.stack([m, np.full_like(m, math.log10(s["re"]) - re_c), np.full_like(m, math.cos(a)),
                      np.full_like(m, math.sin(a))])
 
 
+def mean_on_grid(member, grid=GRID):
+    """A lattice's mean (u, v, w, p) resampled onto `grid` on the GPU:
+    torch tensor [4, mz, my, mx] (lbm_read_mean into a device buffer, then
+    lbm_resample)."""
+    import torch
+    from . import lbm as B
+    nx, ny, nz = member.grid.nx, member.grid.ny, member.grid.nz
+    mx, my, mz = grid
+    src = torch.empty((nz, ny, nx, 4), dtype=torch.float32, device="cuda")
+    B.lbm_read_mean(member.h, src, 1, 0)
+    dst = torch.empty((4, mz, my, mx), dtype=torch.float32, device="cuda")
+    B.lbm_resample(src, (nx, ny, nz), 4, 0, dst, grid, torch.cuda.current_stream().cuda_stream)
+    return dst
+
+
+def fields_on_native_grid(pred, s):
+    """A prediction [4, mz, my, mx] (lattice units, surrogate grid) resampled
+    onto the sample's own grid as [nz, ny, nx, 4] (device), the layout of
+    lbm_init_equilibrium."""
+    import torch
+    from . import lbm as B
+    nx, ny, nz = s["grid"]
+    src = torch.as_tensor(np.ascontiguousarray(pred, dtype=np.float32), device="cuda")
+    dst = torch.empty((4, nz, ny, nx), dtype=torch.float32, device="cuda")
+    B.lbm_resample(src, GRID, 4, 1, dst, (nx, ny, nz), torch.cuda.current_stream().cuda_stream)
+    return dst.permute(1, 2, 3, 0).contiguous()
+
+
 def simulate(samples, storage="f16c", n_ft=15.0, ft_start=5.0, chunk_ft=1.0, log=print):
-    """Mean (u, v, w, p) [n, 4, nz, ny, nx] of each sample from the batched LBM.
-    Members that become unstable are retired and reported (their targets are
-    NaN)."""
+    """Mean (u, v, w, p) of each sample from the batched LBM on its own grid,
+    resampled onto the surrogate grid: [n, 4, nz, ny, nx] at 128x64x64.
+    Each member runs to its own n_ft flow-through times (nx_g / U steps
+    each) and averages from its own ft_start; the batch retires members at
+    their ends.  Members that become unstable are retired and reported (their
+    targets are NaN)."""
     from .lbm import Batch, LBMError
 
-    nx = samples[0]["grid"][0]
-    steps_ft = nx / U_IN
-    t_end = int(math.ceil(n_ft * steps_ft))
-    mean_start = int(round(ft_start * steps_ft / 10.0)) * 10
-    members = [dict(grid=s["grid"], mask=s["mask"], storage=storage, re=s["re"], u_in=U_IN,
-                    l_ref=float(s["grid"][1]), mean_start=mean_start, mean_end=t_end, mean_every=10)
-               for s in samples]
+    ends, members = [], []
+    for s in samples:
+        steps_ft = s["grid"][0] / U_IN
+        t_end = int(math.ceil(n_ft * steps_ft))
+        mean_start = int(round(ft_start * steps_ft / 10.0)) * 10
+        ends.append(t_end)
+        members.append(dict(grid=s["grid"], mask=s["mask"], storage=storage, re=s["re"], u_in=U_IN,
+                            l_ref=float(s["grid"][1]), mean_start=mean_start, mean_end=t_end, mean_every=10))
     b = Batch(members)
     for g, s in enumerate(samples):                 # interpolated bounce-back on the obstacle links
         b.set_wall_distances(g, I.link_wall_distances(s["grid"], s["prims"], s["mask"]))
-    b.set_end([t_end] * len(samples))
+    b.set_end(ends)
     unstable = set()
-    step = int(math.ceil(chunk_ft * steps_ft / 10.0)) * 10
+    step = int(math.ceil(chunk_ft * min(s["grid"][0] for s in samples) / U_IN / 10.0)) * 10
     t0 = time.time()
     while b.info().live > 0:
         b.run(step)
@@ -90,16 +156,14 @@ def simulate(samples, storage="f16c", n_ft=15.0, ft_start=5.0, chunk_ft=1.0, log
             except LBMError:
                 unstable.add(g)
         if unstable:
-            ends = [b.info().t if g in unstable else t_end for g in range(len(samples))]
-            b.set_end(ends)
+            b.set_end([min(b.info().t, ends[g]) if g in unstable else ends[g] for g in range(len(samples))])
     if not unstable:
         b.sync()
-    out = np.full((len(samples), 4) + samples[0]["mask"].shape, np.nan, np.float32)
+    out = np.full((len(samples), 4, GRID[2], GRID[1], GRID[0]), np.nan, np.float32)
     for g in range(len(samples)):
         if g in unstable:
             continue
-        m, ns = b.member(g).mean(dtype=np.float32)
-        out[g] = np.moveaxis(m, -1, 0)
+        out[g] = mean_on_grid(b.member(g)).cpu().numpy()
     info = b.info()
     log(f"  LBM batch of {len(samples)}: {info.t} steps, {info.lattice_updates / 1e9:.1f} G updates in "
         f"{time.time() - t0:.1f} s, unstable {sorted(unstable)}")
@@ -170,32 +234,35 @@ def time_fno(batch=8, reps=10, warmup=3):
 def warm_start_study(samples, ref, inner, start_fields, storage="f16c", windows=(0, 1, 2, 3, 5), width=2.0,
                      log=print):
     """How soon an LBM run gives the mean flow, started from rest or from
-    given fields (the FNO's prediction, as equilibrium populations): for each
+    given fields (the FNO's prediction [4, nz, ny, nx] on the surrogate grid,
+    resampled onto each sample's grid, as equilibrium populations): for each
     window start s, the time average over flow-through times [s, s + width)
     against the converged mean `ref` ([n, 4, nz, ny, nx]; rel-L2 of (u, v, w)
     on the cells `inner`).  Returns {"rest": [...], "fno": [...]} per window
     and the first window start under 5 %."""
     from .lbm import Batch
 
-    nx = samples[0]["grid"][0]
-    ft = nx / U_IN
     out = {}
     for mode in ("rest", "fno"):
         errs = []
         for s0 in windows:
-            t_end = int(math.ceil((s0 + width) * ft / 10.0)) * 10
-            m_start = int(round(s0 * ft / 10.0)) * 10
-            b = Batch([dict(grid=sm["grid"], mask=sm["mask"], storage=storage, re=sm["re"], u_in=U_IN,
-                            l_ref=float(sm["grid"][1]), mean_start=m_start, mean_end=t_end, mean_every=10)
-                       for sm in samples])
+            ends, mems = [], []
+            for sm in samples:
+                ft = sm["grid"][0] / U_IN
+                t_end = int(math.ceil((s0 + width) * ft / 10.0)) * 10
+                ends.append(t_end)
+                mems.append(dict(grid=sm["grid"], mask=sm["mask"], storage=storage, re=sm["re"], u_in=U_IN,
+                                 l_ref=float(sm["grid"][1]), mean_start=int(round(s0 * ft / 10.0)) * 10,
+                                 mean_end=t_end, mean_every=10))
+            b = Batch(mems)
             for g, sm in enumerate(samples):
                 b.set_wall_distances(g, I.link_wall_distances(sm["grid"], sm["prims"], sm["mask"]))
                 if mode == "fno":
-                    b.member(g).init_equilibrium(start_fields[g])
-            b.set_end([t_end] * len(samples))
+                    b.member(g).init_equilibrium(fields_on_native_grid(start_fields[g], sm))
+            b.set_end(ends)
             b.run_to_end()
             b.sync()
-            ms = np.stack([np.moveaxis(b.member(g).mean(dtype=np.float32)[0], -1, 0) for g in range(len(samples))])
+            ms = np.stack([mean_on_grid(b.member(g)).cpu().numpy() for g in range(len(samples))])
             b.close()
             rel, _ = metrics(ms, ref, inner)
             errs.append(float(np.median(rel)))
@@ -232,15 +299,15 @@ def metrics(pred, true, cells):
 
 
 def run(n_train=512, n_test=64, epochs=50, batch=8, lr=1e-3, storage="f16c", n_ft=15.0, sim_batch=64,
-        out=None, log=print, full_region=True, re_range=RE_RANGE, warm=True):
+        out=None, log=print, full_region=True, re_range=RE_RANGE, warm=True, grids="config4", speed=True):
     import torch
     from .fno import FNO
 
     dev = torch.device("cuda")
     report = {"grid": list(GRID), "n_train": n_train, "n_test": n_test, "epochs": epochs, "batch": batch,
-              "lr": lr, "lbm_storage": storage, "flow_throughs": n_ft, "re_range": list(re_range)}
-    train_s = [sample(1000 + k, re_range=re_range) for k in range(n_train)]
-    test_s = [sample(2000 + k, re_range=re_range) for k in range(n_test)]
+              "lr": lr, "lbm_storage": storage, "flow_throughs": n_ft, "re_range": list(re_range), "grids": grids}
+    train_s = [sample(1000 + k, re_range=re_range, grids=grids) for k in range(n_train)]
+    test_s = [sample(2000 + k, re_range=re_range, grids=grids) for k in range(n_test)]
     # 1-2: data from the LBM
     t0 = time.time()
     Y, bad = [], []
@@ -256,7 +323,7 @@ def run(n_train=512, n_test=64, epochs=50, batch=8, lr=1e-3, storage="f16c", n_f
     keep_tr = [k for k in range(n_train) if k not in bad]
     keep_te = [k for k in range(n_test) if n_train + k not in bad]
     X = np.stack([features(s, re_range) for s in allS])
-    masks = np.stack([s["mask"] for s in allS])
+    masks = np.stack([target_mask(s) for s in allS])
     # 3: scaling on the training set (fluid cells)
     lo = np.zeros(4, np.float32)
     hi = np.zeros(4, np.float32)
@@ -278,6 +345,15 @@ def run(n_train=512, n_test=64, epochs=50, batch=8, lr=1e-3, storage="f16c", n_f
     def train(weights, tag):
         Wd = torch.from_numpy(weights).to(dev)
         net = FNO(nx=GRID[0], ny=GRID[1], nz=GRID[2], max_batch=batch)
+        # the output bias starts at the weighted mean of the scaled training
+        # targets: the SIREN's output layer starts small (Sitzmann et al.'s
+        # initialisation), and Adam moves a bias by about lr per step
+        from .fno import flatten, unflatten
+        prm = unflatten(net.cfg, net.params())
+        wsum = np.stack([weights[k] for k in keep_tr]).sum()
+        for c in range(4):
+            prm["Q2_b"][c] = float(sum((Yn[k, c] * weights[k]).sum() for k in keep_tr) / wsum)
+        net.set_params(flatten(net.cfg, prm))
         rng = np.random.Generator(np.random.PCG64(0))
         steps_ep = int(math.ceil(len(keep_tr) / batch))
         total = epochs * steps_ep
@@ -355,10 +431,16 @@ def run(n_train=512, n_test=64, epochs=50, batch=8, lr=1e-3, storage="f16c", n_f
     if warm and len(test_idx) >= 8:
         k8 = list(range(8))
         pred8 = pred[k8]                                  # lattice units, [8, 4, nz, ny, nx]
-        fields = [np.ascontiguousarray(np.moveaxis(pred8[g], 0, -1), dtype=np.float32) for g in k8]
+        fields = [np.ascontiguousarray(pred8[g], dtype=np.float32) for g in k8]
         samp8 = [test_s[keep_te[g]] for g in k8]
         report["warm_start"] = warm_start_study(samp8, true[k8], inner[k8], fields, storage=storage, log=log)
     # speed: one FNO prediction against the LBM run it replaces
+    if not speed:
+        if out:
+            with open(out, "w") as fp:
+                json.dump(report, fp, indent=1)
+        net.close()
+        return report
     st = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     xb = xb_src[:batch].contiguous() if len(test_idx) >= batch else \
@@ -398,15 +480,21 @@ def main():
     ap.add_argument("--storage", default="f16c")
     ap.add_argument("--epochs", type=int, default=50)
     ap.add_argument("--time", action="store_true", help="only time forward and training step (random inputs)")
-    ap.add_argument("--re-range", default=None, help="lo,hi Re on the 64-cell channel height")
+    ap.add_argument("--re-range", default=None, help="lo,hi Re on the channel height (default 1000,10000)")
+    ap.add_argument("--grids", default="config4", choices=["config4", "direct"],
+                    help="config4: uneven grids resampled to 128x64x64; direct: drawn on 128x64x64")
+    ap.add_argument("--n-train", type=int, default=512)
+    ap.add_argument("--n-test", type=int, default=64)
     args = ap.parse_args()
     rr = RE_RANGE if args.re_range is None else tuple(float(v) for v in args.re_range.split(","))
     if args.time:
         print(json.dumps(time_fno()))
     elif args.quick:
-        run(n_train=16, n_test=8, epochs=2, n_ft=2.0, storage=args.storage, out=args.out, sim_batch=24, re_range=rr)
+        run(n_train=16, n_test=8, epochs=2, n_ft=2.0, storage=args.storage, out=args.out, sim_batch=24, re_range=rr,
+            grids=args.grids)
     else:
-        run(epochs=args.epochs, storage=args.storage, out=args.out, re_range=rr)
+        run(n_train=args.n_train, n_test=args.n_test, epochs=args.epochs, storage=args.storage, out=args.out,
+            re_range=rr, grids=args.grids)
 
 
 if __name__ == "__main__":

@@ -38,7 +38,8 @@ class lbm_params(C.Structure):
         ("snap_first", C.c_int64), ("snap_every", C.c_int64), ("snap_count", C.c_int64),
         ("snap_halfres", C.c_int32), ("force_every", C.c_int32),
         ("force_capacity", C.c_int64),
-        ("block_x", C.c_int32), ("block_y", C.c_int32), ("stats", C.c_int32), ("reserved", C.c_int32 * 5),
+        ("block_x", C.c_int32), ("block_y", C.c_int32), ("stats", C.c_int32),
+        ("param4", C.c_int32), ("limiter", C.c_double), ("reserved", C.c_int32 * 2),
     ]
 
 
@@ -93,6 +94,8 @@ def lib():
             "lbm_set_probes": (C.c_int, [_vp, _i64, _vp, _i64, _i64]),
             "lbm_init_equilibrium": (C.c_int, [_vp, _vp]),
             "lbm_read_probes": (C.c_int, [_vp, _vp, _i64, C.POINTER(_i64)]),
+            "lbm_set_plane_monitor": (C.c_int, [_vp, C.c_int32, _i64, _i64]),
+            "lbm_read_plane_monitor": (C.c_int, [_vp, _vp, _i64, C.POINTER(_i64), _vp]),
             "lbm_set_wall_distances": (C.c_int, [_vp, _i64, _vp, _vp, _vp]),
             "lbm_batch_set_wall_distances": (C.c_int, [_vp, C.c_int32, _i64, _vp, _vp, _vp]),
             "lbm_read_snapshot": (C.c_int, [_vp, C.c_int32, _vp]),
@@ -124,6 +127,8 @@ def lib():
             "lbm_load": (C.c_int, [_vp, C.c_char_p]),
             "lbm_totals_noalloc": (C.c_int, [_vp, C.c_int32, C.c_int64, _vp, C.c_int32, C.c_int32,
                                              C.c_int32, _vp, _vp]),
+            "lbm_resample": (C.c_int, [_vp, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32, _vp,
+                                       C.c_int32, C.c_int32, C.c_int32, _vp]),
             "lbm_last_error": (C.c_char_p, [_vp]),
             "lbm_status_string": (C.c_char_p, [C.c_int]),
         }
@@ -212,6 +217,21 @@ def lbm_set_probes(h, cells, every=1, capacity=65536):
     _check(lib().lbm_set_probes(h, len(cells), _ptr(cells), int(every), int(capacity)), h)
 
 
+def lbm_set_plane_monitor(h, z=-1, every=1, capacity=64):
+    _check(lib().lbm_set_plane_monitor(h, int(z), int(every), int(capacity)), h)
+
+
+def lbm_read_plane_monitor(h, nx, ny):
+    """(planes [k, ny, nx, 4] float32, steps [k] int64) recorded so far."""
+    rows = _i64()
+    _check(lib().lbm_read_plane_monitor(h, None, 0, C.byref(rows), None), h)
+    out = np.zeros((rows.value, ny, nx, 4), np.float32)
+    steps = np.zeros(rows.value, np.int64)
+    if rows.value:
+        _check(lib().lbm_read_plane_monitor(h, _ptr(out), rows.value, C.byref(rows), _ptr(steps)), h)
+    return out, steps
+
+
 def lbm_read_probes(h, n_probes):
     rows = C.c_int64()
     _check(lib().lbm_read_probes(h, None, 0, C.byref(rows)), h)
@@ -284,6 +304,16 @@ def lbm_totals_noalloc(pdf, storage, slot_stride, mask, grid, stream, out):
     _check(lib().lbm_totals_noalloc(_ptr(pdf), int(storage), int(slot_stride),
                                     _ptr(mask) if mask is not None else None, nx, ny, nz,
                                     C.c_void_p(stream or 0), _ptr(out)), None)
+
+
+def lbm_resample(src, grid, channels, src_layout, dst, out_grid, stream=None):
+    """Cell-centred trilinear resampling of device fields (see include/lbm.h):
+    src on grid (nx, ny, nz), layout 0 = [z][y][x][C], 1 = [C][z][y][x];
+    dst [C][mz][my][mx] on out_grid (mx, my, mz)."""
+    nx, ny, nz = grid
+    mx, my, mz = out_grid
+    _check(lib().lbm_resample(_ptr(src), nx, ny, nz, int(channels), int(src_layout), _ptr(dst), mx, my, mz,
+                              C.c_void_p(stream or 0)), None)
 
 
 def lbm_reset(h):
@@ -433,6 +463,14 @@ class _Lattice:
     def probes(self):
         """[rows, n_probes, 4] float32: (u, v, w, p) per recorded step."""
         return lbm_read_probes(self.h, getattr(self, "_n_probes", 0))
+
+    def set_plane_monitor(self, z=-1, every=1, capacity=64):
+        """Record the (u, v, w, p) of the plane z (default nz/2) every `every` steps."""
+        lbm_set_plane_monitor(self.h, z, every, capacity)
+
+    def plane_monitor(self):
+        """(planes [k, ny, nx, 4], steps [k]) recorded so far."""
+        return lbm_read_plane_monitor(self.h, self.grid.nx, self.grid.ny)
 
     def stats(self, dtype=np.float64):
         """Velocity covariances [nz, ny, nx, 6] (xx, yy, zz, xy, xz, yz) over

@@ -9,10 +9,10 @@ Q = 27
 
 
 def case(grid, mask=None, omega1=1.8, omega_bulk=1.0, omega_higher=1.0, galilean=1, u_in=0.05,
-         faces=("inlet", "outlet", "wall", "wall"), mean=(0, 0, 0), noise=None):
+         faces=("inlet", "outlet", "wall", "wall"), mean=(0, 0, 0), noise=None, param4=0):
     return dict(grid=tuple(grid), mask=mask, omega1=omega1, omega_bulk=omega_bulk,
                 omega_higher=omega_higher, galilean=galilean, u_in=u_in, faces=tuple(faces),
-                mean=tuple(mean), noise=noise)
+                mean=tuple(mean), noise=noise, param4=param4)
 
 
 def noise_state(grid, mask, seed, amp, weights):
@@ -31,7 +31,7 @@ def run_oracle(c, steps):
     import oracle.lbm as O
     nx, ny, nz = c["grid"]
     p = O.params(nx, ny, nz, c["omega1"], c["omega_bulk"], c["omega_higher"], galilean=c["galilean"],
-                 u_in=c["u_in"], faces=c["faces"], mean=c["mean"])
+                 u_in=c["u_in"], faces=c["faces"], mean=c["mean"], param4=c.get("param4", 0))
     L = O.Lattice(p, c["mask"])
     if c["noise"] is not None:
         seed, amp = c["noise"]
@@ -46,7 +46,7 @@ def make_solver(c, storage, **extra):
     m, e, v = c["mean"]
     s = Solver(c["grid"], c["mask"], storage=storage, omega1=c["omega1"], omega_bulk=c["omega_bulk"],
                omega_higher=c["omega_higher"], galilean_correction=c["galilean"], u_in=c["u_in"],
-               faces=c["faces"], mean_start=m, mean_end=e, mean_every=v, **extra)
+               faces=c["faces"], mean_start=m, mean_end=e, mean_every=v, param4=c.get("param4", 0), **extra)
     if c["noise"] is not None:
         s.init_noise(*c["noise"])
     return s

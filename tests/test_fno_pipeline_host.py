@@ -12,19 +12,45 @@ from paper_2606_16765_gb300 import fno_pipeline as P
 def test_samples_are_deterministic_and_in_range():
     a, b = P.sample(3), P.sample(3)
     assert a["re"] == b["re"] and np.array_equal(a["mask"], b["mask"]) and a["angle"] == b["angle"]
-    res = [P.sample(s)["re"] for s in range(40)]
-    assert min(res) >= P.RE_RANGE[0] and max(res) <= P.RE_RANGE[1]
-    m = a["mask"]
-    assert m.shape == (P.GRID[2], P.GRID[1], P.GRID[0]) and 0 < m.sum() < m.size
-    assert -30.0 <= a["angle"] <= 30.0
+    ss = [P.sample(s) for s in range(40)]
+    res = [s["re"] for s in ss]
+    assert min(res) >= P.RE_RANGE[0] and max(res) <= P.RE_RANGE[1] == 10000.0 and P.RE_RANGE[0] == 1000.0
+    # the batched configuration's grids, each axis from its set, several of them drawn
+    grids = {s["grid"] for s in ss}
+    assert len(grids) > 5
+    for g in grids:
+        assert g[0] in (128, 192, 256) and g[1] in (64, 96, 128) and g[2] in (64, 96, 128)
+    for s in ss[:6]:
+        m = s["mask"]
+        assert m.shape == (s["grid"][2], s["grid"][1], s["grid"][0]) and 0 < m.sum() < m.size
+        assert -30.0 <= s["angle"] <= 30.0
+    d = P.sample(3, grids="direct")
+    assert d["grid"] == P.GRID and d["mask"].shape == (P.GRID[2], P.GRID[1], P.GRID[0])
+
+
+def test_target_mask_samples_the_geometry_on_the_surrogate_grid():
+    """On the surrogate's own grid the target mask is the voxelised mask; on
+    a grid twice as fine along every axis it agrees with the fine mask on
+    every 2x2x2 block that is wholly fluid or wholly solid."""
+    d = P.sample(4, grids="direct")
+    assert np.array_equal(P.target_mask(d), d["mask"])
+    s = next(P.sample(k) for k in range(100) if P.sample(k)["grid"] == (256, 128, 128))
+    m = P.target_mask(s)
+    assert m.shape == (P.GRID[2], P.GRID[1], P.GRID[0])
+    fine = s["mask"].astype(np.float64)
+    box = fine.reshape(64, 2, 64, 2, 128, 2).mean(axis=(1, 3, 5))
+    clear = (box == 0) | (box == 1)                      # blocks entirely fluid or solid
+    assert np.array_equal(m[clear], box[clear].astype(np.uint8))
+    assert m.sum() > 0
 
 
 def test_features_channels():
     s = P.sample(5)
     f = P.features(s)
-    assert f.shape == (4,) + s["mask"].shape
-    assert np.array_equal(f[0], s["mask"].astype(np.float32))
+    assert f.shape == (4, P.GRID[2], P.GRID[1], P.GRID[0])
+    assert np.array_equal(f[0], P.target_mask(s).astype(np.float32))
     centre = 0.5 * (math.log10(P.RE_RANGE[0]) + math.log10(P.RE_RANGE[1]))
+    assert centre == pytest.approx(3.5)
     assert np.allclose(f[1], math.log10(s["re"]) - centre)
     a = math.radians(s["angle"])
     assert np.allclose(f[2], math.cos(a)) and np.allclose(f[3], math.sin(a))

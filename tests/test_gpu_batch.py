@@ -199,3 +199,53 @@ def test_batch_with_wall_distances_equals_independent_runs():
         Fa, Fb = m.forces(), s.forces()
         assert Fa.shape == Fb.shape
         assert np.abs(Fa - Fb).max() <= 1e-12 * np.abs(Fb).max(), g
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+def test_batch_members_match_the_oracle(storage):
+    """Three members on uneven small grids stepped by the batched driver, each
+    compared directly with the FP64 oracle run of its own lattice: convective
+    outflow, interpolated bounce-back on the obstacle links (wall distances
+    of the primitives), FP64 mean and force records.  FP64 pdfs to 1e-12,
+    FP32 to 1e-5 (max relative velocity error and density error)."""
+    from paper_2606_16765_gb300.lbm import Batch
+    faces = ("inlet", "outflow", "wall", "wall")
+    specs = [((40, 16, 12), 1.6, I.Primitive("sphere", (12.0, 7.5, 5.5), (7.0,))),
+             ((57, 21, 14), 1.85, I.Primitive("cylinder", (17.3, 10.2, 6.5), (6.4, 9.0), 12.0)),
+             ((26, 9, 11), 1.3, I.Primitive("torus", (8.0, 4.1, 5.0), (6.5, 2.2)))]
+    steps = 30
+    ms, refs = [], []
+    for grid, w1, prim in specs:
+        nx, ny, nz = grid
+        mask = I.voxelize(grid, [prim])
+        links = I.link_wall_distances(grid, [prim], mask)
+        ms.append(dict(grid=grid, mask=mask, storage=storage, omega1=w1, u_in=0.05, faces=faces,
+                       mean_start=10, mean_end=1000, mean_every=2, force_every=1, force_capacity=256))
+        L = O.Lattice(O.params(nx, ny, nz, w1, u_in=0.05, faces=faces, mean=(10, 1000, 2)), mask)
+        L.set_q(I.dense_wall_distances(grid, links))
+        L.step(steps)
+        refs.append((L, mask, links))
+    b = Batch(ms)
+    for g, (_, _, links) in enumerate(refs):
+        b.set_wall_distances(g, links)
+    b.run(steps)
+    b.sync()
+    tol = {"f64": 1e-12, "f32": 1e-5}[storage]
+    for g, (L, mask, links) in enumerate(refs):
+        m = b.member(g)
+        assert m.t == steps
+        fl = mask == 0
+        rho, u = m.macros()
+        rr, ur = L.macros()
+        eu = np.abs(u - ur)[fl].max() / np.abs(ur[fl]).max()
+        er = np.abs(rho - rr)[fl].max()
+        mean, ns = m.mean()
+        mref, nref = L.means()
+        em = np.abs(mean - mref)[fl].max() / np.abs(mref[..., :3])[fl].max()
+        F, Fr = m.forces(), L.forces()
+        ef = np.abs(F - Fr).max() / np.abs(Fr).max()
+        print(f"batch member {g} {storage}: u {eu:.2e} rho {er:.2e} mean {em:.2e} force {ef:.2e}, "
+              f"{len(links[0])} wall-distance links")
+        assert eu <= tol and er <= tol and em <= tol
+        assert ns == nref == 10
+        assert F.shape == Fr.shape == (steps, 3) and ef <= 10 * tol

@@ -1,5 +1,6 @@
 """GPU parity of the FNO kernels (forward, backward, Adam) against the FP64
-oracle.  Tolerances: FP32 activations with the FP32 contraction: forward
+oracle: App. B's network (feed-forward lift, Fourier layers, SIREN
+projection with omega0 = 30).  Tolerances: FP32 activations with the FP32 contraction: forward
 <= 1e-5 (max relative), gradients <= 1e-4 (relative L2 per parameter group);
 BF16 tensor-core contraction and/or BF16 activations: forward relative L2
 <= 2e-2, gradients cosine >= 0.999 and relative L2 <= 3e-2 (BF16 keeps 8
@@ -25,12 +26,15 @@ def tiny_cfgs(width=8, tiled=False):
     """tiled: a 16x8x8 grid (1024 cells, whole 64-cell tiles: the gradient
     reduction takes its cp.async path) instead of 10x6x8 (480 cells)."""
     if tiled:
-        ocfg = F.FNOConfig(grid=(8, 8, 16), cin=4, width=width, cout=4, modes=(3, 3, 4), layers=2, hidden=16)
+        ocfg = F.FNOConfig(grid=(8, 8, 16), cin=4, width=width, cout=4, modes=(3, 3, 4), layers=2, hidden=16,
+                           lift_hidden=32)
         gcfg = dict(nx=16, ny=8, nz=8, cin=4, width=width, cout=4, mx=4, my=3, mz=3, layers=2, hidden=16,
-                    max_batch=8)
+                    max_batch=8, lift_hidden=32)
         return ocfg, gcfg
-    ocfg = F.FNOConfig(grid=(8, 6, 10), cin=2, width=width, cout=2, modes=(3, 2, 3), layers=2, hidden=5)
-    gcfg = dict(nx=10, ny=6, nz=8, cin=2, width=width, cout=2, mx=3, my=2, mz=3, layers=2, hidden=5, max_batch=8)
+    ocfg = F.FNOConfig(grid=(8, 6, 10), cin=2, width=width, cout=2, modes=(3, 2, 3), layers=2, hidden=5,
+                       lift_hidden=5)
+    gcfg = dict(nx=10, ny=6, nz=8, cin=2, width=width, cout=2, mx=3, my=2, mz=3, layers=2, hidden=5, max_batch=8,
+                lift_hidden=5)
     return ocfg, gcfg
 
 
@@ -131,12 +135,23 @@ def test_whole_tile_grid_matches_oracle(act_bf16, tensor_cores):
             assert rel_l2(g[k], gr[k]) < 3e-2, k
 
 
-def test_adam_trajectory_matches_oracle():
+@pytest.mark.parametrize("act_bf16,tensor_cores", [(0, 0), (1, 1)])
+def test_adam_trajectory_matches_oracle(act_bf16, tensor_cores):
+    """Five Adam steps from the same parameters.  FP32 path: losses to 1e-4
+    and parameters to 1e-5.  BF16 activations with tensor cores (the trained
+    configuration): losses to 2e-2 and every parameter group's displacement
+    from the start against the oracle's.  Adam moves each parameter by about
+    lr per step whatever the gradient's size, so an element whose gradient is
+    within the BF16 gradient error of zero may step the other way; the
+    displacement bounds (cosine >= 0.999, relative L2 <= 0.06) allow that
+    for about 0.1 % of the elements (2 sqrt(f) = 0.06); measured: cosine
+    >= 0.9994, relative L2 <= 0.033."""
     from paper_2606_16765_gb300 import fno as G
-    ocfg, gcfg = tiny_cfgs(3)
-    gcfg.update(act_bf16=0, tensor_cores=0)
+    ocfg, gcfg = tiny_cfgs(3 if not tensor_cores else 8)
+    gcfg.update(act_bf16=act_bf16, tensor_cores=tensor_cores)
     GCFG_CACHE["g"] = gcfg
     x, t, m, p = problem(ocfg, seed=3)
+    p0 = {k: v.copy() for k, v in p.items()}
     net = G.FNO(**gcfg)
     net.set_params(to_gpu_params(ocfg, p))
     m1 = {k: np.zeros_like(v) for k, v in p.items()}
@@ -146,12 +161,18 @@ def test_adam_trajectory_matches_oracle():
         Lg = net.train_step(x, t, m, 1e-3)
         Lr, gr = F.loss_and_grad(p, x.astype(np.float64), t.astype(np.float64), m.astype(np.float64), ocfg)
         p = F.adam_step(p, gr, m1, m2, step, 1e-3)
-        assert abs(Lg - Lr) / Lr < 1e-4
+        assert abs(Lg - Lr) / Lr < (1e-4 if not act_bf16 else 2e-2)
         losses.append(Lg)
     assert losses[-1] < losses[0]
     pg = gpu_grads_as_oracle(ocfg, gcfg, net.params())
     for k in p:
-        assert np.abs(pg[k] - p[k]).max() < 1e-5, k
+        if not act_bf16:
+            assert np.abs(pg[k] - p[k]).max() < 1e-5, k
+        else:
+            dg, dr = pg[k] - p0[k], p[k] - p0[k]
+            print(f"adam bf16 {k}: displacement cosine {cosine(dg, dr):.5f}, rel L2 {rel_l2(dg, dr):.3e}")
+            assert cosine(dg, dr) > 0.999, k
+            assert rel_l2(dg, dr) < 0.06, k
 
 
 def test_full_size_forward_matches_oracle():
@@ -195,6 +216,36 @@ def test_full_size_gradients_match_oracle():
     g_gpu = gpu_grads_as_oracle(ocfg, gcfg, net.grads())
     worst = max(rel_l2(g_gpu[k], g_ref[k]) for k in g_ref)
     print(f"full-size gradients: loss rel err {abs(L_gpu - L_ref) / L_ref:.2e}, worst group rel L2 {worst:.2e}")
+    assert abs(L_gpu - L_ref) / L_ref < 2e-2
+    for k in g_ref:
+        assert cosine(g_gpu[k], g_ref[k]) > 0.999, k
+        assert rel_l2(g_gpu[k], g_ref[k]) < 3e-2, k
+
+
+def test_timed_batch_of_eight_matches_oracle():
+    """Batch 8 (all eight batch columns of the tensor-core contraction) on a
+    128x16x16 grid: nx = 128 keeps the tensor-core x transforms on their
+    timed path, width 32 and hidden 128 the tensor-core projection (k_proj_tc
+    for the forward, k_pw_tc for the training path).  Forward, loss and every
+    gradient group against the oracle at the BF16 bounds."""
+    from paper_2606_16765_gb300 import fno as G
+    ocfg = F.FNOConfig(grid=(16, 16, 128), modes=(8, 8, 16))
+    gcfg = dict(nx=128, ny=16, nz=16, max_batch=8, act_bf16=1, tensor_cores=1)
+    GCFG_CACHE["g"] = gcfg
+    x, t, m, p = problem(ocfg, B=8, seed=41)
+    net = G.FNO(**gcfg)
+    net.set_params(to_gpu_params(ocfg, p))
+    y = net.forward(x)
+    y_ref, tape = F.forward(p, x.astype(np.float64), ocfg, keep=True)
+    per_sample = [rel_l2(y[b], y_ref[b]) for b in range(8)]
+    L_gpu = net.loss_grad(x, t, m)
+    L_ref = F.masked_mse(y_ref, t.astype(np.float64), m.astype(np.float64))
+    g_ref = F.backward(p, tape, y_ref, t.astype(np.float64), m.astype(np.float64), ocfg)
+    g_gpu = gpu_grads_as_oracle(ocfg, gcfg, net.grads())
+    worst = max(rel_l2(g_gpu[k], g_ref[k]) for k in g_ref)
+    print(f"batch 8 at 128x16x16: forward rel L2 per sample max {max(per_sample):.2e}, "
+          f"loss rel err {abs(L_gpu - L_ref) / L_ref:.2e}, worst gradient group rel L2 {worst:.2e}")
+    assert max(per_sample) < 2e-2
     assert abs(L_gpu - L_ref) / L_ref < 2e-2
     for k in g_ref:
         assert cosine(g_gpu[k], g_ref[k]) > 0.999, k

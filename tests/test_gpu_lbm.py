@@ -588,3 +588,81 @@ def test_wall_distance_argument_errors():
         s.set_wall_distances((far, np.array([26], np.int8), np.array([0.5])))
     s.set_wall_distances((cell, d, q))
     s.set_wall_distances((np.zeros(0, np.int64), np.zeros(0, np.int8), np.zeros(0)))   # back to halfway
+
+
+# --------------------------------------------------------------------------
+# fourth-order parametrisation with limiter (Sec. 3.2, Geier et al. 2017)
+# --------------------------------------------------------------------------
+def param4_cases():
+    d = I.sphere_channel_64()
+    yield "sphere channel 64x32x32, outflow, w1 1.95", K.case(
+        d["grid"], d["mask"], omega1=1.95, u_in=0.05, faces=("inlet", "outflow", "wall", "wall"),
+        noise=(51, 2e-3), param4=1, mean=(10, 60, 5))
+    g = (29, 13, 11)
+    yield "ragged periodic box, w1 1.9, large noise (limiter engaged)", K.case(
+        g, I.sphere(g, (10.0, 6.0, 5.0), 2.5), omega1=1.9, u_in=0.0, faces=("periodic",) * 4,
+        noise=(52, 5e-3), param4=1)
+    yield "closed box, w1 1.85, bulk rate 1.3", K.case(
+        (17, 9, 12), None, omega1=1.85, omega_bulk=1.3, u_in=0.0, faces=("wall",) * 4, noise=(53, 5e-3), param4=1)
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+@pytest.mark.parametrize("which", [0, 1, 2])
+def test_parametrised_collision_matches_oracle(storage, which):
+    name, c = list(param4_cases())[which]
+    L = K.run_oracle(c, 60)
+    rho_r, u_r = L.macros()
+    s = K.make_solver(c, storage)
+    s.step(60)
+    s.sync()
+    rho, u = s.macros()
+    fluid = c["mask"] == 0 if c["mask"] is not None else np.ones(rho.shape, bool)
+    eu, er = K.rel_u_err(u, u_r, fluid), K.rho_err(rho, rho_r, fluid)
+    print(f"param4 {name} {storage}: rel u err {eu:.3e} rho err {er:.3e}")
+    tol = {"f64": 1e-12, "f32": 1e-5}[storage]
+    assert eu <= tol and er <= tol
+    if c["mean"][2]:
+        m, ns = s.mean()
+        mref, nref = L.means()
+        assert ns == nref
+        assert np.abs(m - mref)[fluid].max() / np.abs(mref[..., :3])[fluid].max() <= tol
+
+
+def test_parametrisation_argument_errors():
+    from paper_2606_16765_gb300.lbm import Solver, LBMError
+    with pytest.raises(LBMError):
+        Solver((8, 4, 4), None, omega1=1.0, omega_bulk=1.0, param4=1)   # undefined at omega1 = omega_bulk
+    with pytest.raises(LBMError):
+        Solver((8, 4, 4), None, omega1=1.9, param4=1, limiter=0.0)
+
+
+# --------------------------------------------------------------------------
+# monitor plane (Sec. 2: 2D snapshots of the centre x-y plane)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+def test_monitor_plane_records_the_centre_plane_before_each_sampled_step(storage):
+    """Planes of the sphere channel every 7 steps for 30 steps against the
+    oracle's macros of the state before those steps at z = nz / 2, with a
+    ring of 2 planes so that the host flush runs; a second plane position."""
+    d = I.sphere_channel_64()
+    nx, ny, nz = d["grid"]
+    w1 = O.omega_from_re(d["re"], d["u_in"], d["l_ref"])
+    c = K.case(d["grid"], d["mask"], omega1=w1, u_in=d["u_in"], faces=("inlet", "outflow", "wall", "wall"),
+               noise=(61, 1e-3))
+    for z in (-1, 3):
+        s = K.make_solver(c, storage)
+        s.set_plane_monitor(z=z, every=7, capacity=2)
+        s.step(30)
+        s.sync()
+        planes, steps = s.plane_monitor()
+        assert list(steps) == [0, 7, 14, 21, 28] and planes.shape == (5, ny, nx, 4)
+        zz = nz // 2 if z < 0 else z
+        L = K.run_oracle(c, 0)
+        tol = {"f64": 1e-12, "f32": 1e-5}[storage]
+        for k, t in enumerate(steps):
+            L.step(int(t) - L.t)
+            rho, u = L.macros()
+            ref = np.concatenate([u[zz], ((rho[zz] - 1) / 3)[..., None]], -1)
+            ref[c["mask"][zz] != 0] = 0.0
+            err = np.abs(planes[k] - ref).max() / np.abs(ref[..., :3]).max()
+            assert err <= tol, (z, t, err)
