@@ -219,14 +219,14 @@ def epilogue_counts(sch, warmup, steps):
             "force_rows": len(range(lo, hi, sch["force_every"]))}
 
 
-def run_ours(args, storage, d, ws, device_index):
+def run_ours(args, storage, d, ws, device_index, param4=0):
     import torch
     from paper_2606_16765_gb300.lbm import Solver
 
     K, W = args.steps, args.warmup
     sch = schedule(K, W)
     s = Solver(d["grid"], d["mask"], storage=storage, re=d["re"], u_in=d["u_in"], l_ref=d["l_ref"],
-               block_x=args.block_x, **sch)
+               block_x=args.block_x, param4=param4, **sch)
     s.set_wall_distances(d["links"])
     info = s.info()
     s.step(W)
@@ -337,6 +337,24 @@ def run_batch(steps, warmup, storage="f16s", n=32):
     return out
 
 
+def fno_algorithmic_bytes(batch, n, width=32, cin=4, cout=4, layers=4, act=2):
+    """Bytes an FNO forward and a training step must move at least, the
+    activations each written once and read once: FP32 input and output,
+    BF16 (act = 2 B) activations of `width` channels.  Forward: input, lift
+    output, per layer read v and write v', projection read v_L, output.
+    Training adds the stored pre-activations (written in the forward, read in
+    the backward), per layer the layer input re-read and an FP32 gradient
+    read and written, and the projection and lift backward (v_L, x, the
+    output gradient read, FP32 input gradients written)."""
+    cells = batch * n
+    io_in, io_out = cells * cin * 4, cells * cout * 4
+    a = cells * width * act
+    g = cells * width * 4
+    fwd = io_in + a + layers * 2 * a + a + io_out
+    train = fwd + layers * a + layers * (a + a + 2 * g) + (a + io_out + g) + (io_in + g)
+    return fwd, train
+
+
 def run_fno(batch=8, reps=10):
     """FNO surrogate at 128x64x64 (4 Fourier layers, width 32, modes 16x8x8,
     BF16 activations, tensor-core mode contraction): forward and training-step
@@ -349,7 +367,17 @@ def run_fno(batch=8, reps=10):
     r = P.time_fno(batch=batch, reps=reps)
     t_lbm = P.time_lbm_to_end(P.sample(2000))
     fwd = r["forward_ms_per_batch"]
-    return {"grid": list(P.GRID), "batch": batch, "forward_ms_per_batch": fwd,
+    nx, ny, nz = P.GRID
+    b_fwd, b_train = fno_algorithmic_bytes(batch, nx * ny * nz)
+    peak, kind = measured_peaks()
+    roof = {"bound": "hbm", "unit": "GB/s", "peak": peak, "peak_source": kind,
+            "bytes_per_forward": b_fwd, "bytes_per_train_step": b_train,
+            "achieved": b_fwd / (fwd / 1e3) / 1e9, "frac": b_fwd / (fwd / 1e3) / 1e9 / peak,
+            "train_achieved": b_train / (r["train_step_ms"] / 1e3) / 1e9,
+            "train_frac": b_train / (r["train_step_ms"] / 1e3) / 1e9 / peak,
+            "note": "algorithmic bytes: each activation written once and read once (BF16), FP32 input/output "
+                    "and gradients; the implementation's unfused stages move more"}
+    return {"grid": list(P.GRID), "batch": batch, "forward_ms_per_batch": fwd, "roofline": roof,
             "forward_ms_per_sample": fwd / batch, "train_step_ms": r["train_step_ms"],
             "train_samples_per_s": batch / (r["train_step_ms"] / 1e3), "lbm_15ft_seconds_one_sample": t_lbm,
             "speedup_vs_lbm": t_lbm / (fwd / batch / 1e3), "dtype": "bf16 activations, fp32 accumulation"}
@@ -471,7 +499,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--storage", default="f32", choices=["f32", "f16s", "f16c", "bf16s", "f64"])
-    ap.add_argument("--also", default="f16s,f16c", help="comma list of extra storages to report ('' for none)")
+    ap.add_argument("--also", default="f16s,f16c,f32+param4",
+                    help="comma list of extra storages to report, '+param4' for the fourth-order "
+                         "parametrised collision ('' for none)")
     ap.add_argument("--grid", default="1024,512,512")
     ap.add_argument("--block-x", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
@@ -548,18 +578,21 @@ def main():
         "clocks": res["clocks"],
     }
     if rank == 0:
-        for extra in [e for e in args.also.split(",") if e and e != args.storage]:
-            r2 = run_ours(args, extra, d, 1, local)
+        for extra_name in [e for e in args.also.split(",") if e and e != args.storage]:
+            extra, p4 = (extra_name.split("+")[0], 1) if extra_name.endswith("+param4") else (extra_name, 0)
+            r2 = run_ours(args, extra, d, 1, local, param4=p4)
             b2 = 54 * BYTES_PER_POP[extra]
             k2 = 1 if r2["rep"].bulk_n[1] > 0 else 0
             t2 = r2["rep"].bulk_ms[k2] / max(1, r2["rep"].bulk_n[k2])
-            line.setdefault("other_storage", {})[extra] = {
+            line.setdefault("other_storage", {})[extra_name] = {
                 "value": float(r2["info"].fluid_cells) * K / (r2["ms"] / 1e3) / 1e6, "unit": "MLUPS",
                 "ms_per_step": r2["ms"] / K,
                 "interior_kernel_gbs": b2 * r2["info"].interior_cells / (t2 / 1e3) / 1e9,
                 "interior_kernel_frac": b2 * r2["info"].interior_cells / (t2 / 1e3) / 1e9 / peak,
-                "alu_roofline": alu_roofline(f"k_step_bulk<{extra},odd={bool(k2 & 1)},epi=False>",
-                                             r2["info"].interior_cells, t2, r2["clocks"], sms),
+                "alu_roofline": (None if p4 else
+                                 alu_roofline(f"k_step_bulk<{extra},odd={bool(k2 & 1)},epi=False>",
+                                              r2["info"].interior_cells, t2, r2["clocks"], sms)),
+                "collision": "fourth-order parametrisation with limiter (Sec. 3.2)" if p4 else "plain cumulant",
                 "clocks": r2["clocks"]}
         if not args.no_batch:
             line["batch"] = run_batch(args.steps, 20)

@@ -92,26 +92,31 @@ template <> struct Store<__nv_bfloat16> {
 // 15), 11 mantissa bits; normal range 2^-14 .. 2 - 2^-11, subnormal step
 // 2^-25.  Shifted populations of a stable flow stay well inside (-1, 1), so
 // one exponent bit of IEEE binary16 is traded for one more mantissa bit.
-// Encoding scales by 2^-112 so that the FP32 exponent field becomes the
-// 4-bit field, then rounds the 12 dropped mantissa bits to nearest-even;
-// magnitudes beyond the range (and non-finite values) saturate.
+// The code is the FP32 pattern of v 2^-112 with its 12 low mantissa bits
+// dropped: the FP32 exponent field of v 2^-112 is then the 4-bit field.
+//   decode: the code loaded sign-extended and shifted left by 12 puts the sign
+//     on bit 31 and the 15 magnitude bits on bits 12..26 (bits 27..30, copies
+//     of the sign, are masked off); times 2^112.  Two integer operations.
+//   encode: clamp to the largest code (NaN too), scale by 2^-112, round the
+//     dropped bits to nearest (ties away from zero: add half a unit of the
+//     12th bit to the magnitude), keep bits 12..26 and the sign.
 struct F16C {
     uint16_t bits;
 };
 template <> struct Store<F16C> {
     using R = float;
+    static constexpr float MAXV = 1.99951171875f;   // 2 - 2^-11
     static __device__ __forceinline__ float ld(const F16C *p)
     {
-        const uint32_t b = p->bits;
-        return __uint_as_float(((b & 0x8000u) << 16) | ((b & 0x7FFFu) << 12)) * 0x1p112f;
+        const int32_t b = (int32_t)(*reinterpret_cast<const int16_t *>(p));
+        return __uint_as_float(((uint32_t)b << 12) & 0x87FFF000u) * 0x1p112f;
     }
     static __device__ __forceinline__ void st(F16C *p, float v)
     {
+        v = fminf(fmaxf(v, -MAXV), MAXV);
         const uint32_t u = __float_as_uint(v * 0x1p-112f);
-        const uint32_t mag = u & 0x7FFFFFFFu;
-        uint32_t r = mag >= 0x7F800000u ? 0x7FFFu : (mag + 0x7FFu + ((mag >> 12) & 1u)) >> 12;
-        r = r > 0x7FFFu ? 0x7FFFu : r;
-        p->bits = (uint16_t)(((u >> 16) & 0x8000u) | r);
+        const uint32_t r = u + 0x800u;
+        p->bits = (uint16_t)((r >> 12) | ((u >> 16) & 0x8000u));
     }
 };
 

@@ -643,7 +643,8 @@ def test_parametrisation_argument_errors():
 def test_monitor_plane_records_the_centre_plane_before_each_sampled_step(storage):
     """Planes of the sphere channel every 7 steps for 30 steps against the
     oracle's macros of the state before those steps at z = nz / 2, with a
-    ring of 2 planes so that the host flush runs; a second plane position."""
+    ring of 2 planes so that the host flush runs; a second plane position.
+    The planes are recorded in FP32."""
     d = I.sphere_channel_64()
     nx, ny, nz = d["grid"]
     w1 = O.omega_from_re(d["re"], d["u_in"], d["l_ref"])
@@ -658,7 +659,8 @@ def test_monitor_plane_records_the_centre_plane_before_each_sampled_step(storage
         assert list(steps) == [0, 7, 14, 21, 28] and planes.shape == (5, ny, nx, 4)
         zz = nz // 2 if z < 0 else z
         L = K.run_oracle(c, 0)
-        tol = {"f64": 1e-12, "f32": 1e-5}[storage]
+        # the planes are FP32: FP64 storage is held to FP32 rounding
+        tol = {"f64": 1e-6, "f32": 1e-5}[storage]
         for k, t in enumerate(steps):
             L.step(int(t) - L.t)
             rho, u = L.macros()
