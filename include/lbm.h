@@ -117,7 +117,10 @@ typedef struct {
      * omega_bulk = 1) some of these rates leave (0, 2). */
     int32_t param4;         /* 1: the parametrisation above (default 0)          */
     double limiter;         /* its limiter lambda (default 0.01)                 */
-    int32_t reserved[2];
+    int32_t xface_edge;     /* 1: the inlet/outlet cells go through the boundary-
+                               cell records instead of the bulk kernel's face
+                               warps (pays on short rows; batch members always) */
+    int32_t reserved[1];
 } lbm_params;
 
 /* Fill *p with the defaults listed above (re = 1000, u_in = 0.05, l_ref = 1,

@@ -1348,6 +1348,199 @@ __global__ void __launch_bounds__(TPB) k_dftx_inv_tc(const float2 *It, float *ou
     }
 }
 
+// Fourier-layer output in one pass, for BF16 activations, nx = 128, 32
+// retained x modes and width 32.  For a line (b, z, y) of 128 cells a warp
+// computes, for all 32 output channels o,
+//   pre[o][x] = sum_j It[(b, o, z, y)][j] T[j][x]  +  sum_c W[o][c] v[c][x]  +  bias[o]
+//   out[o][x] = act(pre[o][x])
+// i.e. the inverse x stage of the spectral branch (the contraction of
+// k_dftx_inv_tc: It rows and the twiddle table as BF16 hi + lo pairs, three
+// products per tile) and the pointwise path (W as hi + lo pairs against the
+// exact BF16 inputs, two products per tile) accumulated in the same m16n8
+// fragments, so that the spectral branch never goes through memory.  The
+// inputs v of the line (32 channels x 128 cells, 8 KB) are staged in shared
+// memory with 16-byte loads and read back as B fragments by
+// ldmatrix.trans; rows are 256 bytes and their 16-byte chunks are XOR-
+// swizzled by (row % 8) so that those reads hit distinct banks.  Outputs go
+// through a 16-row staging tile, written row by row with 16-byte stores.
+// A warp takes the 16 output channels of one m-tile at a time (64 FP32
+// accumulators).
+constexpr int FUSE_WARPS = 4;
+constexpr int FUSE_C = 32;
+constexpr size_t FUSE_SMEM = sizeof(uint2) * 2 * 4 * 16 * 32     // twiddle fragments, hi and lo
+                           + sizeof(uint4) * 2 * 2 * 2 * 32      // W fragments [hi/lo][mt][ks][lane]
+                           + sizeof(float) * FUSE_C              // bias
+                           + (size_t)FUSE_WARPS * (FUSE_C * TCX_NX * 2 + 16 * TCX_NX * 2);   // v and out tiles
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void ldsm_x4_trans(uint32_t addr, uint32_t &r0, uint32_t &r1, uint32_t &r2, uint32_t &r3)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0, %1, %2, %3}, [%4];\n"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(addr));
+}
+
+// byte offset of element (row, x) in a 256-byte-row tile with swizzled chunks
+__device__ __forceinline__ int swz(int row, int x) { return row * 256 + ((((x >> 3) ^ (row & 7)) & 15) << 4) + (x & 7) * 2; }
+
+__global__ void __launch_bounds__(FUSE_WARPS * 32, 2) k_layer_tc(const float2 *It, const __nv_bfloat16 *v,
+                                                               const float *W, const float *bias, const float2 *twx,
+                                                               __nv_bfloat16 *pre, __nv_bfloat16 *out, int act,
+                                                               int64_t lines_per_sample, int64_t N, int B)
+{
+    extern __shared__ __align__(16) unsigned char fsm[];
+    uint2 *bt = reinterpret_cast<uint2 *>(fsm);                          // [2][4 * 16 * 32]
+    uint4 *wa = reinterpret_cast<uint4 *>(fsm + sizeof(uint2) * 2 * 4 * 16 * 32);   // [2][2][2][32]
+    float *sb = reinterpret_cast<float *>(reinterpret_cast<unsigned char *>(wa) + sizeof(uint4) * 2 * 2 * 2 * 32);
+    unsigned char *tiles = reinterpret_cast<unsigned char *>(sb + FUSE_C);
+    constexpr int BT = 4 * 16 * 32;
+    for (int idx = threadIdx.x; idx < BT; idx += blockDim.x) {
+        const int st = idx >> 9, nt = (idx >> 5) & 15, l = idx & 31;
+        const int xs = 8 * nt + (l >> 2), c = l & 3;
+        __nv_bfloat16 h[4], o[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int k = 16 * c + 4 * st + e;
+            const float2 t = twx[xs * TCX_KX + (k >> 1)];
+            split_bf16((k & 1) ? t.y : t.x, h[e], o[e]);
+        }
+        bt[idx] = make_uint2(pack_bf16_pair(h[0], h[1]), pack_bf16_pair(h[2], h[3]));
+        bt[BT + idx] = make_uint2(pack_bf16_pair(o[0], o[1]), pack_bf16_pair(o[2], o[3]));
+    }
+    for (int idx = threadIdx.x; idx < 2 * 2 * 32; idx += blockDim.x) {
+        const int mt = idx >> 6, ks = (idx >> 5) & 1, l = idx & 31, g = l >> 2, c = l & 3;
+        const int r0 = 16 * mt + g, r1 = r0 + 8;
+        const int k0 = 16 * ks + 2 * c, k2 = k0 + 8;
+        const float w[8] = {W[r0 * FUSE_C + k0], W[r0 * FUSE_C + k0 + 1], W[r1 * FUSE_C + k0], W[r1 * FUSE_C + k0 + 1],
+                            W[r0 * FUSE_C + k2], W[r0 * FUSE_C + k2 + 1], W[r1 * FUSE_C + k2], W[r1 * FUSE_C + k2 + 1]};
+        __nv_bfloat16 h[8], o[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) split_bf16(w[e], h[e], o[e]);
+        wa[idx] = make_uint4(pack_bf16_pair(h[0], h[1]), pack_bf16_pair(h[2], h[3]), pack_bf16_pair(h[4], h[5]),
+                             pack_bf16_pair(h[6], h[7]));
+        wa[2 * 2 * 32 + idx] = make_uint4(pack_bf16_pair(o[0], o[1]), pack_bf16_pair(o[2], o[3]),
+                                          pack_bf16_pair(o[4], o[5]), pack_bf16_pair(o[6], o[7]));
+    }
+    for (int k = threadIdx.x; k < FUSE_C; k += blockDim.x) sb[k] = bias[k];
+    __syncthreads();
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, c = lane & 3;
+    unsigned char *vt = tiles + (size_t)warp * (FUSE_C * TCX_NX * 2 + 16 * TCX_NX * 2);
+    unsigned char *ot = vt + FUSE_C * TCX_NX * 2;
+    const int64_t lines = (int64_t)B * lines_per_sample;
+    for (int64_t line = (int64_t)blockIdx.x * FUSE_WARPS + warp; line < lines; line += (int64_t)gridDim.x * FUSE_WARPS) {
+        const int64_t b = line / lines_per_sample, zy = line - b * lines_per_sample;
+        const int64_t off = zy * TCX_NX;                        // cell of x = 0 within a channel plane
+        // stage v[b][0..31][line][0..127] (16 bytes per lane and step)
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            const int row = 2 * i + (lane >> 4), ch = lane & 15;
+            const uint4 q = *reinterpret_cast<const uint4 *>(v + ((b * FUSE_C + row) * N + off) + ch * 8);
+            *reinterpret_cast<uint4 *>(vt + swz(row, ch * 8)) = q;
+        }
+        __syncwarp();
+#pragma unroll 1
+        for (int mt = 0; mt < 2; ++mt) {
+            float acc[16][4];
+#pragma unroll
+            for (int nt = 0; nt < 16; ++nt)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) acc[nt][e] = 0.f;
+            // pointwise path: W (hi + lo) times the exact BF16 inputs
+#pragma unroll
+            for (int ks = 0; ks < 2; ++ks) {
+                const uint4 ah = wa[(mt * 2 + ks) * 32 + lane], al = wa[2 * 2 * 32 + (mt * 2 + ks) * 32 + lane];
+                const int row = 16 * ks + (lane & 7) + 8 * ((lane >> 3) & 1);
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    uint32_t b0, b1, b2, b3;
+                    ldsm_x4_trans(smem_u32(vt + swz(row, 8 * (2 * j + (lane >> 4)))), b0, b1, b2, b3);
+                    mma_bf16(acc[2 * j], ah.x, ah.y, ah.z, ah.w, make_uint2(b0, b1));
+                    mma_bf16(acc[2 * j], al.x, al.y, al.z, al.w, make_uint2(b0, b1));
+                    mma_bf16(acc[2 * j + 1], ah.x, ah.y, ah.z, ah.w, make_uint2(b2, b3));
+                    mma_bf16(acc[2 * j + 1], al.x, al.y, al.z, al.w, make_uint2(b2, b3));
+                }
+            }
+            // spectral branch: inverse x transform of the rows of channels
+            // 16 mt + g and 16 mt + g + 8
+            const int64_t ra = (b * FUSE_C + 16 * mt + g) * lines_per_sample + zy;
+            const int64_t rb = ra + 8 * lines_per_sample;
+            const float4 *pa = reinterpret_cast<const float4 *>(It + ra * TCX_KX) + 4 * c;
+            const float4 *pb = reinterpret_cast<const float4 *>(It + rb * TCX_KX) + 4 * c;
+            float4 va[4], vb[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                va[q] = pa[q];
+                vb[q] = pb[q];
+            }
+#pragma unroll
+            for (int st = 0; st < 4; ++st) {
+                __nv_bfloat16 ah[8], al[8];
+                split_bf16(va[st].x, ah[0], al[0]); split_bf16(va[st].y, ah[1], al[1]);
+                split_bf16(va[st].z, ah[2], al[2]); split_bf16(va[st].w, ah[3], al[3]);
+                split_bf16(vb[st].x, ah[4], al[4]); split_bf16(vb[st].y, ah[5], al[5]);
+                split_bf16(vb[st].z, ah[6], al[6]); split_bf16(vb[st].w, ah[7], al[7]);
+                const uint32_t h0 = pack_bf16_pair(ah[0], ah[1]), h2 = pack_bf16_pair(ah[2], ah[3]);
+                const uint32_t h1 = pack_bf16_pair(ah[4], ah[5]), h3 = pack_bf16_pair(ah[6], ah[7]);
+                const uint32_t l0 = pack_bf16_pair(al[0], al[1]), l2 = pack_bf16_pair(al[2], al[3]);
+                const uint32_t l1 = pack_bf16_pair(al[4], al[5]), l3 = pack_bf16_pair(al[6], al[7]);
+#pragma unroll
+                for (int nt = 0; nt < 16; ++nt) {
+                    const uint2 bh = bt[(st * 16 + nt) * 32 + lane];
+                    const uint2 bl = bt[BT + (st * 16 + nt) * 32 + lane];
+                    mma_bf16(acc[nt], h0, h1, h2, h3, bh);
+                    mma_bf16(acc[nt], h0, h1, h2, h3, bl);
+                    mma_bf16(acc[nt], l0, l1, l2, l3, bh);
+                }
+            }
+            // epilogue: element e of n-tile nt is output 16 mt + g + 8 (e >> 1)
+            // (local row g + 8 (e >> 1)) at x = 8 nt + 2c + (e & 1)
+#pragma unroll
+            for (int nt = 0; nt < 16; ++nt)
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int r = g + 8 * h;
+                    const float bb = sb[16 * mt + r];
+                    acc[nt][2 * h] += bb;
+                    acc[nt][2 * h + 1] += bb;
+                    float k0, k1;
+                    const float y0 = act_fwd<true>(act, 0.f, acc[nt][2 * h], k0);
+                    const float y1 = act_fwd<true>(act, 0.f, acc[nt][2 * h + 1], k1);
+                    *reinterpret_cast<__nv_bfloat162 *>(ot + swz(r, 8 * nt + 2 * c)) = __floats2bfloat162_rn(y0, y1);
+                }
+            __syncwarp();
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int row = 2 * i + (lane >> 4), ch = lane & 15;
+                *reinterpret_cast<uint4 *>(out + ((b * FUSE_C + 16 * mt + row) * N + off) + ch * 8) =
+                    *reinterpret_cast<const uint4 *>(ot + swz(row, ch * 8));
+            }
+            __syncwarp();
+            if (pre) {
+#pragma unroll
+                for (int nt = 0; nt < 16; ++nt)
+#pragma unroll
+                    for (int h = 0; h < 2; ++h)
+                        *reinterpret_cast<__nv_bfloat162 *>(ot + swz(g + 8 * h, 8 * nt + 2 * c)) =
+                            __floats2bfloat162_rn(acc[nt][2 * h], acc[nt][2 * h + 1]);
+                __syncwarp();
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const int row = 2 * i + (lane >> 4), ch = lane & 15;
+                    *reinterpret_cast<uint4 *>(pre + ((b * FUSE_C + 16 * mt + row) * N + off) + ch * 8) =
+                        *reinterpret_cast<const uint4 *>(ot + swz(row, ch * 8));
+                }
+                __syncwarp();
+            }
+        }
+        __syncwarp();
+    }
+}
+
 // Inference projection y = Q2 sin(omega0 (Q1 v + b1)) + b2 on tensor cores, for
 // BF16 activations with 32 channels, 128 hidden units and co <= 8 outputs:
 // a warp takes 16 cells of one sample per pass.  First product: cells x
@@ -1762,7 +1955,8 @@ bool set_smem_limits(size_t bytes)
            cudaFuncSetAttribute(k_outer_async<float, 1>, a, b) == cudaSuccess &&
            cudaFuncSetAttribute(k_outer_async<float, 2>, a, b) == cudaSuccess &&
            cudaFuncSetAttribute(k_outer_async<__nv_bfloat16, 1>, a, b) == cudaSuccess &&
-           cudaFuncSetAttribute(k_outer_async<__nv_bfloat16, 2>, a, b) == cudaSuccess;
+           cudaFuncSetAttribute(k_outer_async<__nv_bfloat16, 2>, a, b) == cudaSuccess &&
+           cudaFuncSetAttribute(k_layer_tc, a, (int)FUSE_SMEM) == cudaSuccess;
 }
 
 bool on_device(const void *p)
@@ -2157,8 +2351,9 @@ void dft_fwd(fno_ctx *f, const T *x, float2 *S, const float *scale, int B)
 
 // inverse of S (times scale[kz]) into out [B][W][N]: store or add; then, if pre
 // is given, multiply by gelu'(pre)
-template <class TP>
-void dft_inv(fno_ctx *f, const float2 *S, float *out, const float *scale, int accumulate, const TP *pre, int B)
+// z and y stages of the inverse of S (times scale[kz]) into stA: rows
+// [B][W][z][y] of Kx complex x modes
+void dft_inv_zy(fno_ctx *f, const float2 *S, const float *scale, int B)
 {
     const Dims d = dims(f, B);
     k_dftz_inv<<<grid_for(d.BC * d.Ky * d.Kx), TPB, 0, f->s>>>(S, f->stB, f->twz, scale, d);
@@ -2166,6 +2361,13 @@ void dft_inv(fno_ctx *f, const float2 *S, float *out, const float *scale, int ac
     const int SB = dfty_inv_slabs(d);
     k_dfty_inv<<<(int)std::min<int64_t>((Sl + SB - 1) / SB, gb300::sm_count() * 8), TPB, smem_dfty_inv(d), f->s>>>(f->stB, f->stA,
                                                                                                   f->twy, d, Sl, SB);
+}
+
+template <class TP>
+void dft_inv(fno_ctx *f, const float2 *S, float *out, const float *scale, int accumulate, const TP *pre, int B)
+{
+    const Dims d = dims(f, B);
+    dft_inv_zy(f, S, scale, B);
     const int64_t R = d.BC * d.nz * d.ny;
     if (std::is_same<TP, __nv_bfloat16>::value && d.nx == TCX_NX && d.Kx == TCX_KX &&
         (reinterpret_cast<uintptr_t>(out) & 7u) == 0) {
@@ -2204,10 +2406,24 @@ lbm_status forward_impl(fno_ctx *f, const float *x, int B, bool keep = true)
               f->a, false, ACT_GELU, B);
     pw_fwd<T>(f, static_cast<T *>(f->a), c.lift_hidden, W, f->oP2_w, f->oP2_b, nullptr, nullptr, f->v[0], false,
               ACT_NONE, B);
+    // the fused Fourier-layer output (inverse x stage and pointwise path in
+    // one tensor-core pass) where its shape applies
+    const bool fuse = std::is_same<T, __nv_bfloat16>::value && c.nx == TCX_NX && f->Kx == TCX_KX && W == FUSE_C;
     for (int l = 0; l < c.layers; ++l) {
         T *vin = static_cast<T *>(f->v[l]);
         dft_fwd<T>(f, vin, f->Vh[l], f->scale_one, B);
         contract(f, f->Vh[l], f->oR[l], f->G, false, B);
+        if (fuse) {
+            dft_inv_zy(f, f->G, f->scale_inv, B);
+            const int64_t lps = (int64_t)c.ny * c.nz;
+            const int blocks = (int)std::min<int64_t>(((int64_t)B * lps + FUSE_WARPS - 1) / FUSE_WARPS,
+                                                      (int64_t)gb300::sm_count() * 2);
+            k_layer_tc<<<blocks, FUSE_WARPS * 32, FUSE_SMEM, f->s>>>(
+                f->stA, reinterpret_cast<const __nv_bfloat16 *>(vin), f->params + f->oW_w[l], f->params + f->oW_b[l],
+                f->twx, keep ? reinterpret_cast<__nv_bfloat16 *>(f->pre[l]) : nullptr,
+                reinterpret_cast<__nv_bfloat16 *>(f->v[l + 1]), l < c.layers - 1 ? ACT_GELU : ACT_NONE, lps, f->N, B);
+            continue;
+        }
         dft_inv<T>(f, f->G, f->spec, f->scale_inv, 0, nullptr, B);
         pw_fwd<T>(f, vin, W, W, f->oW_w[l], f->oW_b[l], f->spec, keep ? static_cast<T *>(f->pre[l]) : nullptr,
                   f->v[l + 1], false,

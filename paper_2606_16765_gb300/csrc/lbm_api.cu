@@ -182,6 +182,7 @@ struct lbm_ctx {
         a.u_in = p.u_in; a.rho_in = p.rho_in; a.rho_out = p.rho_out;
         a.w1f = (float)a.w1; a.w2f = (float)a.w2; a.w3f = (float)a.w3;
         a.param4 = p.param4 ? 1 : 0;
+        a.xface_bulk = p.xface_edge ? 0 : 1;
         if (a.param4) param4_factors(a.w1, a.w2, p.limiter, a.p4);
         for (int k = 0; k < 6; ++k) a.p4f[k] = (float)a.p4[k];
         const int64_t es = (int64_t)storage_bytes(p.storage);
@@ -260,6 +261,7 @@ static std::string validate(const lbm_grid *g, const lbm_params *p)
     if (p->block_y < 0 || (p->block_x ? p->block_x : 128) * (p->block_y ? p->block_y : 1) > 256)
         return "block_x * block_y must be <= 256";
     if (p->param4 != 0 && p->param4 != 1) return "param4 must be 0 or 1";
+    if (p->xface_edge != 0 && p->xface_edge != 1) return "xface_edge must be 0 or 1";
     if (p->param4) {
         if (!(p->limiter > 0.0)) return "param4 needs limiter > 0";
         const double w1 = p->omega1 > 0 ? p->omega1 : 1.0 / (3.0 * p->u_in * p->l_ref / p->re + 0.5);
@@ -353,8 +355,9 @@ static lbm_status create_impl(const lbm_grid *g, const uint8_t *mask, const lbm_
             return bail(LBM_ERR_CUDA);
         }
     }
-    launch_flags(dmask, ctx->at<uint8_t>(L.flags), g->nx, g->ny, g->nz, p->face_x_lo != LBM_FACE_PERIODIC,
-                 p->face_x_hi != LBM_FACE_PERIODIC, p->face_y == LBM_FACE_WALL, p->face_z == LBM_FACE_WALL, s);
+    launch_flags(dmask, ctx->at<uint8_t>(L.flags), g->nx, g->ny, g->nz,
+                 p->face_x_lo != LBM_FACE_PERIODIC && !p->xface_edge, p->face_x_hi != LBM_FACE_PERIODIC && !p->xface_edge,
+                 p->face_y == LBM_FACE_WALL, p->face_z == LBM_FACE_WALL, s);
     std::vector<uint8_t> hflags(n);
     if (cudaMemcpyAsync(hflags.data(), ctx->at<uint8_t>(L.flags), n, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess) {
@@ -1404,7 +1407,12 @@ extern "C" lbm_status lbm_batch_create(int32_t n, const lbm_grid *grids, const u
     b->block_y = p0.block_y ? p0.block_y : 1;
     for (int g = 0; g < n; ++g) {
         lbm_ctx *c = nullptr;
-        lbm_status st = lbm_create(&grids[g], masks ? masks[g] : nullptr, &params[g], cuda_stream, &c);
+        // members put their inlet/outlet cells into the boundary-cell records:
+        // on rows of 128-256 cells the bulk kernel's face warps would be a
+        // quarter to a half of its warps
+        lbm_params pm = params[g];
+        pm.xface_edge = 1;
+        lbm_status st = lbm_create(&grids[g], masks ? masks[g] : nullptr, &pm, cuda_stream, &c);
         if (st != LBM_OK) {
             const std::string m = "member " + std::to_string(g) + ": " + g_err;
             lbm_batch_destroy(b);

@@ -139,6 +139,7 @@ struct StepArgs {
     int param4;
     double p4[6];
     float p4f[6];
+    int xface_bulk;         // 1: the bulk kernel updates the inlet/outlet cells in its face warps
     int face_x_lo, face_x_hi, face_y, face_z;
     double u_in, rho_in, rho_out;
     // FP32 copies of the rates and boundary constants, so that FP32 kernels

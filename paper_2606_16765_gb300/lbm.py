@@ -39,7 +39,7 @@ class lbm_params(C.Structure):
         ("snap_halfres", C.c_int32), ("force_every", C.c_int32),
         ("force_capacity", C.c_int64),
         ("block_x", C.c_int32), ("block_y", C.c_int32), ("stats", C.c_int32),
-        ("param4", C.c_int32), ("limiter", C.c_double), ("reserved", C.c_int32 * 2),
+        ("param4", C.c_int32), ("limiter", C.c_double), ("xface_edge", C.c_int32), ("reserved", C.c_int32 * 1),
     ]
 
 

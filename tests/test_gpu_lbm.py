@@ -668,3 +668,29 @@ def test_monitor_plane_records_the_centre_plane_before_each_sampled_step(storage
             ref[c["mask"][zz] != 0] = 0.0
             err = np.abs(planes[k] - ref).max() / np.abs(ref[..., :3]).max()
             assert err <= tol, (z, t, err)
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+def test_inlet_outlet_cells_through_the_boundary_records(storage):
+    """xface_edge = 1 (the batch members' setting): the inlet and outlet cells
+    go through the boundary-cell records instead of the bulk kernel's face
+    warps.  Same arithmetic per cell: the populations equal the default
+    path's bitwise, and the oracle's within the storage's tolerance."""
+    d = I.sphere_channel_64()
+    w1 = O.omega_from_re(d["re"], d["u_in"], d["l_ref"])
+    c = K.case(d["grid"], d["mask"], omega1=w1, u_in=d["u_in"], faces=("inlet", "outflow", "wall", "wall"),
+               noise=(71, 1e-3))
+    L = K.run_oracle(c, 40)
+    rho_r, u_r = L.macros()
+    a = K.make_solver(c, storage, xface_edge=1)
+    b = K.make_solver(c, storage)
+    a.step(40)
+    b.step(40)
+    a.sync()
+    b.sync()
+    assert a.info().edge_cells > b.info().edge_cells
+    assert np.array_equal(a.pdfs(), b.pdfs())
+    rho, u = a.macros()
+    fl = c["mask"] == 0
+    tol = {"f64": 1e-12, "f32": 1e-5}[storage]
+    assert K.rel_u_err(u, u_r, fl) <= tol and K.rho_err(rho, rho_r, fl) <= tol
