@@ -1348,6 +1348,82 @@ __global__ void __launch_bounds__(TPB) k_dftx_inv_tc(const float2 *It, float *ou
     }
 }
 
+// Complex DFT along the rows of a slab on tensor cores, for the y stages of
+// the transforms in the BF16-activation configuration:
+//   Y[s][i][jx] = sum_j W(i, j) X[s][j][jx],   W(i, j) = tw[j * Ky + i]        (forward: i = ky, j = y)
+//                                                W(i, j) = conj(tw[i * Ky + j])  (inverse: i = y, j = ky)
+// as the real product [Re Y; Im Y] = [[Wr, -Wi], [Wi, Wr]] [Re X; Im X]
+// with m16n8k16 BF16 operands and FP32 accumulation.  An m-tile is eight
+// outputs i: rows g take the real part of output 8 mt + g, rows g + 8 its
+// imaginary part.  A k-step is eight inputs j, the contraction index
+// running (j, re), (j, im) so that a lane's B register pair is one float2
+// X[s][j][jx] (j = 8 ks + t and 8 ks + t + 4, jx = 8 nt + g).  Both operands
+// enter as BF16 hi + lo pairs (three products per tile, about 2^-16 relative
+// error, as in the x stages).  One warp per slab; the twiddle fragments of
+// every (m-tile, k-step) are built once per block in shared memory.
+template <int NT>
+__global__ void __launch_bounds__(TPB) k_cdft_tc(const float2 *X, float2 *Y, const float2 *tw, int Ky, int inv,
+                                                 int I, int J, int64_t S)
+{
+    extern __shared__ uint4 af[];                        // [hi, lo][MT * KS * 32]
+    constexpr int KX = NT * 8;
+    const int MT = I / 8, KS = J / 8, nf = MT * KS * 32;
+    for (int idx = threadIdx.x; idx < nf; idx += blockDim.x) {
+        const int mt = idx / (KS * 32), ks = (idx / 32) % KS, l = idx & 31, g = l >> 2, t = l & 3;
+        const int i = 8 * mt + g;
+        float2 w[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int j = 8 * ks + t + 4 * h;
+            const float2 v = inv ? tw[i * Ky + j] : tw[j * Ky + i];
+            w[h] = inv ? make_float2(v.x, -v.y) : v;
+        }
+        // a0 = (Wr, -Wi), a1 = (Wi, Wr) of j = 8 ks + t; a2, a3 the same of j + 4
+        const float e[8] = {w[0].x, -w[0].y, w[0].y, w[0].x, w[1].x, -w[1].y, w[1].y, w[1].x};
+        __nv_bfloat16 hh[8], ll[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) split_bf16(e[q], hh[q], ll[q]);
+        af[idx] = make_uint4(pack_bf16_pair(hh[0], hh[1]), pack_bf16_pair(hh[2], hh[3]), pack_bf16_pair(hh[4], hh[5]),
+                             pack_bf16_pair(hh[6], hh[7]));
+        af[nf + idx] = make_uint4(pack_bf16_pair(ll[0], ll[1]), pack_bf16_pair(ll[2], ll[3]),
+                                  pack_bf16_pair(ll[4], ll[5]), pack_bf16_pair(ll[6], ll[7]));
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    for (int64_t s = (int64_t)blockIdx.x * (TPB / 32) + warp; s < S; s += (int64_t)gridDim.x * (TPB / 32)) {
+        const float2 *xs = X + s * J * KX;
+        float2 *ys = Y + s * I * KX;
+        for (int mt = 0; mt < MT; ++mt) {
+            float acc[NT][4];
+#pragma unroll
+            for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc[nt][q] = 0.f;
+            for (int ks = 0; ks < KS; ++ks) {
+                const uint4 ah = af[(mt * KS + ks) * 32 + lane], al = af[nf + (mt * KS + ks) * 32 + lane];
+#pragma unroll
+                for (int nt = 0; nt < NT; ++nt) {
+                    const float2 x0 = xs[(8 * ks + t) * KX + 8 * nt + g];
+                    const float2 x1 = xs[(8 * ks + t + 4) * KX + 8 * nt + g];
+                    __nv_bfloat16 h0, l0, h1, l1, h2, l2, h3, l3;
+                    split_bf16(x0.x, h0, l0); split_bf16(x0.y, h1, l1);
+                    split_bf16(x1.x, h2, l2); split_bf16(x1.y, h3, l3);
+                    const uint2 bh = make_uint2(pack_bf16_pair(h0, h1), pack_bf16_pair(h2, h3));
+                    const uint2 bl = make_uint2(pack_bf16_pair(l0, l1), pack_bf16_pair(l2, l3));
+                    mma_bf16(acc[nt], ah.x, ah.y, ah.z, ah.w, bh);
+                    mma_bf16(acc[nt], ah.x, ah.y, ah.z, ah.w, bl);
+                    mma_bf16(acc[nt], al.x, al.y, al.z, al.w, bh);
+                }
+            }
+            // d0, d1: Re of output 8 mt + g at jx = 8 nt + 2t, +1; d2, d3: Im
+#pragma unroll
+            for (int nt = 0; nt < NT; ++nt)
+                *reinterpret_cast<float4 *>(ys + (int64_t)(8 * mt + g) * KX + 8 * nt + 2 * t) =
+                    make_float4(acc[nt][0], acc[nt][2], acc[nt][1], acc[nt][3]);
+        }
+    }
+}
+
 // Fourier-layer output in one pass, for BF16 activations, nx = 128, 32
 // retained x modes and width 32.  For a line (b, z, y) of 128 cells a warp
 // computes, for all 32 output channels o,
@@ -2319,6 +2395,14 @@ void outer(fno_ctx *f, const float *g, int co, const T *x, int ci, int64_t oW, i
     }
 }
 
+// the y stages on tensor cores: BF16-activation configuration, whole
+// m-tiles and k-steps of eight modes or rows, 32 x modes
+bool ydft_tc(const fno_ctx *f, const Dims &d)
+{
+    return f->c.act_bf16 && d.ny % 8 == 0 && d.Ky % 8 == 0 && d.Kx == 32;
+}
+size_t smem_cdft(const Dims &d) { return 2 * sizeof(uint4) * (size_t)(d.Ky / 8) * (d.ny / 8) * 32; }
+
 Dims dims(const fno_ctx *f, int B)
 {
     return Dims{f->c.nx, f->c.ny, f->c.nz, f->Kx, f->Ky, f->Kz, (int64_t)B * f->c.width};
@@ -2343,9 +2427,14 @@ void dft_fwd(fno_ctx *f, const T *x, float2 *S, const float *scale, int B)
                         f->s>>>(x, f->stA, f->twx, d, R);
     }
     const int64_t Sl = d.BC * d.nz;
-    const int SB = dfty_fwd_slabs(d);
-    k_dfty_fwd<<<(int)std::min<int64_t>((Sl + SB - 1) / SB, gb300::sm_count() * 8), TPB, smem_dfty_fwd(d), f->s>>>(f->stA, f->stB,
-                                                                                                  f->twy, d, Sl, SB);
+    if (ydft_tc(f, d)) {
+        k_cdft_tc<4><<<(int)std::min<int64_t>((Sl + TPB / 32 - 1) / (TPB / 32), gb300::sm_count() * 8), TPB,
+                       smem_cdft(d), f->s>>>(f->stA, f->stB, f->twy, d.Ky, 0, d.Ky, d.ny, Sl);
+    } else {
+        const int SB = dfty_fwd_slabs(d);
+        k_dfty_fwd<<<(int)std::min<int64_t>((Sl + SB - 1) / SB, gb300::sm_count() * 8), TPB, smem_dfty_fwd(d), f->s>>>(
+            f->stA, f->stB, f->twy, d, Sl, SB);
+    }
     k_dftz_fwd<<<grid_for(d.BC * d.Ky * d.Kx), TPB, 0, f->s>>>(f->stB, S, f->twz, scale, d);
 }
 
@@ -2358,9 +2447,14 @@ void dft_inv_zy(fno_ctx *f, const float2 *S, const float *scale, int B)
     const Dims d = dims(f, B);
     k_dftz_inv<<<grid_for(d.BC * d.Ky * d.Kx), TPB, 0, f->s>>>(S, f->stB, f->twz, scale, d);
     const int64_t Sl = d.BC * d.nz;
-    const int SB = dfty_inv_slabs(d);
-    k_dfty_inv<<<(int)std::min<int64_t>((Sl + SB - 1) / SB, gb300::sm_count() * 8), TPB, smem_dfty_inv(d), f->s>>>(f->stB, f->stA,
-                                                                                                  f->twy, d, Sl, SB);
+    if (ydft_tc(f, d)) {
+        k_cdft_tc<4><<<(int)std::min<int64_t>((Sl + TPB / 32 - 1) / (TPB / 32), gb300::sm_count() * 8), TPB,
+                       smem_cdft(d), f->s>>>(f->stB, f->stA, f->twy, d.Ky, 1, d.ny, d.Ky, Sl);
+    } else {
+        const int SB = dfty_inv_slabs(d);
+        k_dfty_inv<<<(int)std::min<int64_t>((Sl + SB - 1) / SB, gb300::sm_count() * 8), TPB, smem_dfty_inv(d), f->s>>>(
+            f->stB, f->stA, f->twy, d, Sl, SB);
+    }
 }
 
 template <class TP>
