@@ -1348,6 +1348,88 @@ __global__ void __launch_bounds__(TPB) k_dftx_inv_tc(const float2 *It, float *ou
     }
 }
 
+// Weight and bias gradients gW[o][i] += sum over cells of g[b][o][cell]
+// x[b][i][cell] and gb[o] += sum g, on tensor cores, for BF16 inputs with
+// ci = 32 and co a multiple of 32: D = A B with the cells as the contraction
+// index, A = g (FP32, entering as BF16 hi + lo pairs, two products per
+// tile), B = x (BF16, exact); a fifth n-tile whose first column is 1 gives
+// the bias gradient.  Grid x: chunks of OUTER_CHUNK cells; grid y: groups of
+// 32 output rows (two m-tiles).  A warp takes every eighth 16-cell k-step of
+// its block's chunk (a k-step never straddles samples: N % 16 == 0); the
+// block adds its warps' fragments in shared memory, then adds the block's
+// sums to gW and gb atomically, as the SIMT reduction does.
+__global__ void __launch_bounds__(TPB) k_outer_tc(const float *g, int co, const __nv_bfloat16 *x, float *gW, float *gb,
+                                                  int64_t N, int B)
+{
+    __shared__ float red[32][33];
+    for (int k = threadIdx.x; k < 32 * 33; k += blockDim.x) (&red[0][0])[k] = 0.f;
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, gq = lane >> 2, t = lane & 3;
+    const int o0 = blockIdx.y * 32;
+    float acc[2][5][4];
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < 5; ++nt)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) acc[mt][nt][e] = 0.f;
+    const uint32_t onev = gq == 0 ? 0x3F803F80u : 0u;                 // bf16 (1, 1) in column 0
+    const uint2 bones = make_uint2(onev, onev);
+    const int64_t total = (int64_t)B * N;
+    const int64_t c0 = (int64_t)blockIdx.x * OUTER_CHUNK;
+    const int64_t c1 = c0 + OUTER_CHUNK < total ? c0 + OUTER_CHUNK : total;
+    for (int64_t k0 = c0 + 16 * warp; k0 < c1; k0 += 16 * (TPB / 32)) {
+        const int64_t bb = k0 / N, n0 = k0 - bb * N;
+        const float *gp = g + (bb * co + o0) * N + n0 + 2 * t;
+        const __nv_bfloat16 *xp = x + (bb * 32 + gq) * N + n0 + 2 * t;
+        uint2 bx[4];
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt) {
+            const __nv_bfloat16 *q = xp + (int64_t)(8 * nt) * N;
+            bx[nt] = make_uint2(*reinterpret_cast<const uint32_t *>(q), *reinterpret_cast<const uint32_t *>(q + 8));
+        }
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt) {
+            const float *r0 = gp + (int64_t)(16 * mt + gq) * N, *r1 = r0 + 8 * N;
+            const float2 p00 = *reinterpret_cast<const float2 *>(r0), p10 = *reinterpret_cast<const float2 *>(r1);
+            const float2 p01 = *reinterpret_cast<const float2 *>(r0 + 8), p11 = *reinterpret_cast<const float2 *>(r1 + 8);
+            __nv_bfloat16 h[8], l[8];
+            split_bf16(p00.x, h[0], l[0]); split_bf16(p00.y, h[1], l[1]);
+            split_bf16(p10.x, h[2], l[2]); split_bf16(p10.y, h[3], l[3]);
+            split_bf16(p01.x, h[4], l[4]); split_bf16(p01.y, h[5], l[5]);
+            split_bf16(p11.x, h[6], l[6]); split_bf16(p11.y, h[7], l[7]);
+            const uint32_t a0 = pack_bf16_pair(h[0], h[1]), a1 = pack_bf16_pair(h[2], h[3]);
+            const uint32_t a2 = pack_bf16_pair(h[4], h[5]), a3 = pack_bf16_pair(h[6], h[7]);
+            const uint32_t c0l = pack_bf16_pair(l[0], l[1]), c1l = pack_bf16_pair(l[2], l[3]);
+            const uint32_t c2l = pack_bf16_pair(l[4], l[5]), c3l = pack_bf16_pair(l[6], l[7]);
+#pragma unroll
+            for (int nt = 0; nt < 4; ++nt) {
+                mma_bf16(acc[mt][nt], a0, a1, a2, a3, bx[nt]);
+                mma_bf16(acc[mt][nt], c0l, c1l, c2l, c3l, bx[nt]);
+            }
+            mma_bf16(acc[mt][4], a0, a1, a2, a3, bones);
+            mma_bf16(acc[mt][4], c0l, c1l, c2l, c3l, bones);
+        }
+    }
+    // fragment (mt, nt): e = 0, 1: row 16 mt + gq, column 8 nt + 2t + e;
+    // e = 2, 3: row 16 mt + gq + 8; the bias sits in column 0 of n-tile 4
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt) {
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                atomicAdd(&red[16 * mt + gq + 8 * (e >> 1)][8 * nt + 2 * t + (e & 1)], acc[mt][nt][e]);
+        if (t == 0) {
+            atomicAdd(&red[16 * mt + gq][32], acc[mt][4][0]);
+            atomicAdd(&red[16 * mt + gq + 8][32], acc[mt][4][2]);
+        }
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < 32 * 32; k += blockDim.x) atomicAdd(&gW[(int64_t)(o0 + k / 32) * 32 + k % 32], red[k / 32][k % 32]);
+    for (int k = threadIdx.x; k < 32; k += blockDim.x) atomicAdd(&gb[o0 + k], red[k][32]);
+}
+
 // Complex DFT along the rows of a slab on tensor cores, for the y stages of
 // the transforms in the BF16-activation configuration:
 //   Y[s][i][jx] = sum_j W(i, j) X[s][j][jx],   W(i, j) = tw[j * Ky + i]        (forward: i = ky, j = y)
@@ -2377,6 +2459,13 @@ void pw_bwd_input(fno_ctx *f, const float *g, int co, int ci, int64_t oW, const 
 template <class T>
 void outer(fno_ctx *f, const float *g, int co, const T *x, int ci, int64_t oW, int64_t ob, int B)
 {
+    if (std::is_same<T, __nv_bfloat16>::value && ci == 32 && co % 32 == 0 && f->N % 16 == 0) {
+        const int64_t total = (int64_t)B * f->N;
+        const dim3 grid((unsigned)((total + OUTER_CHUNK - 1) / OUTER_CHUNK), (unsigned)(co / 32));
+        k_outer_tc<<<grid, TPB, 0, f->s>>>(g, co, reinterpret_cast<const __nv_bfloat16 *>(x), f->grads + oW,
+                                           f->grads + ob, f->N, B);
+        return;
+    }
     const int64_t total = (int64_t)B * f->N;
     const int nb = (int)((total + OUTER_CHUNK - 1) / OUTER_CHUNK);
     const int units = outer_units(co, ci);
