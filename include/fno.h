@@ -53,6 +53,10 @@ typedef struct {
                                     with FP32 accumulation (needs width % 8 == 0) */
     int32_t lift_hidden;         /* hidden width of the lifting network (<= 32)    */
     float omega0;                /* SIREN frequency factor (> 0; default 30)       */
+    int32_t umma;                /* 1: the forward x stage of BF16 rows (nx = 128,
+                                    32 x modes) on tcgen05 tensor cores with TMEM
+                                    accumulators and tensor-map loads           */
+    int32_t reserved;
     uint64_t seed;               /* initial parameters                             */
 } fno_config;
 
@@ -93,6 +97,11 @@ lbm_status fno_adam_step(fno_ctx *f, float lr, float beta1, float beta2, float e
 /* fno_loss_grad followed by fno_adam_step with beta1 0.9, beta2 0.999, eps 1e-8. */
 lbm_status fno_train_step(fno_ctx *f, const float *x, const float *t, const float *m, int32_t batch, float lr,
                           double *loss);
+
+/* Wait for the context's stream and report device conditions: LBM_ERR_TIMEOUT
+ * if a bounded wait of the tcgen05 x stage gave up (its output is then not
+ * valid; the status word is cleared). */
+lbm_status fno_sync(fno_ctx *f);
 
 const char *fno_last_error(const fno_ctx *f);
 

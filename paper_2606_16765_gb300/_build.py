@@ -25,7 +25,7 @@ LIBS = {
     "liblbm.so": ["lbm_api.cu", "lbm_aux.cu", "lbm_step_f64.cu", "lbm_step_f32.cu",
                   "lbm_step_f16.cu", "lbm_step_bf16.cu", "lbm_step_f16c.cu", "lbm_noalloc.cu",
                   "resample.cu"],
-    "libfno.so": ["fno.cu"],
+    "libfno.so": ["fno.cu", "fno_umma.cu"],
 }
 
 

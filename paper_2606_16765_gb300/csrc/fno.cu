@@ -38,6 +38,7 @@
 
 #include "../../include/fno.h"
 #include "sm_count.h"
+#include "fno_umma.h"
 
 namespace {
 
@@ -2159,6 +2160,9 @@ struct fno_ctx {
     float *scale_one = nullptr, *scale_inv = nullptr;
     double *part = nullptr, *res = nullptr;
     int nparts = 0;
+    // tcgen05 forward x stage: one tensor map per layer input buffer, status word
+    std::vector<std::vector<unsigned char>> vmaps;
+    int *ustatus = nullptr;
     std::string err;
     int last_batch = 0;
 
@@ -2306,6 +2310,7 @@ extern "C" lbm_status fno_create(const fno_config *cfg, void *stream, fno_ctx **
     f->nparts = gb300::sm_count() * 4;
     chk(f->part = f->alloc<double>(2 * f->nparts));
     chk(f->res = f->alloc<double>(2));
+    chk(f->ustatus = f->alloc<int>(4));
     if (!ok) {
         g_fno_err = "device allocation failed";
         cudaGetLastError();
@@ -2356,6 +2361,25 @@ extern "C" lbm_status fno_create(const fno_config *cfg, void *stream, fno_ctx **
     ok = ok && cudaMemcpy(f->params, p0.data(), o * sizeof(float), cudaMemcpyHostToDevice) == cudaSuccess &&
          cudaMemset(f->m1, 0, o * sizeof(float)) == cudaSuccess && cudaMemset(f->m2, 0, o * sizeof(float)) == cudaSuccess &&
          cudaMemset(f->grads, 0, o * sizeof(float)) == cudaSuccess;
+    ok = ok && cudaMemset(f->ustatus, 0, 4 * sizeof(int)) == cudaSuccess;
+    if (ok && c.umma) {
+        // tensor maps of the layer inputs [max_batch * width * nz * ny rows][128]
+        if (!(c.act_bf16 && c.nx == 128 && f->Kx == 32) || !umma_set_smem()) {
+            g_fno_err = "umma needs BF16 activations, nx = 128 and 32 x modes, and a GPU that supports tcgen05";
+            fno_destroy(f);
+            return LBM_ERR_ARG;
+        }
+        const int64_t rows = (int64_t)c.max_batch * W * c.nz * c.ny;
+        for (int l = 0; l < c.layers; ++l) {
+            std::vector<unsigned char> m(128);
+            if (!umma_make_row_map(m.data(), f->v[l], rows)) {
+                g_fno_err = "tensor map encoding failed";
+                fno_destroy(f);
+                return LBM_ERR_CUDA;
+            }
+            f->vmaps.push_back(m);
+        }
+    }
     if (!ok) {
         g_fno_err = "initialisation failed";
         cudaGetLastError();
@@ -2499,7 +2523,7 @@ Dims dims(const fno_ctx *f, int B)
 
 // forward truncated DFT of [B][W][N] fields into S[k][b*W + c] times scale[kz]
 template <class T>
-void dft_fwd(fno_ctx *f, const T *x, float2 *S, const float *scale, int B)
+void dft_fwd(fno_ctx *f, const T *x, float2 *S, const float *scale, int B, int layer_map = -1)
 {
     const Dims d = dims(f, B);
     const int64_t R = d.BC * d.nz * d.ny;
@@ -2507,7 +2531,12 @@ void dft_fwd(fno_ctx *f, const T *x, float2 *S, const float *scale, int B)
     // configuration only (whose tolerance covers its 2^-16 rounding); the
     // FP32 configuration keeps the FP32 stage
     const bool tc_input = std::is_same<T, __nv_bfloat16>::value || f->c.act_bf16;
-    if (tc_input && d.nx == TCX_NX && d.Kx == TCX_KX && (reinterpret_cast<uintptr_t>(x) & 15u) == 0) {
+    if (layer_map >= 0 && layer_map < (int)f->vmaps.size() && std::is_same<T, __nv_bfloat16>::value) {
+        // BF16 layer inputs with a tensor map: tcgen05 with TMEM accumulators
+        const int64_t tiles = (R + 127) / 128;
+        const int blocks = (int)std::min<int64_t>(tiles, (int64_t)gb300::sm_count() * 2);
+        umma_dftx_fwd(f->vmaps[layer_map].data(), f->twx, f->stA, R, f->ustatus, blocks, f->s);
+    } else if (tc_input && d.nx == TCX_NX && d.Kx == TCX_KX && (reinterpret_cast<uintptr_t>(x) & 15u) == 0) {
         const int64_t warps = (R + 15) / 16;
         k_dftx_fwd_tc<T><<<(int)std::min<int64_t>((warps + TPB / 32 - 1) / (TPB / 32), gb300::sm_count() * 8), TPB, 0, f->s>>>(
             x, f->stA, f->twx, R);
@@ -2594,7 +2623,7 @@ lbm_status forward_impl(fno_ctx *f, const float *x, int B, bool keep = true)
     const bool fuse = std::is_same<T, __nv_bfloat16>::value && c.nx == TCX_NX && f->Kx == TCX_KX && W == FUSE_C;
     for (int l = 0; l < c.layers; ++l) {
         T *vin = static_cast<T *>(f->v[l]);
-        dft_fwd<T>(f, vin, f->Vh[l], f->scale_one, B);
+        dft_fwd<T>(f, vin, f->Vh[l], f->scale_one, B, c.umma ? l : -1);
         contract(f, f->Vh[l], f->oR[l], f->G, false, B);
         if (fuse) {
             dft_inv_zy(f, f->G, f->scale_inv, B);
@@ -2749,6 +2778,20 @@ extern "C" lbm_status fno_train_step(fno_ctx *f, const float *x, const float *t,
     lbm_status st = fno_loss_grad(f, x, t, m, batch, loss);
     if (st != LBM_OK) return st;
     return fno_adam_step(f, lr, 0.9f, 0.999f, 1e-8f);
+}
+
+extern "C" lbm_status fno_sync(fno_ctx *f)
+{
+    if (!f) return LBM_ERR_ARG;
+    FCK(cudaStreamSynchronize(f->s));
+    int st = 0;
+    FCK(cudaMemcpy(&st, f->ustatus, sizeof st, cudaMemcpyDeviceToHost));
+    if (st != 0) {
+        FCK(cudaMemset(f->ustatus, 0, sizeof(int)));
+        f->err = "a bounded wait of the tcgen05 x stage gave up (code " + std::to_string(st) + ")";
+        return LBM_ERR_TIMEOUT;
+    }
+    return LBM_OK;
 }
 
 extern "C" const char *fno_last_error(const fno_ctx *f) { return f ? f->err.c_str() : g_fno_err.c_str(); }

@@ -19,7 +19,8 @@ class fno_config(C.Structure):
                 ("mx", C.c_int32), ("my", C.c_int32), ("mz", C.c_int32),
                 ("layers", C.c_int32), ("hidden", C.c_int32), ("max_batch", C.c_int32),
                 ("act_bf16", C.c_int32), ("tensor_cores", C.c_int32),
-                ("lift_hidden", C.c_int32), ("omega0", C.c_float), ("seed", C.c_uint64)]
+                ("lift_hidden", C.c_int32), ("omega0", C.c_float), ("umma", C.c_int32), ("reserved", C.c_int32),
+                ("seed", C.c_uint64)]
 
 
 class FNOError(RuntimeError):
@@ -51,6 +52,7 @@ def lib():
             "fno_loss_grad": (C.c_int, [_vp, _vp, _vp, _vp, C.c_int32, C.POINTER(C.c_double)]),
             "fno_adam_step": (C.c_int, [_vp, C.c_float, C.c_float, C.c_float, C.c_float]),
             "fno_train_step": (C.c_int, [_vp, _vp, _vp, _vp, C.c_int32, C.c_float, C.POINTER(C.c_double)]),
+            "fno_sync": (C.c_int, [_vp]),
             "fno_last_error": (C.c_char_p, [_vp]),
         }
         for name, (res, args) in sig.items():
@@ -124,6 +126,10 @@ def fno_train_step(h, x, t, m, batch, lr):
     return loss.value
 
 
+def fno_sync(h):
+    _check(lib().fno_sync(h), h)
+
+
 def make_config(**kw) -> fno_config:
     c = fno_config_default()
     for k, v in kw.items():
@@ -185,6 +191,9 @@ class FNO:
 
     def train_step(self, x, t, m, lr):
         return fno_train_step(self.h, x, t, m, x.shape[0], lr)
+
+    def sync(self):
+        fno_sync(self.h)
 
 
 # ---------------------------------------------------------------------------

@@ -263,3 +263,4 @@ def test_batches_larger_than_max_batch_are_split():
     y_all = net.forward(x)
     for b in range(10):
         assert np.array_equal(y_all[b:b + 1], net.forward(x[b:b + 1]))
+
