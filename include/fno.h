@@ -98,6 +98,14 @@ lbm_status fno_adam_step(fno_ctx *f, float lr, float beta1, float beta2, float e
 lbm_status fno_train_step(fno_ctx *f, const float *x, const float *t, const float *m, int32_t batch, float lr,
                           double *loss);
 
+/* Checkpoint of the trained state: the network's shape (every fno_config
+ * field that fixes the parameter layout), the Adam step count, and the FP32
+ * parameters and both Adam moments, to a binary file ("GBFNOCK1" header).
+ * fno_load accepts only a checkpoint of the same shape (LBM_ERR_IO
+ * otherwise, the context unchanged) and waits for the stream. */
+lbm_status fno_save(fno_ctx *f, const char *path);
+lbm_status fno_load(fno_ctx *f, const char *path);
+
 /* Wait for the context's stream and report device conditions: LBM_ERR_TIMEOUT
  * if a bounded wait of the tcgen05 x stage gave up (its output is then not
  * valid; the status word is cleared). */

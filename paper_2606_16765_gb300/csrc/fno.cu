@@ -28,6 +28,7 @@
 //   k_adam       Adam update of the flat parameter vector
 #include <cmath>
 #include <type_traits>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -2778,6 +2779,77 @@ extern "C" lbm_status fno_train_step(fno_ctx *f, const float *x, const float *t,
     lbm_status st = fno_loss_grad(f, x, t, m, batch, loss);
     if (st != LBM_OK) return st;
     return fno_adam_step(f, lr, 0.9f, 0.999f, 1e-8f);
+}
+
+namespace {
+struct FnoCkpt {
+    char magic[8];
+    int32_t nx, ny, nz, cin, width, cout, mx, my, mz, layers, hidden, lift_hidden;
+    float omega0;
+    int32_t pad;
+    int64_t np, adam_t;
+};
+
+FnoCkpt ckpt_header(const fno_ctx *f)
+{
+    FnoCkpt h{};
+    std::memcpy(h.magic, "GBFNOCK1", 8);
+    const fno_config &c = f->c;
+    h.nx = c.nx; h.ny = c.ny; h.nz = c.nz; h.cin = c.cin; h.width = c.width; h.cout = c.cout;
+    h.mx = c.mx; h.my = c.my; h.mz = c.mz; h.layers = c.layers; h.hidden = c.hidden; h.lift_hidden = c.lift_hidden;
+    h.omega0 = c.omega0;
+    h.np = f->np;
+    h.adam_t = f->adam_t;
+    return h;
+}
+}  // namespace
+
+extern "C" lbm_status fno_save(fno_ctx *f, const char *path)
+{
+    if (!f || !path) return LBM_ERR_ARG;
+    std::vector<float> buf(3 * (size_t)f->np);
+    FCK(cudaStreamSynchronize(f->s));
+    FCK(cudaMemcpy(buf.data(), f->params, f->np * sizeof(float), cudaMemcpyDeviceToHost));
+    FCK(cudaMemcpy(buf.data() + f->np, f->m1, f->np * sizeof(float), cudaMemcpyDeviceToHost));
+    FCK(cudaMemcpy(buf.data() + 2 * f->np, f->m2, f->np * sizeof(float), cudaMemcpyDeviceToHost));
+    const FnoCkpt h = ckpt_header(f);
+    FILE *fp = std::fopen(path, "wb");
+    if (!fp) {
+        f->err = std::string("cannot open ") + path;
+        return LBM_ERR_IO;
+    }
+    bool ok = std::fwrite(&h, sizeof h, 1, fp) == 1 && std::fwrite(buf.data(), sizeof(float), buf.size(), fp) == buf.size();
+    ok = (std::fclose(fp) == 0) && ok;
+    if (!ok) f->err = "checkpoint write failed";
+    return ok ? LBM_OK : LBM_ERR_IO;
+}
+
+extern "C" lbm_status fno_load(fno_ctx *f, const char *path)
+{
+    if (!f || !path) return LBM_ERR_ARG;
+    FILE *fp = std::fopen(path, "rb");
+    if (!fp) {
+        f->err = std::string("cannot open ") + path;
+        return LBM_ERR_IO;
+    }
+    FnoCkpt h{};
+    FnoCkpt mine = ckpt_header(f);
+    const bool same = std::fread(&h, sizeof h, 1, fp) == 1 && std::memcmp(h.magic, mine.magic, 8) == 0 &&
+                      std::memcmp(&h.nx, &mine.nx, offsetof(FnoCkpt, np) - offsetof(FnoCkpt, nx)) == 0 &&
+                      h.np == mine.np;
+    std::vector<float> buf(3 * (size_t)f->np);
+    const bool ok = same && std::fread(buf.data(), sizeof(float), buf.size(), fp) == buf.size();
+    std::fclose(fp);
+    if (!ok) {
+        f->err = same ? "checkpoint truncated" : "checkpoint does not match this network's shape";
+        return LBM_ERR_IO;
+    }
+    FCK(cudaStreamSynchronize(f->s));
+    FCK(cudaMemcpy(f->params, buf.data(), f->np * sizeof(float), cudaMemcpyHostToDevice));
+    FCK(cudaMemcpy(f->m1, buf.data() + f->np, f->np * sizeof(float), cudaMemcpyHostToDevice));
+    FCK(cudaMemcpy(f->m2, buf.data() + 2 * f->np, f->np * sizeof(float), cudaMemcpyHostToDevice));
+    f->adam_t = h.adam_t;
+    return LBM_OK;
 }
 
 extern "C" lbm_status fno_sync(fno_ctx *f)

@@ -53,6 +53,8 @@ def lib():
             "fno_adam_step": (C.c_int, [_vp, C.c_float, C.c_float, C.c_float, C.c_float]),
             "fno_train_step": (C.c_int, [_vp, _vp, _vp, _vp, C.c_int32, C.c_float, C.POINTER(C.c_double)]),
             "fno_sync": (C.c_int, [_vp]),
+            "fno_save": (C.c_int, [_vp, C.c_char_p]),
+            "fno_load": (C.c_int, [_vp, C.c_char_p]),
             "fno_last_error": (C.c_char_p, [_vp]),
         }
         for name, (res, args) in sig.items():
@@ -130,6 +132,14 @@ def fno_sync(h):
     _check(lib().fno_sync(h), h)
 
 
+def fno_save(h, path):
+    _check(lib().fno_save(h, str(path).encode()), h)
+
+
+def fno_load(h, path):
+    _check(lib().fno_load(h, str(path).encode()), h)
+
+
 def make_config(**kw) -> fno_config:
     c = fno_config_default()
     for k, v in kw.items():
@@ -194,6 +204,12 @@ class FNO:
 
     def sync(self):
         fno_sync(self.h)
+
+    def save(self, path):
+        fno_save(self.h, path)
+
+    def load(self, path):
+        fno_load(self.h, path)
 
 
 # ---------------------------------------------------------------------------

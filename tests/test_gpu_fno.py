@@ -264,3 +264,28 @@ def test_batches_larger_than_max_batch_are_split():
     for b in range(10):
         assert np.array_equal(y_all[b:b + 1], net.forward(x[b:b + 1]))
 
+
+
+def test_checkpoint_restores_parameters_and_adam_state(tmp_path):
+    """fno_save after three Adam steps, fno_load into a fresh network: the
+    next training step gives the same loss and the same parameters, bitwise;
+    a checkpoint of another shape is refused."""
+    from paper_2606_16765_gb300 import fno as G
+    ocfg, gcfg = tiny_cfgs(8)
+    gcfg.update(act_bf16=0, tensor_cores=1)
+    x, t, m, p = problem(ocfg, seed=5)
+    a = G.FNO(**gcfg)
+    for _ in range(3):
+        a.train_step(x, t, m, 1e-3)
+    path = tmp_path / "fno.ckpt"
+    a.save(path)
+    b = G.FNO(**gcfg)
+    b.load(path)
+    assert np.array_equal(a.params(), b.params())
+    la, lb = a.train_step(x, t, m, 1e-3), b.train_step(x, t, m, 1e-3)
+    assert la == lb and np.array_equal(a.params(), b.params())
+    other = dict(gcfg, hidden=gcfg["hidden"] + 1)
+    c = G.FNO(**other)
+    with pytest.raises(G.FNOError) as e:
+        c.load(path)
+    assert e.value.status == 7                     # LBM_ERR_IO
