@@ -473,6 +473,10 @@ def run(n_train=512, n_test=64, epochs=50, batch=8, lr=1e-3, storage="f16c", n_f
     return report
 
 
+def _log(*a):
+    print(*a, flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--out", default=None)
@@ -491,10 +495,10 @@ def main():
         print(json.dumps(time_fno()))
     elif args.quick:
         run(n_train=16, n_test=8, epochs=2, n_ft=2.0, storage=args.storage, out=args.out, sim_batch=24, re_range=rr,
-            grids=args.grids)
+            grids=args.grids, log=_log)
     else:
         run(n_train=args.n_train, n_test=args.n_test, epochs=args.epochs, storage=args.storage, out=args.out,
-            re_range=rr, grids=args.grids)
+            re_range=rr, grids=args.grids, log=_log)
 
 
 if __name__ == "__main__":

@@ -305,13 +305,13 @@ def test_plain_fast_path_equals_general_path():
 
 def f16c_round(x32):
     """Nearest value of the 16-bit custom float (4 exponent bits, bias 15,
-    11 mantissa bits, subnormal step 2^-25, saturating at 2 - 2^-11), ties to
-    even, from the format's definition."""
+    11 mantissa bits, subnormal step 2^-25, saturating at 2 - 2^-11), ties
+    away from zero, from the format's definition."""
     x = x32.astype(np.float64)
     a = np.abs(x)
     e = np.floor(np.log2(np.maximum(a, 2.0 ** -14)))
     step = np.where(a < 2.0 ** -14, 2.0 ** -25, 2.0 ** (e - 11))
-    r = np.minimum(np.round(a / step) * step, 2.0 - 2.0 ** -11)
+    r = np.minimum(np.floor(a / step + 0.5) * step, 2.0 - 2.0 ** -11)
     return np.sign(x) * r
 
 
@@ -323,7 +323,7 @@ def test_f16c_storage_encodes_to_nearest():
     n = 64 * 16
     v = np.concatenate([rng.uniform(-1.9, 1.9, 27 * n // 3), rng.uniform(-1e-3, 1e-3, 27 * n // 3),
                         rng.uniform(-1e-6, 1e-6, 27 * n - 2 * (27 * n // 3))])
-    v[:6] = [0.0, 2.5, -3.0, 2.0 ** -14, 2.0 ** -25 * 1.5, 1.0 + 2.0 ** -12]
+    v[:6] = [0.0, 2.5, -3.0, 2.0 ** -14, 2.0 ** -25 * 1.5, 1.0 + 2.0 ** -12]     # the last two are ties
     src = w[:, None] + v.reshape(27, n)
     s.set_pdfs(src.reshape(27, *g[::-1]))
     got = s.pdfs().reshape(27, n) - w[:, None]
