@@ -60,7 +60,8 @@ def conv3(x, w):
     for dz in range(3):
         for dy in range(3):
             for dx in range(3):
-                y += np.einsum("bizyx,oi->bozyx", xp[:, :, dz:dz + Z, dy:dy + Y, dx:dx + X], w[:, :, dz, dy, dx])
+                y += np.einsum("bizyx,oi->bozyx", xp[:, :, dz:dz + Z, dy:dy + Y, dx:dx + X], w[:, :, dz, dy, dx],
+                               optimize=True)
     return y
 
 
@@ -74,8 +75,8 @@ def conv3_backward(x, w, gy):
         for dy in range(3):
             for dx in range(3):
                 sl = (slice(None), slice(None), slice(dz, dz + Z), slice(dy, dy + Y), slice(dx, dx + X))
-                gw[:, :, dz, dy, dx] = np.einsum("bozyx,bizyx->oi", gy, xp[sl])
-                gxp[sl] += np.einsum("bozyx,oi->bizyx", gy, w[:, :, dz, dy, dx])
+                gw[:, :, dz, dy, dx] = np.einsum("bozyx,bizyx->oi", gy, xp[sl], optimize=True)
+                gxp[sl] += np.einsum("bozyx,oi->bizyx", gy, w[:, :, dz, dy, dx], optimize=True)
     return gxp[:, :, 1:-1, 1:-1, 1:-1], gw
 
 
@@ -136,12 +137,14 @@ def upsample_matrix(n):
 
 def up2(x):
     _, _, Z, Y, X = x.shape
-    return np.einsum("az,by,cx,nkzyx->nkabc", upsample_matrix(Z), upsample_matrix(Y), upsample_matrix(X), x)
+    return np.einsum("az,by,cx,nkzyx->nkabc", upsample_matrix(Z), upsample_matrix(Y), upsample_matrix(X), x,
+                     optimize=True)
 
 
 def up2_backward(gy, shape):
     _, _, Z, Y, X = shape
-    return np.einsum("az,by,cx,nkabc->nkzyx", upsample_matrix(Z), upsample_matrix(Y), upsample_matrix(X), gy)
+    return np.einsum("az,by,cx,nkabc->nkzyx", upsample_matrix(Z), upsample_matrix(Y), upsample_matrix(X), gy,
+                     optimize=True)
 
 
 def sigmoid(x):
@@ -211,7 +214,7 @@ def forward(p, x, cfg, keep=False):
         h = np.concatenate([skips[d], u], axis=1)
         h = _block(p, f"dec{d}a", h, tape)
         h = _block(p, f"dec{d}b", h, tape)
-    a = np.einsum("oc,bczyx->bozyx", p["out_w"], h) + p["out_b"][None, :, None, None, None]
+    a = np.einsum("oc,bczyx->bozyx", p["out_w"], h, optimize=True) + p["out_b"][None, :, None, None, None]
     y = sigmoid(a)
     if keep:
         return y, dict(blocks=tape, pools=pools, ups=ups, last=h)
@@ -233,9 +236,9 @@ def backward(p, tape, y, t, m, cfg):
     gy = 2.0 * m[:, None] * (y - t) / (C * m.sum())
     ga = gy * y * (1.0 - y)
     h = tape["last"]
-    g["out_w"] = np.einsum("bozyx,bczyx->oc", ga, h)
+    g["out_w"] = np.einsum("bozyx,bczyx->oc", ga, h, optimize=True)
     g["out_b"] = ga.sum(axis=(0, 2, 3, 4))
-    gh = np.einsum("oc,bozyx->bczyx", p["out_w"], ga)
+    gh = np.einsum("oc,bozyx->bczyx", p["out_w"], ga, optimize=True)
     blocks = list(tape["blocks"])
     nd = len(cfg.channels)
     gskip = [None] * nd

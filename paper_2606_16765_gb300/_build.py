@@ -26,6 +26,7 @@ LIBS = {
                   "lbm_step_f16.cu", "lbm_step_bf16.cu", "lbm_step_f16c.cu", "lbm_noalloc.cu",
                   "resample.cu"],
     "libfno.so": ["fno.cu", "fno_umma.cu"],
+    "libunet.so": ["unet.cu", "unet_gemm.cu"],
 }
 
 
