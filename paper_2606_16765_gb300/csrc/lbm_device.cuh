@@ -333,6 +333,79 @@ __device__ __forceinline__ void chimera_inverse(R *f, R ux, R uy, R uz)
             inv_line<R>(f[xi + 3 * yi], f[xi + 3 * yi + 9], f[xi + 3 * yi + 18], uz, R(tw(xi) * tw(yi)));
 }
 
+// Inverse line transform of a line whose first central moment is zero
+// (m1 = 0): the lines (ay, az) with ay + az even of the x pass when every odd
+// cumulant is zero after the collision.
+template <class R>
+__device__ __forceinline__ void inv_line_even(R &a, R &b, R &c, R u, R K)
+{
+    const R m0 = a, m2 = c;
+    const R s1 = u * (m0 + K);
+    const R s2 = m2 + u * s1;
+    a = R(0.5) * (s2 - s1);
+    c = R(0.5) * (s2 + s1);
+    b = m0 - s2;
+}
+
+// Inverse line transform of a line holding only a first central moment
+// (m0 = m2 = 0 and no rest part, K = 0): s1 = m1, s2 = 2 u m1, hence
+// f- = m1 (u - 1/2), f+ = m1 (u + 1/2), f0 = -2 u m1.
+template <class R>
+__device__ __forceinline__ void inv_line_odd(R &a, R &b, R &c, R m1, R u_lo, R u_hi, R m2u)
+{
+    a = m1 * u_lo;
+    c = m1 * u_hi;
+    b = m1 * m2u;
+}
+
+// Inverse chimera after a collision that leaves every odd-order central
+// moment zero (orders 1, 3, 5: every cumulant of order >= 3 reset).  The
+// x pass then splits into lines with m1 = 0 ((ay, az) with ay + az even) and
+// lines holding only m1 (ay + az odd, where the rest part K is zero too);
+// the y and z passes are the general ones.  Arguments are the nonzero
+// (non-normalised, deviation) central moments.
+template <class R>
+__device__ __forceinline__ void chimera_inverse_even(R *f, R ux, R uy, R uz, R m000, R m200, R m020, R m002, R m110,
+                                                     R m101, R m011, R m211, R m121, R m112, R m220, R m202, R m022,
+                                                     R m222)
+{
+    const R third = R(1.0 / 3.0), ninth = R(1.0 / 9.0);
+    // x pass: line (ay, az) holds (m[0 ay az], m[1 ay az], m[2 ay az]) at
+    // f[3 ay + 9 az + 0..2]
+    f[0] = m000; f[2] = m200; inv_line_even<R>(f[0], f[1], f[2], ux, R(1));            // (0, 0)
+    f[6] = m020; f[8] = m220; inv_line_even<R>(f[6], f[7], f[8], ux, third);           // (2, 0)
+    f[12] = m011; f[14] = m211; inv_line_even<R>(f[12], f[13], f[14], ux, R(0));       // (1, 1)
+    f[18] = m002; f[20] = m202; inv_line_even<R>(f[18], f[19], f[20], ux, third);      // (0, 2)
+    f[24] = m022; f[26] = m222; inv_line_even<R>(f[24], f[25], f[26], ux, ninth);      // (2, 2)
+    const R u_lo = ux - R(0.5), u_hi = ux + R(0.5), m2u = R(-2) * ux;
+    inv_line_odd<R>(f[3], f[4], f[5], m110, u_lo, u_hi, m2u);                          // (1, 0)
+    inv_line_odd<R>(f[9], f[10], f[11], m101, u_lo, u_hi, m2u);                        // (0, 1)
+    inv_line_odd<R>(f[15], f[16], f[17], m121, u_lo, u_hi, m2u);                       // (2, 1)
+    inv_line_odd<R>(f[21], f[22], f[23], m112, u_lo, u_hi, m2u);                       // (1, 2)
+#pragma unroll
+    for (int az = 0; az < 3; ++az)
+#pragma unroll
+        for (int xi = 0; xi < 3; ++xi)
+            inv_line<R>(f[xi + 9 * az], f[xi + 3 + 9 * az], f[xi + 6 + 9 * az], uy, R(tw(xi) * zw(az)));
+#pragma unroll
+    for (int yi = 0; yi < 3; ++yi)
+#pragma unroll
+        for (int xi = 0; xi < 3; ++xi)
+            inv_line<R>(f[xi + 3 * yi], f[xi + 3 * yi + 9], f[xi + 3 * yi + 18], uz, R(tw(xi) * tw(yi)));
+}
+
+// 1/x: for FP32 the hardware estimate refined by one Newton-Raphson step
+// r <- r + r (1 - x r) (the error of the estimate is squared, so the result
+// is within an ulp or so of the rounded quotient); the FP64 path divides.
+template <class R> __device__ __forceinline__ R recip(R x);
+template <> __device__ __forceinline__ double recip<double>(double x) { return 1.0 / x; }
+template <> __device__ __forceinline__ float recip<float>(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return fmaf(r, fmaf(-x, r, 1.0f), r);
+}
+
 template <class R>
 struct Rates {
     R w1, w2, w3;
@@ -404,7 +477,7 @@ __device__ __forceinline__ void collide(R *f, const Rates<R> &rt, R &drho_out, R
         const R M200 = B20[0] + B20[1] + B20[2];
         drho = M000;
         rho = R(1) + drho;
-        ir = R(1) / rho;
+        ir = recip<R>(rho);
         ux = M100 * ir;
         uy = M010 * ir;
         uz = M001 * ir;
@@ -585,6 +658,15 @@ __device__ __forceinline__ void collide(R *f, const Rates<R> &rt, R &drho_out, R
                       + (s200 + s020 + s002) * ninth + (s200 * s020 + s200 * s002 + s020 * s002) * third
                       + s200 * s020 * s002;
         e222s += S42s + S33s - R(2) * S222s;
+    }
+
+    if (PLAIN) {
+        // odd orders are zero: only the even-order moments enter the inverse
+        chimera_inverse_even<R>(f, ux, uy, uz, drho, rho * s200 + drho * third, rho * s020 + drho * third,
+                                rho * s002 + drho * third, rho * s110, rho * s101, rho * s011, rho * s211,
+                                rho * s121, rho * s112, rho * e220s + drho * ninth, rho * e202s + drho * ninth,
+                                rho * e022s + drho * ninth, rho * e222s + drho * t27);
+        return;
     }
 
     // back to non-normalised central moment deviations

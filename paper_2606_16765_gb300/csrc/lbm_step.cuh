@@ -141,9 +141,21 @@ __device__ __forceinline__ void bulk_cell(const StepArgs &a, const StepOut &o, i
     if (EPI) epilogue<R>(a, o, c, drho, ux, uy, uz);
 }
 
+// Blocks per SM asked of the register allocator (256-thread blocks): the
+// 16-bit kernels of the plain collision are bound by instruction issue and
+// take 40 registers (six blocks) without the epilogue; FP32 keeps 48 (five),
+// the general collision 64 (four), FP64 the plain collision 80 (three).
+// Each at no or one spilled value.
+template <class S, bool EPI, bool PLAIN>
+constexpr int bulk_min_blocks()
+{
+    return sizeof(S) == 8 ? (PLAIN ? 3 : 1)
+                          : (!PLAIN ? 4 : (sizeof(S) == 4 ? 5 : (EPI ? 5 : 6)));
+}
+
 // Single-grid bulk kernel: grid (ceil(nx / blockDim.x), ceil(ny / blockDim.y), nz).
 template <class S, bool ODD, bool EPI, bool PLAIN>
-__global__ void __launch_bounds__(256) k_step_bulk(StepArgs a)
+__global__ void __launch_bounds__(256, (bulk_min_blocks<S, EPI, PLAIN>())) k_step_bulk(StepArgs a)
 {
     const int x = (int)(blockIdx.x * blockDim.x + threadIdx.x);
     const int y = (int)(blockIdx.y * blockDim.y + threadIdx.y);
@@ -539,11 +551,23 @@ __device__ __forceinline__ bool samples_at(const BatchMember &B, int64_t t)
 }
 
 template <class S, bool ODD, bool EPI, bool PLAIN>
-__global__ void __launch_bounds__(256) k_batch_bulk(const BatchMember *mem, const int64_t *begin, int nm,
+__global__ void __launch_bounds__(256, (bulk_min_blocks<S, EPI, PLAIN>())) k_batch_bulk(const BatchMember *mem, const int64_t *begin, int nm,
                                                     const int64_t *tdev)
 {
+    // the member's step arguments are staged in shared memory: the cell
+    // update reads its 54 access offsets from there (a broadcast per access)
+    // rather than from the global member table
+    __shared__ StepArgs sa;
     const int m = find_member(begin, nm, blockIdx.x);
     const BatchMember &B = mem[m];
+    {
+        static_assert(sizeof(StepArgs) % 8 == 0, "StepArgs is copied as 8-byte words");
+        const int tid = (int)(threadIdx.x + threadIdx.y * blockDim.x), nt = (int)(blockDim.x * blockDim.y);
+        const unsigned long long *src = reinterpret_cast<const unsigned long long *>(&B.a);
+        unsigned long long *dst = reinterpret_cast<unsigned long long *>(&sa);
+        for (int k = tid; k < (int)(sizeof(StepArgs) / 8); k += nt) dst[k] = src[k];
+    }
+    __syncthreads();
     const int64_t local = (int64_t)blockIdx.x - begin[m];
     const int bx = (int)(local % B.gx);
     const int64_t r = local / B.gx;
@@ -551,10 +575,10 @@ __global__ void __launch_bounds__(256) k_batch_bulk(const BatchMember *mem, cons
     const int z = (int)(r / B.gy);
     const int x = bx * (int)blockDim.x + (int)threadIdx.x;
     const int y = by * (int)blockDim.y + (int)threadIdx.y;
-    if (x >= B.a.nx || y >= B.a.ny) return;
+    if (x >= sa.nx || y >= sa.ny) return;
     StepOut o{nullptr, nullptr, nullptr, nullptr, nullptr};
     if (EPI && samples_at(B, *tdev)) o.msum = B.msum;
-    bulk_cell<S, ODD, EPI, PLAIN, false>(B.a, o, x, y, z);
+    bulk_cell<S, ODD, EPI, PLAIN, false>(sa, o, x, y, z);
 }
 
 // Batched edge kernel: blocks [0, eblocks) are the members' edge blocks,

@@ -3,10 +3,22 @@ activations) against the FP64 oracle (oracle/unet.py).
 
 The convolutions alone are compared exactly up to FP32 summation: their
 inputs and weights are drawn as BF16 values, so the tensor cores' products
-are exact and only the order of the FP32 sums differs from the oracle.  The
-network is compared at BF16 activation precision (every block rounds its
-convolution output and its normalised output to BF16, about 2^-9 relative
-each), hence the looser statistical bounds below."""
+are exact and only the FP32 sums differ from the oracle.  The rounding error
+of a sum of K such products grows as sqrt(K) 2^-24 of its magnitude (the
+roundings act as independent errors of random sign), so the bound is
+4 sqrt(K) 2^-24 of the largest output, K the contraction length.
+
+The network stores every activation in BF16 (each convolution output, each
+normalised output and each up-sampled field are rounded, about 2^-9
+relative).  Max-pooling and ReLU turn such roundings into discrete changes
+(a different maximum of a window, a flipped sign), so on small grids the
+gradients of the early layers move by tens of percent between the FP64 and
+a BF16-stored network.  The network tests therefore compare the GPU with
+the oracle evaluated with the same BF16 storage points (`_rounded`), and
+check that the GPU is no further from the exact FP64 oracle than that
+rounded oracle is."""
+import contextlib
+import math
 import numpy as np
 import pytest
 
@@ -42,6 +54,44 @@ def _conv_case(seed, B, nz, ny, nx, cin, cout):
     return x, w, g
 
 
+def _sum_tol(K):
+    """Bound on the largest error of K-term FP32 sums of exact products,
+    relative to the largest output (see the module docstring)."""
+    return 4.0 * math.sqrt(K) * 2.0 ** -24
+
+
+@contextlib.contextmanager
+def _rounded():
+    """The oracle with the GPU's BF16 storage points: convolution outputs,
+    normalised outputs and up-sampled fields rounded to BF16 (round to
+    nearest even); the backward stays the oracle's exact FP64 adjoint of
+    that forward."""
+    block, up2 = U._block, U.up2
+
+    def rblock(p, name, x, tape):
+        z = bf16(U.conv3(x, p[name + "_w"])).astype(np.float64)
+        n, cache = U.batchnorm(z, p[name + "_g"], p[name + "_b"])
+        tape.append((name, x, cache, n))
+        return bf16(np.maximum(n, 0.0)).astype(np.float64)
+
+    U._block = rblock
+    U.up2 = lambda x: bf16(up2(x)).astype(np.float64)
+    try:
+        yield
+    finally:
+        U._block, U.up2 = block, up2
+
+
+def _rel(a, b):
+    a, b = np.ravel(a), np.ravel(b)
+    return float(np.linalg.norm(a - b) / (np.linalg.norm(b) + 1e-300))
+
+
+def _cos(a, b):
+    a, b = np.ravel(a), np.ravel(b)
+    return float(a @ b / (np.linalg.norm(a) * np.linalg.norm(b) + 1e-300))
+
+
 def _first(a):
     """[B, z, y, x, C] -> [B, C, z, y, x] float64"""
     return np.moveaxis(a.astype(np.float64), -1, 1)
@@ -71,8 +121,9 @@ def test_conv3_forward_matches_fp64(case):
     N.conv3_forward(_dev(x), _dev(w), y)
     ref = np.moveaxis(U.conv3(_first(x), _w5(w)), 1, -1)
     err = np.abs(y.cpu().numpy() - ref).max() / np.abs(ref).max()
-    print(f"conv3 forward {case}: max rel err {err:.2e}")
-    assert err < 1e-5
+    tol = _sum_tol(27 * cin)
+    print(f"conv3 forward {case}: max rel err {err:.2e} (bound {tol:.2e})")
+    assert err < tol
 
 
 @pytest.mark.parametrize("case", CONV_CASES)
@@ -90,8 +141,10 @@ def test_conv3_backward_matches_fp64(case):
     rgw = rgw.reshape(cout, cin, 27)
     ex = np.abs(gx.cpu().numpy() - rgx).max() / np.abs(rgx).max()
     ew = np.abs(gw.cpu().numpy() - rgw).max() / np.abs(rgw).max()
-    print(f"conv3 backward {case}: input gradient {ex:.2e}, weight gradient {ew:.2e}")
-    assert ex < 1e-5 and ew < 1e-5
+    tx, tw = _sum_tol(27 * cout), _sum_tol(B * nz * ny * nx)
+    print(f"conv3 backward {case}: input gradient {ex:.2e} (bound {tx:.2e}), weight gradient {ew:.2e} "
+          f"(bound {tw:.2e})")
+    assert ex < tx and ew < tw
 
 
 def _net_case(B=2, grid=(16, 16, 32), stages=3, channels=(32, 64, 128), bottleneck=128, seed=3):
@@ -134,12 +187,27 @@ def test_forward_matches_oracle():
     net = _gpu_net(kw, cfg, p)
     y = net.forward(x.astype(np.float32))
     net.sync()
-    ref = U.forward(p, x, cfg)
-    d = y - ref
-    rel = np.linalg.norm(d) / np.linalg.norm(ref - ref.mean())
-    print(f"U-Net forward: rel L2 (about the mean) {rel:.2e}, max abs {np.abs(d).max():.2e}")
     net.close()
-    assert rel < 0.03
+    _check_forward(y, p, x, cfg, "U-Net forward")
+
+
+def _check_forward(y, p, x, cfg, label):
+    """The GPU output against the BF16-stored oracle (tight) and against the
+    exact oracle (no further than the BF16-stored oracle is)."""
+    ref = U.forward(p, x, cfg)
+    with _rounded():
+        rnd = U.forward(p, x, cfg)
+    scale = np.linalg.norm(ref - ref.mean())
+    e_gpu_rnd = np.linalg.norm(y - rnd) / scale
+    e_gpu_ref = np.linalg.norm(y - ref) / scale
+    e_rnd_ref = np.linalg.norm(rnd - ref) / scale
+    print(f"{label}: rel L2 about the mean: GPU vs BF16-stored oracle {e_gpu_rnd:.2e}, GPU vs FP64 oracle "
+          f"{e_gpu_ref:.2e}, BF16-stored vs FP64 oracle {e_rnd_ref:.2e}")
+    # the GPU shares the storage points: it sits closer to the BF16-stored
+    # oracle than that is to the exact one, and no further from the exact
+    # oracle than BF16 storage itself moves it
+    assert e_gpu_rnd < e_rnd_ref + 2e-3
+    assert e_gpu_ref < 1.5 * e_rnd_ref + 2e-3
 
 
 def test_gradients_match_oracle():
@@ -150,21 +218,26 @@ def test_gradients_match_oracle():
     L = net.loss_grad(x.astype(np.float32), t.astype(np.float32), m.astype(np.float32))
     net.sync()
     g = N.unflatten(net.cfg, net.grads())
+    net.close()
     Lr, gr = U.loss_and_grad(p, x, t, m, cfg)
-    assert abs(L - Lr) < 1e-3 * Lr
+    with _rounded():
+        Ls, gs = U.loss_and_grad(p, x, t, m, cfg)
+    assert abs(L - Lr) < 1e-3 * Lr and abs(L - Ls) < 1e-3 * Ls
     worst = []
     for k in gr:
         if k == "input":
             continue
-        a, b = g[k].reshape(-1), gr[k].reshape(-1)
-        cos = float(a @ b / (np.linalg.norm(a) * np.linalg.norm(b) + 1e-300))
-        rel = float(np.linalg.norm(a - b) / (np.linalg.norm(b) + 1e-300))
-        worst.append((rel, cos, k))
+        worst.append((_rel(g[k], gs[k]), _cos(g[k], gs[k]), _rel(g[k], gr[k]), _rel(gs[k], gr[k]), k))
     worst.sort(reverse=True)
-    print("U-Net gradients, worst groups (rel L2, cosine):", [(f"{r:.2e}", f"{c:.5f}", k) for r, c, k in worst[:6]])
-    net.close()
-    for rel, cos, k in worst:
-        assert cos > 0.995 and rel < 0.1, (k, rel, cos)
+    print("U-Net gradients, worst groups (rel L2 and cosine vs the BF16-stored oracle; rel L2 of the GPU and of the "
+          "BF16-stored oracle vs the FP64 oracle):",
+          [(f"{a:.2e}", f"{c:.5f}", f"{e:.2e}", f"{r:.2e}", k) for a, c, e, r, k in worst[:6]])
+    for rel, cos, e_ref, r_ref, k in worst:
+        # the GPU's backward also rounds the gradients to BF16 (a smooth
+        # perturbation of a few 2^-9 over the blocks) on top of the forward's
+        # storage effects, which the BF16-stored oracle shares
+        assert rel < r_ref + 0.03, (k, rel, r_ref)
+        assert e_ref < 1.5 * r_ref + 0.03, (k, e_ref, r_ref)
 
 
 def test_adam_steps_follow_the_oracle():
@@ -199,10 +272,7 @@ def test_full_size_forward_matches_oracle():
     y = net.forward(x.astype(np.float32))
     net.sync()
     net.close()
-    ref = U.forward(p, x, cfg)
-    rel = np.linalg.norm(y - ref) / np.linalg.norm(ref - ref.mean())
-    print(f"U-Net 128x64x64 forward: rel L2 (about the mean) {rel:.2e}")
-    assert rel < 0.03
+    _check_forward(y, p, x, cfg, "U-Net 128x64x64 forward")
 
 
 def test_timed_training_step_paper_configuration():
