@@ -507,6 +507,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--batch-members", type=int, default=32,
+                    help="channels of the batch leg (32 is the batched configuration; fewer for small captures)")
     ap.add_argument("--no-fno", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -595,7 +597,7 @@ def main():
                 "collision": "fourth-order parametrisation with limiter (Sec. 3.2)" if p4 else "plain cumulant",
                 "clocks": r2["clocks"]}
         if not args.no_batch:
-            line["batch"] = run_batch(args.steps, 20)
+            line["batch"] = run_batch(args.steps, 20, n=args.batch_members)
         if not args.no_fno:
             line["fno"] = run_fno()
         if not args.no_e2e:

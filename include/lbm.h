@@ -119,7 +119,9 @@ typedef struct {
     double limiter;         /* its limiter lambda (default 0.01)                 */
     int32_t xface_edge;     /* 1: the inlet/outlet cells go through the boundary-
                                cell records instead of the bulk kernel's face
-                               warps (pays on short rows; batch members always) */
+                               warps (default 0: the face warps, whose accesses
+                               are coalesced with their rows; batch members
+                               follow their own setting) */
     int32_t reserved[1];
 } lbm_params;
 

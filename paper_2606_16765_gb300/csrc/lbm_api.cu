@@ -358,71 +358,58 @@ static lbm_status create_impl(const lbm_grid *g, const uint8_t *mask, const lbm_
     launch_flags(dmask, ctx->at<uint8_t>(L.flags), g->nx, g->ny, g->nz,
                  p->face_x_lo != LBM_FACE_PERIODIC && !p->xface_edge, p->face_x_hi != LBM_FACE_PERIODIC && !p->xface_edge,
                  p->face_y == LBM_FACE_WALL, p->face_z == LBM_FACE_WALL, s);
-    std::vector<uint8_t> hflags(n);
-    if (cudaMemcpyAsync(hflags.data(), ctx->at<uint8_t>(L.flags), n, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+    // boundary-cell records on the device (ascending cell order keeps rows
+    // contiguous): cell index and the link code of each of the 27 directions
+    // in the pull view (where population i of the cell comes from); the
+    // scratch (chunk counts and offsets, solid links per direction) sits in
+    // the population array behind the uploaded mask, before it is cleared
+    const int nx = g->nx, ny = g->ny, nz = g->nz;
+    const int64_t nb = record_blocks(n);
+    unsigned char *scr = reinterpret_cast<unsigned char *>(ctx->base + L.pdf) + ((n + 255) / 256) * 256;
+    int *dcounts = reinterpret_cast<int *>(scr);
+    int64_t *doffs = reinterpret_cast<int64_t *>(scr + ((nb * 16 + 255) / 256) * 256);
+    unsigned long long *dsolid = reinterpret_cast<unsigned long long *>(reinterpret_cast<unsigned char *>(doffs) +
+                                                                         ((nb * 8 + 255) / 256) * 256);
+    std::vector<int> hcounts((size_t)nb * 4);
+    launch_record_count(ctx->at<uint8_t>(L.flags), n, dcounts, s);
+    if (cudaMemcpyAsync(hcounts.data(), dcounts, hcounts.size() * sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess) {
         ctx->err = std::string("flag build failed: ") + cudaGetErrorString(cudaGetLastError());
         return bail(LBM_ERR_CUDA);
     }
-    // edge-cell records (ascending cell order keeps rows contiguous): cell
-    // index and the link code of each of the 27 directions in the pull view
-    // (where population i of the cell comes from), plus the constant part
-    // sum 2 c_i w_i of the obstacle force over obstacle links
-    std::vector<uint4> edge;
-    double fw[3] = {0, 0, 0};
-    const int nx = g->nx, ny = g->ny, nz = g->nz;
-    auto link_kind = [&](int sx, int sy, int sz) -> uint32_t {
-        bool wrapped = false;
-        if (sy < 0 || sy >= ny) {
-            if (p->face_y != LBM_FACE_PERIODIC) return LINK_WALL;
-            sy = (sy + ny) % ny; wrapped = true;
-        }
-        if (sz < 0 || sz >= nz) {
-            if (p->face_z != LBM_FACE_PERIODIC) return LINK_WALL;
-            sz = (sz + nz) % nz; wrapped = true;
-        }
-        if (sx < 0) {
-            if (p->face_x_lo == LBM_FACE_INLET) return LINK_INLET;
-            if (p->face_x_lo == LBM_FACE_WALL) return LINK_WALL;
-            sx += nx; wrapped = true;
-        } else if (sx >= nx) {
-            if (p->face_x_hi == LBM_FACE_OUTLET || p->face_x_hi == LBM_FACE_OUTFLOW) return LINK_OUTLET;
-            if (p->face_x_hi == LBM_FACE_WALL) return LINK_WALL;
-            sx -= nx; wrapped = true;
-        }
-        if (hflags[sx + (int64_t)nx * (sy + (int64_t)ny * sz)] & CELL_SOLID) return LINK_SOLID;
-        return wrapped ? LINK_WRAP : LINK_FLUID;
-    };
-    for (int64_t c = 0; c < n; ++c) {
-        const int x = (int)(c % nx), y = (int)((c / nx) % ny), z = (int)(c / ((int64_t)nx * ny));
-        ctx->n_fluid += !(hflags[c] & CELL_SOLID);
-        ctx->n_bulk += (hflags[c] == 0 || hflags[c] == CELL_XFACE);
-        ctx->n_wall += hflags[c] == CELL_WALL;
-        (void)x;
-        if (hflags[c] != CELL_EDGE) continue;
-        uint32_t w[3] = {0, 0, 0};
-        for (int i = 0; i < Q; ++i) {
-            const uint32_t kind = link_kind(x - cx_of(i), y - cy_of(i), z - cz_of(i));
-            w[i / 9] |= kind << (3 * (i % 9));
-            if (kind == LINK_SOLID) {       // population j = 26 - i heads into the obstacle
-                const int j = Q - 1 - i;
-                fw[0] += 2.0 * cx_of(j) * w_of(j);
-                fw[1] += 2.0 * cy_of(j) * w_of(j);
-                fw[2] += 2.0 * cz_of(j) * w_of(j);
-            }
-        }
-        edge.push_back(make_uint4((uint32_t)c, w[0], w[1], w[2]));
+    std::vector<int64_t> hoffs((size_t)nb);
+    int64_t n_edge = 0;
+    for (int64_t b = 0; b < nb; ++b) {
+        ctx->n_fluid += hcounts[4 * b];
+        ctx->n_bulk += hcounts[4 * b + 1];
+        ctx->n_wall += hcounts[4 * b + 2];
+        hoffs[b] = n_edge;
+        n_edge += hcounts[4 * b + 3];
     }
-    if ((int64_t)edge.size() > edge_bound(*g, n_solid)) {
+    if (n_edge > edge_bound(*g, n_solid)) {
         ctx->err = "edge-cell count exceeds its bound";
         return bail(LBM_ERR_OOM);
     }
-    ctx->n_edge = (int64_t)edge.size();
-    for (int d = 0; d < 3; ++d) ctx->force_w[d] = fw[d];
-    if (!edge.empty() && cudaMemcpyAsync(ctx->at<uint4>(L.edge), edge.data(), edge.size() * sizeof(uint4),
-                                         cudaMemcpyHostToDevice, s) != cudaSuccess) {
-        ctx->err = "edge list upload failed";
+    ctx->n_edge = n_edge;
+    unsigned long long hsolid[Q] = {};
+    if (cudaMemcpyAsync(doffs, hoffs.data(), hoffs.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemsetAsync(dsolid, 0, sizeof(hsolid), s) != cudaSuccess) {
+        ctx->err = "edge list build failed";
         return bail(LBM_ERR_CUDA);
+    }
+    launch_record_write(ctx->at<uint8_t>(L.flags), nx, ny, nz, p->face_x_lo, p->face_x_hi, p->face_y, p->face_z, doffs,
+                        ctx->at<uint4>(L.edge), dsolid, s);
+    if (cudaMemcpyAsync(hsolid, dsolid, sizeof(hsolid), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        ctx->err = std::string("edge list build failed: ") + cudaGetErrorString(cudaGetLastError());
+        return bail(LBM_ERR_CUDA);
+    }
+    // the constant part sum 2 c_j w_j of the obstacle force over the links
+    // heading into the obstacle, from the exact per-direction counts
+    for (int j = 0; j < Q; ++j) {
+        ctx->force_w[0] += 2.0 * cx_of(j) * w_of(j) * (double)hsolid[j];
+        ctx->force_w[1] += 2.0 * cy_of(j) * w_of(j) * (double)hsolid[j];
+        ctx->force_w[2] += 2.0 * cz_of(j) * w_of(j) * (double)hsolid[j];
     }
     // state at rest (shifted populations 0), accumulators cleared
     bool ok = cudaMemsetAsync(ctx->base + L.pdf, 0, (size_t)Q * L.slot * storage_bytes(p->storage), s) == cudaSuccess;
@@ -719,28 +706,27 @@ extern "C" lbm_status lbm_set_wall_distances(lbm_ctx *ctx, int64_t n, const int6
     if (ctx->in_batch) return fail(ctx, LBM_ERR_STATE, "set a batch member's wall distances with lbm_batch_set_wall_distances");
     const lbm_grid &g = ctx->g;
     const int64_t N = ctx->L.n;
-    std::vector<uint8_t> flags(N);
-    CK(cudaStreamSynchronize(ctx->stream));
-    CK(cudaMemcpy(flags.data(), ctx->base + ctx->L.flags, N, cudaMemcpyDeviceToHost));
     const lbm_params &p = ctx->p;
-    // a fluid cell at (x, y, z), reached through periodic faces if needed
-    auto inner_fluid = [&](int x, int y, int z, int64_t &c) {
+    // the cell (x, y, z), reached through periodic faces if needed, or -1
+    auto wrap_cell = [&](int x, int y, int z) -> int64_t {
         if (x < 0 || x >= g.nx) {
-            if (p.face_x_lo != LBM_FACE_PERIODIC) return false;
+            if (p.face_x_lo != LBM_FACE_PERIODIC) return -1;
             x = ((x % g.nx) + g.nx) % g.nx;
         }
         if (y < 0 || y >= g.ny) {
-            if (p.face_y != LBM_FACE_PERIODIC) return false;
+            if (p.face_y != LBM_FACE_PERIODIC) return -1;
             y = ((y % g.ny) + g.ny) % g.ny;
         }
         if (z < 0 || z >= g.nz) {
-            if (p.face_z != LBM_FACE_PERIODIC) return false;
+            if (p.face_z != LBM_FACE_PERIODIC) return -1;
             z = ((z % g.nz) + g.nz) % g.nz;
         }
-        c = (int64_t)x + (int64_t)g.nx * ((int64_t)y + (int64_t)g.ny * z);
-        return !(flags[c] & CELL_SOLID);
+        return (int64_t)x + (int64_t)g.nx * ((int64_t)y + (int64_t)g.ny * z);
     };
-    std::map<int64_t, std::pair<uint4, double>> recs;    // keyed by cell * 27 + j: the last entry wins
+    // per link the cells whose class decides it: the fluid cell, the cell
+    // behind the link (inside the grid), and the first and second cells
+    // against the link (x1, x2); their flags are gathered on the device
+    std::vector<int64_t> cand((size_t)4 * n, -1);
     for (int64_t k = 0; k < n; ++k) {
         const int64_t c = cell[k];
         const int j = dir[k];
@@ -749,14 +735,42 @@ extern "C" lbm_status lbm_set_wall_distances(lbm_ctx *ctx, int64_t n, const int6
         const int x = (int)(c % g.nx), y = (int)((c / g.nx) % g.ny), z = (int)(c / ((int64_t)g.nx * g.ny));
         const int cx = cx_of(j), cy = cy_of(j), cz = cz_of(j);
         const int sx = x + cx, sy = y + cy, sz = z + cz;
-        const bool inside = sx >= 0 && sx < g.nx && sy >= 0 && sy < g.ny && sz >= 0 && sz < g.nz;
-        if ((flags[c] & CELL_SOLID) || !inside ||
-            !(flags[(int64_t)sx + (int64_t)g.nx * ((int64_t)sy + (int64_t)g.ny * sz)] & CELL_SOLID))
+        cand[4 * k] = c;
+        if (sx >= 0 && sx < g.nx && sy >= 0 && sy < g.ny && sz >= 0 && sz < g.nz)
+            cand[4 * k + 1] = (int64_t)sx + (int64_t)g.nx * ((int64_t)sy + (int64_t)g.ny * sz);
+        cand[4 * k + 2] = wrap_cell(x - cx, y - cy, z - cz);
+        cand[4 * k + 3] = wrap_cell(x - 2 * cx, y - 2 * cy, z - 2 * cz);
+    }
+    std::vector<uint8_t> fl((size_t)4 * n, 0);
+    if (n > 0) {
+        std::vector<int64_t> idx(cand);
+        for (auto &v : idx) v = v < 0 ? 0 : v;
+        int64_t *didx = nullptr;
+        uint8_t *dfl = nullptr;
+        CK(cudaStreamSynchronize(ctx->stream));
+        CK(cudaMalloc(&didx, idx.size() * sizeof(int64_t)));
+        if (cudaMalloc(&dfl, fl.size()) != cudaSuccess) {
+            cudaFree(didx);
+            return fail(ctx, LBM_ERR_CUDA, "wall-distance scratch allocation failed");
+        }
+        const bool ok = cudaMemcpy(didx, idx.data(), idx.size() * sizeof(int64_t), cudaMemcpyHostToDevice) == cudaSuccess &&
+                        (launch_gather_flags(ctx->at<uint8_t>(ctx->L.flags), didx, (int64_t)idx.size(), dfl, nullptr),
+                         cudaMemcpy(fl.data(), dfl, fl.size(), cudaMemcpyDeviceToHost) == cudaSuccess);
+        cudaFree(didx);
+        cudaFree(dfl);
+        if (!ok) return fail(ctx, LBM_ERR_CUDA, std::string("wall-distance flag gather failed: ") +
+                                                     cudaGetErrorString(cudaGetLastError()));
+    }
+    std::map<int64_t, std::pair<uint4, double>> recs;    // keyed by cell * 27 + j: the last entry wins
+    for (int64_t k = 0; k < n; ++k) {
+        const int64_t c = cell[k];
+        const int j = dir[k];
+        if ((fl[4 * k] & CELL_SOLID) || cand[4 * k + 1] < 0 || !(fl[4 * k + 1] & CELL_SOLID))
             return fail(ctx, LBM_ERR_ARG, "wall distance " + std::to_string(k) +
                                               ": not a link from a fluid cell into an obstacle cell");
-        int64_t x1 = -1, x2 = -1;
-        const bool v1 = inner_fluid(x - cx, y - cy, z - cz, x1);
-        const bool v2 = v1 && inner_fluid(x - 2 * cx, y - 2 * cy, z - 2 * cz, x2);
+        const int64_t x1 = cand[4 * k + 2], x2 = cand[4 * k + 3];
+        const bool v1 = x1 >= 0 && !(fl[4 * k + 2] & CELL_SOLID);
+        const bool v2 = v1 && x2 >= 0 && !(fl[4 * k + 3] & CELL_SOLID);
         const int mode = v1 ? (v2 ? 2 : 1) : 0;
         const int i = Q - 1 - j;                            // returning (pull) direction
         recs[c * Q + j] = {make_uint4((uint32_t)c, (uint32_t)(v1 ? x1 : c), (uint32_t)(v2 ? x2 : c),
@@ -1407,12 +1421,12 @@ extern "C" lbm_status lbm_batch_create(int32_t n, const lbm_grid *grids, const u
     b->block_y = p0.block_y ? p0.block_y : 1;
     for (int g = 0; g < n; ++g) {
         lbm_ctx *c = nullptr;
-        // members put their inlet/outlet cells into the boundary-cell records:
-        // on rows of 128-256 cells the bulk kernel's face warps would be a
-        // quarter to a half of its warps
-        lbm_params pm = params[g];
-        pm.xface_edge = 1;
-        lbm_status st = lbm_create(&grids[g], masks ? masks[g] : nullptr, &pm, cuda_stream, &c);
+        // the inlet/outlet cells ride in the batched bulk kernel's face warps
+        // (coalesced with their rows) unless a member asks for the
+        // boundary-cell records (xface_edge): as records every one of their
+        // 54 accesses is a sector of its own (the plane is strided by nx),
+        // which took a third of a step of the 32-channel batch
+        lbm_status st = lbm_create(&grids[g], masks ? masks[g] : nullptr, &params[g], cuda_stream, &c);
         if (st != LBM_OK) {
             const std::string m = "member " + std::to_string(g) + ": " + g_err;
             lbm_batch_destroy(b);

@@ -57,6 +57,135 @@ void launch_flags(const uint8_t *mask, uint8_t *flags, int nx, int ny, int nz, b
 
 
 // ---------------------------------------------------------------------------
+// Boundary-cell records, built on the device in two passes over fixed chunks
+// of EB_CHUNK cells (one block each): the counts of every chunk, then, after
+// an exclusive scan of the edge counts on the host, each chunk writes its
+// records in ascending cell order at its offset (a block-wide ballot scan),
+// so the list is the same whatever the scheduling.  The link codes follow
+// the pull view of the step kernels: where population i of the cell comes
+// from (x - c_i): a lateral face is a wall unless periodic; then the x
+// faces (inlet, outlet or wall, or a wrap); then an obstacle cell.  Solid
+// links are counted per direction j heading into the obstacle (integer
+// atomics: exact and order-free) for the constant part of the force.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t record_link(const uint8_t *flags, int nx, int ny, int nz, int fxlo, int fxhi,
+                                                int fy, int fz, int sx, int sy, int sz)
+{
+    bool wrapped = false;
+    if (sy < 0 || sy >= ny) {
+        if (fy != FACE_PERIODIC) return LINK_WALL;
+        sy = sy < 0 ? sy + ny : sy - ny;
+        wrapped = true;
+    }
+    if (sz < 0 || sz >= nz) {
+        if (fz != FACE_PERIODIC) return LINK_WALL;
+        sz = sz < 0 ? sz + nz : sz - nz;
+        wrapped = true;
+    }
+    if (sx < 0) {
+        if (fxlo == FACE_INLET) return LINK_INLET;
+        if (fxlo == FACE_WALL) return LINK_WALL;
+        sx += nx;
+        wrapped = true;
+    } else if (sx >= nx) {
+        if (fxhi == FACE_OUTLET || fxhi == FACE_OUTFLOW) return LINK_OUTLET;
+        if (fxhi == FACE_WALL) return LINK_WALL;
+        sx -= nx;
+        wrapped = true;
+    }
+    if (flags[sx + (int64_t)nx * (sy + (int64_t)ny * sz)] & CELL_SOLID) return LINK_SOLID;
+    return wrapped ? LINK_WRAP : LINK_FLUID;
+}
+
+__global__ void __launch_bounds__(EB_THREADS) k_record_count(const uint8_t *flags, int64_t n, int *counts)
+{
+    __shared__ int sc[4];
+    if (threadIdx.x < 4) sc[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t c0 = (int64_t)blockIdx.x * EB_CHUNK;
+    int v[4] = {0, 0, 0, 0};
+    for (int k = threadIdx.x; k < EB_CHUNK; k += blockDim.x) {
+        const int64_t c = c0 + k;
+        if (c >= n) break;
+        const uint8_t fl = flags[c];
+        v[0] += !(fl & CELL_SOLID);
+        v[1] += (fl == 0 || fl == CELL_XFACE);
+        v[2] += fl == CELL_WALL;
+        v[3] += fl == CELL_EDGE;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_down_sync(0xffffffffu, v[q], o);
+        if ((threadIdx.x & 31) == 0) atomicAdd(&sc[q], v[q]);
+    }
+    __syncthreads();
+    if (threadIdx.x < 4) counts[4 * blockIdx.x + threadIdx.x] = sc[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(EB_THREADS) k_record_write(const uint8_t *flags, int nx, int ny, int nz, int fxlo,
+                                                             int fxhi, int fy, int fz, const int64_t *offsets,
+                                                             uint4 *edge, unsigned long long *solid)
+{
+    __shared__ int wt[EB_THREADS / 32];
+    const int64_t n = (int64_t)nx * ny * nz;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int64_t base = offsets[blockIdx.x];
+    const int64_t c0 = (int64_t)blockIdx.x * EB_CHUNK;
+    for (int k0 = 0; k0 < EB_CHUNK; k0 += EB_THREADS) {
+        const int64_t c = c0 + k0 + threadIdx.x;
+        const bool rec = c < n && flags[c] == CELL_EDGE;
+        const unsigned bal = __ballot_sync(0xffffffffu, rec);
+        if (lane == 0) wt[wid] = __popc(bal);
+        __syncthreads();
+        int before = 0, total = 0;
+#pragma unroll
+        for (int q = 0; q < EB_THREADS / 32; ++q) {
+            before += q < wid ? wt[q] : 0;
+            total += wt[q];
+        }
+        if (rec) {
+            const int x = (int)(c % nx), y = (int)((c / nx) % ny), z = (int)(c / ((int64_t)nx * ny));
+            uint32_t w[3] = {0u, 0u, 0u};
+            for (int i = 0; i < Q; ++i) {
+                const uint32_t kind = record_link(flags, nx, ny, nz, fxlo, fxhi, fy, fz, x - cx_of(i), y - cy_of(i),
+                                                  z - cz_of(i));
+                w[i / 9] |= kind << (3 * (i % 9));
+                if (kind == LINK_SOLID) atomicAdd(&solid[Q - 1 - i], 1ull);
+            }
+            edge[base + before + __popc(bal & ((1u << lane) - 1u))] = make_uint4((uint32_t)c, w[0], w[1], w[2]);
+        }
+        base += total;
+        __syncthreads();
+    }
+}
+
+__global__ void k_gather_flags(const uint8_t *flags, const int64_t *idx, int64_t m, uint8_t *out)
+{
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < m; k += (int64_t)gridDim.x * blockDim.x)
+        out[k] = flags[idx[k]];
+}
+
+void launch_gather_flags(const uint8_t *flags, const int64_t *idx, int64_t m, uint8_t *out, cudaStream_t s)
+{
+    k_gather_flags<<<(unsigned)std::min<int64_t>((m + 255) / 256, 4096), 256, 0, s>>>(flags, idx, m, out);
+}
+
+int64_t record_blocks(int64_t n) { return (n + EB_CHUNK - 1) / EB_CHUNK; }
+
+void launch_record_count(const uint8_t *flags, int64_t n, int *counts, cudaStream_t s)
+{
+    k_record_count<<<(unsigned)record_blocks(n), EB_THREADS, 0, s>>>(flags, n, counts);
+}
+
+void launch_record_write(const uint8_t *flags, int nx, int ny, int nz, int fxlo, int fxhi, int fy, int fz,
+                         const int64_t *offsets, uint4 *edge, unsigned long long *solid, cudaStream_t s)
+{
+    k_record_write<<<(unsigned)record_blocks((int64_t)nx * ny * nz), EB_THREADS, 0, s>>>(
+        flags, nx, ny, nz, fxlo, fxhi, fy, fz, offsets, edge, solid);
+}
+
+// ---------------------------------------------------------------------------
 // SplitMix64 (Steele, Lea & Flood 2014; Vigna's reference constants):
 // output `ctr` of the stream started at `seed` is mix(seed + (ctr+1) golden).
 // ---------------------------------------------------------------------------

@@ -240,12 +240,21 @@ __device__ __forceinline__ int classify(const StepArgs &a, int sx, int sy, int s
 // even part of the equilibrium at rho_out with velocity ub at the pressure
 // outlet.  With the convective outflow the own slot already holds the
 // extrapolated value (written after the previous step by k_outflow).
+// Rounded add and multiply that the compiler does not fuse.
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+
 template <class R>
 __device__ __forceinline__ R boundary_value(const StepArgs &a, int kind, int i, R own, R ubx, R uby, R ubz)
 {
     const R w = R(w_of(i));
+    // the inlet term with explicitly rounded operations: the same value in
+    // every kernel that applies it (no contraction left to the compiler)
     if (kind == LINK_INLET)
-        return own + R(6) * w * pick<R>(a.rho_in, a.rho_in_f) * (R(cx_of(i)) * pick<R>(a.u_in, a.u_in_f));
+        return add_rn(own, mul_rn(mul_rn(R(6) * w, pick<R>(a.rho_in, a.rho_in_f)),
+                                  R(cx_of(i)) * pick<R>(a.u_in, a.u_in_f)));
     if (kind == LINK_OUTLET && a.face_x_hi == FACE_OUTFLOW) return own;
     if (kind == LINK_OUTLET) {
         const R cu = R(cx_of(i)) * ubx + R(cy_of(i)) * uby + R(cz_of(i)) * ubz;

@@ -48,6 +48,20 @@ struct AuxArgs {
     int nblocks = 0;
 };
 
+// boundary-cell records on the device (lbm_aux.cu): counts per chunk of
+// EB_CHUNK cells [blocks][4] = fluid, bulk, wall, record cells; then the
+// records at the chunks' exclusive-scan offsets, and the solid links per
+// direction heading into the obstacle
+constexpr int EB_CHUNK = 8192;
+constexpr int EB_THREADS = 256;
+int64_t record_blocks(int64_t n);
+void launch_record_count(const uint8_t *flags, int64_t n, int *counts, cudaStream_t s);
+void launch_record_write(const uint8_t *flags, int nx, int ny, int nz, int fxlo, int fxhi, int fy, int fz,
+                         const int64_t *offsets, uint4 *edge, unsigned long long *solid, cudaStream_t s);
+
+// flags[idx[k]] -> out[k] (the cell classes a host-side check needs)
+void launch_gather_flags(const uint8_t *flags, const int64_t *idx, int64_t m, uint8_t *out, cudaStream_t s);
+
 void launch_flags(const uint8_t *mask, uint8_t *flags, int nx, int ny, int nz, bool xface_lo, bool xface_hi,
                   bool wall_y, bool wall_z, cudaStream_t s);
 void launch_aux(int storage, AuxOp op, const StepArgs &a, bool odd, const AuxArgs &x, cudaStream_t s);

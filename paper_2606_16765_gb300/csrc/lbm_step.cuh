@@ -69,10 +69,9 @@ __device__ __forceinline__ void epilogue(const StepArgs &a, const StepOut &o, in
 // warp of a row hold such a lane, and those warps (a warp-uniform condition)
 // take the variant of the gather and scatter that redirects the links through
 // the x face to the cell's own slot, like the edge kernel; every other warp
-// runs the plain gather/scatter.  FACES = false compiles the face variant
-// out (contexts whose inlet/outlet cells go through the boundary records:
-// the batch members).
-template <class S, bool ODD, bool EPI, bool PLAIN, bool FACES = true>
+// runs the plain gather/scatter.  Contexts created with xface_edge send
+// those cells through the boundary records instead (xface_bulk = 0).
+template <class S, bool ODD, bool EPI, bool PLAIN>
 __device__ __forceinline__ void bulk_cell(const StepArgs &a, const StepOut &o, int x, int y, int z)
 {
     using T = Store<S>;
@@ -82,7 +81,7 @@ __device__ __forceinline__ void bulk_cell(const StepArgs &a, const StepOut &o, i
     if (fl != 0 && fl != CELL_XFACE) return;   // solid or edge cell
     // warp-uniform: does this warp hold x = 0 or x = nx - 1?
     const int xw = x - (int)(threadIdx.x & 31u);
-    const bool face_warp = FACES && a.xface_bulk && (xw == 0 || xw + 32 > a.nx - 1);
+    const bool face_warp = a.xface_bulk && (xw == 0 || xw + 32 > a.nx - 1);
     const bool lo = fl == CELL_XFACE && x == 0;
     const bool hi = fl == CELL_XFACE && x == a.nx - 1;
     const int lo_kind = a.face_x_lo == FACE_INLET ? LINK_INLET : LINK_WALL;
@@ -113,7 +112,7 @@ __device__ __forceinline__ void bulk_cell(const StepArgs &a, const StepOut &o, i
     collide<R, PLAIN>(f, rates_of<R>(a), drho, ux, uy, uz);
     check_density(drho, a.status);
     // the outlet condition of the next (odd) step uses this step's velocity
-    if (FACES && !ODD && hi && a.face_x_hi == FACE_OUTLET) {
+    if (!ODD && hi && a.face_x_hi == FACE_OUTLET) {
         ub[pl] = ux;
         ub[pl + 1] = uy;
         ub[pl + 2] = uz;
@@ -578,7 +577,7 @@ __global__ void __launch_bounds__(256, (bulk_min_blocks<S, EPI, PLAIN>())) k_bat
     if (x >= sa.nx || y >= sa.ny) return;
     StepOut o{nullptr, nullptr, nullptr, nullptr, nullptr};
     if (EPI && samples_at(B, *tdev)) o.msum = B.msum;
-    bulk_cell<S, ODD, EPI, PLAIN, false>(sa, o, x, y, z);
+    bulk_cell<S, ODD, EPI, PLAIN>(sa, o, x, y, z);
 }
 
 // Batched edge kernel: blocks [0, eblocks) are the members' edge blocks,

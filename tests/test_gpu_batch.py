@@ -36,12 +36,10 @@ def members(storage="f32", mean=True, force=True):
 
 
 def independent(d, steps, **extra):
-    """The member's lattice stepped alone; batch members put their inlet and
-    outlet cells into the boundary-cell records (xface_edge), so the same
-    option keeps the force reductions' block partition and thus the bits."""
+    """The member's lattice stepped alone, with the member's own options (the
+    same cell classes, hence the same force-reduction blocks and bits)."""
     from paper_2606_16765_gb300.lbm import Solver
     kw = {k: v for k, v in d.items() if k not in ("grid", "mask")}
-    kw.update(xface_edge=1)
     kw.update(extra)
     s = Solver(d["grid"], d["mask"], **kw)
     s.step(steps)
