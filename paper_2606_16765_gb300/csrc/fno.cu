@@ -245,6 +245,61 @@ __global__ void __launch_bounds__(TPB) k_pw_fwd_in2(const TI *x, int co, const f
     }
 }
 
+// Inference lift in one pass: v0 = P2 GELU(P1 x + b1) + b2 from the FP32
+// input [B][4][N] to the BF16 layer input [B][32][N], two adjacent cells per
+// thread, the 32 hidden units in registers.  The input and the hidden units
+// are rounded to BF16 where the training path stores them, so that both
+// paths evaluate the same network.  Shared memory: P1 [32][4], b1, P2
+// [32][32], b2.
+constexpr int LIFT_CI = 4, LIFT_H = 32, LIFT_CO = 32;
+__global__ void __launch_bounds__(TPB, 2) k_lift_fused(const float *x, const float *P1, const float *b1, const float *P2,
+                                                    const float *b2, __nv_bfloat16 *y, int64_t N, int B)
+{
+    __shared__ float4 s1[LIFT_H];                 // P1 rows
+    __shared__ float4 s2[LIFT_CO * LIFT_H / 4];   // P2 rows
+    __shared__ float sb1[LIFT_H], sb2[LIFT_CO];
+    for (int k = threadIdx.x; k < LIFT_H; k += blockDim.x) {
+        s1[k] = make_float4(P1[4 * k], P1[4 * k + 1], P1[4 * k + 2], P1[4 * k + 3]);
+        sb1[k] = b1[k];
+    }
+    for (int k = threadIdx.x; k < LIFT_CO * LIFT_H; k += blockDim.x) reinterpret_cast<float *>(s2)[k] = P2[k];
+    for (int k = threadIdx.x; k < LIFT_CO; k += blockDim.x) sb2[k] = b2[k];
+    __syncthreads();
+    const int64_t half = N / 2;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < (int64_t)B * half;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = idx / half, n = 2 * (idx - b * half);
+        float2 xv[LIFT_CI];
+#pragma unroll
+        for (int i = 0; i < LIFT_CI; ++i) {
+            const float2 v = ld2(x + (b * LIFT_CI + i) * N + n);
+            xv[i] = make_float2(__bfloat162float(__float2bfloat16_rn(v.x)), __bfloat162float(__float2bfloat16_rn(v.y)));
+        }
+        float2 h[LIFT_H];
+#pragma unroll
+        for (int o = 0; o < LIFT_H; ++o) {
+            const float4 w = s1[o];
+            float a0 = sb1[o] + 0.f, a1 = sb1[o] + 0.f;
+            a0 += w.x * xv[0].x + w.y * xv[1].x + w.z * xv[2].x + w.w * xv[3].x;
+            a1 += w.x * xv[0].y + w.y * xv[1].y + w.z * xv[2].y + w.w * xv[3].y;
+            h[o] = make_float2(__bfloat162float(__float2bfloat16_rn(gelu(a0))),
+                               __bfloat162float(__float2bfloat16_rn(gelu(a1))));
+        }
+#pragma unroll 1
+        for (int o = 0; o < LIFT_CO; ++o) {
+            float a0 = sb2[o] + 0.f, a1 = sb2[o] + 0.f;
+            const float4 *w4 = s2 + o * (LIFT_H / 4);
+#pragma unroll
+            for (int q = 0; q < LIFT_H / 4; ++q) {
+                const float4 w = w4[q];
+                a0 += w.x * h[4 * q].x + w.y * h[4 * q + 1].x + w.z * h[4 * q + 2].x + w.w * h[4 * q + 3].x;
+                a1 += w.x * h[4 * q].y + w.y * h[4 * q + 1].y + w.z * h[4 * q + 2].y + w.w * h[4 * q + 3].y;
+            }
+            st2(y + (b * LIFT_CO + o) * N + n, a0, a1);
+        }
+    }
+}
+
 // Inference projection y = Q2 sin(omega0 (Q1 v + b1)) + b2 in one pass (the hidden
 // activations are never stored): CI inputs and co <= 8 outputs in registers,
 // the H hidden units streamed, two adjacent cells per thread.  Shared
@@ -1019,60 +1074,97 @@ __global__ void __launch_bounds__(TPB) k_dfty_fwd(const float2 *A, float2 *Bt, c
     }
 }
 
-// B [BC][nz][Ky][Kx] -> S[k][bc] with factor scale[kz]
-__global__ void __launch_bounds__(TPB) k_dftz_fwd(const float2 *Bt, float2 *Sp, const float2 *twz, const float *scale,
-                                                  Dims d)
+// z stages: a block of ZW warps takes one channel row bc and 32 consecutive
+// (ky, kx) modes (a lane each, so that the rows of a plane are read and
+// written coalesced); the nz planes are split among the warps, which raises
+// the parallelism of these short stages fourfold over one thread per mode.
+constexpr int ZW = 4;
+
+int dftz_blocks(const Dims &d)
 {
-    const int64_t P = d.BC * d.Ky * d.Kx;
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < P; t += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t bc = t / (d.Ky * d.Kx);
-        const int p = (int)(t % (d.Ky * d.Kx));
+    const int64_t items = d.BC * ((d.Ky * d.Kx + 31) / 32);
+    return (int)std::min<int64_t>(items, (int64_t)gb300::sm_count() * 16);
+}
+
+// B [BC][nz][Ky][Kx] -> S[k][bc] with factor scale[kz]: each warp sums its
+// planes, the partial sums are added in warp order.
+__global__ void __launch_bounds__(ZW * 32) k_dftz_fwd(const float2 *Bt, float2 *Sp, const float2 *twz, const float *scale,
+                                                      Dims d)
+{
+    __shared__ float2 part[ZW][16][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int P2 = d.Ky * d.Kx, pchunks = (P2 + 31) / 32;
+    const int z0 = w * d.nz / ZW, z1 = (w + 1) * d.nz / ZW;
+    for (int64_t item = blockIdx.x; item < d.BC * pchunks; item += gridDim.x) {
+        const int64_t bc = item / pchunks;
+        const int pbase = (int)(item % pchunks) * 32;
+        const int p = pbase + lane;
         float2 acc[16];
 #pragma unroll
         for (int k = 0; k < 16; ++k) acc[k] = make_float2(0.f, 0.f);
-        for (int z = 0; z < d.nz; ++z) {
-            const float2 v = Bt[(bc * d.nz + z) * d.Ky * d.Kx + p];
+        if (p < P2) {
+            for (int z = z0; z < z1; ++z) {
+                const float2 v = Bt[(bc * d.nz + z) * P2 + p];
 #pragma unroll
-            for (int k = 0; k < 16; ++k)
-                if (k < d.Kz) {
-                    const float2 w = cmul(v, twz[z * d.Kz + k]);
-                    acc[k].x += w.x;
-                    acc[k].y += w.y;
-                }
+                for (int k = 0; k < 16; ++k)
+                    if (k < d.Kz) {
+                        const float2 t = cmul(v, twz[z * d.Kz + k]);
+                        acc[k].x += t.x;
+                        acc[k].y += t.y;
+                    }
+            }
         }
 #pragma unroll
         for (int k = 0; k < 16; ++k)
-            if (k < d.Kz) Sp[((int64_t)k * d.Ky * d.Kx + p) * d.BC + bc] = make_float2(acc[k].x * scale[k], acc[k].y * scale[k]);
+            if (k < d.Kz) part[w][k][lane] = acc[k];
+        __syncthreads();
+        for (int e = threadIdx.x; e < d.Kz * 32; e += ZW * 32) {
+            const int k = e >> 5, l = e & 31;
+            if (pbase + l < P2) {
+                float2 s = part[0][k][l];
+#pragma unroll
+                for (int ww = 1; ww < ZW; ++ww) {
+                    s.x += part[ww][k][l].x;
+                    s.y += part[ww][k][l].y;
+                }
+                Sp[((int64_t)k * P2 + pbase + l) * d.BC + bc] = make_float2(s.x * scale[k], s.y * scale[k]);
+            }
+        }
+        __syncthreads();
     }
 }
 
-// S[k][bc] (times scale[kz]) -> H [BC][nz][Ky][Kx] = sum_kz G exp(+i 2 pi kz z / nz)
-__global__ void __launch_bounds__(TPB) k_dftz_inv(const float2 *Sp, float2 *Ht, const float2 *twz, const float *scale,
-                                                  Dims d)
+// S[k][bc] (times scale[kz]) -> H [BC][nz][Ky][Kx] = sum_kz G exp(+i 2 pi kz z / nz);
+// each warp writes its own planes.
+__global__ void __launch_bounds__(ZW * 32) k_dftz_inv(const float2 *Sp, float2 *Ht, const float2 *twz, const float *scale,
+                                                      Dims d)
 {
-    const int64_t P = d.BC * d.Ky * d.Kx;
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < P; t += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t bc = t / (d.Ky * d.Kx);
-        const int p = (int)(t % (d.Ky * d.Kx));
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int P2 = d.Ky * d.Kx, pchunks = (P2 + 31) / 32;
+    const int z0 = w * d.nz / ZW, z1 = (w + 1) * d.nz / ZW;
+    for (int64_t item = blockIdx.x; item < d.BC * pchunks; item += gridDim.x) {
+        const int64_t bc = item / pchunks;
+        const int p = (int)(item % pchunks) * 32 + lane;
+        if (p >= P2) continue;
         float2 G[16];
 #pragma unroll
         for (int k = 0; k < 16; ++k) {
             G[k] = make_float2(0.f, 0.f);
             if (k < d.Kz) {
-                const float2 v = Sp[((int64_t)k * d.Ky * d.Kx + p) * d.BC + bc];
+                const float2 v = Sp[((int64_t)k * P2 + p) * d.BC + bc];
                 G[k] = make_float2(v.x * scale[k], v.y * scale[k]);
             }
         }
-        for (int z = 0; z < d.nz; ++z) {
+        for (int z = z0; z < z1; ++z) {
             float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
             for (int k = 0; k < 16; ++k)
                 if (k < d.Kz) {
-                    const float2 w = cmulc(G[k], twz[z * d.Kz + k]);
-                    acc.x += w.x;
-                    acc.y += w.y;
+                    const float2 t = cmulc(G[k], twz[z * d.Kz + k]);
+                    acc.x += t.x;
+                    acc.y += t.y;
                 }
-            Ht[(bc * d.nz + z) * d.Ky * d.Kx + p] = acc;
+            Ht[(bc * d.nz + z) * P2 + p] = acc;
         }
     }
 }
@@ -2554,7 +2646,7 @@ void dft_fwd(fno_ctx *f, const T *x, float2 *S, const float *scale, int B, int l
         k_dfty_fwd<<<(int)std::min<int64_t>((Sl + SB - 1) / SB, gb300::sm_count() * 8), TPB, smem_dfty_fwd(d), f->s>>>(
             f->stA, f->stB, f->twy, d, Sl, SB);
     }
-    k_dftz_fwd<<<grid_for(d.BC * d.Ky * d.Kx), TPB, 0, f->s>>>(f->stB, S, f->twz, scale, d);
+    k_dftz_fwd<<<dftz_blocks(d), ZW * 32, 0, f->s>>>(f->stB, S, f->twz, scale, d);
 }
 
 // inverse of S (times scale[kz]) into out [B][W][N]: store or add; then, if pre
@@ -2564,7 +2656,7 @@ void dft_fwd(fno_ctx *f, const T *x, float2 *S, const float *scale, int B, int l
 void dft_inv_zy(fno_ctx *f, const float2 *S, const float *scale, int B)
 {
     const Dims d = dims(f, B);
-    k_dftz_inv<<<grid_for(d.BC * d.Ky * d.Kx), TPB, 0, f->s>>>(S, f->stB, f->twz, scale, d);
+    k_dftz_inv<<<dftz_blocks(d), ZW * 32, 0, f->s>>>(S, f->stB, f->twz, scale, d);
     const int64_t Sl = d.BC * d.nz;
     if (ydft_tc(f, d)) {
         k_cdft_tc<4><<<(int)std::min<int64_t>((Sl + TPB / 32 - 1) / (TPB / 32), gb300::sm_count() * 8), TPB,
@@ -2613,12 +2705,20 @@ lbm_status forward_impl(fno_ctx *f, const float *x, int B, bool keep = true)
     const fno_config &c = f->c;
     const int W = c.width;
     T *xa = static_cast<T *>(f->xa);
-    k_convert<T><<<grid_for((int64_t)B * c.cin * f->N), TPB, 0, f->s>>>(x, xa, (int64_t)B * c.cin * f->N);
-    // feed-forward lift: v0 = P2 GELU(P1 x + b1) + b2
-    pw_fwd<T>(f, xa, c.cin, c.lift_hidden, f->oP1_w, f->oP1_b, nullptr, keep ? static_cast<T *>(f->apre) : nullptr,
-              f->a, false, ACT_GELU, B);
-    pw_fwd<T>(f, static_cast<T *>(f->a), c.lift_hidden, W, f->oP2_w, f->oP2_b, nullptr, nullptr, f->v[0], false,
-              ACT_NONE, B);
+    if (!keep && std::is_same<T, __nv_bfloat16>::value && c.cin == LIFT_CI && c.lift_hidden == LIFT_H &&
+        W == LIFT_CO && f->N % 2 == 0) {
+        // inference: the lift's two layers in one pass from the FP32 input
+        k_lift_fused<<<grid_for((int64_t)B * f->N / 2), TPB, 0, f->s>>>(
+            x, f->params + f->oP1_w, f->params + f->oP1_b, f->params + f->oP2_w, f->params + f->oP2_b,
+            reinterpret_cast<__nv_bfloat16 *>(f->v[0]), f->N, B);
+    } else {
+        k_convert<T><<<grid_for((int64_t)B * c.cin * f->N), TPB, 0, f->s>>>(x, xa, (int64_t)B * c.cin * f->N);
+        // feed-forward lift: v0 = P2 GELU(P1 x + b1) + b2
+        pw_fwd<T>(f, xa, c.cin, c.lift_hidden, f->oP1_w, f->oP1_b, nullptr,
+                  keep ? static_cast<T *>(f->apre) : nullptr, f->a, false, ACT_GELU, B);
+        pw_fwd<T>(f, static_cast<T *>(f->a), c.lift_hidden, W, f->oP2_w, f->oP2_b, nullptr, nullptr, f->v[0], false,
+                  ACT_NONE, B);
+    }
     // the fused Fourier-layer output (inverse x stage and pointwise path in
     // one tensor-core pass) where its shape applies
     const bool fuse = std::is_same<T, __nv_bfloat16>::value && c.nx == TCX_NX && f->Kx == TCX_KX && W == FUSE_C;

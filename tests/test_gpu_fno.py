@@ -268,8 +268,11 @@ def test_batches_larger_than_max_batch_are_split():
 
 def test_checkpoint_restores_parameters_and_adam_state(tmp_path):
     """fno_save after three Adam steps, fno_load into a fresh network: the
-    next training step gives the same loss and the same parameters, bitwise;
-    a checkpoint of another shape is refused."""
+    parameters and the next step's loss are the same bitwise; the parameters
+    after that step agree to the rounding of the weight-gradient reduction
+    (block partials added with FP32 atomics, in an order that varies between
+    launches), far below an Adam step, which a lost moment would change by
+    about the learning rate; a checkpoint of another shape is refused."""
     from paper_2606_16765_gb300 import fno as G
     ocfg, gcfg = tiny_cfgs(8)
     gcfg.update(act_bf16=0, tensor_cores=1)
@@ -283,7 +286,8 @@ def test_checkpoint_restores_parameters_and_adam_state(tmp_path):
     b.load(path)
     assert np.array_equal(a.params(), b.params())
     la, lb = a.train_step(x, t, m, 1e-3), b.train_step(x, t, m, 1e-3)
-    assert la == lb and np.array_equal(a.params(), b.params())
+    assert la == lb
+    assert np.max(np.abs(a.params() - b.params())) <= 1e-6
     other = dict(gcfg, hidden=gcfg["hidden"] + 1)
     c = G.FNO(**other)
     with pytest.raises(G.FNOError) as e:
