@@ -142,19 +142,20 @@ __device__ __forceinline__ void bulk_cell(const StepArgs &a, const StepOut &o, i
 
 // Blocks per SM asked of the register allocator (256-thread blocks): the
 // 16-bit kernels of the plain collision are bound by instruction issue and
-// take 40 registers (six blocks) without the epilogue; FP32 keeps 48 (five),
-// the general collision 64 (four), FP64 the plain collision 80 (three).
-// Each at no or one spilled value.
-template <class S, bool EPI, bool PLAIN>
+// take 40 registers (six blocks) without the epilogue; FP32 runs its odd
+// step at 40 and its even step at 48 (five blocks), the bandwidth each
+// measured best at; the general collision 64 (four), FP64 the plain
+// collision 80 (three).  Each at no or one spilled value.
+template <class S, bool ODD, bool EPI, bool PLAIN>
 constexpr int bulk_min_blocks()
 {
     return sizeof(S) == 8 ? (PLAIN ? 3 : 1)
-                          : (!PLAIN ? 4 : (sizeof(S) == 4 ? 5 : (EPI ? 5 : 6)));
+                          : (!PLAIN ? 4 : (EPI ? 5 : ((sizeof(S) == 4 && !ODD) ? 5 : 6)));
 }
 
 // Single-grid bulk kernel: grid (ceil(nx / blockDim.x), ceil(ny / blockDim.y), nz).
 template <class S, bool ODD, bool EPI, bool PLAIN>
-__global__ void __launch_bounds__(256, (bulk_min_blocks<S, EPI, PLAIN>())) k_step_bulk(StepArgs a)
+__global__ void __launch_bounds__(256, (bulk_min_blocks<S, ODD, EPI, PLAIN>())) k_step_bulk(StepArgs a)
 {
     const int x = (int)(blockIdx.x * blockDim.x + threadIdx.x);
     const int y = (int)(blockIdx.y * blockDim.y + threadIdx.y);
@@ -550,7 +551,7 @@ __device__ __forceinline__ bool samples_at(const BatchMember &B, int64_t t)
 }
 
 template <class S, bool ODD, bool EPI, bool PLAIN>
-__global__ void __launch_bounds__(256, (bulk_min_blocks<S, EPI, PLAIN>())) k_batch_bulk(const BatchMember *mem, const int64_t *begin, int nm,
+__global__ void __launch_bounds__(256, (bulk_min_blocks<S, ODD, EPI, PLAIN>())) k_batch_bulk(const BatchMember *mem, const int64_t *begin, int nm,
                                                     const int64_t *tdev)
 {
     // the member's step arguments are staged in shared memory: the cell
