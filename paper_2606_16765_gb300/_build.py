@@ -27,6 +27,7 @@ LIBS = {
                   "resample.cu"],
     "libfno.so": ["fno.cu", "fno_umma.cu"],
     "libunet.so": ["unet.cu", "unet_gemm.cu"],
+    "libffno.so": ["ffno.cu"],
 }
 
 

@@ -10,7 +10,7 @@ import pytest
 from paper_2606_16765_gb300 import _build
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-DECL = re.compile(r"^\s*(?:[A-Za-z_][\w\s\*]*?)\b((?:lbm|fno|unet)_\w+)\s*\(", re.M)
+DECL = re.compile(r"^\s*(?:[A-Za-z_][\w\s\*]*?)\b((?:lbm|fno|ffno|unet)_\w+)\s*\(", re.M)
 
 
 def declared(header):
