@@ -175,3 +175,41 @@ def flatten(cfg, d):
         a = np.asarray(d[name]).reshape(shape)
         parts.append(np.stack([a.real, a.imag], -1).reshape(-1) if cplx else a.reshape(-1))
     return np.concatenate(parts).astype(np.float32)
+
+
+def time_ffno(batch=8, reps=2, warmup=1):
+    """Forward and training-step time (ms, CUDA events) of the default
+    factorised surrogate (128x64x64, batch 8) on random inputs resident on
+    the device."""
+    import torch
+    net = FFNO(max_batch=batch)
+    c = net.cfg
+    g = torch.Generator(device="cuda").manual_seed(0)
+    x = torch.rand((batch, c.cin, c.nz, c.ny, c.nx), device="cuda", generator=g)
+    t = torch.rand((batch, c.cout, c.nz, c.ny, c.nx), device="cuda", generator=g)
+    w = torch.ones((batch, c.nz, c.ny, c.nx), device="cuda")
+    y = torch.zeros((batch, c.cout, c.nz, c.ny, c.nx), device="cuda")
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0.record(st)
+        for _ in range(reps):
+            fn()
+        e1.record(st)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    fwd = timed(lambda: net.forward(x, y))
+    train = timed(lambda: (net.loss_grad(x, t, w), net.adam(1e-6)))
+    net.close()
+    return {"batch": batch, "forward_ms_per_batch": fwd, "train_step_ms": train,
+            "train_samples_per_s": batch / train * 1e3}
+
+
+if __name__ == "__main__":
+    import json
+    print(json.dumps(time_ffno()))
